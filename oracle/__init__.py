@@ -1,0 +1,217 @@
+"""FP64 CPU oracle of the Aether.jl finite-volume MHD step (arXiv 2608.14048).
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use this module; the CUDA library and its
+Python binding never import it, and it shares no code with them.
+
+The numerics live in plain C (``mhd.c``, ``dust.c``, ``mlp.c``), compiled here
+with gcc at ``-O2 -ffp-contract=off`` (no fused multiply-add, so x86 and Arm
+give the same bits).  This file only marshals numpy arrays into those calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRCS = ["mhd.c", "dust.c", "mlp.c"]
+_LIB_PATH = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+CART, SPH = 0, 1
+PERIODIC, OUTFLOW = 0, 1
+DONOR, PLM, PPM = 0, 1, 2
+VL2, RK2 = 0, 1
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("coord", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("bc", C.c_int * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("rho_floor", C.c_double),
+                ("p_floor", C.c_double), ("recon", C.c_int),
+                ("integrator", C.c_int), ("cfl", C.c_double), ("mhd", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("mom", C.c_double * 3),
+                ("energy", C.c_double), ("max_divb_rel", C.c_double),
+                ("floor_hits", C.c_long)]
+
+
+class DustParams(C.Structure):
+    _fields_ = [("nd", C.c_int), ("t_stop", C.POINTER(C.c_double)),
+                ("rho_floor_dust", C.c_double), ("gas_accel", C.c_double * 3)]
+
+
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile the oracle's C sources into ``liborc.so`` next to them."""
+    srcs = [os.path.join(_HERE, s) for s in _SRCS if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h"),
+                                                       os.path.join(_HERE, "oracle_internal.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+           "-Wall", "-Wno-unknown-pragmas"]
+    if openmp:
+        cmd.append("-fopenmp")
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd += srcs + ["-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            dp = C.POINTER(C.c_double)
+            L.orc_mhd_step.argtypes = [C.POINTER(Grid), C.POINTER(Params), C.c_double,
+                                       dp, dp, dp, dp, C.POINTER(C.c_long)]
+            L.orc_mhd_step.restype = C.c_int
+            L.orc_mhd_dt.argtypes = [C.POINTER(Grid), C.POINTER(Params), dp, dp, dp, dp]
+            L.orc_mhd_dt.restype = C.c_double
+            L.orc_mhd_diag.argtypes = [C.POINTER(Grid), C.POINTER(Params), dp, dp, dp, dp,
+                                       C.POINTER(Diag)]
+            L.orc_mhd_diag.restype = None
+            L.orc_hlld.argtypes = [C.c_double, dp, dp, C.c_double, dp]
+            L.orc_hlld.restype = C.c_int
+            L.orc_recon_line.argtypes = [C.c_int, C.c_int, dp, dp, dp]
+            L.orc_recon_line.restype = None
+            L.orc_corner_emf.argtypes = [C.c_double] * 4 + [dp] + [C.c_double] * 4
+            L.orc_corner_emf.restype = C.c_double
+            if hasattr(L, "orc_drag_solve"):
+                L.orc_drag_solve.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, dp, dp]
+                L.orc_drag_solve.restype = None
+                L.orc_dust_step.argtypes = [C.POINTER(Grid), C.POINTER(Params),
+                                            C.POINTER(DustParams), C.c_double, dp, dp,
+                                            C.POINTER(C.c_long)]
+                L.orc_dust_step.restype = C.c_int
+                L.orc_dust_dt.argtypes = [C.POINTER(Grid), C.POINTER(Params),
+                                          C.POINTER(DustParams), dp, dp]
+                L.orc_dust_dt.restype = C.c_double
+            if hasattr(L, "orc_mlp_forward"):
+                ip = C.POINTER(C.c_int)
+                L.orc_mlp_forward.argtypes = [C.c_int, ip, dp, C.c_int, dp, dp]
+                L.orc_mlp_forward.restype = None
+                L.orc_mlp_grad.argtypes = [C.c_int, ip, dp, C.c_int, dp, dp, dp]
+                L.orc_mlp_grad.restype = C.c_double
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), coord=CART, bc=(PERIODIC,) * 3) -> Grid:
+    nx, ny, nz = n
+    return Grid(nx, ny, nz, coord, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi),
+                (C.c_int * 3)(*bc))
+
+
+def make_params(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, mhd=True,
+                rho_floor=1e-12, p_floor=1e-10) -> Params:
+    return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0)
+
+
+class State:
+    """Host FP64 state of one block: cons[5][nz][ny][nx] and the three face
+    arrays with the shapes of the C interface."""
+
+    def __init__(self, cons, b1=None, b2=None, b3=None):
+        # always private copies: the oracle advances them in place
+        self.cons = np.array(cons, dtype=np.float64, order="C", copy=True)
+        nz, ny, nx = self.cons.shape[1:]
+        z = lambda s: np.zeros(s, dtype=np.float64)
+        self.b1 = np.array(b1 if b1 is not None else z((nz, ny, nx + 1)), dtype=np.float64, order="C", copy=True)
+        self.b2 = np.array(b2 if b2 is not None else z((nz, ny + 1, nx)), dtype=np.float64, order="C", copy=True)
+        self.b3 = np.array(b3 if b3 is not None else z((nz + 1, ny, nx)), dtype=np.float64, order="C", copy=True)
+
+    def copy(self) -> "State":
+        return State(self.cons.copy(), self.b1.copy(), self.b2.copy(), self.b3.copy())
+
+
+def step(grid: Grid, params: Params, dt: float, s: State) -> int:
+    """Advance ``s`` in place by one full step; returns the floor-hit count."""
+    hits = C.c_long(0)
+    rc = lib().orc_mhd_step(C.byref(grid), C.byref(params), float(dt), _dp(s.cons),
+                            _dp(s.b1), _dp(s.b2), _dp(s.b3), C.byref(hits))
+    if rc != 0:
+        raise RuntimeError(f"orc_mhd_step failed: {rc}")
+    return hits.value
+
+
+def compute_dt(grid: Grid, params: Params, s: State) -> float:
+    return lib().orc_mhd_dt(C.byref(grid), C.byref(params), _dp(s.cons), _dp(s.b1),
+                            _dp(s.b2), _dp(s.b3))
+
+
+def diagnostics(grid: Grid, params: Params, s: State) -> dict:
+    d = Diag()
+    lib().orc_mhd_diag(C.byref(grid), C.byref(params), _dp(s.cons), _dp(s.b1), _dp(s.b2),
+                       _dp(s.b3), C.byref(d))
+    return {"mass": d.mass, "mom": list(d.mom), "energy": d.energy,
+            "max_divb_rel": d.max_divb_rel}
+
+
+def hlld(gamma: float, wl, wr, bn: float):
+    """Face-frame HLLD flux; returns (flux[7], region)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.zeros(7)
+    reg = lib().orc_hlld(float(gamma), _dp(wl), _dp(wr), float(bn), _dp(f))
+    return f, reg
+
+
+def recon_line(recon: int, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = w.size
+    wl = np.zeros(max(n - 1, 0))
+    wr = np.zeros(max(n - 1, 0))
+    lib().orc_recon_line(recon, n, _dp(w), _dp(wl), _dp(wr))
+    return wl, wr
+
+
+def corner_emf(ea_m, ea_p, eb_m, eb_p, eref, fa_m, fa_p, fb_m, fb_p) -> float:
+    r = np.ascontiguousarray(np.asarray(eref, dtype=np.float64).reshape(4))
+    return lib().orc_corner_emf(ea_m, ea_p, eb_m, eb_p, _dp(r), fa_m, fa_p, fb_m, fb_p)
+
+
+def run(grid: Grid, params: Params, s: State, nsteps: int = None, t_end: float = None,
+        dts=None):
+    """Advance with the CFL step of Eq. 11 (or a given dt sequence); returns
+    the list of dt values used."""
+    used = []
+    t = 0.0
+    k = 0
+    while True:
+        if dts is not None:
+            if k >= len(dts):
+                break
+            dt = dts[k]
+        else:
+            if nsteps is not None and k >= nsteps:
+                break
+            dt = compute_dt(grid, params, s)
+            if t_end is not None:
+                if t >= t_end * (1 - 1e-14):
+                    break
+                dt = min(dt, t_end - t)
+        step(grid, params, dt, s)
+        used.append(dt)
+        t += dt
+        k += 1
+    return used
