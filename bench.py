@@ -1,0 +1,301 @@
+"""Benchmark of the GB300 MHD step: cell-updates/s on one GPU (replicas on N).
+
+Default workload: 3-D decaying MHD turbulence, 256^3 periodic, FP32 bulk,
+PLM + HLLD + CT + VL2, CFL 0.3 (rho = 1, beta = 1 uniform B_x, solenoidal
+Gaussian velocity with P(k) ~ k^-2 on 2 <= k <= 8, rms Mach 2, gamma =
+1.0001).  One "step" is one full VL2 step (both stages, CFL dt computed on
+the device), counted once per cell (zone-cycles).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--prec fp32|fp64|fp32_p64] [--recon plm|ppm] [--n 256]
+
+Prints ONE JSON line (rank 0).  With --gpus N > 1 (torchrun) every rank
+advances its own independent replica (the step has no cross-GPU exchange in
+this build: replicas only); value = all ranks' cell-updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s on 1 GB300 (FP32/learned vs FP64 plain) at stated L1; % HBM roofline"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
+    ap.add_argument("--recon", default="plm", choices=["plm", "ppm"])
+    ap.add_argument("--path", default="fused", choices=["fused", "unfused"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(a):
+    return {"workload": f"mhd_decaying_turbulence_{a.n}^3", "grid": [a.n, a.n, a.n],
+            "recon": a.recon.upper(), "riemann": "HLLD", "ct": "upwind corner EMF (GS05)",
+            "integrator": "VL2", "cfl": 0.3, "gamma": 1.0001, "mach_rms": 2.0, "beta": 1.0,
+            "precision": a.prec, "path": a.path, "seed": 20260816,
+            "l2": f"inputs larger than L2 (state {a.n}^3 x 8 vars x 2 registers)"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2608_14048_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2608_14048_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM traffic of the dominant kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_input(a):
+    from paper_2608_14048_gb300 import inputs as I
+    return I.turbulence_box(n=a.n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
+
+
+def cpu_baseline(a, st_full):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
+    same generator on a 64^3 box, stepped until ~10 s of CPU work."""
+    import oracle as O
+    from paper_2608_14048_gb300 import inputs as I
+    n = 64
+    st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
+    g = O.make_grid((n, n, n))
+    p = O.make_params(gamma=st.gamma, recon=O.PLM if a.recon == "plm" else O.PPM)
+    s = O.State(st.cons, st.b1, st.b2, st.b3)
+    dt = O.compute_dt(g, p, s)
+    t0 = time.perf_counter()
+    O.step(g, p, dt, s)
+    one = time.perf_counter() - t0
+    k = max(1, min(20, int(10.0 / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        O.step(g, p, dt, s)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n ** 3 * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {n}^3 box of the same turbulence generator, {k} VL2 steps "
+                      f"({el:.1f} s), OpenMP over {cores} host threads"}
+
+
+def run_reference(a):
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    st = None
+    base = cpu_baseline(a, st)
+    steps = a.steps
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+            "n_gpus": a.gpus, "steps": steps, "warmup": a.warmup,
+            "ms_per_step": 64 ** 3 / base["value"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a), "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2608_14048_gb300 import aether as A
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # CPU baseline first (rank 0, N = 1), before the GPU work starts
+    base = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        base = cpu_baseline(a, None)
+
+    st = make_input(a)
+    prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]
+    cfg = A.make_config(gamma=st.gamma, recon=A.PLM if a.recon == "plm" else A.PPM,
+                        integrator=A.VL2, cfl=0.3, precision=prec,
+                        path=A.FUSED if a.path == "fused" else A.UNFUSED)
+    stream = torch.cuda.current_stream(dev)
+    sv = A.Solver(cfg, [A.make_block((a.n, a.n, a.n))], stream=stream)
+    sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+    cells = a.n ** 3
+
+    for _ in range(a.warmup):
+        sv.run(1)
+    sv.sync()
+
+    A.aeth_profile(sv.ctx, True)
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sv.run(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    kms, klaunch, kbytes, all_launches = A.aeth_profile_read(sv.ctx)
+    A.aeth_profile(sv.ctx, False)
+    sv.sync()
+    diag = sv.diagnostics()
+
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    value = cells * a.steps * ws / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: every step copies
+    # the state in from pinned host memory and reads it back
+    ke = a.e2e_steps or min(a.steps, 10)
+    shp = sv.shapes(0)
+    hin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (st.cons, st.b1, st.b2, st.b3)]
+    hout = [torch.empty(s, dtype=torch.float64).pin_memory() for s in shp]
+    h2d = sum(x.numel() * 8 for x in hin)
+    d2h = sum(x.numel() * 8 for x in hout)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        A.aeth_set_state(sv.ctx, 0, *hin)
+        sv.run(1)
+        A.aeth_get_state(sv.ctx, 0, *hout)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = cells * ke * ws / e2e_s
+    sv.close()
+
+    hbm, peak_kind = peaks()
+    achieved = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None
+    kernel_key = f"{a.path}_{a.prec}_{a.recon}"
+    traffic = ncu_traffic(kernel_key)
+    launches_per_step = klaunch / max(a.steps, 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32+f64"}[a.prec],
+        "data": "synthetic", "config": workload_config(a),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "kernel": "stage kernel" if a.path == "fused" else "k_flux",
+                     "peak_kind": peak_kind,
+                     "algo_bytes_per_launch": kbytes / max(klaunch, 1),
+                     "kernel_ms_per_launch": kms / max(klaunch, 1),
+                     "kernel_share_of_step": (kms / ms) if ms > 0 else None,
+                     "cell_rate_hbm_frac": value / ws * 160.0 / (hbm * 1e9)
+                     if a.prec != "fp64" else value / ws * 320.0 / (hbm * 1e9)},
+        "cpu_baseline": base,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": ke},
+        "clocks": clocks,
+        "gpu_launches": all_launches,
+        "diag_after": {"max_divb_rel": diag["max_divb_rel"], "floor_hits": diag["floor_hits"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * aether_gb.h -- C ABI of the GB300 (sm_103a) finite-volume MHD step.
+ *
+ * The library advances the ideal-MHD equations (paper Sec. 2.1, Eqs. 1-5) on
+ * one GPU with the unsplit Godunov scheme of the Aether.jl paper
+ * (arXiv 2608.14048): per-direction reconstruction of primitive variables
+ * and HLLD Riemann fluxes (Sec. 2.4), the finite-volume update of Eq. 8,
+ * constrained transport of face-centred B with upwinded corner EMFs (Sec. 2.5,
+ * Eq. 9), a two-stage predictor-corrector (Sec. 2.6), and the CFL step of
+ * Eq. 11.  Multifluid dust (Sec. 2.2) advances with IMEX2P and a closed-form
+ * implicit drag solve.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: AETH_OK (0) or a negative aeth_status.  aeth_last_error()
+ *   gives a human-readable reason for the last failure on that context.
+ * - Host arrays passed in or out are caller-owned FP64, row-major with i
+ *   fastest: cons[5][nz][ny][nx] = (rho, M1, M2, M3, E);
+ *   b1[nz][ny][nx+1], b2[nz][ny+1][nx], b3[nz+1][ny][nx] are the face-averaged
+ *   normal field components.  Along a periodic axis the last face is the
+ *   image of the first (the library reads the first, writes both).
+ *   The library converts to its working precision on the device.  Pinned
+ *   host memory makes the copies asynchronous-fast; pageable memory works.
+ * - Device memory belongs to the library (cudaMalloc at aeth_finalize) or to
+ *   a caller-provided arena (aeth_bind_arena), which must outlive the ctx.
+ * - All device work is enqueued on the bound CUDA stream (default: the
+ *   legacy default stream).  aeth_step is asynchronous; device-side errors
+ *   (non-finite state, floors hit in strict mode) are latched in a device
+ *   status word and returned by the next aeth_sync, aeth_compute_dt,
+ *   aeth_get_state or aeth_diagnostics.
+ * - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef AETHER_GB_H
+#define AETHER_GB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aeth_ctx aeth_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  AETH_OK = 0,
+  AETH_ERR_ARG = -1,         /* invalid argument or size */
+  AETH_ERR_OOM = -2,         /* device or host allocation failed */
+  AETH_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  AETH_ERR_NONFINITE = -4,   /* NaN/Inf found in the state */
+  AETH_ERR_FLOOR = -5,       /* floors applied while strict_floors = 1 */
+  AETH_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+  AETH_ERR_STATE = -7,       /* call out of order (e.g. step before finalize) */
+  AETH_ERR_UNSUPPORTED = -8  /* option combination not built */
+} aeth_status;
+
+/* equation of state (Sec. 2.1) */
+enum { AETH_EOS_ADIABATIC_MHD = 0, AETH_EOS_ADIABATIC_HYDRO = 1 };
+/* reconstruction (Sec. 2.4) */
+enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2 };
+/* Riemann solver (Sec. 2.4); AETH_RIEMANN_MLP = learned flux with HLLD
+ * fallback */
+enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_MLP = 2 };
+/* time integrator (Sec. 2.6) */
+enum { AETH_INT_VL2 = 0, AETH_INT_RK2 = 1, AETH_INT_IMEX2P = 2 };
+/* working precision: all-FP64; FP32; FP32 with the pressure recovery of
+ * Eq. 5 (E minus kinetic minus magnetic energy) evaluated in FP64 */
+enum { AETH_FP64 = 0, AETH_FP32 = 1, AETH_FP32_P64 = 2 };
+/* coordinates (Sec. 2.3) */
+enum { AETH_COORD_CART = 0, AETH_COORD_SPH = 1 };
+/* boundary kind per axis, both sides (Sec. 2.3) */
+enum { AETH_BC_PERIODIC = 0, AETH_BC_OUTFLOW = 1 };
+/* kernel path */
+enum { AETH_PATH_FUSED = 0, AETH_PATH_UNFUSED = 1 };
+
+typedef struct {
+  int eos;            /* AETH_EOS_* */
+  double gamma;       /* adiabatic index of the ideal-gas closure */
+  double rho_floor;   /* density floor of the cons->prim conversion */
+  double p_floor;     /* pressure floor */
+  int recon;          /* AETH_RECON_* of the final stage */
+  int riemann;        /* AETH_RIEMANN_* */
+  int integrator;     /* AETH_INT_* */
+  double cfl;         /* Courant factor C of Eq. 11 */
+  int precision;      /* AETH_FP64 / AETH_FP32 / AETH_FP32_P64 */
+  int path;           /* AETH_PATH_FUSED (default) or AETH_PATH_UNFUSED */
+  int strict_floors;  /* 1: a floor hit latches AETH_ERR_FLOOR */
+  int n_dust;         /* number of pressureless dust species (0: none) */
+  const double* t_stop; /* [n_dust] constant stopping times (copied) */
+} aeth_config;
+
+typedef struct {
+  int nx, ny, nz;     /* interior cells along x1, x2, x3 (each >= 1) */
+  int coord;          /* AETH_COORD_* */
+  double x1min, x1max, x2min, x2max, x3min, x3max;
+  int bc[3];          /* AETH_BC_* per axis */
+} aeth_block_desc;
+
+typedef struct {
+  double mass;          /* sum rho V over all blocks */
+  double mom[3];        /* sum M_d V */
+  double energy;        /* sum E V */
+  double max_divb_rel;  /* max over cells |sum_f +-A_f B_f| / sum_f A_f|B_f| */
+  long long floor_hits; /* cells floored since the last diagnostics call */
+  long long mlp_fallbacks; /* faces recomputed with HLLD by the MLP path */
+} aeth_diag;
+
+/* Create a context from a configuration (Sec. 3.4 "Simulation(...)").
+ * Copies everything it needs from *cfg.  Errors: AETH_ERR_ARG for invalid
+ * enums/values, AETH_ERR_UNSUPPORTED for combinations not built. */
+aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out);
+
+/* Enqueue all further device work on `cuda_stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */
+aeth_status aeth_bind_stream(aeth_ctx* ctx, void* cuda_stream);
+
+/* Use [dev_ptr, dev_ptr + bytes) as the device arena instead of allocating.
+ * Must be called before aeth_finalize; dev_ptr must be 256-byte aligned and
+ * outlive the context.  Query the size with aeth_plan. */
+aeth_status aeth_bind_arena(aeth_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Add one mesh block (Sec. 2.3; blocks may differ in size, coordinates and
+ * boundary kinds).  Blocks are independent boxes: ghost zones are filled
+ * from each block's own boundary conditions.  Returns its id (0, 1, ...)
+ * in *block_id. */
+aeth_status aeth_add_block(aeth_ctx* ctx, const aeth_block_desc* desc,
+                           int* block_id);
+
+/* Compute the device-memory layout; *bytes_needed receives the arena size. */
+aeth_status aeth_plan(aeth_ctx* ctx, size_t* bytes_needed);
+
+/* Lay out device memory (in the bound arena, else cudaMalloc) and build
+ * the launch tables.  *bytes_needed (may be NULL) receives the size.
+ * AETH_ERR_ARG if a bound arena is too small. */
+aeth_status aeth_finalize(aeth_ctx* ctx, size_t* bytes_needed);
+
+/* Copy one block's state from host FP64 arrays (layout above) to the
+ * device, converting to the working precision.  Synchronous with respect
+ * to the host arrays (they may be reused when the call returns). */
+aeth_status aeth_set_state(aeth_ctx* ctx, int block, const double* cons,
+                           const double* b1f, const double* b2f,
+                           const double* b3f);
+
+/* Copy one block's state back to host FP64 arrays.  Synchronises the
+ * stream; returns any latched device error. */
+aeth_status aeth_get_state(aeth_ctx* ctx, int block, double* cons,
+                           double* b1f, double* b2f, double* b3f);
+
+/* Eq. 11 over every block: dt = C * Cmax * min over cells and directions of
+ * dx_d / (|v_d| + c_d), with c_d the directional fast speed (sound speed in
+ * hydro, 0 for dust) and Cmax = 1 (VL2, RK2) or 1/(1 + 1/sqrt 2)
+ * (IMEX2P).  Synchronises; also leaves dt on the device for
+ * aeth_step(ctx, 0). */
+aeth_status aeth_compute_dt(aeth_ctx* ctx, double* dt);
+
+/* Enqueue one full step (all stages) of length dt on every block.
+ * dt > 0: use it; dt == 0: use the device-resident dt of the last
+ * aeth_compute_dt / aeth_run.  Asynchronous. */
+aeth_status aeth_step(aeth_ctx* ctx, double dt);
+
+/* Enqueue nsteps steps, each using the CFL step of Eq. 11 computed on the
+ * device from the current state (no host round trip); the step sequence is
+ * captured once into a CUDA graph and replayed.  Asynchronous. */
+aeth_status aeth_run(aeth_ctx* ctx, int nsteps);
+
+/* Wait for the stream; return the latched device status. */
+aeth_status aeth_sync(aeth_ctx* ctx);
+
+/* FP64 volume integrals and max relative div B over all blocks (the
+ * history quantities of Sec. 3.5).  Synchronises. */
+aeth_status aeth_diagnostics(aeth_ctx* ctx, aeth_diag* out);
+
+/* Dust state of species k of a block: rho_mom[4][nz][ny][nx] =
+ * (rho_k, M1_k, M2_k, M3_k), host FP64 (Sec. 2.2, Eqs. 6-7). */
+aeth_status aeth_set_dust(aeth_ctx* ctx, int block, int k,
+                          const double* rho_mom);
+aeth_status aeth_get_dust(aeth_ctx* ctx, int block, int k, double* rho_mom);
+
+/* Load the learned-flux network (14 inputs, 3 hidden layers of 128 with
+ * SiLU, 7 outputs; FP32 weights, converted to BF16 on the device).  Layout:
+ * per layer l, W_l[out][in] then b_l[out]; n = total floats. */
+aeth_status aeth_load_mlp(aeth_ctx* ctx, const float* params, size_t n);
+
+/* Kernel timing for roofline measurements (no counterpart in the paper; the
+ * paper times whole cycles only).  enable = 1: every later aeth_step /
+ * aeth_run launches its kernels directly (no graph replay) and brackets each
+ * launch of the dominant stage kernel with CUDA events on the bound stream.
+ * aeth_profile_read synchronises and returns the summed device time (ms) of
+ * those launches, their count, and the algorithmic HBM bytes they moved
+ * (each launch: its cells x words read and written once x element size).
+ * *all_launches counts every kernel the library launched since enable.
+ * enable = 0 stops and clears the record. */
+aeth_status aeth_profile(aeth_ctx* ctx, int enable);
+aeth_status aeth_profile_read(aeth_ctx* ctx, double* total_ms,
+                              long long* launches, double* algo_bytes,
+                              long long* all_launches);
+
+/* Reason for the last failure on ctx (static storage inside ctx). */
+const char* aeth_last_error(const aeth_ctx* ctx);
+
+/* Release device memory the library allocated and the context itself.
+ * A bound arena is not freed.  NULL is ignored. */
+void aeth_destroy(aeth_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

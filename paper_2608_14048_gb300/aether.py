@@ -1,0 +1,338 @@
+"""Thin Python binding of the C ABI in include/aether_gb.h.
+
+Argument marshalling only: every step of the MHD update runs in the CUDA
+library libaether_gb.so.  The functions keep the C names (aeth_create,
+aeth_step, ...); `Solver` is a small convenience wrapper over them.
+
+PyTorch is used only for device memory and streams: a torch CUDA tensor can
+serve as the library's arena (aeth_bind_arena) and the current torch stream
+can be bound (aeth_bind_stream).  If the library is missing this module
+raises at import of the library (no CPU fallback exists).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaether_gb.so")
+
+AETH_OK = 0
+STATUS = {0: "AETH_OK", -1: "AETH_ERR_ARG", -2: "AETH_ERR_OOM", -3: "AETH_ERR_CUDA",
+          -4: "AETH_ERR_NONFINITE", -5: "AETH_ERR_FLOOR", -6: "AETH_ERR_TIMEOUT",
+          -7: "AETH_ERR_STATE", -8: "AETH_ERR_UNSUPPORTED"}
+EOS_MHD, EOS_HYDRO = 0, 1
+DONOR, PLM, PPM = 0, 1, 2
+HLLD, MLP = 0, 2
+VL2, RK2, IMEX2P = 0, 1, 2
+FP64, FP32, FP32_P64 = 0, 1, 2
+CART, SPH = 0, 1
+PERIODIC, OUTFLOW = 0, 1
+FUSED, UNFUSED = 0, 1
+
+# every symbol include/aether_gb.h declares
+EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
+           "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
+           "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
+           "aeth_load_mlp", "aeth_profile", "aeth_profile_read", "aeth_last_error",
+           "aeth_destroy"]
+
+
+class AethError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class aeth_config(C.Structure):
+    _fields_ = [("eos", C.c_int), ("gamma", C.c_double), ("rho_floor", C.c_double),
+                ("p_floor", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
+                ("integrator", C.c_int), ("cfl", C.c_double), ("precision", C.c_int),
+                ("path", C.c_int), ("strict_floors", C.c_int), ("n_dust", C.c_int),
+                ("t_stop", C.POINTER(C.c_double))]
+
+
+class aeth_block_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("coord", C.c_int),
+                ("x1min", C.c_double), ("x1max", C.c_double), ("x2min", C.c_double),
+                ("x2max", C.c_double), ("x3min", C.c_double), ("x3max", C.c_double),
+                ("bc", C.c_int * 3)]
+
+
+class aeth_diag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("mom", C.c_double * 3), ("energy", C.c_double),
+                ("max_divb_rel", C.c_double), ("floor_hits", C.c_longlong),
+                ("mlp_fallbacks", C.c_longlong)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libaether_gb.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "aeth_create": ([C.POINTER(aeth_config), C.POINTER(P)], C.c_int),
+        "aeth_bind_stream": ([P, P], C.c_int),
+        "aeth_bind_arena": ([P, P, C.c_size_t], C.c_int),
+        "aeth_add_block": ([P, C.POINTER(aeth_block_desc), C.POINTER(C.c_int)], C.c_int),
+        "aeth_plan": ([P, C.POINTER(C.c_size_t)], C.c_int),
+        "aeth_finalize": ([P, C.POINTER(C.c_size_t)], C.c_int),
+        "aeth_set_state": ([P, C.c_int, P, P, P, P], C.c_int),
+        "aeth_get_state": ([P, C.c_int, P, P, P, P], C.c_int),
+        "aeth_compute_dt": ([P, dp], C.c_int),
+        "aeth_step": ([P, C.c_double], C.c_int),
+        "aeth_run": ([P, C.c_int], C.c_int),
+        "aeth_sync": ([P], C.c_int),
+        "aeth_diagnostics": ([P, C.POINTER(aeth_diag)], C.c_int),
+        "aeth_set_dust": ([P, C.c_int, C.c_int, P], C.c_int),
+        "aeth_get_dust": ([P, C.c_int, C.c_int, P], C.c_int),
+        "aeth_load_mlp": ([P, P, C.c_size_t], C.c_int),
+        "aeth_profile": ([P, C.c_int], C.c_int),
+        "aeth_profile_read": ([P, dp, C.POINTER(C.c_longlong), dp, C.POINTER(C.c_longlong)],
+                              C.c_int),
+        "aeth_last_error": ([P], C.c_char_p),
+        "aeth_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Host pointer of a numpy array or a (CPU, pinned or not) torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "need C-contiguous float64"
+        return a.ctypes.data_as(C.c_void_p)
+    import torch  # noqa: WPS433 (only when a tensor is passed)
+    assert isinstance(a, torch.Tensor) and a.dtype == torch.float64 and a.is_contiguous()
+    assert a.device.type == "cpu", "state arrays are host buffers"
+    return C.c_void_p(a.data_ptr())
+
+
+# ---- C names -------------------------------------------------------------
+
+def aeth_create(cfg: aeth_config):
+    h = C.c_void_p()
+    _check(None, load_library().aeth_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def aeth_bind_stream(ctx, stream_ptr: int):
+    _check(ctx, load_library().aeth_bind_stream(ctx, C.c_void_p(stream_ptr)))
+
+
+def aeth_bind_arena(ctx, dev_ptr: int, nbytes: int):
+    _check(ctx, load_library().aeth_bind_arena(ctx, C.c_void_p(dev_ptr), nbytes))
+
+
+def aeth_add_block(ctx, desc: aeth_block_desc) -> int:
+    bid = C.c_int(-1)
+    _check(ctx, load_library().aeth_add_block(ctx, C.byref(desc), C.byref(bid)))
+    return bid.value
+
+
+def aeth_plan(ctx) -> int:
+    n = C.c_size_t(0)
+    _check(ctx, load_library().aeth_plan(ctx, C.byref(n)))
+    return n.value
+
+
+def aeth_finalize(ctx) -> int:
+    n = C.c_size_t(0)
+    _check(ctx, load_library().aeth_finalize(ctx, C.byref(n)))
+    return n.value
+
+
+def aeth_set_state(ctx, block, cons, b1=None, b2=None, b3=None):
+    _check(ctx, load_library().aeth_set_state(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2), _ptr(b3)))
+
+
+def aeth_get_state(ctx, block, cons, b1=None, b2=None, b3=None):
+    _check(ctx, load_library().aeth_get_state(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2), _ptr(b3)))
+
+
+def aeth_compute_dt(ctx) -> float:
+    dt = C.c_double(0)
+    _check(ctx, load_library().aeth_compute_dt(ctx, C.byref(dt)))
+    return dt.value
+
+
+def aeth_step(ctx, dt: float):
+    _check(ctx, load_library().aeth_step(ctx, float(dt)))
+
+
+def aeth_run(ctx, nsteps: int):
+    _check(ctx, load_library().aeth_run(ctx, int(nsteps)))
+
+
+def aeth_sync(ctx):
+    _check(ctx, load_library().aeth_sync(ctx))
+
+
+def aeth_diagnostics(ctx) -> dict:
+    d = aeth_diag()
+    _check(ctx, load_library().aeth_diagnostics(ctx, C.byref(d)))
+    return {"mass": d.mass, "mom": list(d.mom), "energy": d.energy,
+            "max_divb_rel": d.max_divb_rel, "floor_hits": d.floor_hits,
+            "mlp_fallbacks": d.mlp_fallbacks}
+
+
+def aeth_set_dust(ctx, block, k, rho_mom):
+    _check(ctx, load_library().aeth_set_dust(ctx, block, k, _ptr(rho_mom)))
+
+
+def aeth_get_dust(ctx, block, k, rho_mom):
+    _check(ctx, load_library().aeth_get_dust(ctx, block, k, _ptr(rho_mom)))
+
+
+def aeth_load_mlp(ctx, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, load_library().aeth_load_mlp(ctx, p.ctypes.data_as(C.c_void_p), p.size))
+
+
+def aeth_profile(ctx, enable: bool):
+    _check(ctx, load_library().aeth_profile(ctx, 1 if enable else 0))
+
+
+def aeth_profile_read(ctx):
+    """(total device ms, launches, algorithmic bytes) of the timed dominant-
+    kernel launches, and the count of all kernels launched since enable."""
+    ms = C.c_double(0)
+    n = C.c_longlong(0)
+    b = C.c_double(0)
+    al = C.c_longlong(0)
+    _check(ctx, load_library().aeth_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(b),
+                                                 C.byref(al)))
+    return ms.value, n.value, b.value, al.value
+
+
+def aeth_last_error(ctx) -> str:
+    r = load_library().aeth_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def aeth_destroy(ctx):
+    if ctx:
+        load_library().aeth_destroy(ctx)
+
+
+def _check(ctx, rc):
+    if rc != AETH_OK:
+        msg = aeth_last_error(ctx) if ctx else ""
+        raise AethError(rc, msg)
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=FP64, mhd=True,
+                path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
+                riemann=HLLD):
+    cfg = aeth_config()
+    cfg.eos = EOS_MHD if mhd else EOS_HYDRO
+    cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
+    cfg.recon, cfg.riemann, cfg.integrator, cfg.cfl = recon, riemann, integrator, cfl
+    cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors
+    if t_stop is not None and len(t_stop) > 0:
+        arr = (C.c_double * len(t_stop))(*t_stop)
+        cfg.n_dust = len(t_stop)
+        cfg.t_stop = C.cast(arr, C.POINTER(C.c_double))
+        cfg._keep = arr
+    else:
+        cfg.n_dust = 0
+        cfg.t_stop = None
+    return cfg
+
+
+def make_block(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), coord=CART, bc=(PERIODIC,) * 3):
+    d = aeth_block_desc()
+    d.nx, d.ny, d.nz = n
+    d.coord = coord
+    d.x1min, d.x2min, d.x3min = lo
+    d.x1max, d.x2max, d.x3max = hi
+    d.bc = (C.c_int * 3)(*bc)
+    return d
+
+
+class Solver:
+    """One library context with its blocks.  `arena="torch"` allocates the
+    device arena as a torch uint8 tensor; `stream` binds a torch stream."""
+
+    def __init__(self, cfg: aeth_config, blocks, arena: str = "torch", stream=None):
+        self.ctx = aeth_create(cfg)
+        self.cfg = cfg
+        self.blocks = []
+        self._arena = None
+        try:
+            if stream is not None:
+                aeth_bind_stream(self.ctx, stream.cuda_stream)
+            for b in blocks:
+                self.blocks.append(aeth_add_block(self.ctx, b))
+            self.descs = list(blocks)
+            if arena == "torch":
+                import torch
+                nbytes = aeth_plan(self.ctx)
+                self._arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+                base = self._arena.data_ptr()
+                aligned = (base + 255) // 256 * 256
+                aeth_bind_arena(self.ctx, aligned, nbytes)
+            self.bytes = aeth_finalize(self.ctx)
+        except Exception:
+            aeth_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def close(self):
+        if self.ctx:
+            aeth_destroy(self.ctx)
+            self.ctx = None
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shapes(self, b):
+        d = self.descs[b]
+        nx, ny, nz = d.nx, d.ny, d.nz
+        return (5, nz, ny, nx), (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
+
+    def set_state(self, b, cons, b1=None, b2=None, b3=None):
+        aeth_set_state(self.ctx, b, cons, b1, b2, b3)
+
+    def get_state(self, b):
+        s = self.shapes(b)
+        out = [np.empty(x) for x in s]
+        aeth_get_state(self.ctx, b, *out)
+        return out
+
+    def compute_dt(self):
+        return aeth_compute_dt(self.ctx)
+
+    def step(self, dt):
+        aeth_step(self.ctx, dt)
+
+    def run(self, nsteps):
+        aeth_run(self.ctx, nsteps)
+
+    def sync(self):
+        aeth_sync(self.ctx)
+
+    def diagnostics(self):
+        return aeth_diagnostics(self.ctx)

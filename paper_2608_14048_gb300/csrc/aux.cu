@@ -1,0 +1,529 @@
+// Ghost fill (Sec. 2.3), host<->device state conversion, the CFL reduction
+// of Eq. 11 and the FP64 history diagnostics, for every working precision.
+#include <cmath>
+
+#include "runtime.hpp"
+
+namespace aeth {
+
+// ------------------------------------------------------------------------
+// block pointers
+// ------------------------------------------------------------------------
+
+template <typename R>
+BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
+  const BlockInfo& B = c->blocks[b];
+  BlockPtrs<R> P{};
+  P.L = B.L;
+  const long long sz = B.L.size();
+  // every array starts on a 256-byte boundary
+  const long long pitch = (sz * (long long)sizeof(R) + 255) / 256 * 256 / (long long)sizeof(R);
+  for (int r = 0; r < 2; ++r) {
+    R* base = (R*)(c->arena + B.off_reg[r]);
+    for (int v = 0; v < NVAR; ++v) P.reg[r][v] = base + v * pitch;
+  }
+  if (B.off_scratch != (size_t)-1) {
+    R* s = (R*)(c->arena + B.off_scratch);
+    int q = 0;
+    for (int v = 0; v < NPRIM; ++v) P.w[v] = s + (q++) * pitch;
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 5; ++v) P.f[d][v] = s + (q++) * pitch;
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 2; ++v) P.e[d][v] = s + (q++) * pitch;
+    for (int d = 0; d < 3; ++d) P.edge[d] = s + (q++) * pitch;
+  }
+  if (c->cfg.n_dust > 0) {
+    for (int r = 0; r < 2; ++r) P.dust[r] = (R*)(c->arena + B.off_dust[r]);
+  }
+  // geometry tables: 11 separable factors x 3 axes
+  const R* t = (const R*)(c->arena + B.off_geo);
+  const int g = B.L.g;
+  long long ax[3] = {B.L.n[0] + 2 * g + 2, B.L.n[1] + 2 * g + 2, B.L.n[2] + 2 * g + 2};
+  long long o = 0;
+  auto sep = [&](Sep<R>& s) {
+    s.x = t + o; o += ax[0];
+    s.y = t + o; o += ax[1];
+    s.z = t + o; o += ax[2];
+    s.g = g;
+  };
+  for (int d = 0; d < 3; ++d) sep(P.geo.area[d]);
+  sep(P.geo.vol);
+  for (int d = 0; d < 3; ++d) sep(P.geo.edge[d]);
+  sep(P.geo.invr);
+  sep(P.geo.cotr);
+  for (int d = 0; d < 3; ++d) sep(P.geo.width[d]);
+  return P;
+}
+
+template BlockPtrs<float> block_ptrs<float>(const aeth_ctx*, int);
+template BlockPtrs<double> block_ptrs<double>(const aeth_ctx*, int);
+
+// Number of R entries in one block's geometry tables.
+size_t geometry_len(const Layout& L) {
+  return 11ull * (size_t)(L.n[0] + L.n[1] + L.n[2] + 3 * (2 * L.g + 2));
+}
+
+// Exact separable factors of Sec. 2.3, computed in FP64 on the host.
+template <typename R>
+static aeth_status build_geometry_T(aeth_ctx* c) {
+  for (size_t b = 0; b < c->blocks.size(); ++b) {
+    const BlockInfo& B = c->blocks[b];
+    const Layout& L = B.L;
+    const int g = L.g;
+    const double lo[3] = {B.desc.x1min, B.desc.x2min, B.desc.x3min};
+    const double hi[3] = {B.desc.x1max, B.desc.x2max, B.desc.x3max};
+    double dx[3];
+    for (int d = 0; d < 3; ++d) dx[d] = (hi[d] - lo[d]) / L.n[d];
+    std::vector<double> h;
+    auto xf = [&](int d, int i) { return lo[d] + i * dx[d]; };
+    auto push = [&](int d, auto fn) {
+      for (int i = -g; i < L.n[d] + g + 2; ++i) h.push_back(fn(i));
+    };
+    const bool sph = L.coord == AETH_COORD_SPH;
+    auto one = [](int) { return 1.0; };
+    if (!sph) {
+      auto cst = [&](int d) { return [&, d](int) { return dx[d]; }; };
+      // area[0] = dy*dz, area[1] = dx*dz, area[2] = dx*dy
+      push(0, one); push(1, cst(1)); push(2, cst(2));
+      push(0, cst(0)); push(1, one); push(2, cst(2));
+      push(0, cst(0)); push(1, cst(1)); push(2, one);
+      push(0, cst(0)); push(1, cst(1)); push(2, cst(2));          // vol
+      push(0, cst(0)); push(1, one); push(2, one);                // edge[0]
+      push(0, one); push(1, cst(1)); push(2, one);                // edge[1]
+      push(0, one); push(1, one); push(2, cst(2));                // edge[2]
+      push(0, one); push(1, one); push(2, one);                   // invr (unused)
+      push(0, one); push(1, one); push(2, one);                   // cotr (unused)
+      push(0, cst(0)); push(1, one); push(2, one);                // width[0]
+      push(0, one); push(1, cst(1)); push(2, one);                // width[1]
+      push(0, one); push(1, one); push(2, cst(2));                // width[2]
+    } else {
+      auto r = [&](int i) { return xf(0, i); };
+      auto th = [&](int j) { return xf(1, j); };
+      const double dphi = dx[2];
+      auto dcos = [&](int j) { return cos(th(j)) - cos(th(j + 1)); };
+      auto r2f = [&](int i) { return r(i) * r(i); };
+      auto hdr2 = [&](int i) { return 0.5 * (r(i + 1) * r(i + 1) - r(i) * r(i)); };
+      auto vdr3 = [&](int i) { return (r(i + 1) * r(i + 1) * r(i + 1) - r(i) * r(i) * r(i)) / 3.0; };
+      auto cphi = [&](int) { return dphi; };
+      // area[0] = r_-^2 (cos th- - cos th+) dphi
+      push(0, r2f); push(1, dcos); push(2, cphi);
+      // area[1] = 1/2 (r+^2 - r-^2) sin th- dphi
+      push(0, hdr2); push(1, [&](int j) { return sin(th(j)); }); push(2, cphi);
+      // area[2] = 1/2 (r+^2 - r-^2) (th+ - th-)
+      push(0, hdr2); push(1, [&](int) { return dx[1]; }); push(2, one);
+      // vol = (r+^3 - r-^3)/3 (cos th- - cos th+) dphi
+      push(0, vdr3); push(1, dcos); push(2, cphi);
+      // edge[0] = dr ; edge[1] = r_- dth ; edge[2] = r_- sin th- dphi
+      push(0, [&](int) { return dx[0]; }); push(1, one); push(2, one);
+      push(0, r); push(1, [&](int) { return dx[1]; }); push(2, one);
+      push(0, r); push(1, [&](int j) { return sin(th(j)); }); push(2, cphi);
+      // <1/r> = (A_r+ - A_r-)/(2V) = (r+^2 - r-^2) / (2 (r+^3 - r-^3)/3)
+      push(0, [&](int i) { return (r(i + 1) * r(i + 1) - r(i) * r(i)) / (2.0 * vdr3(i)); });
+      push(1, one); push(2, one);
+      // <cot th / r> = (A_th+ - A_th-)/V
+      push(0, [&](int i) { return hdr2(i) / vdr3(i); });
+      push(1, [&](int j) { return (sin(th(j + 1)) - sin(th(j))) / dcos(j); });
+      push(2, one);
+      // widths at the volume-weighted centroid
+      auto rc = [&](int i) {
+        double a = r(i), bb = r(i + 1);
+        return 0.75 * (pow(bb, 4) - pow(a, 4)) / (pow(bb, 3) - pow(a, 3));
+      };
+      auto thc = [&](int j) {
+        double a = th(j), bb = th(j + 1);
+        return (sin(bb) - sin(a) - bb * cos(bb) + a * cos(a)) / (cos(a) - cos(bb));
+      };
+      push(0, [&](int) { return dx[0]; }); push(1, one); push(2, one);
+      push(0, rc); push(1, [&](int) { return dx[1]; }); push(2, one);
+      push(0, rc); push(1, [&](int j) { return sin(thc(j)); }); push(2, cphi);
+    }
+    if (h.size() != B.geo_len)
+      return fail(c, AETH_ERR_STATE, "geometry table size mismatch (%zu vs %zu)", h.size(), B.geo_len);
+    std::vector<R> hr(h.begin(), h.end());
+    AETH_CK(c, cudaMemcpyAsync(c->arena + B.off_geo, hr.data(), hr.size() * sizeof(R),
+                               cudaMemcpyHostToDevice, c->stream));
+    AETH_CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return AETH_OK;
+}
+
+aeth_status build_geometry(aeth_ctx* c) {
+  return c->elem == 8 ? build_geometry_T<double>(c) : build_geometry_T<float>(c);
+}
+
+// ------------------------------------------------------------------------
+// ghost fill, one axis at a time (edges and corners come out right)
+// ------------------------------------------------------------------------
+
+template <typename R>
+__global__ void k_fill_axis(Layout L, Arr8<R> a, int nv, int d) {
+  const int g = L.g;
+  int lo[3], ext[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e < d) { lo[e] = -g; ext[e] = L.n[e] + 2 * g + 1; }
+    else if (e == d) { lo[e] = 0; ext[e] = 2 * g + 1; }
+    else { lo[e] = 0; ext[e] = L.n[e] + 1; }
+  }
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t1 = blockIdx.y * blockDim.y + threadIdx.y;
+  const int t2 = blockIdx.z * blockDim.z + threadIdx.z;
+  if (t0 >= ext[0] || t1 >= ext[1] || t2 >= ext[2]) return;
+  int c[3] = {t0 + lo[0], t1 + lo[1], t2 + lo[2]};
+  const int n = L.n[d];
+  const int t = c[d];
+  c[d] = t < g ? t - g : n + (t - g);      // -g..-1, n..n+g
+  const int p = c[d];
+  const long long dst = L.idx(c[0], c[1], c[2]);
+  for (int v = 0; v < nv; ++v) {
+    const bool face_d = (v == 5 + d);
+    int s;
+    if (L.bc[d] == AETH_BC_PERIODIC) {
+      s = ((p % n) + n) % n;
+    } else if (face_d) {
+      if (p >= 0 && p <= n) continue;       // faces 0..n are real
+      s = p < 0 ? 0 : n;
+    } else {
+      s = p < 0 ? 0 : n - 1;
+    }
+    int sc[3] = {c[0], c[1], c[2]};
+    sc[d] = s;
+    a.p[v][dst] = a.p[v][L.idx(sc[0], sc[1], sc[2])];
+  }
+}
+
+template <typename R>
+void launch_fill(const BlockPtrs<R>& P, R* const* arrs, int nv, cudaStream_t st) {
+  Arr8<R> a{};
+  for (int v = 0; v < nv; ++v) a.p[v] = arrs[v];
+  const Layout& L = P.L;
+  for (int d = 0; d < 3; ++d) {
+    int ext[3];
+    for (int e = 0; e < 3; ++e)
+      ext[e] = e < d ? L.n[e] + 2 * L.g + 1 : (e == d ? 2 * L.g + 1 : L.n[e] + 1);
+    dim3 blk(32, 4, 2);
+    dim3 grd((ext[0] + 31) / 32, (ext[1] + 3) / 4, (ext[2] + 1) / 2);
+    k_fill_axis<R><<<grd, blk, 0, st>>>(L, a, nv, d);
+  }
+}
+template void launch_fill<float>(const BlockPtrs<float>&, float* const*, int, cudaStream_t);
+template void launch_fill<double>(const BlockPtrs<double>&, double* const*, int, cudaStream_t);
+
+// ------------------------------------------------------------------------
+// host FP64 <-> device working precision (interior only)
+// ------------------------------------------------------------------------
+
+template <typename R>
+__global__ void k_load(Layout L, Arr8<R> a, int mhd, const double* __restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  if (i > nx || j > ny || k > nz) return;
+  const long long nc = (long long)nx * ny * nz;
+  const long long d = L.idx(i, j, k);
+  if (i < nx && j < ny && k < nz) {
+    const long long c = ((long long)k * ny + j) * nx + i;
+    for (int v = 0; v < 5; ++v) a.p[v][d] = (R)s[v * nc + c];
+  }
+  if (!mhd) return;
+  const double* b1 = s + 5 * nc;
+  const double* b2 = b1 + (long long)nz * ny * (nx + 1);
+  const double* b3 = b2 + (long long)nz * (ny + 1) * nx;
+  if (j < ny && k < nz) a.p[5][d] = (R)b1[((long long)k * ny + j) * (nx + 1) + i];
+  if (i < nx && k < nz) a.p[6][d] = (R)b2[((long long)k * (ny + 1) + j) * nx + i];
+  if (i < nx && j < ny) a.p[7][d] = (R)b3[((long long)k * ny + j) * nx + i];
+}
+
+template <typename R>
+__global__ void k_store(Layout L, Arr8<R> a, int mhd, double* __restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  if (i > nx || j > ny || k > nz) return;
+  const long long nc = (long long)nx * ny * nz;
+  if (i < nx && j < ny && k < nz) {
+    const long long c = ((long long)k * ny + j) * nx + i;
+    const long long d = L.idx(i, j, k);
+    for (int v = 0; v < 5; ++v) s[v * nc + c] = (double)a.p[v][d];
+  }
+  if (!mhd) return;
+  double* b1 = s + 5 * nc;
+  double* b2 = b1 + (long long)nz * ny * (nx + 1);
+  double* b3 = b2 + (long long)nz * (ny + 1) * nx;
+  // periodic axes: the last face is the image of the first
+  const int i1 = (i == nx && L.bc[0] == AETH_BC_PERIODIC) ? 0 : i;
+  const int j2 = (j == ny && L.bc[1] == AETH_BC_PERIODIC) ? 0 : j;
+  const int k3 = (k == nz && L.bc[2] == AETH_BC_PERIODIC) ? 0 : k;
+  if (j < ny && k < nz) b1[((long long)k * ny + j) * (nx + 1) + i] = (double)a.p[5][L.idx(i1, j, k)];
+  if (i < nx && k < nz) b2[((long long)k * (ny + 1) + j) * nx + i] = (double)a.p[6][L.idx(i, j2, k)];
+  if (i < nx && j < ny) b3[((long long)k * ny + j) * nx + i] = (double)a.p[7][L.idx(i, j, k3)];
+}
+
+template <typename R>
+static aeth_status load_store_T(aeth_ctx* c, int b, bool load) {
+  BlockPtrs<R> P = block_ptrs<R>(c, b);
+  Arr8<R> a{};
+  for (int v = 0; v < NVAR; ++v) a.p[v] = P.reg[0][v];
+  const Layout& L = P.L;
+  dim3 blk(32, 4, 2);
+  dim3 grd((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 3) / 4, (L.n[2] + 1 + 1) / 2);
+  if (load) k_load<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), c->d_stage);
+  else k_store<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), c->d_stage);
+  AETH_CK(c, cudaGetLastError());
+  return AETH_OK;
+}
+
+aeth_status enqueue_load(aeth_ctx* c, int b) {
+  return c->elem == 8 ? load_store_T<double>(c, b, true) : load_store_T<float>(c, b, true);
+}
+aeth_status enqueue_store(aeth_ctx* c, int b) {
+  return c->elem == 8 ? load_store_T<double>(c, b, false) : load_store_T<float>(c, b, false);
+}
+
+// dust species k: rho_mom[4][nz][ny][nx] <-> register A
+template <typename R>
+__global__ void k_dust_io(Layout L, R* __restrict__ dreg, int k, int load,
+                          double* __restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int kk = blockIdx.z * blockDim.z + threadIdx.z;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  if (i >= nx || j >= ny || kk >= nz) return;
+  const long long nc = (long long)nx * ny * nz;
+  const long long c = ((long long)kk * ny + j) * nx + i;
+  const long long d = L.idx(i, j, kk);
+  const long long sz = L.size();
+  for (int v = 0; v < 4; ++v) {
+    R* arr = dreg + (long long)(4 * k + v) * sz;
+    if (load) arr[d] = (R)s[v * nc + c];
+    else s[v * nc + c] = (double)arr[d];
+  }
+}
+
+template <typename R>
+static aeth_status dust_io_T(aeth_ctx* c, int b, int k, bool load) {
+  BlockPtrs<R> P = block_ptrs<R>(c, b);
+  const Layout& L = P.L;
+  dim3 blk(32, 4, 2);
+  dim3 grd((L.n[0] + 31) / 32, (L.n[1] + 3) / 4, (L.n[2] + 1) / 2);
+  k_dust_io<R><<<grd, blk, 0, c->stream>>>(L, P.dust[0], k, load ? 1 : 0, c->d_stage);
+  AETH_CK(c, cudaGetLastError());
+  return AETH_OK;
+}
+aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k) {
+  return c->elem == 8 ? dust_io_T<double>(c, b, k, true) : dust_io_T<float>(c, b, k, true);
+}
+aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k) {
+  return c->elem == 8 ? dust_io_T<double>(c, b, k, false) : dust_io_T<float>(c, b, k, false);
+}
+
+// ------------------------------------------------------------------------
+// CFL reduction (Eq. 11): per-cell min over directions, block min, then one
+// block reduces all partials.  Non-finite states latch ST_NONFINITE.
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R, bool P64>
+__global__ void __launch_bounds__(256) k_dt(Layout L, Geometry<R> geo, Arr8<R> a, int mhd,
+                                            double gamma, double rho_floor, double p_floor,
+                                            const R* __restrict__ dust, int nd,
+                                            double* __restrict__ partial, int* status) {
+  __shared__ double sm[8];
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const long long nc = (long long)nx * ny * nz;
+  double m = INFINITY;
+  bool bad = false;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % nx);
+    const int j = (int)((t / nx) % ny);
+    const int k = (int)(t / ((long long)nx * ny));
+    const long long c = L.idx(i, j, k);
+    R rho = a.p[0][c];
+    if (!(rho >= (R)rho_floor)) { if (!(rho == rho)) bad = true; rho = (R)rho_floor; }
+    const R v[3] = {a.p[1][c] / rho, a.p[2][c] / rho, a.p[3][c] / rho};
+    R bc[3] = {0, 0, 0};
+    if (mhd) {
+      bc[0] = R(0.5) * (a.p[5][c] + a.p[5][c + 1]);
+      bc[1] = R(0.5) * (a.p[6][c] + a.p[6][c + L.sx]);
+      bc[2] = R(0.5) * (a.p[7][c] + a.p[7][c + L.sx * L.sy]);
+    }
+    R pr;
+    if (P64) {
+      double ke = 0.5 * ((double)a.p[1][c] * a.p[1][c] + (double)a.p[2][c] * a.p[2][c] +
+                         (double)a.p[3][c] * a.p[3][c]) / (double)rho;
+      double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
+      pr = (R)((gamma - 1.0) * ((double)a.p[4][c] - ke - me));
+    } else {
+      pr = (R)(gamma - 1.0) * (a.p[4][c] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
+                               R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+    }
+    if (!(pr >= (R)p_floor)) { if (!(pr == pr)) bad = true; pr = (R)p_floor; }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
+      const R w = geo.width[d](i, j, k);
+      double dtd = (double)(w / (fabs(v[d]) + cf));
+      if (!(dtd > 0.0)) bad = true;
+      m = fmin(m, dtd);
+    }
+    // pressureless dust species: c = 0 (Eq. 11)
+    for (int s = 0; s < nd; ++s) {
+      const long long sz = L.size();
+      const R rk = dust[(long long)(4 * s) * sz + c];
+      if (!(rk > R(0))) continue;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const R vk = fabs(dust[(long long)(4 * s + 1 + d) * sz + c] / rk);
+        if (vk > R(0)) m = fmin(m, (double)(geo.width[d](i, j, k) / vk));
+      }
+    }
+  }
+  m = warp_min(m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;
+    v = warp_min(v);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void k_dt_final(const double* __restrict__ partial, int n, double scale,
+                           double* __restrict__ dt) {
+  __shared__ double sm[32];
+  double m = INFINITY;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) m = fmin(m, partial[t]);
+  m = warp_min(m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;
+    v = warp_min(v);
+    if (threadIdx.x == 0) *dt = scale * v;
+  }
+}
+
+template <typename R, bool P64>
+static aeth_status dt_T(aeth_ctx* c) {
+  for (size_t b = 0; b < c->blocks.size(); ++b) {
+    BlockPtrs<R> P = block_ptrs<R>(c, (int)b);
+    Arr8<R> a{};
+    for (int v = 0; v < NVAR; ++v) a.p[v] = P.reg[0][v];
+    const BlockInfo& B = c->blocks[b];
+    k_dt<R, P64><<<B.dt_blocks, 256, 0, c->stream>>>(
+        P.L, P.geo, a, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor,
+        P.dust[0], c->cfg.n_dust, c->d_partials + B.dt_offset, c->d_status);
+  }
+  c->n_launch += (long long)c->blocks.size() + 1;
+  const double scale = c->cfg.cfl * cmax_of(c->cfg.integrator);
+  k_dt_final<<<1, 1024, 0, c->stream>>>(c->d_partials, c->n_partials, scale, c->d_dt);
+  AETH_CK(c, cudaGetLastError());
+  return AETH_OK;
+}
+
+aeth_status enqueue_dt(aeth_ctx* c) {
+  if (c->cfg.precision == AETH_FP64) return dt_T<double, false>(c);
+  if (c->cfg.precision == AETH_FP32) return dt_T<float, false>(c);
+  return dt_T<float, true>(c);
+}
+
+__global__ void k_set_dt(double* d, double v) { *d = v; }
+
+aeth_status enqueue_set_dt(aeth_ctx* c, double dt) {
+  k_set_dt<<<1, 1, 0, c->stream>>>(c->d_dt, dt);
+  c->n_launch += 1;
+  AETH_CK(c, cudaGetLastError());
+  return AETH_OK;
+}
+
+// ------------------------------------------------------------------------
+// diagnostics: FP64 volume integrals and max relative div B
+// ------------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_diag(Layout L, Geometry<R> geo, Arr8<R> a, int mhd,
+                                              double* __restrict__ partial) {
+  __shared__ double sm[6][8];
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const long long nc = (long long)nx * ny * nz;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % nx);
+    const int j = (int)((t / nx) % ny);
+    const int k = (int)(t / ((long long)nx * ny));
+    const long long c = L.idx(i, j, k);
+    const double V = (double)geo.vol(i, j, k);
+    for (int v = 0; v < 5; ++v) acc[v] += (double)a.p[v][c] * V;
+    if (mhd) {
+      const double f[6] = {a.p[5][c], a.p[5][c + 1], a.p[6][c], a.p[6][c + L.sx],
+                           a.p[7][c], a.p[7][c + L.sx * L.sy]};
+      const double ar[6] = {geo.area[0](i, j, k), geo.area[0](i + 1, j, k),
+                            geo.area[1](i, j, k), geo.area[1](i, j + 1, k),
+                            geo.area[2](i, j, k), geo.area[2](i, j, k + 1)};
+      const double div = ar[1] * f[1] - ar[0] * f[0] + ar[3] * f[3] - ar[2] * f[2] +
+                         ar[5] * f[5] - ar[4] * f[4];
+      double den = 0;
+      for (int q = 0; q < 6; ++q) den += ar[q] * fabs(f[q]);
+      if (den > 0) acc[5] = fmax(acc[5], fabs(div) / den);
+    }
+  }
+  for (int q = 0; q < 5; ++q) acc[q] = warp_sum(acc[q]);
+  for (int o = 16; o > 0; o >>= 1) acc[5] = fmax(acc[5], __shfl_xor_sync(0xffffffffu, acc[5], o));
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 6; ++q) sm[q][w] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < 6; ++q) {
+      double v = threadIdx.x < nw ? sm[q][threadIdx.x] : 0.0;
+      if (q < 5) v = warp_sum(v);
+      else for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (threadIdx.x == 0) partial[6 * blockIdx.x + q] = v;
+    }
+  }
+}
+
+__global__ void k_diag_final(const double* __restrict__ partial, int n, double* out) {
+  // single thread, fixed order: deterministic totals
+  if (threadIdx.x != 0) return;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = 0; t < n; ++t) {
+    for (int q = 0; q < 5; ++q) s[q] += partial[6 * t + q];
+    s[5] = fmax(s[5], partial[6 * t + 5]);
+  }
+  for (int q = 0; q < 6; ++q) out[q] = s[q];
+}
+
+template <typename R>
+static aeth_status diag_T(aeth_ctx* c) {
+  for (size_t b = 0; b < c->blocks.size(); ++b) {
+    BlockPtrs<R> P = block_ptrs<R>(c, (int)b);
+    Arr8<R> a{};
+    for (int v = 0; v < NVAR; ++v) a.p[v] = P.reg[0][v];
+    const BlockInfo& B = c->blocks[b];
+    k_diag<R><<<B.dt_blocks, 256, 0, c->stream>>>(P.L, P.geo, a, is_mhd(c),
+                                                   c->d_partials + 6 * B.dt_offset);
+  }
+  k_diag_final<<<1, 32, 0, c->stream>>>(c->d_partials, c->n_partials, c->d_diag);
+  AETH_CK(c, cudaGetLastError());
+  return AETH_OK;
+}
+
+aeth_status enqueue_diag(aeth_ctx* c) {
+  return c->elem == 8 ? diag_T<double>(c) : diag_T<float>(c);
+}
+
+}  // namespace aeth

@@ -1,0 +1,447 @@
+// C-ABI entry points of include/aether_gb.h: context, block table, device
+// arena, host<->device state transfer, step sequencing and CUDA graphs.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "runtime.hpp"
+
+using namespace aeth;
+
+namespace aeth {
+template <typename R, bool P64> aeth_status step_unfused(aeth_ctx* c);
+template <typename R, bool P64> aeth_status step_fused(aeth_ctx* c);
+template <typename R, bool P64> aeth_status step_dust(aeth_ctx* c);
+size_t geometry_len(const Layout& L);
+bool fused_supported(const aeth_ctx* c);
+
+aeth_status enqueue_step(aeth_ctx* c, bool cfl_on_device) {
+  if (cfl_on_device) {
+    aeth_status s = enqueue_dt(c);
+    if (s != AETH_OK) return s;
+  }
+  const int p = c->cfg.precision;
+  if (c->cfg.n_dust > 0) {
+    if (p == AETH_FP64) return step_dust<double, false>(c);
+    if (p == AETH_FP32) return step_dust<float, false>(c);
+    return step_dust<float, true>(c);
+  }
+  const bool fused = c->cfg.path == AETH_PATH_FUSED && fused_supported(c);
+  if (fused) {
+    if (p == AETH_FP64) return step_fused<double, false>(c);
+    if (p == AETH_FP32) return step_fused<float, false>(c);
+    return step_fused<float, true>(c);
+  }
+  if (p == AETH_FP64) return step_unfused<double, false>(c);
+  if (p == AETH_FP32) return step_unfused<float, false>(c);
+  return step_unfused<float, true>(c);
+}
+}  // namespace aeth
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+extern "C" {
+
+aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
+  if (!cfg || !out) return AETH_ERR_ARG;
+  *out = nullptr;
+  aeth_ctx* c = new (std::nothrow) aeth_ctx();
+  if (!c) return AETH_ERR_OOM;
+  c->cfg = *cfg;
+  aeth_status bad = AETH_OK;
+  if (cfg->eos != AETH_EOS_ADIABATIC_MHD && cfg->eos != AETH_EOS_ADIABATIC_HYDRO) bad = AETH_ERR_ARG;
+  if (!(cfg->gamma > 1.0)) bad = AETH_ERR_ARG;
+  if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM) bad = AETH_ERR_ARG;
+  if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_MLP) bad = AETH_ERR_ARG;
+  if (cfg->integrator < AETH_INT_VL2 || cfg->integrator > AETH_INT_IMEX2P) bad = AETH_ERR_ARG;
+  if (cfg->precision < AETH_FP64 || cfg->precision > AETH_FP32_P64) bad = AETH_ERR_ARG;
+  if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) bad = AETH_ERR_ARG;
+  if (cfg->path != AETH_PATH_FUSED && cfg->path != AETH_PATH_UNFUSED) bad = AETH_ERR_ARG;
+  if (cfg->n_dust < 0 || cfg->n_dust > 32) bad = AETH_ERR_ARG;
+  if (cfg->n_dust > 0 && !cfg->t_stop) bad = AETH_ERR_ARG;
+  if (bad != AETH_OK) {
+    delete c;
+    return bad;
+  }
+  if (cfg->n_dust > 0) {
+    if (cfg->eos != AETH_EOS_ADIABATIC_HYDRO || cfg->integrator != AETH_INT_IMEX2P) {
+      delete c;
+      return AETH_ERR_UNSUPPORTED;
+    }
+    c->t_stop.assign(cfg->t_stop, cfg->t_stop + cfg->n_dust);
+    for (double t : c->t_stop)
+      if (!(t > 0.0)) { delete c; return AETH_ERR_ARG; }
+    c->cfg.t_stop = c->t_stop.data();
+  } else if (cfg->integrator == AETH_INT_IMEX2P) {
+    delete c;
+    return AETH_ERR_UNSUPPORTED;
+  }
+  c->elem = cfg->precision == AETH_FP64 ? 8 : 4;
+  c->g = ghost_width(cfg->recon);
+  *out = c;
+  return AETH_OK;
+}
+
+aeth_status aeth_bind_stream(aeth_ctx* c, void* stream) {
+  if (!c) return AETH_ERR_ARG;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->stream = (cudaStream_t)stream;
+  return AETH_OK;
+}
+
+aeth_status aeth_bind_arena(aeth_ctx* c, void* p, size_t bytes) {
+  if (!c || !p) return AETH_ERR_ARG;
+  if (c->finalized) return fail(c, AETH_ERR_STATE, "arena must be bound before aeth_finalize");
+  if (((uintptr_t)p) % 256 != 0) return fail(c, AETH_ERR_ARG, "arena must be 256-byte aligned");
+  c->arena = (char*)p;
+  c->arena_bytes = bytes;
+  c->own_arena = false;
+  return AETH_OK;
+}
+
+aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
+  if (!c || !d) return AETH_ERR_ARG;
+  if (c->finalized || c->planned) return fail(c, AETH_ERR_STATE, "blocks must be added before plan/finalize");
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(c, AETH_ERR_ARG, "block sizes must be >= 1");
+  if ((long long)d->nx * d->ny * d->nz > (1ll << 31))
+    return fail(c, AETH_ERR_ARG, "block of %lld cells exceeds 2^31", (long long)d->nx * d->ny * d->nz);
+  if (!(d->x1max > d->x1min && d->x2max > d->x2min && d->x3max > d->x3min))
+    return fail(c, AETH_ERR_ARG, "block extents must be increasing");
+  if (d->coord != AETH_COORD_CART && d->coord != AETH_COORD_SPH) return fail(c, AETH_ERR_ARG, "bad coord");
+  for (int q = 0; q < 3; ++q)
+    if (d->bc[q] != AETH_BC_PERIODIC && d->bc[q] != AETH_BC_OUTFLOW) return fail(c, AETH_ERR_ARG, "bad bc");
+  const int g = c->g;
+  const int nn[3] = {d->nx, d->ny, d->nz};
+  for (int q = 0; q < 3; ++q)
+    if (d->bc[q] == AETH_BC_PERIODIC && nn[q] < g && nn[q] != 1)
+      return fail(c, AETH_ERR_ARG, "periodic axis %d needs n >= ghost width %d (or n == 1)", q, g);
+  if (d->coord == AETH_COORD_SPH) {
+    if (!(d->x1min - g * (d->x1max - d->x1min) / d->nx > 0.0))
+      return fail(c, AETH_ERR_ARG, "spherical block: r (incl. ghosts) must stay > 0");
+    const double dth = (d->x2max - d->x2min) / d->ny;
+    if (!(d->x2min - g * dth > 0.0 && d->x2max + g * dth < M_PI))
+      return fail(c, AETH_ERR_ARG, "spherical block: theta (incl. ghosts) must avoid the axis");
+  }
+  BlockInfo B{};
+  B.desc = *d;
+  Layout& L = B.L;
+  L.n[0] = d->nx; L.n[1] = d->ny; L.n[2] = d->nz;
+  L.g = g;
+  for (int q = 0; q < 3; ++q) L.bc[q] = d->bc[q];
+  L.coord = d->coord;
+  L.sx = ((long long)OX + d->nx + g + 1 + 3) / 4 * 4;
+  L.sy = d->ny + 2 * g + 1;
+  L.sz = d->nz + 2 * g + 1;
+  B.ncell = (long long)d->nx * d->ny * d->nz;
+  c->blocks.push_back(B);
+  if (id) *id = (int)c->blocks.size() - 1;
+  return AETH_OK;
+}
+
+aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
+  if (!c) return AETH_ERR_ARG;
+  if (c->blocks.empty()) return fail(c, AETH_ERR_STATE, "no blocks");
+  size_t off = 0;
+  size_t max_stage = 0;
+  int npart = 0;
+  const bool unfused = !(c->cfg.path == AETH_PATH_FUSED && fused_supported(c));
+  for (auto& B : c->blocks) {
+    const long long sz = B.L.size();
+    const size_t arr = align256((size_t)sz * c->elem);
+    for (int r = 0; r < 2; ++r) {
+      B.off_reg[r] = off;
+      off += NVAR * arr;
+    }
+    if (unfused || c->cfg.n_dust > 0) {
+      B.off_scratch = off;
+      off += (NPRIM + 15 + 6 + 3) * arr;
+    } else {
+      B.off_scratch = (size_t)-1;
+    }
+    if (c->cfg.n_dust > 0) {
+      for (int r = 0; r < 2; ++r) {
+        B.off_dust[r] = off;
+        off += align256((size_t)4 * c->cfg.n_dust * sz * c->elem);
+      }
+    }
+    B.geo_len = geometry_len(B.L);
+    B.off_geo = off;
+    off += align256(B.geo_len * c->elem);
+    const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz;
+    size_t st = (size_t)(5 * nx * ny * nz + nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx);
+    if (c->cfg.n_dust > 0) st = std::max(st, (size_t)(4 * nx * ny * nz));
+    max_stage = std::max(max_stage, st * sizeof(double));
+    long long want = (B.ncell + 255) / 256;
+    B.dt_blocks = (int)std::max(1ll, std::min(want, 2048ll));
+    B.dt_offset = npart;
+    npart += B.dt_blocks;
+  }
+  c->off_stage = off;
+  c->stage_bytes = align256(max_stage);
+  off += c->stage_bytes;
+  c->off_partials = off;
+  c->n_partials = npart;
+  off += align256((size_t)6 * npart * sizeof(double));
+  c->off_scalars = off;
+  off += 4096;
+  c->need = off;
+  c->planned = true;
+  if (bytes) *bytes = off;
+  return AETH_OK;
+}
+
+aeth_status aeth_finalize(aeth_ctx* c, size_t* bytes) {
+  if (!c) return AETH_ERR_ARG;
+  if (c->finalized) return fail(c, AETH_ERR_STATE, "already finalized");
+  aeth_status s = aeth_plan(c, bytes);
+  if (s != AETH_OK) return s;
+  if (c->arena) {
+    if (c->arena_bytes < c->need)
+      return fail(c, AETH_ERR_ARG, "bound arena has %zu bytes, %zu needed", c->arena_bytes, c->need);
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, c->need);
+    if (e != cudaSuccess)
+      return fail(c, AETH_ERR_OOM, "cudaMalloc(%zu) failed: %s", c->need, cudaGetErrorString(e));
+    c->arena = (char*)p;
+    c->arena_bytes = c->need;
+    c->own_arena = true;
+  }
+  AETH_CK(c, cudaMemsetAsync(c->arena, 0, c->need, c->stream));
+  c->d_stage = (double*)(c->arena + c->off_stage);
+  c->d_partials = (double*)(c->arena + c->off_partials);
+  char* sc = c->arena + c->off_scalars;
+  c->d_dt = (double*)sc;
+  c->d_diag = (double*)(sc + 64);
+  c->d_status = (int*)(sc + 256);
+  c->d_floor = (unsigned long long*)(sc + 320);
+  c->d_fallback = (unsigned long long*)(sc + 384);
+  s = build_geometry(c);
+  if (s != AETH_OK) return s;
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  c->finalized = true;
+  return AETH_OK;
+}
+
+static aeth_status check_block(aeth_ctx* c, int b) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  if (b < 0 || b >= (int)c->blocks.size()) return fail(c, AETH_ERR_ARG, "block %d out of range", b);
+  return AETH_OK;
+}
+
+static aeth_status read_status(aeth_ctx* c) {
+  int st = 0;
+  AETH_CK(c, cudaMemcpyAsync(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  if (st & ST_NONFINITE) return fail(c, AETH_ERR_NONFINITE, "non-finite value in the state");
+  if (st & ST_TIMEOUT) return fail(c, AETH_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (st & ST_FLOOR) return fail(c, AETH_ERR_FLOOR, "floor applied with strict_floors set");
+  return AETH_OK;
+}
+
+aeth_status aeth_set_state(aeth_ctx* c, int b, const double* cons, const double* b1,
+                           const double* b2, const double* b3) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (!cons) return fail(c, AETH_ERR_ARG, "cons is NULL");
+  const auto& B = c->blocks[b];
+  const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz, nc = nx * ny * nz;
+  double* d = c->d_stage;
+  AETH_CK(c, cudaMemcpyAsync(d, cons, 5 * nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (is_mhd(c)) {
+    if (!b1 || !b2 || !b3) return fail(c, AETH_ERR_ARG, "face fields are NULL");
+    double* p1 = d + 5 * nc;
+    double* p2 = p1 + nz * ny * (nx + 1);
+    double* p3 = p2 + nz * (ny + 1) * nx;
+    AETH_CK(c, cudaMemcpyAsync(p1, b1, nz * ny * (nx + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    AETH_CK(c, cudaMemcpyAsync(p2, b2, nz * (ny + 1) * nx * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    AETH_CK(c, cudaMemcpyAsync(p3, b3, (nz + 1) * ny * nx * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  s = enqueue_load(c, b);
+  if (s != AETH_OK) return s;
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return AETH_OK;
+}
+
+aeth_status aeth_get_state(aeth_ctx* c, int b, double* cons, double* b1, double* b2, double* b3) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (!cons) return fail(c, AETH_ERR_ARG, "cons is NULL");
+  s = enqueue_store(c, b);
+  if (s != AETH_OK) return s;
+  const auto& B = c->blocks[b];
+  const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz, nc = nx * ny * nz;
+  double* d = c->d_stage;
+  AETH_CK(c, cudaMemcpyAsync(cons, d, 5 * nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (is_mhd(c) && b1 && b2 && b3) {
+    double* p1 = d + 5 * nc;
+    double* p2 = p1 + nz * ny * (nx + 1);
+    double* p3 = p2 + nz * (ny + 1) * nx;
+    AETH_CK(c, cudaMemcpyAsync(b1, p1, nz * ny * (nx + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    AETH_CK(c, cudaMemcpyAsync(b2, p2, nz * (ny + 1) * nx * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    AETH_CK(c, cudaMemcpyAsync(b3, p3, (nz + 1) * ny * nx * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+aeth_status aeth_set_dust(aeth_ctx* c, int b, int k, const double* rm) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (k < 0 || k >= c->cfg.n_dust || !rm) return fail(c, AETH_ERR_ARG, "bad dust species or NULL");
+  const auto& B = c->blocks[b];
+  AETH_CK(c, cudaMemcpyAsync(c->d_stage, rm, 4 * B.ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  s = enqueue_dust_load(c, b, k);
+  if (s != AETH_OK) return s;
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return AETH_OK;
+}
+
+aeth_status aeth_get_dust(aeth_ctx* c, int b, int k, double* rm) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (k < 0 || k >= c->cfg.n_dust || !rm) return fail(c, AETH_ERR_ARG, "bad dust species or NULL");
+  s = enqueue_dust_store(c, b, k);
+  if (s != AETH_OK) return s;
+  const auto& B = c->blocks[b];
+  AETH_CK(c, cudaMemcpyAsync(rm, c->d_stage, 4 * B.ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+aeth_status aeth_compute_dt(aeth_ctx* c, double* dt) {
+  if (!c || !dt) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  aeth_status s = enqueue_dt(c);
+  if (s != AETH_OK) return s;
+  AETH_CK(c, cudaMemcpyAsync(dt, c->d_dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+aeth_status aeth_step(aeth_ctx* c, double dt) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, AETH_ERR_ARG, "dt must be finite and >= 0");
+  if (dt > 0.0) {
+    aeth_status s = enqueue_set_dt(c, dt);
+    if (s != AETH_OK) return s;
+  }
+  return enqueue_step(c, false);
+}
+
+aeth_status aeth_run(aeth_ctx* c, int nsteps) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  if (nsteps < 0) return fail(c, AETH_ERR_ARG, "nsteps < 0");
+  if (nsteps == 0) return AETH_OK;
+  if (c->profile) {
+    // timed launches: no graph, events around the dominant kernel
+    for (int n = 0; n < nsteps; ++n) {
+      aeth_status s = enqueue_step(c, true);
+      if (s != AETH_OK) return s;
+    }
+    return AETH_OK;
+  }
+  if (!c->graph) {
+    // capture one CFL-driven step on a private stream, then replay it
+    cudaStream_t cap;
+    AETH_CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = cap;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    aeth_status s = AETH_OK;
+    if (e == cudaSuccess) s = enqueue_step(c, true);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    c->stream = saved;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+      return fail(c, AETH_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(e), cudaGetErrorString(e2));
+    if (s != AETH_OK) {
+      cudaGraphDestroy(g);
+      return s;
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, AETH_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  for (int n = 0; n < nsteps; ++n) AETH_CK(c, cudaGraphLaunch(c->graph, c->stream));
+  return AETH_OK;
+}
+
+aeth_status aeth_sync(aeth_ctx* c) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  AETH_CK(c, cudaGetLastError());
+  return read_status(c);
+}
+
+aeth_status aeth_diagnostics(aeth_ctx* c, aeth_diag* out) {
+  if (!c || !out) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  aeth_status s = enqueue_diag(c);
+  if (s != AETH_OK) return s;
+  double h[6];
+  unsigned long long fl = 0, fb = 0;
+  AETH_CK(c, cudaMemcpyAsync(h, c->d_diag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaMemcpyAsync(&fl, c->d_floor, sizeof fl, cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaMemcpyAsync(&fb, c->d_fallback, sizeof fb, cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaMemsetAsync(c->d_floor, 0, sizeof fl, c->stream));
+  AETH_CK(c, cudaMemsetAsync(c->d_fallback, 0, sizeof fb, c->stream));
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  out->mass = h[0];
+  out->mom[0] = h[1]; out->mom[1] = h[2]; out->mom[2] = h[3];
+  out->energy = h[4];
+  out->max_divb_rel = h[5];
+  out->floor_hits = (long long)fl;
+  out->mlp_fallbacks = (long long)fb;
+  return read_status(c);
+}
+
+aeth_status aeth_load_mlp(aeth_ctx* c, const float* params, size_t n);
+
+aeth_status aeth_profile(aeth_ctx* c, int enable) {
+  if (!c) return AETH_ERR_ARG;
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  c->profile = enable != 0;
+  c->prof_used = 0;
+  c->prof_bytes = 0;
+  c->n_launch = 0;
+  return AETH_OK;
+}
+
+aeth_status aeth_profile_read(aeth_ctx* c, double* ms, long long* n, double* bytes,
+                              long long* all) {
+  if (!c) return AETH_ERR_ARG;
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  double tot = 0;
+  for (size_t q = 0; q + 1 < c->prof_used; q += 2) {
+    float t = 0;
+    AETH_CK(c, cudaEventElapsedTime(&t, c->prof_ev[q], c->prof_ev[q + 1]));
+    tot += t;
+  }
+  if (ms) *ms = tot;
+  if (n) *n = (long long)(c->prof_used / 2);
+  if (bytes) *bytes = c->prof_bytes;
+  if (all) *all = c->n_launch;
+  return AETH_OK;
+}
+
+const char* aeth_last_error(const aeth_ctx* c) { return c ? c->err : "null context"; }
+
+void aeth_destroy(aeth_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->own_arena && c->arena) cudaFree(c->arena);
+  if (c->d_mlp) cudaFree(c->d_mlp);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

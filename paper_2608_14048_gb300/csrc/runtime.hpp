@@ -1,0 +1,149 @@
+// Host runtime of the GB300 MHD library: context, block table, device arena.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/aether_gb.h"
+#include "common.cuh"
+
+namespace aeth {
+
+// Per-block device pointers for one working precision R.
+template <typename R>
+struct BlockPtrs {
+  Layout L;
+  Geometry<R> geo;
+  R* reg[2][NVAR];     // register A (U^n / u1) and B (stage state / u2)
+  R* w[NPRIM];         // primitives (unfused path)
+  R* f[3][5];          // hydro fluxes per direction (unfused path)
+  R* e[3][2];          // face EMFs per direction: components t1, t2
+  R* edge[3];          // corner EMFs by component
+  R* dust[2];          // dust registers: [species][4] arrays each (IMEX2P)
+};
+
+struct BlockInfo {
+  aeth_block_desc desc;
+  Layout L;
+  long long ncell;        // interior cells
+  size_t off_reg[2];      // arena offsets of the two registers (8 arrays)
+  size_t off_scratch;     // unfused scratch (w, f, e, edge)
+  size_t off_geo;         // geometry tables (R)
+  size_t off_dust[2];     // dust registers (n_dust * 4 arrays each)
+  size_t geo_len;         // number of R entries in the geometry tables
+  int dt_blocks;          // CUDA blocks of this block's dt/diag reductions
+  int dt_offset;          // their first slot in the partials array
+};
+
+struct StepStats;
+
+}  // namespace aeth
+
+struct aeth_ctx {
+  aeth_config cfg;
+  std::vector<double> t_stop;
+  std::vector<aeth::BlockInfo> blocks;
+  cudaStream_t stream = nullptr;
+  bool finalized = false;
+  bool planned = false;
+  int g = 2;                 // ghost width
+  size_t elem = 8;           // sizeof working real
+  // arena
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own_arena = false;
+  size_t need = 0;
+  size_t off_stage = 0, stage_bytes = 0;   // FP64 host<->device staging
+  size_t off_partials = 0;                 // reduction partials (double)
+  int n_partials = 0;
+  size_t off_scalars = 0;                  // dt, status, counters
+  // device scalars (inside the arena)
+  double* d_dt = nullptr;        // current step
+  double* d_partials = nullptr;
+  int* d_status = nullptr;       // latched error bits
+  unsigned long long* d_floor = nullptr;
+  unsigned long long* d_fallback = nullptr;
+  double* d_diag = nullptr;      // 8 doubles
+  double* d_stage = nullptr;
+  // CUDA graph of one CFL-driven step (aeth_run)
+  cudaGraphExec_t graph = nullptr;
+  // MLP parameters (device, bf16/fp32) for the learned flux
+  void* d_mlp = nullptr;
+  size_t mlp_n = 0;
+  // kernel timing (aeth_profile)
+  bool profile = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs: start, stop
+  size_t prof_used = 0;               // events recorded so far
+  double prof_bytes = 0;              // algorithmic bytes of the timed launches
+  long long n_launch = 0;             // kernels launched (all kinds)
+  // error text
+  char err[512] = {0};
+};
+
+namespace aeth {
+
+enum : int { ST_NONFINITE = 1, ST_FLOOR = 2, ST_TIMEOUT = 4 };
+
+inline aeth_status fail(aeth_ctx* c, aeth_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->err, sizeof c->err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define AETH_CK(ctx, call)                                                   \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return ::aeth::fail((ctx), AETH_ERR_CUDA, "%s failed: %s (%s:%d)", #call, \
+                          cudaGetErrorString(e_), __FILE__, __LINE__);        \
+  } while (0)
+
+// Device pointers of block b for precision R.
+template <typename R>
+BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b);
+
+// Kernel sequences (unfused.cu / fused.cu / aux.cu).
+aeth_status enqueue_step(aeth_ctx* c, bool cfl_on_device);
+aeth_status enqueue_dt(aeth_ctx* c);
+aeth_status enqueue_diag(aeth_ctx* c);
+aeth_status enqueue_load(aeth_ctx* c, int b);
+aeth_status enqueue_store(aeth_ctx* c, int b);
+aeth_status enqueue_set_dt(aeth_ctx* c, double dt);
+aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k);
+aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k);
+aeth_status build_geometry(aeth_ctx* c);
+
+// Bracket one launch of the dominant kernel with events (aeth_profile).
+inline void prof_begin(aeth_ctx* c) {
+  if (!c->profile) return;
+  if (c->prof_used + 2 > c->prof_ev.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->prof_ev.push_back(e);
+    }
+  }
+  cudaEventRecord(c->prof_ev[c->prof_used], c->stream);
+}
+inline void prof_end(aeth_ctx* c, double algo_bytes) {
+  if (!c->profile) return;
+  cudaEventRecord(c->prof_ev[c->prof_used + 1], c->stream);
+  c->prof_used += 2;
+  c->prof_bytes += algo_bytes;
+}
+
+inline int ghost_width(int recon) { return recon == AETH_RECON_PPM ? 3 : (recon == AETH_RECON_PLM ? 2 : 1); }
+
+inline double cmax_of(int integrator) {
+  // IMEX2P: explicit Courant fraction 1/lambda, lambda = 1 + 1/sqrt(2)
+  return integrator == AETH_INT_IMEX2P ? 1.0 / (1.0 + 1.0 / 1.4142135623730951) : 1.0;
+}
+
+inline bool is_mhd(const aeth_ctx* c) { return c->cfg.eos == AETH_EOS_ADIABATIC_MHD; }
+
+}  // namespace aeth

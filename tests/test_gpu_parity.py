@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle,
+element by element, on seeded inputs with the oracle's dt sequence.
+
+Tolerances (relative L1 per variable):
+* FP64 path: 1e-12.  Both sides evaluate the same formulas in double; the
+  GPU contracts multiply-adds and multiplies separable geometry factors, so
+  results differ by a few ulps per operation, compounded over the steps.
+* FP32 paths: 1e-5, the bound stated for FP32 steps against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_14048_gb300 import aether as A
+from paper_2608_14048_gb300 import inputs as I
+from tests.gpu_helpers import compare, gpu_run, oracle_run, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def _state(n=(20, 18, 13), seed=3, mhd=True, **kw):
+    return I.smooth_random_mhd(I.Block(n), seed, v_rms=0.8, b_rms=0.6,
+                               B0=(0.3, -0.2, 0.1) if mhd else (0, 0, 0), mhd=mhd, **kw)
+
+
+@pytest.mark.parametrize("path", [A.FUSED, A.UNFUSED])
+@pytest.mark.parametrize("recon,integ", [("plm", "vl2"), ("ppm", "vl2"), ("plm", "rk2"),
+                                         ("donor", "rk2"), ("ppm", "rk2")])
+def test_fp64_parity_random_box(recon, integ, path):
+    st = _state()
+    ref, dts = oracle_run(st, recon, integ, nsteps=5)
+    (out,), diag = gpu_run([st], dts, recon, integ, "fp64", path=path)
+    errs = compare(out, ref)
+    assert max(errs) < FP64_TOL, errs
+    assert diag["max_divb_rel"] < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_p64"])
+@pytest.mark.parametrize("recon", ["plm", "ppm"])
+def test_fp32_parity_random_box(prec, recon):
+    st = _state(seed=5)
+    ref, dts = oracle_run(st, recon, "vl2", nsteps=5)
+    (out,), _ = gpu_run([st], dts, recon, "vl2", prec)
+    errs = compare(out, ref)
+    assert max(errs) < FP32_TOL, errs
+
+
+def test_hydro_mode_parity():
+    st = _state(seed=9, mhd=False)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=5, mhd=False)
+    (out,), _ = gpu_run([st], dts, "plm", "vl2", "fp64", mhd=False)
+    errs = compare(out, ref, mhd=False)
+    assert max(errs) < FP64_TOL, errs
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sod_outflow_parity(axis):
+    st = I.riemann_1d(axis, 64, I.SOD_LEFT, I.SOD_RIGHT, 1.4, ntrans=3)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=20, mhd=False)
+    (out,), _ = gpu_run([st], dts, "plm", "vl2", "fp64", mhd=False)
+    errs = compare(out, ref, mhd=False)
+    assert max(errs[:2] + errs[3:]) < FP64_TOL or max(errs) < FP64_TOL, errs
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_brio_wu_outflow_parity(axis):
+    st = I.brio_wu(axis, 48)
+    ref, dts = oracle_run(st, "ppm", "vl2", nsteps=15)
+    (out,), _ = gpu_run([st], dts, "ppm", "vl2", "fp64")
+    errs = compare(out, ref)
+    # transverse momenta are exactly zero on both sides for some axes
+    assert all(e < FP64_TOL for e in errs if np.isfinite(e)), errs
+
+
+def test_linear_wave_32cube_parity():
+    # the 32^3 fast-wave configuration, 20 steps, FP64; compared on the
+    # perturbation q - q_background
+    st = I.linear_fast_wave(32)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=20)
+    (out,), diag = gpu_run([st], dts, "plm", "vl2", "fp64")
+    cons, b1, b2, b3 = out
+    bg = [np.mean(st.cons[v]) for v in range(5)]
+    for v in range(5):
+        e = rel_l1(cons[v] - bg[v], ref.cons[v] - bg[v])
+        assert e < 1e-9, (v, e)
+    for a, r, f0 in ((b1, ref.b1, st.b1), (b2, ref.b2, st.b2), (b3, ref.b3, st.b3)):
+        m = np.mean(f0)
+        assert rel_l1(a - m, r - m) < 1e-9
+    assert diag["max_divb_rel"] < 1e-12
+
+
+def test_compute_dt_matches_oracle():
+    import torch
+    st = _state(seed=13)
+    g = O.make_grid(st.block.n)
+    for prec, tol in (("fp64", 1e-14), ("fp32", 1e-6)):
+        p = O.make_params()
+        dt_ref = O.compute_dt(g, p, O.State(st.cons, st.b1, st.b2, st.b3))
+        cfg = A.make_config(precision={"fp64": A.FP64, "fp32": A.FP32}[prec])
+        sv = A.Solver(cfg, [A.make_block(st.block.n)], stream=torch.cuda.current_stream())
+        try:
+            sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+            dt = sv.compute_dt()
+        finally:
+            sv.close()
+        assert abs(dt - dt_ref) <= tol * dt_ref, (prec, dt, dt_ref)
+
+
+def test_device_cfl_run_matches_oracle_sequence():
+    # aeth_run computes dt on the device each step (graph replay)
+    st = _state(seed=17)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)
+    (out,), _ = gpu_run([st], dts, "plm", "vl2", "fp64", use_run=True)
+    errs = compare(out, ref)
+    assert max(errs) < 1e-11, errs
+
+
+def test_multiple_blocks_one_context():
+    sts = [_state(n=(12, 10, 9), seed=21), _state(n=(16, 8, 11), seed=22),
+           _state(n=(9, 9, 9), seed=23)]
+    refs, dts = [], None
+    r0, dts = oracle_run(sts[0], "plm", "vl2", nsteps=3)
+    refs.append(r0)
+    for s in sts[1:]:
+        r, _ = oracle_run(s, "plm", "vl2", dts=dts)
+        refs.append(r)
+    outs, _ = gpu_run(sts, dts, "plm", "vl2", "fp64")
+    for o, r in zip(outs, refs):
+        assert max(compare(o, r)) < FP64_TOL
+
+
+@pytest.mark.parametrize("n", [(1, 12, 10), (16, 1, 1), (8, 8, 1), (33, 5, 7)])
+def test_degenerate_and_ragged_shapes(n):
+    st = _state(n=n, seed=31)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=3)
+    (out,), _ = gpu_run([st], dts, "plm", "vl2", "fp64")
+    errs = compare(out, ref)
+    assert all(e < FP64_TOL for e in errs if np.isfinite(e)), errs
+
+
+def test_diagnostics_conservation_fp64():
+    import torch
+    st = _state(seed=41)
+    cfg = A.make_config(precision=A.FP64)
+    sv = A.Solver(cfg, [A.make_block(st.block.n)], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        d0 = sv.diagnostics()
+        sv.run(6)
+        d1 = sv.diagnostics()
+    finally:
+        sv.close()
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    assert abs(d1["energy"] - d0["energy"]) < 1e-13 * d0["energy"]
+    assert d1["max_divb_rel"] < 1e-12
+    assert d1["floor_hits"] == 0
+
+
+def test_errors_are_reported():
+    cfg = A.make_config()
+    cfg.gamma = 0.5
+    with pytest.raises(A.AethError):
+        A.aeth_create(cfg)
+    import torch
+    sv = A.Solver(A.make_config(), [A.make_block((8, 8, 8))], stream=torch.cuda.current_stream())
+    try:
+        with pytest.raises(A.AethError):
+            A.aeth_step(sv.ctx, float("nan"))
+        with pytest.raises(A.AethError):
+            sv.set_state(3, np.zeros((5, 8, 8, 8)))
+        # a non-finite state is latched and reported, not silently advanced
+        cons = np.ones((5, 8, 8, 8)); cons[1:4] = 0; cons[4] = 2.0
+        cons[0, 3, 3, 3] = np.nan
+        b1 = np.zeros((8, 8, 9)); b2 = np.zeros((8, 9, 8)); b3 = np.zeros((9, 8, 8))
+        sv.set_state(0, cons, b1, b2, b3)
+        with pytest.raises(A.AethError) as ei:
+            sv.compute_dt()
+        assert ei.value.code == -4
+    finally:
+        sv.close()
