@@ -35,7 +35,7 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
   if (c->cfg.n_dust > 0) {
     for (int r = 0; r < 2; ++r) P.dust[r] = (R*)(c->arena + B.off_dust[r]);
   }
-  // geometry tables: 11 separable factors x 3 axes
+  // geometry tables: 12 separable factors x 3 axes
   const R* t = (const R*)(c->arena + B.off_geo);
   const int g = B.L.g;
   long long ax[3] = {B.L.n[0] + 2 * g + 2, B.L.n[1] + 2 * g + 2, B.L.n[2] + 2 * g + 2};
@@ -60,7 +60,7 @@ template BlockPtrs<double> block_ptrs<double>(const aeth_ctx*, int);
 
 // Number of R entries in one block's geometry tables.
 size_t geometry_len(const Layout& L) {
-  return 11ull * (size_t)(L.n[0] + L.n[1] + L.n[2] + 3 * (2 * L.g + 2));
+  return 12ull * (size_t)(L.n[0] + L.n[1] + L.n[2] + 3 * (2 * L.g + 2));
 }
 
 // Exact separable factors of Sec. 2.3, computed in FP64 on the host.

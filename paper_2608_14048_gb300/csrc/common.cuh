@@ -131,124 +131,144 @@ __device__ __forceinline__ R fast_speed(R gamma, R rho, R p, R bn, R bt1, R bt2)
   return sqrt(R(0.5) * (s + sqrt(disc)));
 }
 
+// Single-star state of one side (MK05): density, transverse velocity and
+// field, total energy, from the side state and S_M, p_T*.
 template <typename R>
-struct Side {
-  R u[7];   // rho, Mn, Mt1, Mt2, E, Bt1, Bt2
-  R f[7];
-  R pt;
-};
-
-template <typename R>
-__device__ __forceinline__ void side_state(R gamma, const R* w, R bn, Side<R>& s) {
-  R rho = w[0], vn = w[1], v1 = w[2], v2 = w[3], p = w[4], b1 = w[5], b2 = w[6];
-  R bb = bn * bn + b1 * b1 + b2 * b2;
-  R pt = p + R(0.5) * bb;
-  R e = p / (gamma - R(1)) + R(0.5) * rho * (vn * vn + v1 * v1 + v2 * v2) + R(0.5) * bb;
-  R vb = vn * bn + v1 * b1 + v2 * b2;
-  s.u[0] = rho; s.u[1] = rho * vn; s.u[2] = rho * v1; s.u[3] = rho * v2;
-  s.u[4] = e; s.u[5] = b1; s.u[6] = b2;
-  s.f[0] = rho * vn;
-  s.f[1] = rho * vn * vn + pt - bn * bn;
-  s.f[2] = rho * vn * v1 - bn * b1;
-  s.f[3] = rho * vn * v2 - bn * b2;
-  s.f[4] = (e + pt) * vn - bn * vb;
-  s.f[5] = b1 * vn - bn * v1;
-  s.f[6] = b2 * vn - bn * v2;
-  s.pt = pt;
+__device__ __forceinline__ void hlld_star(R rho, R un, R v1, R v2, R b1, R b2, R e, R pt,
+                                          R sa, R sm, R pts, R bn, R& rs, R& v1s, R& v2s,
+                                          R& b1s, R& b2s, R& es) {
+  const R su = sa - un;
+  const R inv_ssm = R(1) / (sa - sm);
+  rs = rho * su * inv_ssm;
+  const R dd = rho * su * (sa - sm) - bn * bn;
+  if (fabs(dd) < Eps<R>::hlld * pts) {
+    v1s = v1; v2s = v2; b1s = b1; b2s = b2;
+  } else {
+    const R inv_dd = R(1) / dd;
+    const R fv = bn * (sm - un) * inv_dd;
+    const R fb = (rho * su * su - bn * bn) * inv_dd;
+    v1s = v1 - b1 * fv;
+    v2s = v2 - b2 * fv;
+    b1s = b1 * fb;
+    b2s = b2 * fb;
+  }
+  const R vb = un * bn + v1 * b1 + v2 * b2;
+  const R vbs = sm * bn + v1s * b1s + v2s * b2s;
+  es = (su * e - pt * un + pts * sm + bn * (vb - vbs)) * inv_ssm;
 }
 
+// HLLD flux.  Left/right states as scalars; all intermediate values stay in
+// registers (no runtime-indexed arrays).  Returns the solver region
+// 0..5 (L, *L, **L, **R, *R, R).
 template <typename R>
-__device__ void hlld(R gamma, const R* wl, const R* wr, R bn, R* flux) {
-  Side<R> L, Rt;
-  side_state(gamma, wl, bn, L);
-  side_state(gamma, wr, bn, Rt);
-  R cfl = fast_speed(gamma, wl[0], wl[4], bn, wl[5], wl[6]);
-  R cfr = fast_speed(gamma, wr[0], wr[4], bn, wr[5], wr[6]);
-  R cmax = fmax(cfl, cfr);
-  R sl = fmin(wl[1], wr[1]) - cmax;
-  R sr = fmax(wl[1], wr[1]) + cmax;
+__device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R byl, R bzl,
+                                      R rr, R ur, R vr, R wr, R pr, R byr, R bzr, R bn,
+                                      R* f) {
+  const R gm1 = gamma - R(1);
+  const R bb_l = bn * bn + byl * byl + bzl * bzl;
+  const R bb_r = bn * bn + byr * byr + bzr * bzr;
+  const R ptl = pl + R(0.5) * bb_l, ptr = pr + R(0.5) * bb_r;
+  const R el = pl / gm1 + R(0.5) * rl * (ul * ul + vl * vl + wl * wl) + R(0.5) * bb_l;
+  const R er = pr / gm1 + R(0.5) * rr * (ur * ur + vr * vr + wr * wr) + R(0.5) * bb_r;
+  // physical fluxes
+  const R vbl = ul * bn + vl * byl + wl * bzl, vbr = ur * bn + vr * byr + wr * bzr;
+  const R fl0 = rl * ul, fr0 = rr * ur;
+  const R fl1 = rl * ul * ul + ptl - bn * bn, fr1 = rr * ur * ur + ptr - bn * bn;
+  const R fl2 = rl * ul * vl - bn * byl, fr2 = rr * ur * vr - bn * byr;
+  const R fl3 = rl * ul * wl - bn * bzl, fr3 = rr * ur * wr - bn * bzr;
+  const R fl4 = (el + ptl) * ul - bn * vbl, fr4 = (er + ptr) * ur - bn * vbr;
+  const R fl5 = byl * ul - bn * vl, fr5 = byr * ur - bn * vr;
+  const R fl6 = bzl * ul - bn * wl, fr6 = bzr * ur - bn * wr;
+  // fast speeds and outer waves
+  R cfl, cfr;
+  {
+    const R a2 = gamma * pl / rl, b2 = bb_l / rl, s = a2 + b2;
+    const R disc = fmax(s * s - R(4) * a2 * bn * bn / rl, R(0));
+    cfl = sqrt(R(0.5) * (s + sqrt(disc)));
+  }
+  {
+    const R a2 = gamma * pr / rr, b2 = bb_r / rr, s = a2 + b2;
+    const R disc = fmax(s * s - R(4) * a2 * bn * bn / rr, R(0));
+    cfr = sqrt(R(0.5) * (s + sqrt(disc)));
+  }
+  const R cmax = fmax(cfl, cfr);
+  const R sl = fmin(ul, ur) - cmax;
+  const R sr = fmax(ul, ur) + cmax;
   if (sl > R(0)) {
-#pragma unroll
-    for (int q = 0; q < 7; ++q) flux[q] = L.f[q];
-    return;
+    f[0] = fl0; f[1] = fl1; f[2] = fl2; f[3] = fl3; f[4] = fl4; f[5] = fl5; f[6] = fl6;
+    return 0;
   }
   if (sr < R(0)) {
-#pragma unroll
-    for (int q = 0; q < 7; ++q) flux[q] = Rt.f[q];
-    return;
+    f[0] = fr0; f[1] = fr1; f[2] = fr2; f[3] = fr3; f[4] = fr4; f[5] = fr5; f[6] = fr6;
+    return 5;
   }
-  R sul = sl - wl[1], sur = sr - wr[1];
-  R den = sur * wr[0] - sul * wl[0];
-  R sm = (sur * wr[0] * wr[1] - sul * wl[0] * wl[1] - Rt.pt + L.pt) / den;
-  R pts = (sur * wr[0] * L.pt - sul * wl[0] * Rt.pt +
-           wl[0] * wr[0] * sur * sul * (wr[1] - wl[1])) / den;
-
-  // single-star states of both sides
-  R us[2][7], vs1[2], vs2[2];
-  R rs[2];
-#pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    const R* w = a ? wr : wl;
-    const Side<R>& S = a ? Rt : L;
-    R sa = a ? sr : sl;
-    R su = sa - w[1];
-    R rho_s = w[0] * su / (sa - sm);
-    R dd = w[0] * su * (sa - sm) - bn * bn;
-    R v1s, v2s, b1s, b2s;
-    if (fabs(dd) < Eps<R>::hlld * pts) {
-      v1s = w[2]; v2s = w[3]; b1s = w[5]; b2s = w[6];
-    } else {
-      R fv = bn * (sm - w[1]) / dd;
-      R fb = (w[0] * su * su - bn * bn) / dd;
-      v1s = w[2] - w[5] * fv;
-      v2s = w[3] - w[6] * fv;
-      b1s = w[5] * fb;
-      b2s = w[6] * fb;
-    }
-    R vb = w[1] * bn + w[2] * w[5] + w[3] * w[6];
-    R vbs = sm * bn + v1s * b1s + v2s * b2s;
-    R es = (su * S.u[4] - S.pt * w[1] + pts * sm + bn * (vb - vbs)) / (sa - sm);
-    us[a][0] = rho_s; us[a][1] = rho_s * sm; us[a][2] = rho_s * v1s;
-    us[a][3] = rho_s * v2s; us[a][4] = es; us[a][5] = b1s; us[a][6] = b2s;
-    rs[a] = rho_s; vs1[a] = v1s; vs2[a] = v2s;
-  }
-  R sql = sqrt(rs[0]), sqr = sqrt(rs[1]);
-  R abn = fabs(bn);
-  bool degen = R(0.5) * bn * bn < Eps<R>::hlld * pts;
-  R ssl = degen ? sm : sm - abn / sql;
-  R ssr = degen ? sm : sm + abn / sqr;
-
+  const R sul = sl - ul, sur = sr - ur;
+  const R inv_den = R(1) / (sur * rr - sul * rl);
+  const R sm = (sur * rr * ur - sul * rl * ul - ptr + ptl) * inv_den;
+  const R pts = (sur * rr * ptl - sul * rl * ptr + rl * rr * sur * sul * (ur - ul)) * inv_den;
+  R rsl, v1sl, v2sl, b1sl, b2sl, esl;
+  R rsr, v1sr, v2sr, b1sr, b2sr, esr;
+  hlld_star(rl, ul, vl, wl, byl, bzl, el, ptl, sl, sm, pts, bn, rsl, v1sl, v2sl, b1sl, b2sl, esl);
+  hlld_star(rr, ur, vr, wr, byr, bzr, er, ptr, sr, sm, pts, bn, rsr, v1sr, v2sr, b1sr, b2sr, esr);
+  const R sql = sqrt(rsl), sqr = sqrt(rsr);
+  const R abn = fabs(bn);
+  const bool degen = R(0.5) * bn * bn < Eps<R>::hlld * pts;
+  const R ssl = degen ? sm : sm - abn / sql;
+  const R ssr = degen ? sm : sm + abn / sqr;
   int region;
   if (ssl >= R(0)) region = 1;
   else if (sm >= R(0)) region = 2;
   else if (ssr >= R(0)) region = 3;
   else region = 4;
-
-  const int a = (region == 1 || region == 2) ? 0 : 1;
-  const Side<R>& S = a ? Rt : L;
-  const R sa = a ? sr : sl;
-  if (region == 1 || region == 4) {
-#pragma unroll
-    for (int q = 0; q < 7; ++q) flux[q] = S.f[q] + sa * (us[a][q] - S.u[q]);
-    return;
+  const bool right = region >= 3;
+  // selected side: physical flux, conserved vector, outer speed, star state
+  const R s_a = right ? sr : sl;
+  const R F0 = right ? fr0 : fl0, F1 = right ? fr1 : fl1, F2 = right ? fr2 : fl2;
+  const R F3 = right ? fr3 : fl3, F4 = right ? fr4 : fl4, F5 = right ? fr5 : fl5;
+  const R F6 = right ? fr6 : fl6;
+  const R rho = right ? rr : rl, un = right ? ur : ul, v1 = right ? vr : vl, v2 = right ? wr : wl;
+  const R u4 = right ? er : el, b1 = right ? byr : byl, b2 = right ? bzr : bzl;
+  const R rs = right ? rsr : rsl, v1s = right ? v1sr : v1sl, v2s = right ? v2sr : v2sl;
+  const R b1s = right ? b1sr : b1sl, b2s = right ? b2sr : b2sl, es = right ? esr : esl;
+  // F* = F + S (U* - U)
+  R g0 = F0 + s_a * (rs - rho);
+  R g1 = F1 + s_a * (rs * sm - rho * un);
+  R g2 = F2 + s_a * (rs * v1s - rho * v1);
+  R g3 = F3 + s_a * (rs * v2s - rho * v2);
+  R g4 = F4 + s_a * (es - u4);
+  R g5 = F5 + s_a * (b1s - b1);
+  R g6 = F6 + s_a * (b2s - b2);
+  if (region == 2 || region == 3) {
+    // double-star states: shared velocity and field, sqrt(rho*) weighted
+    const R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
+    const R inv = R(1) / (sql + sqr);
+    const R v1ss = (sql * v1sl + sqr * v1sr + (b1sr - b1sl) * sgn) * inv;
+    const R v2ss = (sql * v2sl + sqr * v2sr + (b2sr - b2sl) * sgn) * inv;
+    const R b1ss = (sql * b1sr + sqr * b1sl + sql * sqr * (v1sr - v1sl) * sgn) * inv;
+    const R b2ss = (sql * b2sr + sqr * b2sl + sql * sqr * (v2sr - v2sl) * sgn) * inv;
+    const R vbss = sm * bn + v1ss * b1ss + v2ss * b2ss;
+    const R vbs = sm * bn + v1s * b1s + v2s * b2s;
+    const R sq = right ? sqr : sql;
+    const R ess = es + (right ? R(1) : R(-1)) * sq * (vbs - vbss) * sgn;
+    const R sst = right ? ssr : ssl;
+    // F** = F* + S* (U** - U*); rho** = rho* and u** = S_M, so the mass
+    // and normal-momentum entries of U** - U* vanish
+    g2 += sst * (rs * v1ss - rs * v1s);
+    g3 += sst * (rs * v2ss - rs * v2s);
+    g4 += sst * (ess - es);
+    g5 += sst * (b1ss - b1s);
+    g6 += sst * (b2ss - b2s);
   }
-  R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
-  R inv = R(1) / (sql + sqr);
-  R b1l = us[0][5], b2l = us[0][6], b1r = us[1][5], b2r = us[1][6];
-  R v1ss = (sql * vs1[0] + sqr * vs1[1] + (b1r - b1l) * sgn) * inv;
-  R v2ss = (sql * vs2[0] + sqr * vs2[1] + (b2r - b2l) * sgn) * inv;
-  R b1ss = (sql * b1r + sqr * b1l + sql * sqr * (vs1[1] - vs1[0]) * sgn) * inv;
-  R b2ss = (sql * b2r + sqr * b2l + sql * sqr * (vs2[1] - vs2[0]) * sgn) * inv;
-  R vbss = sm * bn + v1ss * b1ss + v2ss * b2ss;
-  R sq = a ? sqr : sql;
-  R vbs = sm * bn + vs1[a] * us[a][5] + vs2[a] * us[a][6];
-  R side_sign = a ? R(1) : R(-1);
-  R ess = us[a][4] + side_sign * sq * (vbs - vbss) * sgn;
-  R uss[7] = {rs[a], rs[a] * sm, rs[a] * v1ss, rs[a] * v2ss, ess, b1ss, b2ss};
-  R sst = a ? ssr : ssl;
-#pragma unroll
-  for (int q = 0; q < 7; ++q)
-    flux[q] = S.f[q] + sa * (us[a][q] - S.u[q]) + sst * (uss[q] - us[a][q]);
+  f[0] = g0; f[1] = g1; f[2] = g2; f[3] = g3; f[4] = g4; f[5] = g5; f[6] = g6;
+  return region;
+}
+
+// Array form: W = (rho, vn, vt1, vt2, p, Bt1, Bt2), flux (rho, Mn, Mt1, Mt2,
+// E, Bt1, Bt2).
+template <typename R>
+__device__ __forceinline__ int hlld(R gamma, const R* wl, const R* wr, R bn, R* flux) {
+  return hlld_s(gamma, wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6], wr[0], wr[1], wr[2],
+                wr[3], wr[4], wr[5], wr[6], bn, flux);
 }
 
 // Upwind selection of Gardiner & Stone (2005): lower-index value for a

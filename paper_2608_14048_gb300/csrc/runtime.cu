@@ -147,7 +147,6 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
   size_t off = 0;
   size_t max_stage = 0;
   int npart = 0;
-  const bool unfused = !(c->cfg.path == AETH_PATH_FUSED && fused_supported(c));
   for (auto& B : c->blocks) {
     const long long sz = B.L.size();
     const size_t arr = align256((size_t)sz * c->elem);
@@ -155,12 +154,10 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
       B.off_reg[r] = off;
       off += NVAR * arr;
     }
-    if (unfused || c->cfg.n_dust > 0) {
-      B.off_scratch = off;
-      off += (NPRIM + 15 + 6 + 3) * arr;
-    } else {
-      B.off_scratch = (size_t)-1;
-    }
+    // stage scratch: primitives (unfused) or reference EMFs (fused) in the
+    // first slots, then face fluxes, face EMFs and corner EMFs
+    B.off_scratch = off;
+    off += (NPRIM + 15 + 6 + 3) * arr;
     if (c->cfg.n_dust > 0) {
       for (int r = 0; r < 2; ++r) {
         B.off_dust[r] = off;

@@ -202,7 +202,11 @@ __global__ void k_update(Layout L, Geometry<R> geo, UpdArgs<R> A, int mhd) {
     const R Af = geo.area[d](i, j, k);
     R base = A.w0 * A.a[5 + d][c];
     if (A.w1 != R(0)) base += A.w1 * A.b[5 + d][c];
-    A.out[5 + d][c] = base - bdt * circ / Af;
+    const R nb = base - bdt * circ / Af;
+    A.out[5 + d][c] = nb;
+    // periodic axis: face n is the image of face 0; keep it current so
+    // every reader (CFL, diagnostics) sees a consistent field
+    if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0) A.out[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
   }
 }
 
