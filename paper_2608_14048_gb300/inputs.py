@@ -118,7 +118,8 @@ def face_field_from_potential(b: Block, A, B0=(0.0, 0.0, 0.0)):
     b1 = (I3[:, 1:, :] - I3[:, :-1, :] - (I2[1:, :, :] - I2[:-1, :, :])) / a1
     b2 = (I1[1:, :, :] - I1[:-1, :, :] - (I3[:, :, 1:] - I3[:, :, :-1])) / a2
     b3 = (I2[:, :, 1:] - I2[:, :, :-1] - (I1[:, 1:, :] - I1[:, :-1, :])) / a3
-    return b1 + B0[0], b2 + B0[1], b3 + B0[2]
+    return (np.ascontiguousarray(b1 + B0[0]), np.ascontiguousarray(b2 + B0[1]),
+            np.ascontiguousarray(b3 + B0[2]))
 
 
 def _assemble(b: Block, gamma, rho, v, p, b1, b2, b3, meta=None) -> InitialState:
