@@ -18,7 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaether_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# FP32 division and square root use the hardware approximations (max 2 ulp);
+# FP64 arithmetic is unaffected by these two flags.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+              "-prec-div=false", "-prec-sqrt=false",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")] + ARCH
 
 

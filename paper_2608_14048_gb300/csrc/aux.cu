@@ -339,14 +339,14 @@ __global__ void __launch_bounds__(256) k_dt(Layout L, Geometry<R> geo, Arr8<R> a
                                             double* __restrict__ partial, int* status) {
   __shared__ double sm[8];
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const long long nc = (long long)nx * ny * nz;
+  const int rows = ny * nz;
   double m = INFINITY;
   bool bad = false;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % nx);
-    const int j = (int)((t / nx) % ny);
-    const int k = (int)(t / ((long long)nx * ny));
+  // one x-row per block iteration, threads along x (coalesced, 32-bit
+  // index arithmetic)
+  for (int r = blockIdx.x; r < rows; r += gridDim.x)
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const int j = r % ny, k = r / ny;
     const long long c = L.idx(i, j, k);
     R rho = a.p[0][c];
     if (!(rho >= (R)rho_floor)) { if (!(rho == rho)) bad = true; rho = (R)rho_floor; }
@@ -456,13 +456,11 @@ __global__ void __launch_bounds__(256) k_diag(Layout L, Geometry<R> geo, Arr8<R>
                                               double* __restrict__ partial) {
   __shared__ double sm[6][8];
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const long long nc = (long long)nx * ny * nz;
+  const int rows = ny * nz;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % nx);
-    const int j = (int)((t / nx) % ny);
-    const int k = (int)(t / ((long long)nx * ny));
+  for (int r = blockIdx.x; r < rows; r += gridDim.x)
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const int j = r % ny, k = r / ny;
     const long long c = L.idx(i, j, k);
     const double V = (double)geo.vol(i, j, k);
     for (int v = 0; v < 5; ++v) acc[v] += (double)a.p[v][c] * V;
@@ -497,14 +495,25 @@ __global__ void __launch_bounds__(256) k_diag(Layout L, Geometry<R> geo, Arr8<R>
 }
 
 __global__ void k_diag_final(const double* __restrict__ partial, int n, double* out) {
-  // single thread, fixed order: deterministic totals
-  if (threadIdx.x != 0) return;
+  // fixed assignment of partials to threads and a fixed reduction tree:
+  // deterministic totals
+  __shared__ double sm[6][256];
   double s[6] = {0, 0, 0, 0, 0, 0};
-  for (int t = 0; t < n; ++t) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
     for (int q = 0; q < 5; ++q) s[q] += partial[6 * t + q];
     s[5] = fmax(s[5], partial[6 * t + 5]);
   }
-  for (int q = 0; q < 6; ++q) out[q] = s[q];
+  for (int q = 0; q < 6; ++q) sm[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      for (int q = 0; q < 5; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + w];
+      sm[5][threadIdx.x] = fmax(sm[5][threadIdx.x], sm[5][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 6; ++q) out[q] = sm[q][0];
 }
 
 template <typename R>
@@ -517,7 +526,7 @@ static aeth_status diag_T(aeth_ctx* c) {
     k_diag<R><<<B.dt_blocks, 256, 0, c->stream>>>(P.L, P.geo, a, is_mhd(c),
                                                    c->d_partials + 6 * B.dt_offset);
   }
-  k_diag_final<<<1, 32, 0, c->stream>>>(c->d_partials, c->n_partials, c->d_diag);
+  k_diag_final<<<1, 256, 0, c->stream>>>(c->d_partials, c->n_partials, c->d_diag);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }

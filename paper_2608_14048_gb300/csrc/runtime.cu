@@ -171,8 +171,9 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
     size_t st = (size_t)(5 * nx * ny * nz + nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx);
     if (c->cfg.n_dust > 0) st = std::max(st, (size_t)(4 * nx * ny * nz));
     max_stage = std::max(max_stage, st * sizeof(double));
-    long long want = (B.ncell + 255) / 256;
-    B.dt_blocks = (int)std::max(1ll, std::min(want, 2048ll));
+    // reductions: one CUDA block per x-row, at most 2048 blocks per mesh block
+    long long rows = (long long)B.desc.ny * B.desc.nz;
+    B.dt_blocks = (int)std::max(1ll, std::min(rows, 2048ll));
     B.dt_offset = npart;
     npart += B.dt_blocks;
   }
