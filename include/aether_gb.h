@@ -194,6 +194,30 @@ aeth_status aeth_profile_read(aeth_ctx* ctx, double* total_ms,
                               long long* launches, double* algo_bytes,
                               long long* all_launches);
 
+/* Allocation-free CFL step (the paper has no counterpart: it is a service
+ * for callers that may not allocate device memory, e.g. code running inside
+ * another framework's caching allocator or a host callback, or under a
+ * budget that forbids cudaMalloc after start-up).  Computes the dt of
+ * Eq. 11 for ONE Cartesian block whose FP64 state the caller already holds
+ * on the device in the host-array layout above (cons[5][nz][ny][nx],
+ * b1/b2/b3 face arrays; b* ignored and may be NULL when mhd = 0), with cell
+ * widths dx1, dx2, dx3 and Cmax = 1, and writes it to the device double
+ * *d_dt on `cuda_stream` (NULL = legacy default stream).  Asynchronous.
+ * Allocates nothing: its reduction scratch is a fixed static device array
+ * of one double per x-row, so ny * nz must be <= 262144 (2 MiB; every GPU
+ * that loads the library keeps it until exit); larger grids are rejected
+ * with AETH_ERR_ARG.  A non-finite state makes *d_dt NaN.  The first call
+ * on each device looks up that device's scratch address and should happen
+ * before any stream capture.  All calls share the scratch: calls that
+ * overlap on the GPU race; serialise them.  Returns AETH_ERR_ARG for bad
+ * sizes or pointers, AETH_ERR_CUDA if a launch fails. */
+aeth_status aeth_cfl_dt_noalloc(const double* d_cons, const double* d_b1,
+                                const double* d_b2, const double* d_b3,
+                                int nx, int ny, int nz, double dx1,
+                                double dx2, double dx3, double gamma,
+                                double rho_floor, double p_floor, double cfl,
+                                int mhd, double* d_dt, void* cuda_stream);
+
 /* Reason for the last failure on ctx (static storage inside ctx). */
 const char* aeth_last_error(const aeth_ctx* ctx);
 

@@ -36,8 +36,8 @@ FUSED, UNFUSED = 0, 1
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
            "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
-           "aeth_load_mlp", "aeth_profile", "aeth_profile_read", "aeth_last_error",
-           "aeth_destroy"]
+           "aeth_load_mlp", "aeth_profile", "aeth_profile_read", "aeth_cfl_dt_noalloc",
+           "aeth_last_error", "aeth_destroy"]
 
 
 class AethError(RuntimeError):
@@ -100,6 +100,9 @@ def load_library(path: str = LIB_PATH):
         "aeth_profile": ([P, C.c_int], C.c_int),
         "aeth_profile_read": ([P, dp, C.POINTER(C.c_longlong), dp, C.POINTER(C.c_longlong)],
                               C.c_int),
+        "aeth_cfl_dt_noalloc": ([P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_int, P, P], C.c_int),
         "aeth_last_error": ([P], C.c_char_p),
         "aeth_destroy": ([P], None),
     }
@@ -219,6 +222,19 @@ def aeth_profile_read(ctx):
     _check(ctx, load_library().aeth_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(b),
                                                  C.byref(al)))
     return ms.value, n.value, b.value, al.value
+
+
+def aeth_cfl_dt_noalloc(d_cons, d_b1, d_b2, d_b3, n, dx, gamma, rho_floor, p_floor, cfl, mhd,
+                        d_dt, stream_ptr=0):
+    """Allocation-free CFL step of one Cartesian block: all pointers are
+    device addresses (ints) the caller owns; the result lands in d_dt."""
+    nx, ny, nz = n
+    rc = load_library().aeth_cfl_dt_noalloc(
+        C.c_void_p(d_cons), C.c_void_p(d_b1), C.c_void_p(d_b2), C.c_void_p(d_b3), nx, ny, nz,
+        float(dx[0]), float(dx[1]), float(dx[2]), float(gamma), float(rho_floor), float(p_floor),
+        float(cfl), 1 if mhd else 0, C.c_void_p(d_dt), C.c_void_p(stream_ptr))
+    if rc != AETH_OK:
+        raise AethError(rc, "aeth_cfl_dt_noalloc")
 
 
 def aeth_last_error(ctx) -> str:
