@@ -215,3 +215,37 @@ def run(grid: Grid, params: Params, s: State, nsteps: int = None, t_end: float =
         t += dt
         k += 1
     return used
+
+
+# ---- multifluid dust (dust.c) ------------------------------------------
+
+def make_dust_params(t_stop, rho_floor_dust=1e-20, gas_accel=(0.0, 0.0, 0.0)):
+    ts = np.ascontiguousarray(t_stop, dtype=np.float64)
+    dp = DustParams(len(ts), _dp(ts), rho_floor_dust, (C.c_double * 3)(*gas_accel))
+    dp._keep = ts
+    return dp
+
+
+def drag_solve(h, rho_g, v_g, rho_d, v_d, t_stop):
+    """One implicit drag solve of one velocity component; returns (v_g', v_d')."""
+    rd = np.ascontiguousarray(rho_d, dtype=np.float64)
+    vd = np.array(v_d, dtype=np.float64)
+    ts = np.ascontiguousarray(t_stop, dtype=np.float64)
+    vg = C.c_double(v_g)
+    lib().orc_drag_solve(len(rd), float(h), float(rho_g), _dp(rd), _dp(ts), C.byref(vg), _dp(vd))
+    return vg.value, vd
+
+
+def dust_step(grid, params, dparams, dt, cons, dust) -> int:
+    """One IMEX2P step of gas (hydro) + dust, in place on the numpy arrays
+    cons[5][nz][ny][nx] and dust[nd][4][nz][ny][nx]."""
+    hits = C.c_long(0)
+    rc = lib().orc_dust_step(C.byref(grid), C.byref(params), C.byref(dparams), float(dt),
+                             _dp(cons), _dp(dust), C.byref(hits))
+    if rc != 0:
+        raise RuntimeError(f"orc_dust_step failed: {rc}")
+    return hits.value
+
+
+def dust_dt(grid, params, dparams, cons, dust) -> float:
+    return lib().orc_dust_dt(C.byref(grid), C.byref(params), C.byref(dparams), _dp(cons), _dp(dust))

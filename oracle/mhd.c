@@ -797,3 +797,18 @@ void orc_mhd_diag(const orc_grid* g, const orc_params* p, const double* cons,
       }
   out->max_divb_rel = rel;
 }
+
+/* ------------------------------------------------------------------ */
+/* L(U) for other integrators (dust.c): the stage above with zero base   */
+/* weights and beta*dt = 1 returns exactly the right-hand side of Eq. 8  */
+/* (flux divergence plus curvilinear sources) in `out`.                  */
+/* ------------------------------------------------------------------ */
+long orc_rhs(const Mesh* m, const orc_params* p, int recon, double** u, double** b,
+             double** out_u, double** out_b) {
+  Work wk;
+  if (work_alloc(&wk, m) != 0) return -1;
+  long hits = stage(m, p, recon, &wk, u, b, 0.0, u, b, 0.0, NULL, NULL, 1.0, 1.0, out_u,
+                    out_b);
+  work_free(&wk);
+  return hits;
+}

@@ -33,4 +33,9 @@ void orc_load(const Mesh* m, const double* cons, const double* b1,
 void orc_store(const Mesh* m, double** u, int nu, double** b, double* cons,
                double* b1, double* b2, double* b3);
 
+
+
+/* L(U) of Eq. 8 (gas, hydro or MHD) on the interior; see mhd.c. */
+long orc_rhs(const Mesh* m, const orc_params* p, int recon, double** u, double** b,
+             double** out_u, double** out_b);
 #endif
