@@ -34,6 +34,7 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
   }
   if (c->cfg.n_dust > 0) {
     for (int r = 0; r < 2; ++r) P.dust[r] = (R*)(c->arena + B.off_dust[r]);
+    P.dflux = (R*)(c->arena + B.off_dflux);
   }
   // geometry tables: 12 separable factors x 3 axes
   const R* t = (const R*)(c->arena + B.off_geo);

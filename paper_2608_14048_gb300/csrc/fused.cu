@@ -444,3 +444,25 @@ template aeth_status step_fused<float, true>(aeth_ctx*);
 template aeth_status step_fused<double, false>(aeth_ctx*);
 
 }  // namespace aeth
+
+namespace aeth {
+// Hydro-gas flux pass for other integrators (dust runs): the same fused
+// prim + reconstruction + HLLD sweep, writing the stage's face fluxes.
+template <typename R, bool P64>
+void hydro_flux_pass(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src) {
+  FluxOut<R> o{};
+  for (int d = 0; d < 3; ++d) {
+    for (int v = 0; v < 5; ++v) o.f[d][v] = P.f[d][v];
+    o.e[d][0] = P.e[d][0];
+    o.e[d][1] = P.e[d][1];
+    o.eref[d] = P.w[d];
+  }
+  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, false>(c, P, src, o);
+  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, false>(c, P, src, o);
+  else launch_flux3<R, P64, 2, false>(c, P, src, o);
+  c->n_launch += 1;
+}
+template void hydro_flux_pass<float, false>(aeth_ctx*, const BlockPtrs<float>&, int, int);
+template void hydro_flux_pass<float, true>(aeth_ctx*, const BlockPtrs<float>&, int, int);
+template void hydro_flux_pass<double, false>(aeth_ctx*, const BlockPtrs<double>&, int, int);
+}  // namespace aeth

@@ -118,6 +118,8 @@ aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
   for (int q = 0; q < 3; ++q)
     if (d->bc[q] == AETH_BC_PERIODIC && nn[q] < g && nn[q] != 1)
       return fail(c, AETH_ERR_ARG, "periodic axis %d needs n >= ghost width %d (or n == 1)", q, g);
+  if (d->coord == AETH_COORD_SPH && c->cfg.n_dust > 0)
+    return fail(c, AETH_ERR_UNSUPPORTED, "dust runs support Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH) {
     if (!(d->x1min - g * (d->x1max - d->x1min) / d->nx > 0.0))
       return fail(c, AETH_ERR_ARG, "spherical block: r (incl. ghosts) must stay > 0");
@@ -163,6 +165,8 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
         B.off_dust[r] = off;
         off += align256((size_t)4 * c->cfg.n_dust * sz * c->elem);
       }
+      B.off_dflux = off;
+      off += align256((size_t)12 * c->cfg.n_dust * sz * c->elem);
     }
     B.geo_len = geometry_len(B.L);
     B.off_geo = off;

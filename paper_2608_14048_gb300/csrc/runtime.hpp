@@ -23,6 +23,7 @@ struct BlockPtrs {
   R* e[3][2];          // face EMFs per direction: components t1, t2
   R* edge[3];          // corner EMFs by component
   R* dust[2];          // dust registers: [species][4] arrays each (IMEX2P)
+  R* dflux;            // dust fluxes: [direction][species][4] arrays
 };
 
 struct BlockInfo {
@@ -33,6 +34,7 @@ struct BlockInfo {
   size_t off_scratch;     // unfused scratch (w, f, e, edge)
   size_t off_geo;         // geometry tables (R)
   size_t off_dust[2];     // dust registers (n_dust * 4 arrays each)
+  size_t off_dflux;       // dust face fluxes [3][n_dust][4] arrays
   size_t geo_len;         // number of R entries in the geometry tables
   int dt_blocks;          // CUDA blocks of this block's dt/diag reductions
   int dt_offset;          // their first slot in the partials array

@@ -404,3 +404,46 @@ def brio_wu(axis: int, n: int) -> InitialState:
     left = {"rho": 1.0, "v": (0, 0, 0), "p": 1.0, "B": bl}
     right = {"rho": 0.125, "v": (0, 0, 0), "p": 0.1, "B": br}
     return riemann_1d(axis, n, left, right, 2.0)
+
+
+# ---------------------------------------------------------------------------
+# multifluid dust box (128^3 configuration and its smaller parity cases)
+# ---------------------------------------------------------------------------
+
+def dust_stopping_times(nd=8, lo=1e-4, hi=1.0):
+    """Stopping times log-spaced from lo to hi (units of L / c_s = 1)."""
+    return list(np.logspace(math.log10(lo), math.log10(hi), nd))
+
+
+def dust_box(block: Block, seed: int, nd=8, gamma=5.0 / 3.0, v_rms=0.5, dv_rms=0.1,
+             t_stop=None, eps_range=(-3.0, 0.0)):
+    """Hydro gas rho = 1, P = 1/gamma (c_s = 1), low-k random velocity of rms
+    v_rms; nd pressureless species with dust-to-gas ratios 10^U(eps_range)
+    and velocities v_g + dv_k (independent low-k fields of rms dv_rms).
+    Returns (gas InitialState, dust[nd][4][nz][ny][nx], t_stop)."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = _cell_mesh(block)
+    nrm = lambda x, d: (x - block.lo[d]) / (block.hi[d] - block.lo[d])
+    S = (nrm(X, 0), nrm(Y, 1), nrm(Z, 2))
+
+    def field(rms):
+        comp = [_eval_modes(_random_modes(rng, 2, 6), *S) for _ in range(3)]
+        r = math.sqrt(float(np.mean(comp[0] ** 2 + comp[1] ** 2 + comp[2] ** 2))) or 1.0
+        return [q * (rms / r) for q in comp]
+
+    vg = field(v_rms)
+    shape = X.shape
+    rho = np.ones(shape)
+    p = np.full(shape, 1.0 / gamma)
+    nx, ny, nz = block.n
+    z = (np.zeros((nz, ny, nx + 1)), np.zeros((nz, ny + 1, nx)), np.zeros((nz + 1, ny, nx)))
+    gas = _assemble(block, gamma, rho, vg, p, *z, {"seed": seed})
+    eps = 10.0 ** rng.uniform(eps_range[0], eps_range[1], size=nd)
+    dust = np.zeros((nd, 4) + shape)
+    for k in range(nd):
+        dv = field(dv_rms)
+        dust[k, 0] = eps[k] * rho
+        for q in range(3):
+            dust[k, 1 + q] = dust[k, 0] * (vg[q] + dv[q])
+    ts = list(t_stop) if t_stop is not None else dust_stopping_times(nd)
+    return gas, np.ascontiguousarray(dust), ts
