@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="turb256", choices=WORKLOADS)
     return ap.parse_args()
 
 
@@ -55,7 +56,28 @@ def dist_env():
     return ws, rank, local
 
 
+WORKLOADS = ("turb256", "batched512", "dust128", "wave32")
+
+
 def workload_config(a):
+    if a.workload == "batched512":
+        return {"workload": "batched_512_uneven_mhd_boxes", "blocks": 512,
+                "sides": [16, 24, 32, 48, 64], "spherical_every": 3, "recon": a.recon.upper(),
+                "riemann": "HLLD", "ct": "upwind corner EMF (GS05)", "integrator": "VL2",
+                "cfl": 0.3, "gamma": 5.0 / 3.0, "precision": a.prec, "path": a.path,
+                "seed": 20260818, "launch": "one launch per pass over all blocks",
+                "l2": "inputs larger than L2 (2.5e7 cells x 8 vars x 2 registers)"}
+    if a.workload == "dust128":
+        return {"workload": "multifluid_dust_128^3_8_species", "grid": [128, 128, 128],
+                "species": 8, "t_stop": "log-spaced 1e-4..1", "integrator": "IMEX2P",
+                "recon": a.recon.upper(), "gas": "adiabatic hydro gamma 5/3, HLLD (=HLLC)",
+                "drag": "closed-form arrowhead, FP64", "precision": a.prec, "seed": 20260817,
+                "l2": "inputs larger than L2 (128^3 x 37 vars x 2 registers)"}
+    if a.workload == "wave32":
+        return {"workload": "linear_fast_wave_32^3", "grid": [32, 32, 32], "recon": "PLM",
+                "riemann": "HLLD", "integrator": "VL2", "cfl": 0.3, "precision": a.prec,
+                "amplitude": 1e-6,
+                "l2": "inputs smaller than L2; L2 is flushed between timed steps"}
     return {"workload": f"mhd_decaying_turbulence_{a.n}^3", "grid": [a.n, a.n, a.n],
             "recon": a.recon.upper(), "riemann": "HLLD", "ct": "upwind corner EMF (GS05)",
             "integrator": "VL2", "cfl": 0.3, "gamma": 1.0001, "mach_rms": 2.0, "beta": 1.0,
@@ -206,18 +228,54 @@ def main():
 
     # CPU baseline first (rank 0, N = 1), before the GPU work starts
     base = None
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload == "turb256":
         base = cpu_baseline(a, None)
 
-    st = make_input(a)
     prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]
-    cfg = A.make_config(gamma=st.gamma, recon=A.PLM if a.recon == "plm" else A.PPM,
-                        integrator=A.VL2, cfl=0.3, precision=prec,
-                        path=A.FUSED if a.path == "fused" else A.UNFUSED)
+    rec = A.PLM if a.recon == "plm" else A.PPM
+    path = A.FUSED if a.path == "fused" else A.UNFUSED
+    dust = None
+    if a.workload == "batched512":
+        from paper_2608_14048_gb300 import inputs as I
+        states = I.batched_boxes(512, 20260818, gl=2, workers=min(16, os.cpu_count() or 1))
+        cfg = A.make_config(gamma=5.0 / 3.0, recon=rec, integrator=A.VL2, cfl=0.3,
+                            precision=prec, path=path)
+    elif a.workload == "dust128":
+        from paper_2608_14048_gb300 import inputs as I
+        gas, dust, ts = I.dust_box(I.Block((128, 128, 128)), 20260817, nd=8)
+        states = [gas]
+        cfg = A.make_config(gamma=gas.gamma, recon=rec, integrator=A.IMEX2P, cfl=0.3,
+                            precision=prec, mhd=False, t_stop=ts)
+    elif a.workload == "wave32":
+        from paper_2608_14048_gb300 import inputs as I
+        states = [I.linear_fast_wave(32)]
+        cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
+                            precision=prec, path=path)
+    else:
+        states = [make_input(a)]
+        cfg = A.make_config(gamma=states[0].gamma, recon=rec, integrator=A.VL2, cfl=0.3,
+                            precision=prec, path=path)
+    blocks = [A.make_block(s_.block.n, s_.block.lo, s_.block.hi, s_.block.coord, s_.block.bc)
+              for s_ in states]
     stream = torch.cuda.current_stream(dev)
-    sv = A.Solver(cfg, [A.make_block((a.n, a.n, a.n))], stream=stream)
-    sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
-    cells = a.n ** 3
+    sv = A.Solver(cfg, blocks, stream=stream)
+    mhd_run = a.workload != "dust128"
+
+    def upload(host=None):
+        for q, s_ in enumerate(states):
+            if host is None:
+                sv.set_state(q, s_.cons, s_.b1, s_.b2, s_.b3)
+            else:
+                A.aeth_set_state(sv.ctx, q, *host[q])
+        if dust is not None:
+            for k in range(dust.shape[0]):
+                A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]))
+
+    upload()
+    cells = sum(int(np.prod(s_.block.n)) for s_ in states)
+    flush = None
+    if a.workload == "wave32":
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     for _ in range(a.warmup):
         sv.run(1)
@@ -231,13 +289,25 @@ def main():
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sv.run(a.steps)
-    e1.record(stream)
+    if flush is None:
+        e0.record(stream)
+        sv.run(a.steps)
+        e1.record(stream)
+    else:
+        # small working set: flush L2 before every timed step and time the
+        # steps only (events around each step)
+        ms_acc = 0.0
+        for _ in range(a.steps):
+            flush.zero_()
+            e0.record(stream)
+            sv.run(1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_acc += e0.elapsed_time(e1)
     torch.cuda.synchronize(dev)
     if ws > 1:
         torch.distributed.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = e0.elapsed_time(e1) if flush is None else ms_acc
     clocks = clk.stop()
     kms, klaunch, kbytes, all_launches = A.aeth_profile_read(sv.ctx)
     A.aeth_profile(sv.ctx, False)
@@ -254,25 +324,37 @@ def main():
     # end to end through the public API with host buffers: every step copies
     # the state in from pinned host memory and reads it back
     ke = a.e2e_steps or min(a.steps, 10)
-    shp = sv.shapes(0)
-    hin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (st.cons, st.b1, st.b2, st.b3)]
-    hout = [torch.empty(s, dtype=torch.float64).pin_memory() for s in shp]
-    h2d = sum(x.numel() * 8 for x in hin)
-    d2h = sum(x.numel() * 8 for x in hout)
+    hin = [[torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+            for x in (s_.cons, s_.b1, s_.b2, s_.b3)] for s_ in states]
+    hout = [[torch.empty(shp, dtype=torch.float64).pin_memory() for shp in sv.shapes(q)]
+            for q in range(len(states))]
+    if not mhd_run:
+        hin = [[h[0], None, None, None] for h in hin]
+        hout = [[h[0], None, None, None] for h in hout]
+    nbytes = lambda lst: sum(x.numel() * 8 for h in lst for x in h if x is not None)
+    h2d, d2h = nbytes(hin), nbytes(hout)
+    if dust is not None:
+        h2d += dust.nbytes
+        d2h += dust.nbytes
+        dbuf = [np.empty(dust.shape[1:]) for _ in range(dust.shape[0])]
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(ke):
-        A.aeth_set_state(sv.ctx, 0, *hin)
+        upload(hin)
         sv.run(1)
-        A.aeth_get_state(sv.ctx, 0, *hout)
+        for q in range(len(states)):
+            A.aeth_get_state(sv.ctx, q, *hout[q])
+        if dust is not None:
+            for k in range(dust.shape[0]):
+                A.aeth_get_dust(sv.ctx, 0, k, dbuf[k])
     e2e_s = time.perf_counter() - t0
     e2e_val = cells * ke * ws / e2e_s
     sv.close()
 
     hbm, peak_kind = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None
-    kernel_key = f"{a.path}_{a.prec}_{a.recon}"
-    traffic = ncu_traffic(kernel_key)
+    kernel_key = f"{a.path}_{a.prec}_{a.recon}" if a.workload == "turb256" else None
+    traffic = ncu_traffic(kernel_key) if kernel_key else None
     launches_per_step = klaunch / max(a.steps, 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
@@ -287,8 +369,8 @@ def main():
                      "algo_bytes_per_launch": kbytes / max(klaunch, 1),
                      "kernel_ms_per_launch": kms / max(klaunch, 1),
                      "kernel_share_of_step": (kms / ms) if ms > 0 else None,
-                     "cell_rate_hbm_frac": value / ws * 160.0 / (hbm * 1e9)
-                     if a.prec != "fp64" else value / ws * 320.0 / (hbm * 1e9)},
+                     "cell_rate_hbm_frac": value / ws * (160.0 if a.prec != "fp64" else 320.0)
+                     / (hbm * 1e9) if mhd_run else value / ws * 740.0 / (hbm * 1e9)},
         "cpu_baseline": base,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": ke},

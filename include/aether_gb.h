@@ -194,6 +194,14 @@ aeth_status aeth_profile_read(aeth_ctx* ctx, double* total_ms,
                               long long* launches, double* algo_bytes,
                               long long* all_launches);
 
+/* Autotuner of the flux pass's tile shape (no counterpart in the paper):
+ * times the fused flux pass for z-chunks of 8, 16, 32 and 64 planes per
+ * tile on the current state and keeps the fastest (written to *kchunk, may
+ * be NULL).  NOTE: it ADVANCES the state by 12 steps with the current
+ * device dt; call it on a scratch copy or before loading the real state.
+ * Until called, the chunk is the largest that gives every SM >= 4 tiles. */
+aeth_status aeth_autotune(aeth_ctx* ctx, int* kchunk);
+
 /* Allocation-free CFL step (the paper has no counterpart: it is a service
  * for callers that may not allocate device memory, e.g. code running inside
  * another framework's caching allocator or a host callback, or under a

@@ -36,7 +36,8 @@ FUSED, UNFUSED = 0, 1
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
            "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
-           "aeth_load_mlp", "aeth_profile", "aeth_profile_read", "aeth_cfl_dt_noalloc",
+           "aeth_load_mlp", "aeth_profile", "aeth_profile_read", "aeth_autotune",
+           "aeth_cfl_dt_noalloc",
            "aeth_last_error", "aeth_destroy"]
 
 
@@ -100,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "aeth_profile": ([P, C.c_int], C.c_int),
         "aeth_profile_read": ([P, dp, C.POINTER(C.c_longlong), dp, C.POINTER(C.c_longlong)],
                               C.c_int),
+        "aeth_autotune": ([P, C.POINTER(C.c_int)], C.c_int),
         "aeth_cfl_dt_noalloc": ([P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_int, P, P], C.c_int),
@@ -222,6 +224,14 @@ def aeth_profile_read(ctx):
     _check(ctx, load_library().aeth_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(b),
                                                  C.byref(al)))
     return ms.value, n.value, b.value, al.value
+
+
+def aeth_autotune(ctx) -> int:
+    """Time the flux pass's z-chunk candidates on the current state (which
+    it advances) and keep the fastest; returns the chosen chunk."""
+    kc = C.c_int(0)
+    _check(ctx, load_library().aeth_autotune(ctx, C.byref(kc)))
+    return kc.value
 
 
 def aeth_cfl_dt_noalloc(d_cons, d_b1, d_b2, d_b3, n, dx, gamma, rho_floor, p_floor, cfl, mhd,

@@ -18,6 +18,7 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
   const long long sz = B.L.size();
   // every array starts on a 256-byte boundary
   const long long pitch = (sz * (long long)sizeof(R) + 255) / 256 * 256 / (long long)sizeof(R);
+  P.pitch = pitch;
   for (int r = 0; r < 2; ++r) {
     R* base = (R*)(c->arena + B.off_reg[r]);
     for (int v = 0; v < NVAR; ++v) P.reg[r][v] = base + v * pitch;
@@ -150,6 +151,49 @@ static aeth_status build_geometry_T(aeth_ctx* c) {
 
 aeth_status build_geometry(aeth_ctx* c) {
   return c->elem == 8 ? build_geometry_T<double>(c) : build_geometry_T<float>(c);
+}
+
+// Device block table and the tile prefix sums of every pass kind.
+// Default z extent of a flux tile: the largest of {64, 32, 16, 8, 4} that
+// still gives every SM at least four tiles (small grids need short
+// chunks to fill the GPU; long chunks amortise the z-halo warm-up).
+static int default_kchunk(const aeth_ctx* c) {
+  const int want = 4 * c->num_sms;
+  for (int kc : {64, 32, 16, 8, 4}) {
+    long long tiles = 0;
+    for (const auto& B : c->blocks) tiles += tiles_of(B.L, PK_FLUX, kc);
+    if (tiles >= want) return kc;
+  }
+  return 4;
+}
+
+template <typename R>
+static aeth_status build_tables_T(aeth_ctx* c) {
+  const int nb = (int)c->blocks.size();
+  if (c->kchunk <= 0) c->kchunk = default_kchunk(c);
+  std::vector<BlockPtrs<R>> tab(nb);
+  for (int b = 0; b < nb; ++b) tab[b] = block_ptrs<R>(c, b);
+  c->h_prefix.assign((size_t)PK_N * (nb + 1), 0);
+  for (int kind = 0; kind < PK_N; ++kind) {
+    int* p = c->h_prefix.data() + kind * (nb + 1);
+    long long acc = 0;
+    for (int b = 0; b < nb; ++b) {
+      p[b] = (int)acc;
+      acc += tiles_of(c->blocks[b].L, kind, c->kchunk);
+    }
+    if (acc > (1ll << 30)) return fail(c, AETH_ERR_ARG, "too many tiles (%lld)", acc);
+    p[nb] = (int)acc;
+  }
+  AETH_CK(c, cudaMemcpyAsync(c->d_tab, tab.data(), nb * sizeof(BlockPtrs<R>),
+                             cudaMemcpyHostToDevice, c->stream));
+  AETH_CK(c, cudaMemcpyAsync(c->d_prefix, c->h_prefix.data(), c->h_prefix.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, c->stream));
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return AETH_OK;
+}
+
+aeth_status build_tables(aeth_ctx* c) {
+  return c->elem == 8 ? build_tables_T<double>(c) : build_tables_T<float>(c);
 }
 
 // ------------------------------------------------------------------------
@@ -334,58 +378,61 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <typename R, bool P64>
-__global__ void __launch_bounds__(256) k_dt(Layout L, Geometry<R> geo, Arr8<R> a, int mhd,
-                                            double gamma, double rho_floor, double p_floor,
-                                            const R* __restrict__ dust, int nd,
-                                            double* __restrict__ partial, int* status) {
+__global__ void __launch_bounds__(256)
+    k_dt(const BlockPtrs<R>* __restrict__ tab, const int* __restrict__ pre, int nb, int total,
+         int mhd, double gamma, double rho_floor, double p_floor, int nd,
+         double* __restrict__ partial, int* status) {
   __shared__ double sm[8];
-  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const int rows = ny * nz;
   double m = INFINITY;
   bool bad = false;
-  // one x-row per block iteration, threads along x (coalesced, 32-bit
-  // index arithmetic)
-  for (int r = blockIdx.x; r < rows; r += gridDim.x)
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const int j = r % ny, k = r / ny;
-    const long long c = L.idx(i, j, k);
-    R rho = a.p[0][c];
-    if (!(rho >= (R)rho_floor)) { if (!(rho == rho)) bad = true; rho = (R)rho_floor; }
-    const R v[3] = {a.p[1][c] / rho, a.p[2][c] / rho, a.p[3][c] / rho};
-    R bc[3] = {0, 0, 0};
-    if (mhd) {
-      bc[0] = R(0.5) * (a.p[5][c] + a.p[5][c + 1]);
-      bc[1] = R(0.5) * (a.p[6][c] + a.p[6][c + L.sx]);
-      bc[2] = R(0.5) * (a.p[7][c] + a.p[7][c + L.sx * L.sy]);
-    }
-    R pr;
-    if (P64) {
-      double ke = 0.5 * ((double)a.p[1][c] * a.p[1][c] + (double)a.p[2][c] * a.p[2][c] +
-                         (double)a.p[3][c] * a.p[3][c]) / (double)rho;
-      double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
-      pr = (R)((gamma - 1.0) * ((double)a.p[4][c] - ke - me));
-    } else {
-      pr = (R)(gamma - 1.0) * (a.p[4][c] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
-                               R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
-    }
-    if (!(pr >= (R)p_floor)) { if (!(pr == pr)) bad = true; pr = (R)p_floor; }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
-      const R w = geo.width[d](i, j, k);
-      double dtd = (double)(w / (fabs(v[d]) + cf));
-      if (!(dtd > 0.0)) bad = true;
-      m = fmin(m, dtd);
-    }
-    // pressureless dust species: c = 0 (Eq. 11)
-    for (int s = 0; s < nd; ++s) {
-      const long long sz = L.size();
-      const R rk = dust[(long long)(4 * s) * sz + c];
-      if (!(rk > R(0))) continue;
+  // one x-row of one block per iteration, threads along x
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int b = find_block(pre, nb, t);
+    const BlockPtrs<R>& P = tab[b];
+    const Layout L = P.L;
+    const int r = t - pre[b];
+    const int j = r % L.n[1], k = r / L.n[1];
+    const R* const* a = P.reg[0];
+    for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+      const long long c = L.idx(i, j, k);
+      R rho = a[0][c];
+      if (!(rho >= (R)rho_floor)) { if (!(rho == rho)) bad = true; rho = (R)rho_floor; }
+      const R v[3] = {a[1][c] / rho, a[2][c] / rho, a[3][c] / rho};
+      R bc[3] = {0, 0, 0};
+      if (mhd) {
+        bc[0] = R(0.5) * (a[5][c] + a[5][c + 1]);
+        bc[1] = R(0.5) * (a[6][c] + a[6][c + L.sx]);
+        bc[2] = R(0.5) * (a[7][c] + a[7][c + L.sx * L.sy]);
+      }
+      R pr;
+      if (P64) {
+        double ke = 0.5 * ((double)a[1][c] * a[1][c] + (double)a[2][c] * a[2][c] +
+                           (double)a[3][c] * a[3][c]) / (double)rho;
+        double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
+        pr = (R)((gamma - 1.0) * ((double)a[4][c] - ke - me));
+      } else {
+        pr = (R)(gamma - 1.0) * (a[4][c] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
+                                 R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+      }
+      if (!(pr >= (R)p_floor)) { if (!(pr == pr)) bad = true; pr = (R)p_floor; }
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const R vk = fabs(dust[(long long)(4 * s + 1 + d) * sz + c] / rk);
-        if (vk > R(0)) m = fmin(m, (double)(geo.width[d](i, j, k) / vk));
+        const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
+        const R w = P.geo.width[d](i, j, k);
+        double dtd = (double)(w / (fabs(v[d]) + cf));
+        if (!(dtd > 0.0)) bad = true;
+        m = fmin(m, dtd);
+      }
+      // pressureless dust species: c = 0 (Eq. 11)
+      for (int s = 0; s < nd; ++s) {
+        const long long sz = L.size();
+        const R rk = P.dust[0][(long long)(4 * s) * sz + c];
+        if (!(rk > R(0))) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const R vk = fabs(P.dust[0][(long long)(4 * s + 1 + d) * sz + c] / rk);
+          if (vk > R(0)) m = fmin(m, (double)(P.geo.width[d](i, j, k) / vk));
+        }
       }
     }
   }
@@ -417,18 +464,14 @@ __global__ void k_dt_final(const double* __restrict__ partial, int n, double sca
 
 template <typename R, bool P64>
 static aeth_status dt_T(aeth_ctx* c) {
-  for (size_t b = 0; b < c->blocks.size(); ++b) {
-    BlockPtrs<R> P = block_ptrs<R>(c, (int)b);
-    Arr8<R> a{};
-    for (int v = 0; v < NVAR; ++v) a.p[v] = P.reg[0][v];
-    const BlockInfo& B = c->blocks[b];
-    k_dt<R, P64><<<B.dt_blocks, 256, 0, c->stream>>>(
-        P.L, P.geo, a, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor,
-        P.dust[0], c->cfg.n_dust, c->d_partials + B.dt_offset, c->d_status);
-  }
-  c->n_launch += (long long)c->blocks.size() + 1;
+  const int nb = (int)c->blocks.size();
+  k_dt<R, P64><<<c->dt_grid, 256, 0, c->stream>>>(
+      (const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_ROWS * (nb + 1), nb,
+      prefix_total(c, PK_ROWS), is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor,
+      c->cfg.n_dust, c->d_partials, c->d_status);
+  c->n_launch += 2;
   const double scale = c->cfg.cfl * cmax_of(c->cfg.integrator);
-  k_dt_final<<<1, 1024, 0, c->stream>>>(c->d_partials, c->n_partials, scale, c->d_dt);
+  k_dt_final<<<1, 1024, 0, c->stream>>>(c->d_partials, c->dt_grid, scale, c->d_dt);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }
@@ -453,29 +496,34 @@ aeth_status enqueue_set_dt(aeth_ctx* c, double dt) {
 // ------------------------------------------------------------------------
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_diag(Layout L, Geometry<R> geo, Arr8<R> a, int mhd,
-                                              double* __restrict__ partial) {
+__global__ void __launch_bounds__(256)
+    k_diag(const BlockPtrs<R>* __restrict__ tab, const int* __restrict__ pre, int nb, int total,
+           int mhd, double* __restrict__ partial) {
   __shared__ double sm[6][8];
-  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const int rows = ny * nz;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int r = blockIdx.x; r < rows; r += gridDim.x)
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const int j = r % ny, k = r / ny;
-    const long long c = L.idx(i, j, k);
-    const double V = (double)geo.vol(i, j, k);
-    for (int v = 0; v < 5; ++v) acc[v] += (double)a.p[v][c] * V;
-    if (mhd) {
-      const double f[6] = {a.p[5][c], a.p[5][c + 1], a.p[6][c], a.p[6][c + L.sx],
-                           a.p[7][c], a.p[7][c + L.sx * L.sy]};
-      const double ar[6] = {geo.area[0](i, j, k), geo.area[0](i + 1, j, k),
-                            geo.area[1](i, j, k), geo.area[1](i, j + 1, k),
-                            geo.area[2](i, j, k), geo.area[2](i, j, k + 1)};
-      const double div = ar[1] * f[1] - ar[0] * f[0] + ar[3] * f[3] - ar[2] * f[2] +
-                         ar[5] * f[5] - ar[4] * f[4];
-      double den = 0;
-      for (int q = 0; q < 6; ++q) den += ar[q] * fabs(f[q]);
-      if (den > 0) acc[5] = fmax(acc[5], fabs(div) / den);
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int b = find_block(pre, nb, t);
+    const BlockPtrs<R>& P = tab[b];
+    const Layout L = P.L;
+    const int r = t - pre[b];
+    const int j = r % L.n[1], k = r / L.n[1];
+    const R* const* a = P.reg[0];
+    for (int i = threadIdx.x; i < L.n[0]; i += blockDim.x) {
+      const long long c = L.idx(i, j, k);
+      const double V = (double)P.geo.vol(i, j, k);
+      for (int v = 0; v < 5; ++v) acc[v] += (double)a[v][c] * V;
+      if (mhd) {
+        const double f[6] = {a[5][c], a[5][c + 1], a[6][c], a[6][c + L.sx],
+                             a[7][c], a[7][c + L.sx * L.sy]};
+        const double ar[6] = {P.geo.area[0](i, j, k), P.geo.area[0](i + 1, j, k),
+                              P.geo.area[1](i, j, k), P.geo.area[1](i, j + 1, k),
+                              P.geo.area[2](i, j, k), P.geo.area[2](i, j, k + 1)};
+        const double div = ar[1] * f[1] - ar[0] * f[0] + ar[3] * f[3] - ar[2] * f[2] +
+                           ar[5] * f[5] - ar[4] * f[4];
+        double den = 0;
+        for (int q = 0; q < 6; ++q) den += ar[q] * fabs(f[q]);
+        if (den > 0) acc[5] = fmax(acc[5], fabs(div) / den);
+      }
     }
   }
   for (int q = 0; q < 5; ++q) acc[q] = warp_sum(acc[q]);
@@ -519,15 +567,11 @@ __global__ void k_diag_final(const double* __restrict__ partial, int n, double* 
 
 template <typename R>
 static aeth_status diag_T(aeth_ctx* c) {
-  for (size_t b = 0; b < c->blocks.size(); ++b) {
-    BlockPtrs<R> P = block_ptrs<R>(c, (int)b);
-    Arr8<R> a{};
-    for (int v = 0; v < NVAR; ++v) a.p[v] = P.reg[0][v];
-    const BlockInfo& B = c->blocks[b];
-    k_diag<R><<<B.dt_blocks, 256, 0, c->stream>>>(P.L, P.geo, a, is_mhd(c),
-                                                   c->d_partials + 6 * B.dt_offset);
-  }
-  k_diag_final<<<1, 256, 0, c->stream>>>(c->d_partials, c->n_partials, c->d_diag);
+  const int nb = (int)c->blocks.size();
+  k_diag<R><<<c->dt_grid, 256, 0, c->stream>>>((const BlockPtrs<R>*)c->d_tab,
+                                               c->d_prefix + PK_ROWS * (nb + 1), nb,
+                                               prefix_total(c, PK_ROWS), is_mhd(c), c->d_partials);
+  k_diag_final<<<1, 256, 0, c->stream>>>(c->d_partials, c->dt_grid, c->d_diag);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }

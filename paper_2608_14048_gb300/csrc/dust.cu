@@ -18,7 +18,7 @@ namespace aeth {
 template <typename R>
 void launch_fill(const BlockPtrs<R>& P, R* const* arrs, int nv, cudaStream_t st);
 template <typename R, bool P64>
-void hydro_flux_pass(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src);
+void hydro_flux_pass(aeth_ctx* c, int block, int recon, int src);
 
 constexpr double kImexG = 1.0 + 0.70710678118654752440;
 constexpr double kImexD = 1.0 - 1.0 / (2.0 * kImexG);
@@ -239,7 +239,7 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
     launch_fill<R>(P, arr, na, s);
     c->n_launch += 3;
   }
-  hydro_flux_pass<R, P64>(c, P, c->cfg.recon, src);
+  hydro_flux_pass<R, P64>(c, b, c->cfg.recon, src);
   dim3 blk(32, 4, 2);
   dim3 grd((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 3) / 4, (L.n[2] + 1 + 1) / 2);
   const R dfl = (R)1e-20;

@@ -1,5 +1,12 @@
 // Fused stage of the MHD step (Sec. 2.4-2.6) in three passes:
 //
+// Every pass is ONE launch over all mesh blocks of the context: a device
+// table holds each block's layout, geometry and array pointers, and each
+// pass kind has a prefix sum of tiles per block, so a CTA finds its block
+// by binary search.  The flux pass is persistent (grid-stride over tiles,
+// grid sized to the SM count); uneven block sizes only change the number
+// of tiles per block.
+//
 //  1. k_flux3: conserved->primitive, reconstruction and HLLD for all three
 //     face directions of every cell in one sweep.  A CTA owns a TX x TY
 //     column tile and marches along z: each x-y plane of primitives (with
@@ -23,6 +30,32 @@ constexpr int TY = 8;
 constexpr int NT = TX * TY;
 
 bool fused_supported(const aeth_ctx*) { return true; }
+
+__host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
+
+// Where a tile's block comes from: the device block table (passes over
+// several blocks; binary search of the tile prefix sums), or the kernel's
+// parameter space (passes over one block: uniform constant-bank loads).
+template <typename R>
+struct TableSrc {
+  const BlockPtrs<R>* tab;
+  const int* pre;
+  int nb;
+  __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
+    const int b = find_block(pre, nb, t);
+    loc = t - pre[b];
+    return tab[b];
+  }
+};
+template <typename R>
+struct ParamSrc {
+  BlockPtrs<R> P;
+  int base;   // first tile of the block in the pass's numbering
+  __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
+    loc = t - base;
+    return P;
+  }
+};
 
 template <typename R>
 struct FluxOut {
@@ -62,6 +95,17 @@ __device__ __forceinline__ int prim_cell(const Layout& L, const ConstArr8<R>& u,
   return hits;
 }
 
+// Same, with the 8 state arrays at base + v * pitch.
+template <typename R, bool P64, bool MHD>
+__device__ __forceinline__ int prim_cell_s(const Layout& L, const R* __restrict__ base,
+                                           long long pitch, long long c, R gm1, R rho_floor,
+                                           R p_floor, R* w) {
+  ConstArr8<R> u;
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) u.p[v] = base + v * pitch;
+  return prim_cell<R, P64, MHD>(L, u, c, gm1, rho_floor, p_floor, w);
+}
+
 __device__ __forceinline__ bool in_prim_range(const Layout& L, int i, int j, int k) {
   return i >= -L.g && i < L.n[0] + L.g && j >= -L.g && j < L.n[1] + L.g && k >= -L.g &&
          k < L.n[2] + L.g;
@@ -80,189 +124,209 @@ __device__ __forceinline__ void recon_var(Get get, R& wl, R& wr) {
   recon_face<RECON>(s, wl, wr);
 }
 
-// Solve one face of direction D and store its outputs.
+// Store the outputs of one face of direction D.  Scratch arrays sit at
+// sb + slot * pitch: E_ref 0..2, fluxes 8 + 5 D + v, face EMFs 23 + 2 D + q.
 template <int D, typename R>
-__device__ __forceinline__ void store_face(const FluxOut<R>& o, long long fc, const R* fx) {
+__device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, long long fc,
+                                           const R* fx) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  o.f[D][0][fc] = fx[0];
-  o.f[D][1 + D][fc] = fx[1];
-  o.f[D][1 + T1][fc] = fx[2];
-  o.f[D][1 + T2][fc] = fx[3];
-  o.f[D][4][fc] = fx[4];
-  o.e[D][0][fc] = fx[6];    // E_t1 =  F(B_t2)
-  o.e[D][1][fc] = -fx[5];   // E_t2 = -F(B_t1)
+  R* f = sb + (8 + 5 * D) * pitch + fc;
+  f[0] = fx[0];
+  f[(1 + D) * pitch] = fx[1];
+  f[(1 + T1) * pitch] = fx[2];
+  f[(1 + T2) * pitch] = fx[3];
+  f[4 * pitch] = fx[4];
+  R* e = sb + (23 + 2 * D) * pitch + fc;
+  e[0] = fx[6];        // E_t1 =  F(B_t2)
+  e[pitch] = -fx[5];   // E_t2 = -F(B_t1)
 }
 
-// two CTAs per SM in FP32 (<= 128 registers); FP64 takes the full file
-template <typename R, bool P64, int RECON, bool MHD>
+// ------------------------------------------------------------------------
+// 1. flux pass.  Persistent: CTAs stride over the tiles of all blocks.
+//    Two CTAs per SM in FP32 (<= 128 registers); FP64 takes the full file.
+// ------------------------------------------------------------------------
+template <typename R, bool P64, int RECON, bool MHD, typename Src>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1)
-    k_flux3(Layout L, ConstArr8<R> u, FluxOut<R> o, R gamma, R rho_floor, R p_floor, int kchunk,
+    k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits) {
   constexpr int RL = RECON + 1, RH = RECON;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
   constexpr int QN = RL + RH + 1;
   __shared__ R sw[NPRIM][WY][WX];
-
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i0 = -1 + (int)blockIdx.x * TX, j0 = -1 + (int)blockIdx.y * TY;
-  const int i = i0 + tx, j = j0 + ty;
-  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-  const int k0 = -1 + (int)blockIdx.z * kchunk;
-  const int k1 = min(nz, k0 + kchunk - 1);
-  const bool active = i <= nx && j <= ny;
   const R gm1 = gamma - R(1);
   int hits = 0;
 
-  // z register queue of the own column: planes k-RL .. k+RH, 7 variables
-  // (the z-face normal field comes from the face array)
-  R q[7][QN];
-  auto load_q = [&](int slot, int kk) {
-    R w[8];
-    if (active && in_prim_range(L, i, j, kk)) {
-      prim_cell<R, P64, MHD>(L, u, L.idx(i, j, kk), gm1, rho_floor, p_floor, w);
-    } else {
-      w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
-    }
-    // z-face frame order: rho, vz, vx, vy, p, Bx, By
-    q[0][slot] = w[0]; q[1][slot] = w[3]; q[2][slot] = w[1]; q[3][slot] = w[2];
-    q[4][slot] = w[4]; q[5][slot] = w[5]; q[6][slot] = w[6];
-  };
-#pragma unroll
-  for (int t = 0; t < QN - 1; ++t) load_q(t + 1, k0 - RL + t);
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    int loc;
+    const BlockPtrs<R>& P = S.get(t, loc);
+    const Layout L = P.L;
+    const int ntx = ceil_div_d(L.n[0] + 2, TX), nty = ceil_div_d(L.n[1] + 2, TY);
+    const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
+    const R* __restrict__ ub = P.reg[src][0];   // state arrays at ub + v * pitch
+    R* __restrict__ sb = P.w[0];                 // scratch arrays at sb + slot * pitch
+    const long long pitch = P.pitch;
+    const int i0 = -1 + bx * TX, j0 = -1 + by * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int k0 = -1 + bz * kchunk;
+    const int k1 = min(nz, k0 + kchunk - 1);
+    const bool active = i <= nx && j <= ny;
 
-  for (int k = k0; k <= k1; ++k) {
-    __syncthreads();
-    // stage plane k (tile + halo) in shared memory
-    for (int t = threadIdx.x; t < WX * WY; t += NT) {
-      const int rx = t % WX, ry = t / WX;
-      const int ci = i0 - RL + rx, cj = j0 - RL + ry;
+    // z register queue of the own column: planes k-RL .. k+RH, 7 variables
+    // (the z-face normal field comes from the face array)
+    R q[7][QN];
+    auto load_q = [&](int slot, int kk) {
       R w[8];
-      if (in_prim_range(L, ci, cj, k)) {
-        hits += prim_cell<R, P64, MHD>(L, u, L.idx(ci, cj, k), gm1, rho_floor, p_floor, w);
+      if (active && in_prim_range(L, i, j, kk)) {
+        prim_cell_s<R, P64, MHD>(L, ub, pitch, L.idx(i, j, kk), gm1, rho_floor, p_floor, w);
       } else {
         w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
       }
+      // z-face frame order: rho, vz, vx, vy, p, Bx, By
+      q[0][slot] = w[0]; q[1][slot] = w[3]; q[2][slot] = w[1]; q[3][slot] = w[2];
+      q[4][slot] = w[4]; q[5][slot] = w[5]; q[6][slot] = w[6];
+    };
 #pragma unroll
-      for (int v = 0; v < NPRIM; ++v) sw[v][ry][rx] = w[v];
-    }
-    // advance the z queue: drop plane k-RL-1, add plane k+RH
-#pragma unroll
-    for (int v = 0; v < 7; ++v)
-#pragma unroll
-      for (int t = 0; t < QN - 1; ++t) q[v][t] = q[v][t + 1];
-    load_q(QN - 1, k + RH);
-    __syncthreads();
-    if (!active) continue;
+    for (int s = 0; s < QN - 1; ++s) load_q(s + 1, k0 - RL + s);
 
-    const long long fc = L.idx(i, j, k);
-    const int sx = tx + RL, sy = ty + RL;
-    R wl[7], wr[7], fx[7];
-    // ---- x-face (i-1/2, j, k): frame (rho, vx, vy, vz, p, By, Bz)
-    if (i >= 0 && k >= -1) {
-      const int slot[7] = {0, 1, 2, 3, 4, 6, 7};
+    for (int k = k0; k <= k1; ++k) {
+      __syncthreads();
+      // stage plane k (tile + halo) in shared memory
+      for (int s = threadIdx.x; s < WX * WY; s += NT) {
+        const int rx = s % WX, ry = s / WX;
+        const int ci = i0 - RL + rx, cj = j0 - RL + ry;
+        R w[8];
+        if (in_prim_range(L, ci, cj, k)) {
+          hits += prim_cell_s<R, P64, MHD>(L, ub, pitch, L.idx(ci, cj, k), gm1, rho_floor,
+                                           p_floor, w);
+        } else {
+          w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
+        }
 #pragma unroll
-      for (int v = 0; v < 7; ++v) {
-        if (!MHD && v >= 5) { wl[v] = wr[v] = R(0); continue; }
-        recon_var<RECON>([&](int off) { return sw[slot[v]][sy][sx + off]; }, wl[v], wr[v]);
+        for (int v = 0; v < NPRIM; ++v) sw[v][ry][rx] = w[v];
       }
-      const R bn = MHD ? u.p[5][fc] : R(0);
-      hlld(gamma, wl, wr, bn, fx);
-      store_face<0>(o, fc, fx);
-    }
-    // ---- y-face (i, j-1/2, k): frame (rho, vy, vz, vx, p, Bz, Bx)
-    if (j >= 0) {
-      const int slot[7] = {0, 2, 3, 1, 4, 7, 5};
+      // advance the z queue: drop plane k-RL-1, add plane k+RH
 #pragma unroll
-      for (int v = 0; v < 7; ++v) {
-        if (!MHD && v >= 5) { wl[v] = wr[v] = R(0); continue; }
-        recon_var<RECON>([&](int off) { return sw[slot[v]][sy + off][sx]; }, wl[v], wr[v]);
-      }
-      const R bn = MHD ? u.p[6][fc] : R(0);
-      hlld(gamma, wl, wr, bn, fx);
-      store_face<1>(o, fc, fx);
-    }
-    // ---- z-face (i, j, k-1/2): frame (rho, vz, vx, vy, p, Bx, By)
-    if (k >= 0) {
+      for (int v = 0; v < 7; ++v)
 #pragma unroll
-      for (int v = 0; v < 7; ++v) {
-        if (!MHD && v >= 5) { wl[v] = wr[v] = R(0); continue; }
-        recon_var<RECON>([&](int off) { return q[v][off + RL]; }, wl[v], wr[v]);
+        for (int s = 0; s < QN - 1; ++s) q[v][s] = q[v][s + 1];
+      load_q(QN - 1, k + RH);
+      __syncthreads();
+      if (!active) continue;
+
+      const long long fc = L.idx(i, j, k);
+      const int sx = tx + RL, sy = ty + RL;
+      R wl[7], wr[7], fx[7];
+      // ---- x-face (i-1/2, j, k): frame (rho, vx, vy, vz, p, By, Bz)
+      if (i >= 0) {
+        const int slot[7] = {0, 1, 2, 3, 4, 6, 7};
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          if (!MHD && v >= 5) { wl[v] = wr[v] = R(0); continue; }
+          recon_var<RECON>([&](int off) { return sw[slot[v]][sy][sx + off]; }, wl[v], wr[v]);
+        }
+        const R bn = MHD ? ub[5 * pitch + fc] : R(0);
+        hlld(gamma, wl, wr, bn, fx);
+        store_face<0>(sb, pitch, fc, fx);
       }
-      const R bn = MHD ? u.p[7][fc] : R(0);
-      hlld(gamma, wl, wr, bn, fx);
-      store_face<2>(o, fc, fx);
-    }
-    // ---- cell-centred reference EMF, E = -v x B
-    if (MHD) {
-      const R vx = sw[1][sy][sx], vy = sw[2][sy][sx], vz = sw[3][sy][sx];
-      const R bx = sw[5][sy][sx], by = sw[6][sy][sx], bz = sw[7][sy][sx];
-      o.eref[0][fc] = -(vy * bz - vz * by);
-      o.eref[1][fc] = -(vz * bx - vx * bz);
-      o.eref[2][fc] = -(vx * by - vy * bx);
+      // ---- y-face (i, j-1/2, k): frame (rho, vy, vz, vx, p, Bz, Bx)
+      if (j >= 0) {
+        const int slot[7] = {0, 2, 3, 1, 4, 7, 5};
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          if (!MHD && v >= 5) { wl[v] = wr[v] = R(0); continue; }
+          recon_var<RECON>([&](int off) { return sw[slot[v]][sy + off][sx]; }, wl[v], wr[v]);
+        }
+        const R bn = MHD ? ub[6 * pitch + fc] : R(0);
+        hlld(gamma, wl, wr, bn, fx);
+        store_face<1>(sb, pitch, fc, fx);
+      }
+      // ---- z-face (i, j, k-1/2): frame (rho, vz, vx, vy, p, Bx, By)
+      if (k >= 0) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          if (!MHD && v >= 5) { wl[v] = wr[v] = R(0); continue; }
+          recon_var<RECON>([&](int off) { return q[v][off + RL]; }, wl[v], wr[v]);
+        }
+        const R bn = MHD ? ub[7 * pitch + fc] : R(0);
+        hlld(gamma, wl, wr, bn, fx);
+        store_face<2>(sb, pitch, fc, fx);
+      }
+      // ---- cell-centred reference EMF, E = -v x B
+      if (MHD) {
+        const R vx = sw[1][sy][sx], vy = sw[2][sy][sx], vz = sw[3][sy][sx];
+        const R bx_ = sw[5][sy][sx], by_ = sw[6][sy][sx], bz_ = sw[7][sy][sx];
+        sb[fc] = -(vy * bz_ - vz * by_);
+        sb[pitch + fc] = -(vz * bx_ - vx * bz_);
+        sb[2 * pitch + fc] = -(vx * by_ - vy * bx_);
+      }
     }
   }
   if (hits) atomicAdd(floor_hits, (unsigned long long)hits);
 }
 
-// ------------------------------------------------------------------------
-// corner EMFs from face EMFs, mass fluxes and the reference EMF arrays
-// ------------------------------------------------------------------------
-template <typename R>
-struct EmfRefArgs {
-  const R* eref[3];
-  const R* f0[3];
-  const R* e[3][2];
-  R* edge[3];
+// Tile coordinates of the 32x4x2 elementwise passes.
+struct CellTile {
+  int b, P[3];
+  bool ok;
 };
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_emf_ref(Layout L, EmfRefArgs<R> A) {
-  int P[3];
-  P[0] = blockIdx.x * blockDim.x + threadIdx.x;
-  P[1] = blockIdx.y * blockDim.y + threadIdx.y;
-  P[2] = blockIdx.z * blockDim.z + threadIdx.z;
-  if (P[0] > L.n[0] || P[1] > L.n[1] || P[2] > L.n[2]) return;
-  const long long iP = L.idx(P[0], P[1], P[2]);
+__device__ __forceinline__ CellTile cell_tile(const BlockPtrs<R>& B, int loc, const int* ext_add) {
+  CellTile ct;
+  ct.b = 0;
+  const Layout& L = B.L;
+  const int ntx = ceil_div_d(L.n[0] + ext_add[0], CELL_BX);
+  const int nty = ceil_div_d(L.n[1] + ext_add[1], CELL_BY);
+  const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
+  ct.P[0] = bx * CELL_BX + (int)(threadIdx.x % CELL_BX);
+  ct.P[1] = by * CELL_BY + (int)((threadIdx.x / CELL_BX) % CELL_BY);
+  ct.P[2] = bz * CELL_BZ + (int)(threadIdx.x / (CELL_BX * CELL_BY));
+  ct.ok = true;
+  return ct;
+}
+
+// ------------------------------------------------------------------------
+// 2. corner EMFs from face EMFs, mass fluxes and the reference EMF arrays
+// ------------------------------------------------------------------------
+template <typename R, typename Src>
+__global__ void __launch_bounds__(256) k_emf_ref(Src S, int t0, int t1) {
+  const int add[3] = {1, 1, 1};
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    int loc;
+    const BlockPtrs<R>& A = S.get(t, loc);
+    const CellTile ct = cell_tile(A, loc, add);
+    const Layout L = A.L;
+    const int* P = ct.P;
+    if (P[0] > L.n[0] || P[1] > L.n[1] || P[2] > L.n[2]) continue;
+    const long long iP = L.idx(P[0], P[1], P[2]);
 #pragma unroll
-  for (int cc = 0; cc < 3; ++cc) {
-    if (P[cc] >= L.n[cc]) continue;
-    const int a = (cc + 1) % 3, b = (cc + 2) % 3;
-    const long long sa = L.stride(a), sb = L.stride(b);
-    const long long iA = iP - sa, iB = iP - sb, iAB = iP - sa - sb;
-    const R* er = A.eref[cc];
-    A.edge[cc][iP] = corner_emf(A.e[a][1][iB], A.e[a][1][iP], A.e[b][0][iA], A.e[b][0][iP],
-                                er[iAB], er[iB], er[iA], er[iP], A.f0[a][iB], A.f0[a][iP],
-                                A.f0[b][iA], A.f0[b][iP]);
+    for (int cc = 0; cc < 3; ++cc) {
+      if (P[cc] >= L.n[cc]) continue;
+      const int a = (cc + 1) % 3, b = (cc + 2) % 3;
+      const long long sa = L.stride(a), sb = L.stride(b);
+      const long long iA = iP - sa, iB = iP - sb, iAB = iP - sa - sb;
+      const R* er = A.w[cc];
+      A.edge[cc][iP] = corner_emf(A.e[a][1][iB], A.e[a][1][iP], A.e[b][0][iA], A.e[b][0][iP],
+                                  er[iAB], er[iB], er[iA], er[iP], A.f[a][0][iB], A.f[a][0][iP],
+                                  A.f[b][0][iA], A.f[b][0][iP]);
+    }
   }
 }
 
 // ------------------------------------------------------------------------
-// update: out = w0*A + w1*B + beta*dt*L (Eq. 8 + Eq. 12), CT (Eq. 9)
+// 3. update: out = w0*A + w1*B + beta*dt*L (Eq. 8 + Eq. 12), CT (Eq. 9)
 // ------------------------------------------------------------------------
-template <typename R>
-struct UpdFArgs {
-  const R* a[NVAR];
-  const R* b[NVAR];
-  const R* src[NVAR];
-  R* out[NVAR];
-  const R* f[3][5];
-  const R* edge[3];
-  R w0, w1, beta;
-  const double* dt;
-};
-
 template <typename R, bool P64, bool MHD, bool SPH>
-__global__ void __launch_bounds__(256) k_update_f(Layout L, Geometry<R> geo, UpdFArgs<R> A,
-                                                 R gamma, R rho_floor, R p_floor) {
-  int P[3];
-  P[0] = blockIdx.x * blockDim.x + threadIdx.x;
-  P[1] = blockIdx.y * blockDim.y + threadIdx.y;
-  P[2] = blockIdx.z * blockDim.z + threadIdx.z;
-  if (P[0] > L.n[0] || P[1] > L.n[1] || P[2] > L.n[2]) return;
+__device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P, int src, int out,
+                                            R w0, R w1, R bdt, R gamma, R rho_floor, R p_floor) {
+  const Layout& L = B.L;
+  const Geometry<R>& geo = B.geo;
   const int i = P[0], j = P[1], k = P[2];
   const long long c = L.idx(i, j, k);
-  const R bdt = A.beta * (R)(*A.dt);
-  const bool has_b = A.w1 != R(0);
+  const bool has_b = w1 != R(0);
+  R* const* outp = B.reg[out];
   if (i < L.n[0] && j < L.n[1] && k < L.n[2]) {
     const long long cp[3] = {c + 1, c + L.sx, c + L.sx * L.sy};
     R V, Am[3], Ap[3];
@@ -277,13 +341,13 @@ __global__ void __launch_bounds__(256) k_update_f(Layout L, Geometry<R> geo, Upd
       Am[1] = Ap[1] = geo.area[1](0, 0, 0);
       Am[2] = Ap[2] = geo.area[2](0, 0, 0);
     }
-    R src[5] = {0, 0, 0, 0, 0};
+    R srcv[5] = {0, 0, 0, 0, 0};
     if (SPH) {
       // curvilinear momentum sources from the stress tensor (Eq. 12) of
       // the stage state
       ConstArr8<R> s;
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) s.p[v] = A.src[v];
+      for (int v = 0; v < NVAR; ++v) s.p[v] = B.reg[src][v];
       R w[8];
       prim_cell<R, P64, MHD>(L, s, c, gamma - R(1), rho_floor, p_floor, w);
       const R rho = w[0], vv[3] = {w[1], w[2], w[3]};
@@ -293,19 +357,19 @@ __global__ void __launch_bounds__(256) k_update_f(Layout L, Geometry<R> geo, Upd
         return rho * vv[x] * vv[y] + (x == y ? ps : R(0)) - bb[x] * bb[y];
       };
       const R ir = geo.invr(i, j, k), ct = geo.cotr(i, j, k);
-      src[1] = (T(1, 1) + T(2, 2)) * ir;
-      src[2] = T(2, 2) * ct - T(0, 1) * ir;
-      src[3] = -T(2, 0) * ir - T(2, 1) * ct;
+      srcv[1] = (T(1, 1) + T(2, 2)) * ir;
+      srcv[2] = T(2, 2) * ct - T(0, 1) * ir;
+      srcv[3] = -T(2, 0) * ir - T(2, 1) * ct;
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R div = R(0);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) div += Ap[d] * A.f[d][v][cp[d]] - Am[d] * A.f[d][v][c];
-      const R rhs = -div / V + src[v];
-      R base = A.w0 * A.a[v][c];
-      if (has_b) base += A.w1 * A.b[v][c];
-      A.out[v][c] = base + bdt * rhs;
+      for (int d = 0; d < 3; ++d) div += Ap[d] * B.f[d][v][cp[d]] - Am[d] * B.f[d][v][c];
+      const R rhs = -div / V + srcv[v];
+      R base = w0 * B.reg[0][v][c];
+      if (has_b) base += w1 * B.reg[1][v][c];
+      outp[v][c] = base + bdt * rhs;
     }
   }
   if (!MHD) return;
@@ -319,114 +383,191 @@ __global__ void __launch_bounds__(256) k_update_f(Layout L, Geometry<R> geo, Upd
     const long long q1 = c + L.stride(e1), q2 = c + L.stride(e2);
     R circ;
     if (SPH) {
-      circ = A.edge[e2][q1] * geo.edge[e2](Q1[0], Q1[1], Q1[2]) -
-             A.edge[e2][c] * geo.edge[e2](i, j, k) -
-             (A.edge[e1][q2] * geo.edge[e1](Q2[0], Q2[1], Q2[2]) -
-              A.edge[e1][c] * geo.edge[e1](i, j, k));
+      circ = B.edge[e2][q1] * geo.edge[e2](Q1[0], Q1[1], Q1[2]) -
+             B.edge[e2][c] * geo.edge[e2](i, j, k) -
+             (B.edge[e1][q2] * geo.edge[e1](Q2[0], Q2[1], Q2[2]) -
+              B.edge[e1][c] * geo.edge[e1](i, j, k));
     } else {
       const R l2 = geo.edge[e2](0, 0, 0), l1 = geo.edge[e1](0, 0, 0);
-      circ = A.edge[e2][q1] * l2 - A.edge[e2][c] * l2 - (A.edge[e1][q2] * l1 - A.edge[e1][c] * l1);
+      circ = B.edge[e2][q1] * l2 - B.edge[e2][c] * l2 - (B.edge[e1][q2] * l1 - B.edge[e1][c] * l1);
     }
     const R Af = SPH ? geo.area[d](i, j, k) : geo.area[d](0, 0, 0);
-    R base = A.w0 * A.a[5 + d][c];
-    if (has_b) base += A.w1 * A.b[5 + d][c];
+    R base = w0 * B.reg[0][5 + d][c];
+    if (has_b) base += w1 * B.reg[1][5 + d][c];
     const R nb = base - bdt * circ / Af;
-    A.out[5 + d][c] = nb;
+    outp[5 + d][c] = nb;
+    // periodic axis: face n is the image of face 0
     if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0)
-      A.out[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
+      outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
+  }
+}
+
+template <typename R, bool P64, bool MHD, typename Src>
+__global__ void __launch_bounds__(256)
+    k_update_f(Src S, int t0, int t1, int src, int out, R w0, R w1, R beta,
+               const double* __restrict__ dt, R gamma, R rho_floor, R p_floor) {
+  const int add[3] = {1, 1, 1};
+  const R bdt = beta * (R)(*dt);
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    int loc;
+    const BlockPtrs<R>& B = S.get(t, loc);
+    const CellTile ct = cell_tile(B, loc, add);
+    if (ct.P[0] > B.L.n[0] || ct.P[1] > B.L.n[1] || ct.P[2] > B.L.n[2]) continue;
+    if (B.L.coord == AETH_COORD_SPH)
+      update_cell<R, P64, MHD, true>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor);
+    else
+      update_cell<R, P64, MHD, false>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor);
+  }
+}
+
+// ------------------------------------------------------------------------
+// ghost fill of one register, one axis per launch (Sec. 2.3)
+// ------------------------------------------------------------------------
+template <typename R, typename Src>
+__global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, int nv, int d) {
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    int loc;
+    const BlockPtrs<R>& B = S.get(t, loc);
+    const Layout L = B.L;
+    const int g = L.g;
+    int lo[3], ext[3];
+    for (int e = 0; e < 3; ++e) {
+      if (e < d) { lo[e] = -g; ext[e] = L.n[e] + 2 * g + 1; }
+      else if (e == d) { lo[e] = 0; ext[e] = 2 * g + 1; }
+      else { lo[e] = 0; ext[e] = L.n[e] + 1; }
+    }
+    const int ntx = ceil_div_d(ext[0], CELL_BX), nty = ceil_div_d(ext[1], CELL_BY);
+    const int t0c = (loc % ntx) * CELL_BX + (int)(threadIdx.x % CELL_BX);
+    const int t1c = ((loc / ntx) % nty) * CELL_BY + (int)((threadIdx.x / CELL_BX) % CELL_BY);
+    const int t2c = (loc / (ntx * nty)) * CELL_BZ + (int)(threadIdx.x / (CELL_BX * CELL_BY));
+    if (t0c >= ext[0] || t1c >= ext[1] || t2c >= ext[2]) continue;
+    int c[3] = {t0c + lo[0], t1c + lo[1], t2c + lo[2]};
+    const int n = L.n[d];
+    const int tt = c[d];
+    c[d] = tt < g ? tt - g : n + (tt - g);
+    const int p = c[d];
+    const long long dst = L.idx(c[0], c[1], c[2]);
+    for (int v = 0; v < nv; ++v) {
+      const bool face_d = (v == 5 + d);
+      int s;
+      if (L.bc[d] == AETH_BC_PERIODIC) {
+        s = ((p % n) + n) % n;
+      } else if (face_d) {
+        if (p >= 0 && p <= n) continue;
+        s = p < 0 ? 0 : n;
+      } else {
+        s = p < 0 ? 0 : n - 1;
+      }
+      int sc[3] = {c[0], c[1], c[2]};
+      sc[d] = s;
+      R* arr = B.reg[reg][v];
+      arr[dst] = arr[L.idx(sc[0], sc[1], sc[2])];
+    }
   }
 }
 
 // ------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------
-constexpr int KCHUNK = 32;
+struct TileRange {
+  int t0, t1;
+};
+
+static TileRange range_of(const aeth_ctx* c, int kind, int block) {
+  const int nb = (int)c->blocks.size();
+  const int* p = c->h_prefix.data() + kind * (nb + 1);
+  if (block < 0) return {0, p[nb]};
+  return {p[block], p[block + 1]};
+}
+
+template <typename R>
+static const BlockPtrs<R>* dtab(const aeth_ctx* c) {
+  return (const BlockPtrs<R>*)c->d_tab;
+}
+
+static const int* dpre(const aeth_ctx* c, int kind) {
+  return c->d_prefix + kind * ((int)c->blocks.size() + 1);
+}
+
+// Launch a pass either from the device table (several blocks) or with the
+// block's pointers in the kernel parameters (one block).
+template <typename R, typename F>
+static void with_src(aeth_ctx* c, int kind, int block, F launch) {
+  const int nb = (int)c->blocks.size();
+  if (nb == 1 || block >= 0) {
+    const int b = block >= 0 ? block : 0;
+    const TileRange r = range_of(c, kind, b);
+    launch(ParamSrc<R>{block_ptrs<R>(c, b), r.t0}, r);
+  } else {
+    launch(TableSrc<R>{dtab<R>(c), dpre(c, kind), nb}, range_of(c, kind, -1));
+  }
+}
+
+template <typename R>
+static void launch_fill_all(aeth_ctx* c, int reg, int nv, int block) {
+  for (int d = 0; d < 3; ++d) {
+    with_src<R>(c, PK_FILL0 + d, block, [&](auto S, TileRange r) {
+      if (r.t1 <= r.t0) return;
+      k_fill_b<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1, reg, nv, d);
+    });
+  }
+  c->n_launch += 3;
+}
 
 template <typename R, bool P64, int RECON, bool MHD>
-static void launch_flux3(aeth_ctx* c, const BlockPtrs<R>& P, int src, const FluxOut<R>& o) {
-  const Layout& L = P.L;
-  ConstArr8<R> u{};
-  for (int v = 0; v < NVAR; ++v) u.p[v] = P.reg[src][v];
-  const int kc = std::min(KCHUNK, L.n[2] + 2);
-  dim3 grd((L.n[0] + 2 + TX - 1) / TX, (L.n[1] + 2 + TY - 1) / TY, (L.n[2] + 2 + kc - 1) / kc);
-  k_flux3<R, P64, RECON, MHD><<<grd, NT, 0, c->stream>>>(L, u, o, (R)c->cfg.gamma,
-                                                         (R)c->cfg.rho_floor, (R)c->cfg.p_floor,
-                                                         kc, c->d_floor);
+static void launch_flux3(aeth_ctx* c, int src, int block) {
+  const int per_sm = sizeof(R) == 4 ? 2 : 1;
+  with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
+    const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
+    k_flux3<R, P64, RECON, MHD><<<grid, NT, 0, c->stream>>>(
+        S, r.t0, r.t1, src, (R)c->cfg.gamma, (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk,
+        c->d_floor);
+  });
+  c->n_launch += 1;
 }
 
 template <typename R, bool P64, bool MHD>
-static void stage_fused(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src, R w0, int has_b,
-                        R w1, R beta, int out) {
-  const Layout& L = P.L;
-  cudaStream_t st = c->stream;
-  const int nv = MHD ? NVAR : 5;
-  launch_fill<R>(P, P.reg[src], nv, st);
-  FluxOut<R> o{};
-  for (int d = 0; d < 3; ++d) {
-    for (int v = 0; v < 5; ++v) o.f[d][v] = P.f[d][v];
-    o.e[d][0] = P.e[d][0];
-    o.e[d][1] = P.e[d][1];
-    o.eref[d] = P.w[d];   // the primitive scratch slots hold E_ref here
-  }
-  // algorithmic traffic of the flux pass: the stage state read once
-  // (8 words), outputs written once (15 fluxes + 6 face EMFs + 3 E_ref)
-  const double cells = (double)(L.n[0] + 2) * (L.n[1] + 2) * (L.n[2] + 2);
-  prof_begin(c);
-  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD>(c, P, src, o);
-  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD>(c, P, src, o);
-  else launch_flux3<R, P64, 2, MHD>(c, P, src, o);
-  prof_end(c, cells * ((MHD ? 8 : 5) + (MHD ? 24 : 15)) * sizeof(R));
+static void flux_pass(aeth_ctx* c, int recon, int src, int block) {
+  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD>(c, src, block);
+  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD>(c, src, block);
+  else launch_flux3<R, P64, 2, MHD>(c, src, block);
+}
 
-  dim3 blk(32, 4, 2);
-  dim3 grd((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 3) / 4, (L.n[2] + 1 + 1) / 2);
-  if (MHD) {
-    EmfRefArgs<R> ea{};
-    for (int d = 0; d < 3; ++d) {
-      ea.eref[d] = P.w[d];
-      ea.f0[d] = P.f[d][0];
-      ea.e[d][0] = P.e[d][0];
-      ea.e[d][1] = P.e[d][1];
-      ea.edge[d] = P.edge[d];
-    }
-    k_emf_ref<R><<<grd, blk, 0, st>>>(L, ea);
-  }
-  UpdFArgs<R> ua{};
-  for (int v = 0; v < NVAR; ++v) {
-    ua.a[v] = P.reg[0][v];
-    ua.b[v] = P.reg[1][v];
-    ua.src[v] = P.reg[src][v];
-    ua.out[v] = P.reg[out][v];
-  }
-  for (int d = 0; d < 3; ++d) {
-    for (int v = 0; v < 5; ++v) ua.f[d][v] = P.f[d][v];
-    ua.edge[d] = P.edge[d];
-  }
-  ua.w0 = w0;
-  ua.w1 = has_b ? w1 : R(0);
-  ua.beta = beta;
-  ua.dt = c->d_dt;
-  const R gm = (R)c->cfg.gamma, rf = (R)c->cfg.rho_floor, pf = (R)c->cfg.p_floor;
-  if (L.coord == AETH_COORD_SPH)
-    k_update_f<R, P64, MHD, true><<<grd, blk, 0, st>>>(L, P.geo, ua, gm, rf, pf);
-  else
-    k_update_f<R, P64, MHD, false><<<grd, blk, 0, st>>>(L, P.geo, ua, gm, rf, pf);
-  c->n_launch += 3 + 1 + (MHD ? 1 : 0) + 1;
+// Algorithmic HBM bytes of one flux pass: every cell's stage state read
+// once and its outputs (15 fluxes + 6 face EMFs + 3 E_ref) written once.
+static double flux_algo_bytes(const aeth_ctx* c, bool mhd) {
+  double cells = 0;
+  for (const auto& B : c->blocks)
+    cells += (double)(B.L.n[0] + 2) * (B.L.n[1] + 2) * (B.L.n[2] + 2);
+  return cells * ((mhd ? 8 : 5) + (mhd ? 24 : 15)) * (double)c->elem;
+}
+
+template <typename R, bool P64, bool MHD>
+static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int out) {
+  launch_fill_all<R>(c, src, MHD ? NVAR : 5, -1);
+  prof_begin(c);
+  flux_pass<R, P64, MHD>(c, recon, src, -1);
+  prof_end(c, flux_algo_bytes(c, MHD));
+  with_src<R>(c, PK_CELL, -1, [&](auto S, TileRange r) {
+    if (MHD) k_emf_ref<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1);
+    k_update_f<R, P64, MHD><<<r.t1 - r.t0, 256, 0, c->stream>>>(
+        S, r.t0, r.t1, src, out, w0, w1, beta, c->d_dt, (R)c->cfg.gamma, (R)c->cfg.rho_floor,
+        (R)c->cfg.p_floor);
+  });
+  c->n_launch += MHD ? 2 : 1;
 }
 
 template <typename R, bool P64, bool MHD>
 static aeth_status step_fused_T(aeth_ctx* c) {
   const int recon = c->cfg.recon;
-  const int nb = (int)c->blocks.size();
   if (c->cfg.integrator == AETH_INT_VL2) {
-    for (int b = 0; b < nb; ++b)
-      stage_fused<R, P64, MHD>(c, block_ptrs<R>(c, b), AETH_RECON_DONOR, 0, R(1), 0, R(0), R(0.5), 1);
-    for (int b = 0; b < nb; ++b)
-      stage_fused<R, P64, MHD>(c, block_ptrs<R>(c, b), recon, 1, R(1), 0, R(0), R(1), 0);
+    // predictor: U^{n+1/2} = U^n - dt/2 L_donor(U^n)   (register A -> B)
+    stage_fused<R, P64, MHD>(c, AETH_RECON_DONOR, 0, R(1), R(0), R(0.5), 1);
+    // corrector: U^{n+1} = U^n - dt L(U^{n+1/2})         (B -> A, in place)
+    stage_fused<R, P64, MHD>(c, recon, 1, R(1), R(0), R(1), 0);
   } else if (c->cfg.integrator == AETH_INT_RK2) {
-    for (int b = 0; b < nb; ++b)
-      stage_fused<R, P64, MHD>(c, block_ptrs<R>(c, b), recon, 0, R(1), 0, R(0), R(1), 1);
-    for (int b = 0; b < nb; ++b)
-      stage_fused<R, P64, MHD>(c, block_ptrs<R>(c, b), recon, 1, R(0.5), 1, R(0.5), R(0.5), 0);
+    stage_fused<R, P64, MHD>(c, recon, 0, R(1), R(0), R(1), 1);
+    stage_fused<R, P64, MHD>(c, recon, 1, R(0.5), R(0.5), R(0.5), 0);
   } else {
     return fail(c, AETH_ERR_UNSUPPORTED, "integrator %d not available", c->cfg.integrator);
   }
@@ -443,26 +584,13 @@ template aeth_status step_fused<float, false>(aeth_ctx*);
 template aeth_status step_fused<float, true>(aeth_ctx*);
 template aeth_status step_fused<double, false>(aeth_ctx*);
 
-}  // namespace aeth
-
-namespace aeth {
-// Hydro-gas flux pass for other integrators (dust runs): the same fused
-// prim + reconstruction + HLLD sweep, writing the stage's face fluxes.
+// Hydro-gas flux pass of one block for other integrators (dust runs).
 template <typename R, bool P64>
-void hydro_flux_pass(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src) {
-  FluxOut<R> o{};
-  for (int d = 0; d < 3; ++d) {
-    for (int v = 0; v < 5; ++v) o.f[d][v] = P.f[d][v];
-    o.e[d][0] = P.e[d][0];
-    o.e[d][1] = P.e[d][1];
-    o.eref[d] = P.w[d];
-  }
-  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, false>(c, P, src, o);
-  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, false>(c, P, src, o);
-  else launch_flux3<R, P64, 2, false>(c, P, src, o);
-  c->n_launch += 1;
+void hydro_flux_pass(aeth_ctx* c, int block, int recon, int src) {
+  flux_pass<R, P64, false>(c, recon, src, block);
 }
-template void hydro_flux_pass<float, false>(aeth_ctx*, const BlockPtrs<float>&, int, int);
-template void hydro_flux_pass<float, true>(aeth_ctx*, const BlockPtrs<float>&, int, int);
-template void hydro_flux_pass<double, false>(aeth_ctx*, const BlockPtrs<double>&, int, int);
+template void hydro_flux_pass<float, false>(aeth_ctx*, int, int, int);
+template void hydro_flux_pass<float, true>(aeth_ctx*, int, int, int);
+template void hydro_flux_pass<double, false>(aeth_ctx*, int, int, int);
+
 }  // namespace aeth

@@ -175,12 +175,17 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
     size_t st = (size_t)(5 * nx * ny * nz + nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx);
     if (c->cfg.n_dust > 0) st = std::max(st, (size_t)(4 * nx * ny * nz));
     max_stage = std::max(max_stage, st * sizeof(double));
-    // reductions: one CUDA block per x-row, at most 2048 blocks per mesh block
-    long long rows = (long long)B.desc.ny * B.desc.nz;
-    B.dt_blocks = (int)std::max(1ll, std::min(rows, 2048ll));
-    B.dt_offset = npart;
-    npart += B.dt_blocks;
+    npart += B.desc.ny * B.desc.nz;   // x-rows of this block
   }
+  // batched reductions: at most 4096 CTAs, each reducing whole x-rows
+  c->dt_grid = std::max(1, std::min(npart, 4096));
+  npart = c->dt_grid;
+  // device block table and tile prefix sums of the batched passes
+  const int nb = (int)c->blocks.size();
+  c->off_tab = off;
+  off += align256((size_t)nb * sizeof(BlockPtrs<double>));
+  c->off_prefix = off;
+  off += align256((size_t)PK_N * (nb + 1) * sizeof(int));
   c->off_stage = off;
   c->stage_bytes = align256(max_stage);
   off += c->stage_bytes;
@@ -222,6 +227,13 @@ aeth_status aeth_finalize(aeth_ctx* c, size_t* bytes) {
   c->d_floor = (unsigned long long*)(sc + 320);
   c->d_fallback = (unsigned long long*)(sc + 384);
   s = build_geometry(c);
+  if (s != AETH_OK) return s;
+  int dev = 0;
+  AETH_CK(c, cudaGetDevice(&dev));
+  AETH_CK(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  c->d_tab = c->arena + c->off_tab;
+  c->d_prefix = (int*)(c->arena + c->off_prefix);
+  s = build_tables(c);
   if (s != AETH_OK) return s;
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   c->finalized = true;
@@ -432,6 +444,48 @@ aeth_status aeth_profile_read(aeth_ctx* c, double* ms, long long* n, double* byt
   if (n) *n = (long long)(c->prof_used / 2);
   if (bytes) *bytes = c->prof_bytes;
   if (all) *all = c->n_launch;
+  return AETH_OK;
+}
+
+aeth_status aeth_autotune(aeth_ctx* c, int* kchunk_out) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  // three timed steps per candidate (the state advances, as documented)
+  const bool prof = c->profile;
+  c->profile = true;
+  int best = c->kchunk;
+  double best_ms = 1e300;
+  for (int kc : {8, 16, 32, 64}) {
+    c->kchunk = kc;
+    aeth_status s = build_tables(c);
+    if (s != AETH_OK) return s;
+    c->prof_used = 0;
+    c->prof_bytes = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+      s = enqueue_dt(c);
+      if (s == AETH_OK) s = enqueue_step(c, false);
+      if (s != AETH_OK) return s;
+    }
+    double ms = 0;
+    long long n = 0;
+    s = aeth_profile_read(c, &ms, &n, nullptr, nullptr);
+    if (s != AETH_OK) return s;
+    if (n > 0 && ms / n < best_ms) {
+      best_ms = ms / n;
+      best = kc;
+    }
+  }
+  c->kchunk = best;
+  aeth_status s = build_tables(c);
+  if (s != AETH_OK) return s;
+  c->profile = prof;
+  c->prof_used = 0;
+  c->prof_bytes = 0;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (kchunk_out) *kchunk_out = best;
   return AETH_OK;
 }
 

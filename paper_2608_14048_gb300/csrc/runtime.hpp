@@ -24,6 +24,8 @@ struct BlockPtrs {
   R* edge[3];          // corner EMFs by component
   R* dust[2];          // dust registers: [species][4] arrays each (IMEX2P)
   R* dflux;            // dust fluxes: [direction][species][4] arrays
+  long long pitch;     // elements between consecutive arrays of a register
+                       // and of the scratch (w, f, e, edge in that order)
 };
 
 struct BlockInfo {
@@ -40,7 +42,32 @@ struct BlockInfo {
   int dt_offset;          // their first slot in the partials array
 };
 
-struct StepStats;
+// Pass kinds of the batched launches; each has a prefix sum of tiles per
+// mesh block so that one launch covers every block.
+enum PassKind : int { PK_FLUX = 0, PK_CELL = 1, PK_FILL0 = 2, PK_FILL1 = 3, PK_FILL2 = 4,
+                      PK_ROWS = 5, PK_N = 6 };
+
+// Tile geometry of each pass kind (threads per tile fixed per kind).
+constexpr int FLUX_TX = 32, FLUX_TY = 8;
+constexpr int CELL_BX = 32, CELL_BY = 4, CELL_BZ = 2;
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Tiles of one block for a pass kind (kchunk: z extent of a flux tile).
+inline int tiles_of(const Layout& L, int kind, int kchunk) {
+  const int g = L.g;
+  if (kind == PK_FLUX)
+    return ceil_div(L.n[0] + 2, FLUX_TX) * ceil_div(L.n[1] + 2, FLUX_TY) *
+           ceil_div(L.n[2] + 2, kchunk);
+  if (kind == PK_CELL)
+    return ceil_div(L.n[0] + 1, CELL_BX) * ceil_div(L.n[1] + 1, CELL_BY) *
+           ceil_div(L.n[2] + 1, CELL_BZ);
+  if (kind == PK_ROWS) return L.n[1] * L.n[2];
+  const int d = kind - PK_FILL0;
+  int ext[3];
+  for (int e = 0; e < 3; ++e) ext[e] = e < d ? L.n[e] + 2 * g + 1 : (e == d ? 2 * g + 1 : L.n[e] + 1);
+  return ceil_div(ext[0], CELL_BX) * ceil_div(ext[1], CELL_BY) * ceil_div(ext[2], CELL_BZ);
+}
 
 }  // namespace aeth
 
@@ -81,6 +108,15 @@ struct aeth_ctx {
   size_t prof_used = 0;               // events recorded so far
   double prof_bytes = 0;              // algorithmic bytes of the timed launches
   long long n_launch = 0;             // kernels launched (all kinds)
+  // batched launches: device block table and tile prefix sums
+  size_t off_tab = 0, off_prefix = 0;
+  void* d_tab = nullptr;              // BlockPtrs<R>[nb]
+  int* d_prefix = nullptr;            // [PK_N][nb + 1]
+  std::vector<int> h_prefix;          // host copy
+  int kchunk = 0;                     // z extent of a flux tile (0: choose;
+                                      // aeth_autotune times candidates)
+  int num_sms = 152;
+  int dt_grid = 1;                    // CTAs of the batched reductions
   // error text
   char err[512] = {0};
 };
@@ -119,6 +155,22 @@ aeth_status enqueue_set_dt(aeth_ctx* c, double dt);
 aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k);
 aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k);
 aeth_status build_geometry(aeth_ctx* c);
+aeth_status build_tables(aeth_ctx* c);
+
+// Device-side tile -> block lookup (prefix[b] <= t < prefix[b+1]).
+__device__ __forceinline__ int find_block(const int* __restrict__ pre, int nb, int t) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+inline int prefix_total(const aeth_ctx* c, int kind) {
+  const int nb = (int)c->blocks.size();
+  return c->h_prefix[kind * (nb + 1) + nb];
+}
 
 // Bracket one launch of the dominant kernel with events (aeth_profile).
 inline void prof_begin(aeth_ctx* c) {

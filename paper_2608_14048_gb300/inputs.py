@@ -21,8 +21,12 @@ import numpy as np
 CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 
-# Gauss-Legendre nodes for the edge integrals of the vector potential.
-_GL_X, _GL_W = np.polynomial.legendre.leggauss(6)
+# Gauss-Legendre nodes for the edge integrals of the vector potential.  The
+# discrete divergence of the face field is zero for any order (each edge
+# integral is shared by the faces around it); the order only sets how well
+# the face averages match the analytic curl.
+_GL = {q: np.polynomial.legendre.leggauss(q) for q in (2, 3, 4, 6)}
+_GL_X, _GL_W = _GL[6]
 
 
 @dataclass
@@ -76,9 +80,10 @@ def _face_areas(b: Block):
     return a1, a2, a3
 
 
-def _edge_integrals(b: Block, A):
+def _edge_integrals(b: Block, A, gl=6):
     """Line integrals of the vector potential A(x1, x2, x3) -> (A1, A2, A3)
-    (physical components) along every cell edge."""
+    (physical components) along every cell edge (Gauss-Legendre order gl)."""
+    glx, glw = _GL[gl]
     f = [b.faces(d) for d in range(3)]
     sph = b.coord == SPH
 
@@ -88,8 +93,8 @@ def _edge_integrals(b: Block, A):
         xs = f[d]
         mids = 0.5 * (xs[1:] + xs[:-1])
         half = 0.5 * (xs[1:] - xs[:-1])
-        pts = mids[:, None] + half[:, None] * _GL_X[None, :]       # (n_d, q)
-        wts = half[:, None] * _GL_W[None, :]
+        pts = mids[:, None] + half[:, None] * glx[None, :]         # (n_d, q)
+        wts = half[:, None] * glw[None, :]
         grids = [None, None, None]
         grids[d] = pts[:, :, None, None]
         grids[e1] = f[e1][None, None, :, None]
@@ -111,9 +116,9 @@ def _edge_integrals(b: Block, A):
     return along(0), along(1), along(2)
 
 
-def face_field_from_potential(b: Block, A, B0=(0.0, 0.0, 0.0)):
+def face_field_from_potential(b: Block, A, B0=(0.0, 0.0, 0.0), gl=6):
     """Face-averaged B = B0 + curl A from Stokes' theorem on each face."""
-    I1, I2, I3 = _edge_integrals(b, A)
+    I1, I2, I3 = _edge_integrals(b, A, gl)
     a1, a2, a3 = _face_areas(b)
     b1 = (I3[:, 1:, :] - I3[:, :-1, :] - (I2[1:, :, :] - I2[:-1, :, :])) / a1
     b2 = (I1[1:, :, :] - I1[:-1, :, :] - (I3[:, :, 1:] - I3[:, :, :-1])) / a2
@@ -243,7 +248,7 @@ def _eval_modes(modes, s1, s2, s3):
 
 
 def smooth_random_mhd(block: Block, seed: int, gamma=5.0 / 3.0, kmax=2, nmodes=6,
-                      v_rms=0.5, b_rms=0.5, B0=(0.0, 0.0, 0.0), mhd=True) -> InitialState:
+                      v_rms=0.5, b_rms=0.5, B0=(0.0, 0.0, 0.0), mhd=True, gl=6) -> InitialState:
     """Random smooth state: rho in [0.5, 2], P in [0.1, 1], v and B from
     low-k random fields (B from a vector potential).  Modes are periodic in
     the block's normalised coordinates s = (x - lo)/(hi - lo)."""
@@ -271,7 +276,7 @@ def smooth_random_mhd(block: Block, seed: int, gamma=5.0 / 3.0, kmax=2, nmodes=6
             t1, t2, t3 = nrm(x1, 0), nrm(x2, 1), nrm(x3, 2)
             return tuple(_eval_modes(m, t1, t2, t3) for m in amods)
 
-        b1, b2, b3 = face_field_from_potential(b, A, (0.0, 0.0, 0.0))
+        b1, b2, b3 = face_field_from_potential(b, A, (0.0, 0.0, 0.0), gl)
         bc2 = np.mean((0.5 * (b1[:, :, 1:] + b1[:, :, :-1])) ** 2 +
                       (0.5 * (b2[:, 1:, :] + b2[:, :-1, :])) ** 2 +
                       (0.5 * (b3[1:, :, :] + b3[:-1, :, :])) ** 2)
@@ -447,3 +452,40 @@ def dust_box(block: Block, seed: int, nd=8, gamma=5.0 / 3.0, v_rms=0.5, dv_rms=0
             dust[k, 1 + q] = dust[k, 0] * (vg[q] + dv[q])
     ts = list(t_stop) if t_stop is not None else dust_stopping_times(nd)
     return gas, np.ascontiguousarray(dust), ts
+
+
+# ---------------------------------------------------------------------------
+# batched independent boxes of uneven sizes (512-box configuration)
+# ---------------------------------------------------------------------------
+
+SPH_BOX = dict(lo=(1.0, math.pi / 4, 0.0), hi=(2.0, 3 * math.pi / 4, math.pi / 2))
+
+
+def _one_box(args):
+    b, seed, sizes, sph_every, gamma, nmodes, gl = args
+    rng = np.random.default_rng([seed, b])
+    n = tuple(int(x) for x in rng.choice(sizes, size=3))
+    if sph_every and b % sph_every == sph_every - 1:
+        blk = Block(n, SPH_BOX["lo"], SPH_BOX["hi"], SPH, (OUTFLOW, OUTFLOW, PERIODIC))
+    else:
+        blk = Block(n)
+    return smooth_random_mhd(blk, seed + 1 + b, gamma=gamma, nmodes=nmodes, v_rms=0.5,
+                             b_rms=0.5, gl=gl)
+
+
+def batched_boxes(nblocks: int, seed: int, sizes=(16, 24, 32, 48, 64), sph_every=3,
+                  gamma=5.0 / 3.0, nmodes=4, gl=6, workers=0):
+    """Independent MHD boxes: side lengths drawn uniformly from `sizes` per
+    axis; every `sph_every`-th box (block_id % sph_every == sph_every - 1) is
+    a spherical-polar wedge r in [1,2], theta in [pi/4, 3pi/4], phi in
+    [0, pi/2] (outflow in r and theta, periodic in phi), the others are
+    periodic unit boxes.  Fields: random smooth rho in [0.5, 2], P in
+    [0.1, 1], low-k v and B (B from a vector potential), rms 0.5."""
+    jobs = [(b, seed, tuple(sizes), sph_every, gamma, nmodes, gl) for b in range(nblocks)]
+    if workers and workers > 1:
+        # spawned workers: safe to use before or after CUDA initialisation
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_one_box, jobs, chunksize=4))
+    return [_one_box(j) for j in jobs]

@@ -220,3 +220,18 @@ def test_mixed_cartesian_spherical_blocks():
     outs, _ = gpu_run(sts, dts, "plm", "vl2", "fp64")
     assert max(compare(outs[0], r0)) < FP64_TOL
     assert max(compare(outs[1], r1)) < FP64_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_batched_uneven_blocks_one_launch_per_pass(prec, tol):
+    # the 512-box configuration in miniature: 15 boxes with sides drawn from
+    # {6, 8, 10, 13}, every third one spherical-polar, advanced together
+    sts = I.batched_boxes(15, 20260818, sizes=(6, 8, 10, 13), nmodes=3)
+    r0, dts = oracle_run(sts[0], "plm", "vl2", nsteps=3)
+    refs = [r0] + [oracle_run(s, "plm", "vl2", dts=dts)[0] for s in sts[1:]]
+    outs, diag = gpu_run(sts, dts, "plm", "vl2", prec)
+    for q, (o, r) in enumerate(zip(outs, refs)):
+        errs = compare(o, r)
+        assert max(errs) < tol, (q, sts[q].block.n, sts[q].block.coord, errs)
+    if prec == "fp64":
+        assert diag["max_divb_rel"] < 1e-12
