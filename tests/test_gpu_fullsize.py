@@ -6,8 +6,14 @@ One VL2 step moves information at most 1 (predictor flux) + 1 (EMF ring)
 + 2 (PLM stencil) + 1 (EMF ring) = 5 cells, so a sub-box cut out of the
 periodic input with an 8-cell halo on every side gives the oracle exactly
 the data the GPU used for its centre; the centre is compared element by
-element (relative L1 per variable <= 1e-5, the FP32 bound).  dt comes from
-the oracle's CFL evaluation of the full input.
+element (relative L1 <= 1e-5, the FP32 bound).  dt comes from the oracle's
+CFL evaluation of the full input.
+
+Normalisation: the five conserved variables use their own L1 norm; the face
+field components use the L1 norm of the whole face field (mean over its
+three components), because two of them start at exactly zero in this
+workload (uniform B_x), so their own norm after one step is O(dt) and would
+turn FP32 round-off of the O(1) field into a spurious large ratio.
 """
 import numpy as np
 import pytest
@@ -67,7 +73,8 @@ def test_turbulence_256_fp32_one_step_sampled():
         ref = [s.cons[:, h, h, h], s.b1[h, h, HALO:HALO + m + 1], s.b2[h, HALO:HALO + m + 1, h],
                s.b3[HALO:HALO + m + 1, h, h]]
         errs = [rel_l1(centre[0][v], ref[0][v]) for v in range(5)]
-        errs += [rel_l1(centre[q], ref[q]) for q in (1, 2, 3)]
+        bnorm = sum(np.sum(np.abs(ref[q])) / ref[q].size for q in (1, 2, 3)) / 3
+        errs += [float(np.mean(np.abs(centre[q] - ref[q]))) / bnorm for q in (1, 2, 3)]
         assert max(errs) < 1e-5, (c0, errs)
 
 
