@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turb256", choices=WORKLOADS)
+    ap.add_argument("--drag", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -71,7 +73,8 @@ def workload_config(a):
         return {"workload": "multifluid_dust_128^3_8_species", "grid": [128, 128, 128],
                 "species": 8, "t_stop": "log-spaced 1e-4..1", "integrator": "IMEX2P",
                 "recon": a.recon.upper(), "gas": "adiabatic hydro gamma 5/3, HLLD (=HLLC)",
-                "drag": "closed-form arrowhead, FP64", "precision": a.prec, "seed": 20260817,
+                "drag": f"closed-form arrowhead, {a.drag.upper()}", "precision": a.prec,
+                "seed": 20260817,
                 "l2": "inputs larger than L2 (128^3 x 37 vars x 2 registers)"}
     if a.workload == "wave32":
         return {"workload": "linear_fast_wave_32^3", "grid": [32, 32, 32], "recon": "PLM",
@@ -245,7 +248,8 @@ def main():
         gas, dust, ts = I.dust_box(I.Block((128, 128, 128)), 20260817, nd=8)
         states = [gas]
         cfg = A.make_config(gamma=gas.gamma, recon=rec, integrator=A.IMEX2P, cfl=0.3,
-                            precision=prec, mhd=False, t_stop=ts)
+                            precision=prec, mhd=False, t_stop=ts,
+                            drag_precision=A.FP64 if a.drag == "fp64" else A.FP32)
     elif a.workload == "wave32":
         from paper_2608_14048_gb300 import inputs as I
         states = [I.linear_fast_wave(32)]
@@ -272,6 +276,12 @@ def main():
                 A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]))
 
     upload()
+    kchunk = None
+    if not a.no_autotune and a.workload != "dust128":
+        # tile shape chosen by the autotuner on this workload's own state,
+        # then the state is reloaded (the autotuner advances it)
+        kchunk = A.aeth_autotune(sv.ctx)
+        upload()
     cells = sum(int(np.prod(s_.block.n)) for s_ in states)
     flush = None
     if a.workload == "wave32":
@@ -377,6 +387,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": all_launches,
         "diag_after": {"max_divb_rel": diag["max_divb_rel"], "floor_hits": diag["floor_hits"]},
+        "flux_tile": {"tx": 32, "ty": 8, "kchunk": kchunk, "autotuned": kchunk is not None},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -86,6 +86,8 @@ typedef struct {
   int strict_floors;  /* 1: a floor hit latches AETH_ERR_FLOOR */
   int n_dust;         /* number of pressureless dust species (0: none) */
   const double* t_stop; /* [n_dust] constant stopping times (copied) */
+  int drag_precision; /* AETH_FP64 (default, 0): implicit drag solve in FP64;
+                         AETH_FP32: in FP32 (dust runs only) */
 } aeth_config;
 
 typedef struct {

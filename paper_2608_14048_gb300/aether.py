@@ -52,7 +52,7 @@ class aeth_config(C.Structure):
                 ("p_floor", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
                 ("integrator", C.c_int), ("cfl", C.c_double), ("precision", C.c_int),
                 ("path", C.c_int), ("strict_floors", C.c_int), ("n_dust", C.c_int),
-                ("t_stop", C.POINTER(C.c_double))]
+                ("t_stop", C.POINTER(C.c_double)), ("drag_precision", C.c_int)]
 
 
 class aeth_block_desc(C.Structure):
@@ -267,12 +267,13 @@ def _check(ctx, rc):
 
 def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=FP64, mhd=True,
                 path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
-                riemann=HLLD):
+                riemann=HLLD, drag_precision=FP64):
     cfg = aeth_config()
     cfg.eos = EOS_MHD if mhd else EOS_HYDRO
     cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
     cfg.recon, cfg.riemann, cfg.integrator, cfg.cfl = recon, riemann, integrator, cfl
     cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors
+    cfg.drag_precision = drag_precision
     if t_stop is not None and len(t_stop) > 0:
         arr = (C.c_double * len(t_stop))(*t_stop)
         cfg.n_dust = len(t_stop)

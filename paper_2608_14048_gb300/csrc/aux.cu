@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(256)
          int mhd, double gamma, double rho_floor, double p_floor, int nd,
          double* __restrict__ partial, int* status) {
   __shared__ double sm[8];
-  double m = INFINITY;
+  R m = R(INFINITY);   // running minimum in the working precision
   bool bad = false;
   // one x-row of one block per iteration, threads along x
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(256)
       for (int d = 0; d < 3; ++d) {
         const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
         const R w = P.geo.width[d](i, j, k);
-        double dtd = (double)(w / (fabs(v[d]) + cf));
-        if (!(dtd > 0.0)) bad = true;
+        const R dtd = w / (fabs(v[d]) + cf);
+        if (!(dtd > R(0))) bad = true;
         m = fmin(m, dtd);
       }
       // pressureless dust species: c = 0 (Eq. 11)
@@ -431,13 +431,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const R vk = fabs(P.dust[0][(long long)(4 * s + 1 + d) * sz + c] / rk);
-          if (vk > R(0)) m = fmin(m, (double)(P.geo.width[d](i, j, k) / vk));
+          if (vk > R(0)) m = fmin(m, P.geo.width[d](i, j, k) / vk);
         }
       }
     }
   }
-  m = warp_min(m);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  const double md = warp_min((double)m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = md;
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;

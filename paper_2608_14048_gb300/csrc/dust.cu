@@ -6,6 +6,10 @@
 // implicit drag of every cell in closed form (arrowhead system, O(N) per
 // velocity component) in FP64, whatever the transport precision.
 //
+// The stage combinations run in the working precision; the drag solve runs
+// in FP64 by default (aeth_config.drag_precision) and its few divisions are
+// hoisted: 1/rho_k and 1/(1 + a_k) per species, one 1/den per cell.
+//
 // IMEX2P with implicit weight g = 1 + 1/sqrt 2 and explicit weight
 // d = 1 - 1/(2g) in two registers (A, B):
 //   stage 2: X = U^n + g dt L(U^n), W = U^n + d dt L(U^n), U2 = drag_h(X),
@@ -85,12 +89,13 @@ struct DustUpd {
   R* da;               // dust register A (base)
   R* db;               // dust register B (base)
   const R* df;         // dust fluxes (base)
-  double t_stop[32];
+  double inv_t_stop[32];   // 1 / t_stop
   const double* dt;
   R dfloor;
 };
 
-template <typename R, int NDMAX>
+// Stage combination in the working precision R, implicit drag in DT.
+template <typename R, typename DT, int NDMAX>
 __global__ void __launch_bounds__(256)
     k_dust_update(Layout L, R idx1, R idx2, R idx3, DustUpd<R> A, int nd, int stage,
                   unsigned long long* floor_hits) {
@@ -102,24 +107,18 @@ __global__ void __launch_bounds__(256)
   const long long sz = L.size();
   const long long st[3] = {1, L.sx, L.sx * L.sy};
   const R inv[3] = {idx1, idx2, idx3};
-  const double dt = *A.dt;
-  const double g = kImexG, d = kImexD;
-  // explicit right-hand sides and the stage's pre-drag state
-  double gx[5], gw[5];
-  double dx[NDMAX][4], dw[NDMAX][4];
+  const R dt = (R)(*A.dt);
+  const R g = (R)kImexG, d = (R)kImexD;
+  // explicit right-hand sides and the stage's pre-drag state X
+  R gx[5];
+  R dx[NDMAX][4];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     R div = R(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) div += (A.gf[a][v][c + st[a]] - A.gf[a][v][c]) * inv[a];
-    const double Lv = -(double)div;
-    const double u = A.ga[v][c];
-    if (stage == 2) {
-      gx[v] = u + g * dt * Lv;
-      gw[v] = u + d * dt * Lv;
-    } else {
-      gx[v] = u + (1.0 - d) * dt * Lv;
-    }
+    const R u = A.ga[v][c];
+    gx[v] = u - (stage == 2 ? g : R(1) - d) * dt * div;
   }
 #pragma unroll
   for (int s = 0; s < NDMAX; ++s) {
@@ -132,72 +131,74 @@ __global__ void __launch_bounds__(256)
         const R* f = A.df + (long long)(((a * nd + s) * 4 + q)) * sz;
         div += (f[c + st[a]] - f[c]) * inv[a];
       }
-      const double Lv = -(double)div;
-      const double u = A.da[(long long)(4 * s + q) * sz + c];
-      if (stage == 2) {
-        dx[s][q] = u + g * dt * Lv;
-        dw[s][q] = u + d * dt * Lv;
-      } else {
-        dx[s][q] = u + (1.0 - d) * dt * Lv;
-      }
+      const R u = A.da[(long long)(4 * s + q) * sz + c];
+      dx[s][q] = u - (stage == 2 ? g : R(1) - d) * dt * div;
     }
   }
-  // closed-form implicit drag with h = g dt, per velocity component
-  const double h = g * dt;
-  double gy[5], dy[NDMAX][4];
-  const double rg = gx[0];
-  gy[0] = rg;
-  double ke0 = 0.0, ke1 = 0.0;
+  // closed-form implicit drag with h = g dt (Sec. 2.2).  With
+  // a_k = h / t_k, w_k = a_k / (1 + a_k):
+  //   rho_g v_g' = (M_g* + sum_k w_k M_k*) * rho_g / (rho_g + sum_k rho_k w_k)
+  //   v_k' = (v_k* + a_k v_g') / (1 + a_k)
+  // which needs only 1/rho_k, 1/(1 + a_k) per species and one 1/den.
+  const DT h = (DT)kImexG * (DT)(*A.dt);
+  R gy[5], dy[NDMAX][4];
+  const DT rg = gx[0];
+  gy[0] = gx[0];
+  DT ak[NDMAX], ia[NDMAX], wk[NDMAX], ir[NDMAX];
+  DT den = rg;
 #pragma unroll
   for (int s = 0; s < NDMAX; ++s) {
     if (s >= nd) break;
+    ak[s] = h * (DT)A.inv_t_stop[s];
+    ia[s] = DT(1) / (DT(1) + ak[s]);
+    wk[s] = ak[s] * ia[s];
+    const DT r = dx[s][0];
+    ir[s] = r > DT(0) ? DT(1) / r : DT(0);
+    den += r * wk[s];
     dy[s][0] = dx[s][0];
   }
+  const DT inv_den = DT(1) / den;
+  DT dke = 0;   // change of the dust kinetic energy
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double num = gx[1 + q], den = rg;   // rho_g v_g* = M_g*
+    DT num = gx[1 + q];   // rho_g v_g* = M_g*
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
-      const double a = h / A.t_stop[s];
-      const double w = a / (1.0 + a);
-      const double r = dx[s][0];
-      const double v = r > 0.0 ? dx[s][1 + q] / r : 0.0;
-      num += r * w * v;
-      den += r * w;
+      num += wk[s] * (DT)dx[s][1 + q];   // rho_k w_k v_k* = w_k M_k*
     }
-    const double vg = num / den;
-    gy[1 + q] = rg * vg;
+    const DT vg = num * inv_den;
+    gy[1 + q] = (R)(rg * vg);
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
-      const double a = h / A.t_stop[s];
-      const double r = dx[s][0];
-      const double v0 = r > 0.0 ? dx[s][1 + q] / r : 0.0;
-      const double v1 = (v0 + a * vg) / (1.0 + a);
-      dy[s][1 + q] = r * v1;
-      ke0 += 0.5 * r * v0 * v0;
-      ke1 += 0.5 * r * v1 * v1;
+      const DT r = dx[s][0];
+      const DT v0 = (DT)dx[s][1 + q] * ir[s];
+      const DT v1 = (v0 + ak[s] * vg) * ia[s];
+      dy[s][1 + q] = (R)(r * v1);
+      dke += DT(0.5) * r * (v1 - v0) * (v1 + v0);
     }
   }
   // total energy conserved: drift energy becomes gas heat
-  gy[4] = gx[4] - (ke1 - ke0);
+  gy[4] = (R)((DT)gx[4] - dke);
   int hits = 0;
 #pragma unroll
   for (int s = 0; s < NDMAX; ++s) {
     if (s >= nd) break;
-    if (dy[s][0] < (double)A.dfloor) {
+    if (dy[s][0] < A.dfloor) {
       dy[s][0] = A.dfloor;
-      dy[s][1] = dy[s][2] = dy[s][3] = 0.0;
+      dy[s][1] = dy[s][2] = dy[s][3] = R(0);
       ++hits;
     }
   }
   if (stage == 2) {
-    const double cw = (1.0 - g) / g;
+    // A <- W + (1-g)/g (U2 - X), with W = U^n + d dt L = (1 - d/g) U^n + (d/g) X
+    const R cw = (R(1) - g) / g, cu = R(1) - d / g, cx = d / g;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      A.gb[v][c] = (R)gy[v];
-      A.ga[v][c] = (R)(gw[v] + cw * (gy[v] - gx[v]));
+      const R u = A.ga[v][c];
+      A.gb[v][c] = gy[v];
+      A.ga[v][c] = cu * u + cx * gx[v] + cw * (gy[v] - gx[v]);
     }
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
@@ -205,21 +206,51 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const long long o = (long long)(4 * s + q) * sz + c;
-        A.db[o] = (R)dy[s][q];
-        A.da[o] = (R)(dw[s][q] + cw * (dy[s][q] - dx[s][q]));
+        const R u = A.da[o];
+        A.db[o] = dy[s][q];
+        A.da[o] = cu * u + cx * dx[s][q] + cw * (dy[s][q] - dx[s][q]);
       }
     }
   } else {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) A.ga[v][c] = (R)gy[v];
+    for (int v = 0; v < 5; ++v) A.ga[v][c] = gy[v];
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) A.da[(long long)(4 * s + q) * sz + c] = (R)dy[s][q];
+      for (int q = 0; q < 4; ++q) A.da[(long long)(4 * s + q) * sz + c] = dy[s][q];
     }
   }
   if (hits) atomicAdd(floor_hits, (unsigned long long)hits);
+}
+
+// Ghost fill of n cell-centred arrays at base + a * sz, one axis.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fill_cells(Layout L, R* base, int narr, int d) {
+  const int g = L.g;
+  int lo[3], ext[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e < d) { lo[e] = -g; ext[e] = L.n[e] + 2 * g + 1; }
+    else if (e == d) { lo[e] = 0; ext[e] = 2 * g + 1; }
+    else { lo[e] = 0; ext[e] = L.n[e] + 1; }
+  }
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t1 = blockIdx.y * blockDim.y + threadIdx.y;
+  const int t2 = blockIdx.z * blockDim.z + threadIdx.z;
+  if (t0 >= ext[0] || t1 >= ext[1] || t2 >= ext[2]) return;
+  int c[3] = {t0 + lo[0], t1 + lo[1], t2 + lo[2]};
+  const int n = L.n[d];
+  const int t = c[d];
+  c[d] = t < g ? t - g : n + (t - g);
+  const int p = c[d];
+  int s;
+  if (L.bc[d] == AETH_BC_PERIODIC) s = ((p % n) + n) % n;
+  else s = p < 0 ? 0 : n - 1;
+  int sc[3] = {c[0], c[1], c[2]};
+  sc[d] = s;
+  const long long dst = L.idx(c[0], c[1], c[2]), srcx = L.idx(sc[0], sc[1], sc[2]);
+  const long long sz = L.size();
+  for (int a = 0; a < narr; ++a) base[a * sz + dst] = base[a * sz + srcx];
 }
 
 template <typename R, bool P64>
@@ -232,13 +263,15 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
   launch_fill<R>(P, P.reg[src], 5, s);
   c->n_launch += 3;
   const long long sz = L.size();
-  for (int a0 = 0; a0 < 4 * nd; a0 += 5) {
-    R* arr[5];
-    const int na = std::min(5, 4 * nd - a0);
-    for (int q = 0; q < na; ++q) arr[q] = P.dust[src] + (long long)(a0 + q) * sz;
-    launch_fill<R>(P, arr, na, s);
-    c->n_launch += 3;
+  (void)sz;
+  for (int d = 0; d < 3; ++d) {
+    int ext[3];
+    for (int e = 0; e < 3; ++e)
+      ext[e] = e < d ? L.n[e] + 2 * L.g + 1 : (e == d ? 2 * L.g + 1 : L.n[e] + 1);
+    dim3 fb(32, 4, 2), fg((ext[0] + 31) / 32, (ext[1] + 3) / 4, (ext[2] + 1) / 2);
+    k_fill_cells<R><<<fg, fb, 0, s>>>(L, P.dust[src], 4 * nd, d);
   }
+  c->n_launch += 3;
   hydro_flux_pass<R, P64>(c, b, c->cfg.recon, src);
   dim3 blk(32, 4, 2);
   dim3 grd((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 3) / 4, (L.n[2] + 1 + 1) / 2);
@@ -269,7 +302,7 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
   u.da = P.dust[0];
   u.db = P.dust[1];
   u.df = P.dflux;
-  for (int q = 0; q < nd; ++q) u.t_stop[q] = c->t_stop[q];
+  for (int q = 0; q < nd; ++q) u.inv_t_stop[q] = 1.0 / c->t_stop[q];
   u.dt = c->d_dt;
   u.dfloor = dfl;
   // inverse cell widths (Cartesian: area / volume = 1 / dx_d)
@@ -277,10 +310,14 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
   const R i2 = (R)(B.desc.ny / (B.desc.x2max - B.desc.x2min));
   const R i3 = (R)(B.desc.nz / (B.desc.x3max - B.desc.x3min));
   dim3 grd2((L.n[0] + 31) / 32, (L.n[1] + 3) / 4, (L.n[2] + 1) / 2);
-  if (nd <= 8)
-    k_dust_update<R, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
-  else
-    k_dust_update<R, 32><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+  const bool d64 = c->cfg.drag_precision == AETH_FP64;
+  if (nd <= 8) {
+    if (d64) k_dust_update<R, double, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+    else k_dust_update<R, R, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+  } else {
+    if (d64) k_dust_update<R, double, 32><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+    else k_dust_update<R, R, 32><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+  }
   c->n_launch += 3 + 1;
 }
 

@@ -402,7 +402,9 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
   }
 }
 
-template <typename R, bool P64, bool MHD, typename Src>
+// COORD: 0 every block Cartesian, 1 every block spherical, 2 mixed (the
+// coordinate system is then read per tile).
+template <typename R, bool P64, bool MHD, int COORD, typename Src>
 __global__ void __launch_bounds__(256)
     k_update_f(Src S, int t0, int t1, int src, int out, R w0, R w1, R beta,
                const double* __restrict__ dt, R gamma, R rho_floor, R p_floor) {
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(256)
     const BlockPtrs<R>& B = S.get(t, loc);
     const CellTile ct = cell_tile(B, loc, add);
     if (ct.P[0] > B.L.n[0] || ct.P[1] > B.L.n[1] || ct.P[2] > B.L.n[2]) continue;
-    if (B.L.coord == AETH_COORD_SPH)
+    if (COORD == 1 || (COORD == 2 && B.L.coord == AETH_COORD_SPH))
       update_cell<R, P64, MHD, true>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor);
     else
       update_cell<R, P64, MHD, false>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor);
@@ -548,11 +550,22 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
   prof_begin(c);
   flux_pass<R, P64, MHD>(c, recon, src, -1);
   prof_end(c, flux_algo_bytes(c, MHD));
+  int nsph = 0;
+  for (const auto& B : c->blocks) nsph += B.L.coord == AETH_COORD_SPH;
+  const int mode = nsph == 0 ? 0 : (nsph == (int)c->blocks.size() ? 1 : 2);
   with_src<R>(c, PK_CELL, -1, [&](auto S, TileRange r) {
     if (MHD) k_emf_ref<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1);
-    k_update_f<R, P64, MHD><<<r.t1 - r.t0, 256, 0, c->stream>>>(
-        S, r.t0, r.t1, src, out, w0, w1, beta, c->d_dt, (R)c->cfg.gamma, (R)c->cfg.rho_floor,
-        (R)c->cfg.p_floor);
+    const R g = (R)c->cfg.gamma, rf = (R)c->cfg.rho_floor, pf = (R)c->cfg.p_floor;
+    const int n = r.t1 - r.t0;
+    if (mode == 0)
+      k_update_f<R, P64, MHD, 0><<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta,
+                                                          c->d_dt, g, rf, pf);
+    else if (mode == 1)
+      k_update_f<R, P64, MHD, 1><<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta,
+                                                          c->d_dt, g, rf, pf);
+    else
+      k_update_f<R, P64, MHD, 2><<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta,
+                                                          c->d_dt, g, rf, pf);
   });
   c->n_launch += MHD ? 2 : 1;
 }

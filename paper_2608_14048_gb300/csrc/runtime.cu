@@ -59,6 +59,7 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (cfg->path != AETH_PATH_FUSED && cfg->path != AETH_PATH_UNFUSED) bad = AETH_ERR_ARG;
   if (cfg->n_dust < 0 || cfg->n_dust > 32) bad = AETH_ERR_ARG;
   if (cfg->n_dust > 0 && !cfg->t_stop) bad = AETH_ERR_ARG;
+  if (cfg->drag_precision != AETH_FP64 && cfg->drag_precision != AETH_FP32) bad = AETH_ERR_ARG;
   if (bad != AETH_OK) {
     delete c;
     return bad;

@@ -91,3 +91,30 @@ def test_dust_cfl_and_device_run():
     b = gas.block
     dt_ref = O.dust_dt(O.make_grid(b.n), O.make_params(mhd=False), O.make_dust_params(ts), rc, rd)
     assert abs(dt_dev - dt_ref) <= 1e-13 * dt_ref
+
+
+def test_dust_fp32_drag_against_fp64_oracle():
+    # is FP64 needed for the drag solve at the smallest stopping times? The
+    # closed form sums positive weights only, so FP32 drag is expected to stay
+    # inside the FP32 bound on the stiff 8-species case.
+    import torch
+    gas, dust, ts = I.dust_box(I.Block((16, 16, 16)), 84, nd=8)
+    rc, rd, dts = _oracle(gas, dust, ts, 3)
+    cfg = A.make_config(gamma=gas.gamma, recon=A.PLM, integrator=A.IMEX2P, precision=A.FP32,
+                        mhd=False, t_stop=ts, drag_precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block(gas.block.n)], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, gas.cons)
+        for k in range(8):
+            A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]))
+        for dt in dts:
+            sv.step(dt)
+        cons = sv.get_state(0)[0]
+        d = np.empty_like(dust)
+        for k in range(8):
+            buf = np.empty(dust.shape[1:])
+            A.aeth_get_dust(sv.ctx, 0, k, buf)
+            d[k] = buf
+    finally:
+        sv.close()
+    assert max(_errs(cons, d, rc, rd)) < 1e-5
