@@ -249,3 +249,33 @@ def dust_step(grid, params, dparams, dt, cons, dust) -> int:
 
 def dust_dt(grid, params, dparams, cons, dust) -> float:
     return lib().orc_dust_dt(C.byref(grid), C.byref(params), C.byref(dparams), _dp(cons), _dp(dust))
+
+
+# ---- learned-flux MLP reference (mlp.c) --------------------------------
+
+def mlp_forward(dims, params, x):
+    """FP64 forward pass; x[n][dims[0]] -> y[n][dims[-1]]."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    y = np.zeros((n, dims[-1]))
+    lib().orc_mlp_forward(len(dims) - 1, d.ctypes.data_as(C.POINTER(C.c_int)), _dp(p), n,
+                          _dp(x), _dp(y))
+    return y
+
+
+def mlp_grad(dims, params, x, target):
+    """(loss, gradient) of 0.5/n sum |y - t|^2 by backpropagation."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    g = np.zeros_like(p)
+    loss = lib().orc_mlp_grad(len(dims) - 1, d.ctypes.data_as(C.POINTER(C.c_int)), _dp(p),
+                              x.shape[0], _dp(x), _dp(t), _dp(g))
+    return loss, g
+
+
+def mlp_param_count(dims):
+    return sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(len(dims) - 1))
