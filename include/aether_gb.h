@@ -88,6 +88,8 @@ typedef struct {
   const double* t_stop; /* [n_dust] constant stopping times (copied) */
   int drag_precision; /* AETH_FP64 (default, 0): implicit drag solve in FP64;
                          AETH_FP32: in FP32 (dust runs only) */
+  double mlp_tau;     /* learned flux: residual-check tolerance (fraction of the
+                         HLL dissipation bracket); <= 0 selects 0.25 */
 } aeth_config;
 
 typedef struct {
@@ -177,10 +179,47 @@ aeth_status aeth_set_dust(aeth_ctx* ctx, int block, int k,
                           const double* rho_mom);
 aeth_status aeth_get_dust(aeth_ctx* ctx, int block, int k, double* rho_mom);
 
-/* Load the learned-flux network (14 inputs, 3 hidden layers of 128 with
- * SiLU, 7 outputs; FP32 weights, converted to BF16 on the device).  Layout:
- * per layer l, W_l[out][in] then b_l[out]; n = total floats. */
+/* Learned Riemann flux (no counterpart in the paper, which solves every face
+ * with HLLD): a 14 -> 128 -> 128 -> 128 -> 7 MLP with SiLU hidden layers.
+ * Inputs: the face-frame left/right primitive states and the normal field,
+ * divided by rho_L and c = max(c_f,L, c_f,R) (rho_L = 1 dropped, zero-padded
+ * to 16); outputs: the 7 face fluxes divided by rho_L c, rho_L c^2 (x3),
+ * rho_L c^3 gamma/(gamma-1), sqrt(rho_L) c^2 (x2).  Parameter layout (FP32): per layer l,
+ * W_l[out][in] row-major then b_l[out]; 52103 floats in all.
+ *
+ * aeth_load_mlp: copy the network to the device (BF16 weights, FP32 biases;
+ * the library allocates ~75 KB).  With config riemann = AETH_RIEMANN_MLP the
+ * step evaluates it on the tensor cores for every face and falls back to
+ * HLLD on faces failing the residual check against HLLE (tolerance
+ * mlp_tau) or the positivity of the implied intermediate states; fallbacks
+ * are counted in aeth_diag.mlp_fallbacks.  FP32/FP32_P64 gas runs only. */
 aeth_status aeth_load_mlp(aeth_ctx* ctx, const float* params, size_t n);
+
+/* Tensor-core forward pass of the loaded network on n dimensionless feature
+ * rows (device d_X [n][16]) into device d_Y [n][8].  Asynchronous. */
+aeth_status aeth_mlp_infer(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
+
+/* Training data from the solver itself: for every stride-th interior cell of
+ * every block, the PLM states of its three lower faces (dimensionless
+ * features, 16 floats per sample, device array d_X) and their HLLD fluxes
+ * (dimensionless, 8 floats per sample, last one zero, d_Y).  At most
+ * `capacity` samples are written; *n_out receives the count.  Synchronous. */
+aeth_status aeth_mlp_collect(aeth_ctx* ctx, int stride, float* d_X, float* d_Y,
+                             long long capacity, long long* n_out);
+
+/* Training kernels (caller-owned device buffers, enqueued on cuda_stream):
+ * aeth_mlp_grad: loss 0.5/n sum |y - t|^2 (device float *d_loss) and its
+ * gradient (d_grad, same layout as the parameters) by backpropagation over
+ * n samples (d_X [n][16], d_Y [n][8]); d_work holds aeth_mlp_work_floats(n)
+ * floats.  aeth_mlp_adam: one Adam update of n parameters (step >= 1). */
+aeth_status aeth_mlp_work_floats(int n, size_t* work_floats);
+aeth_status aeth_mlp_grad(const float* d_params, const float* d_X,
+                          const float* d_Y, int n, float* d_grad, float* d_work,
+                          size_t work_floats, float* d_loss, void* cuda_stream);
+aeth_status aeth_mlp_adam(float* d_params, const float* d_grad, float* d_m,
+                          float* d_v, long long n, int step, float lr,
+                          float beta1, float beta2, float eps,
+                          void* cuda_stream);
 
 /* Kernel timing for roofline measurements (no counterpart in the paper; the
  * paper times whole cycles only).  enable = 1: every later aeth_step /

@@ -36,7 +36,8 @@ FUSED, UNFUSED = 0, 1
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
            "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
-           "aeth_load_mlp", "aeth_profile", "aeth_profile_read", "aeth_autotune",
+           "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
+           "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
            "aeth_cfl_dt_noalloc",
            "aeth_last_error", "aeth_destroy"]
 
@@ -52,7 +53,8 @@ class aeth_config(C.Structure):
                 ("p_floor", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
                 ("integrator", C.c_int), ("cfl", C.c_double), ("precision", C.c_int),
                 ("path", C.c_int), ("strict_floors", C.c_int), ("n_dust", C.c_int),
-                ("t_stop", C.POINTER(C.c_double)), ("drag_precision", C.c_int)]
+                ("t_stop", C.POINTER(C.c_double)), ("drag_precision", C.c_int),
+                ("mlp_tau", C.c_double)]
 
 
 class aeth_block_desc(C.Structure):
@@ -98,6 +100,12 @@ def load_library(path: str = LIB_PATH):
         "aeth_set_dust": ([P, C.c_int, C.c_int, P], C.c_int),
         "aeth_get_dust": ([P, C.c_int, C.c_int, P], C.c_int),
         "aeth_load_mlp": ([P, P, C.c_size_t], C.c_int),
+        "aeth_mlp_infer": ([P, P, P, C.c_int], C.c_int),
+        "aeth_mlp_collect": ([P, C.c_int, P, P, C.c_longlong, C.POINTER(C.c_longlong)], C.c_int),
+        "aeth_mlp_work_floats": ([C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "aeth_mlp_grad": ([P, P, P, C.c_int, P, P, C.c_size_t, P, P], C.c_int),
+        "aeth_mlp_adam": ([P, P, P, P, C.c_longlong, C.c_int, C.c_float, C.c_float, C.c_float,
+                           C.c_float, P], C.c_int),
         "aeth_profile": ([P, C.c_int], C.c_int),
         "aeth_profile_read": ([P, dp, C.POINTER(C.c_longlong), dp, C.POINTER(C.c_longlong)],
                               C.c_int),
@@ -210,6 +218,42 @@ def aeth_load_mlp(ctx, params: np.ndarray):
     _check(ctx, load_library().aeth_load_mlp(ctx, p.ctypes.data_as(C.c_void_p), p.size))
 
 
+MLP_DIMS = [14, 128, 128, 128, 7]
+MLP_NPARAM = sum(MLP_DIMS[l + 1] * MLP_DIMS[l] + MLP_DIMS[l + 1] for l in range(4))
+
+
+def aeth_mlp_infer(ctx, d_X: int, d_Y: int, n: int):
+    _check(ctx, load_library().aeth_mlp_infer(ctx, C.c_void_p(d_X), C.c_void_p(d_Y), int(n)))
+
+
+def aeth_mlp_collect(ctx, stride: int, d_X: int, d_Y: int, capacity: int) -> int:
+    n = C.c_longlong(0)
+    _check(ctx, load_library().aeth_mlp_collect(ctx, int(stride), C.c_void_p(d_X), C.c_void_p(d_Y),
+                                                int(capacity), C.byref(n)))
+    return n.value
+
+
+def aeth_mlp_work_floats(n: int) -> int:
+    w = C.c_size_t(0)
+    _check(None, load_library().aeth_mlp_work_floats(int(n), C.byref(w)))
+    return w.value
+
+
+def aeth_mlp_grad(d_params, d_X, d_Y, n, d_grad, d_work, work_floats, d_loss, stream=0):
+    _check(None, load_library().aeth_mlp_grad(C.c_void_p(d_params), C.c_void_p(d_X),
+                                              C.c_void_p(d_Y), int(n), C.c_void_p(d_grad),
+                                              C.c_void_p(d_work), int(work_floats),
+                                              C.c_void_p(d_loss), C.c_void_p(stream)))
+
+
+def aeth_mlp_adam(d_params, d_grad, d_m, d_v, n, step, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                  stream=0):
+    _check(None, load_library().aeth_mlp_adam(C.c_void_p(d_params), C.c_void_p(d_grad),
+                                              C.c_void_p(d_m), C.c_void_p(d_v), int(n), int(step),
+                                              float(lr), float(beta1), float(beta2), float(eps),
+                                              C.c_void_p(stream)))
+
+
 def aeth_profile(ctx, enable: bool):
     _check(ctx, load_library().aeth_profile(ctx, 1 if enable else 0))
 
@@ -267,13 +311,14 @@ def _check(ctx, rc):
 
 def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=FP64, mhd=True,
                 path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
-                riemann=HLLD, drag_precision=FP64):
+                riemann=HLLD, drag_precision=FP64, mlp_tau=0.0):
     cfg = aeth_config()
     cfg.eos = EOS_MHD if mhd else EOS_HYDRO
     cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
     cfg.recon, cfg.riemann, cfg.integrator, cfg.cfl = recon, riemann, integrator, cfl
     cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors
     cfg.drag_precision = drag_precision
+    cfg.mlp_tau = mlp_tau
     if t_stop is not None and len(t_stop) > 0:
         arr = (C.c_double * len(t_stop))(*t_stop)
         cfg.n_dust = len(t_stop)

@@ -37,6 +37,7 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
     for (int r = 0; r < 2; ++r) P.dust[r] = (R*)(c->arena + B.off_dust[r]);
     P.dflux = (R*)(c->arena + B.off_dflux);
   }
+  if (c->cfg.riemann == AETH_RIEMANN_MLP) P.fstate = (R*)(c->arena + B.off_fstate);
   // geometry tables: 12 separable factors x 3 axes
   const R* t = (const R*)(c->arena + B.off_geo);
   const int g = B.L.g;

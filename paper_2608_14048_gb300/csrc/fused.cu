@@ -19,6 +19,7 @@
 //  3. k_update_f: finite-volume update (Eq. 8, curvilinear sources of
 //     Eq. 12) and constrained transport (Eq. 9) with the stage combination.
 #include "runtime.hpp"
+#include "stage.cuh"
 
 namespace aeth {
 
@@ -64,66 +65,6 @@ struct FluxOut {
   R* eref[3];
 };
 
-// Primitive variables of cell (i,j,k) (Eq. 5 with the floors of Sec. 2.1):
-// w = (rho, v1, v2, v3, p, Bc1, Bc2, Bc3).  Returns the number of floors hit.
-template <typename R, bool P64, bool MHD>
-__device__ __forceinline__ int prim_cell(const Layout& L, const ConstArr8<R>& u, long long c,
-                                         R gm1, R rho_floor, R p_floor, R* w) {
-  int hits = 0;
-  R rho = u.p[0][c];
-  if (rho < rho_floor) { rho = rho_floor; ++hits; }
-  const R ir = R(1) / rho;
-  const R v1 = u.p[1][c] * ir, v2 = u.p[2][c] * ir, v3 = u.p[3][c] * ir;
-  R b1 = 0, b2 = 0, b3 = 0;
-  if (MHD) {
-    b1 = R(0.5) * (u.p[5][c] + u.p[5][c + 1]);
-    b2 = R(0.5) * (u.p[6][c] + u.p[6][c + L.sx]);
-    b3 = R(0.5) * (u.p[7][c] + u.p[7][c + L.sx * L.sy]);
-  }
-  R pr;
-  if (P64) {
-    const double m1 = u.p[1][c], m2 = u.p[2][c], m3 = u.p[3][c];
-    const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / (double)rho;
-    const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
-    pr = (R)((double)gm1 * ((double)u.p[4][c] - ke - me));
-  } else {
-    pr = gm1 * (u.p[4][c] - R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3) -
-                R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3));
-  }
-  if (pr < p_floor) { pr = p_floor; ++hits; }
-  w[0] = rho; w[1] = v1; w[2] = v2; w[3] = v3; w[4] = pr; w[5] = b1; w[6] = b2; w[7] = b3;
-  return hits;
-}
-
-// Same, with the 8 state arrays at base + v * pitch.
-template <typename R, bool P64, bool MHD>
-__device__ __forceinline__ int prim_cell_s(const Layout& L, const R* __restrict__ base,
-                                           long long pitch, long long c, R gm1, R rho_floor,
-                                           R p_floor, R* w) {
-  ConstArr8<R> u;
-#pragma unroll
-  for (int v = 0; v < NVAR; ++v) u.p[v] = base + v * pitch;
-  return prim_cell<R, P64, MHD>(L, u, c, gm1, rho_floor, p_floor, w);
-}
-
-__device__ __forceinline__ bool in_prim_range(const Layout& L, int i, int j, int k) {
-  return i >= -L.g && i < L.n[0] + L.g && j >= -L.g && j < L.n[1] + L.g && k >= -L.g &&
-         k < L.n[2] + L.g;
-}
-
-// Reconstruct face states of one variable from a stencil with stride.
-template <int RECON, typename R, typename Get>
-__device__ __forceinline__ void recon_var(Get get, R& wl, R& wr) {
-  constexpr int RL = RECON + 1;
-  R s[6];
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    const int off = t - 3;   // cell offset from the face's right cell
-    s[t] = (off >= -RL && off <= RECON) ? get(off) : R(0);
-  }
-  recon_face<RECON>(s, wl, wr);
-}
-
 // Store the outputs of one face of direction D.  Scratch arrays sit at
 // sb + slot * pitch: E_ref 0..2, fluxes 8 + 5 D + v, face EMFs 23 + 2 D + q.
 template <int D, typename R>
@@ -145,7 +86,9 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // 1. flux pass.  Persistent: CTAs stride over the tiles of all blocks.
 //    Two CTAs per SM in FP32 (<= 128 registers); FP64 takes the full file.
 // ------------------------------------------------------------------------
-template <typename R, bool P64, int RECON, bool MHD, typename Src>
+// SOLVER 0: HLLD; 1: write the face states (wl, wr, bn) for the learned
+// flux instead of solving.
+template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits) {
@@ -227,8 +170,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1)
           recon_var<RECON>([&](int off) { return sw[slot[v]][sy][sx + off]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[5 * pitch + fc] : R(0);
-        hlld(gamma, wl, wr, bn, fx);
-        store_face<0>(sb, pitch, fc, fx);
+        if (SOLVER == 0) {
+          hlld(gamma, wl, wr, bn, fx);
+          store_face<0>(sb, pitch, fc, fx);
+        } else {
+          R* fs = P.fstate + (0 * 15) * pitch + fc;
+#pragma unroll
+          for (int v = 0; v < 7; ++v) { fs[v * pitch] = wl[v]; fs[(7 + v) * pitch] = wr[v]; }
+          fs[14 * pitch] = bn;
+        }
       }
       // ---- y-face (i, j-1/2, k): frame (rho, vy, vz, vx, p, Bz, Bx)
       if (j >= 0) {
@@ -239,8 +189,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1)
           recon_var<RECON>([&](int off) { return sw[slot[v]][sy + off][sx]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[6 * pitch + fc] : R(0);
-        hlld(gamma, wl, wr, bn, fx);
-        store_face<1>(sb, pitch, fc, fx);
+        if (SOLVER == 0) {
+          hlld(gamma, wl, wr, bn, fx);
+          store_face<1>(sb, pitch, fc, fx);
+        } else {
+          R* fs = P.fstate + (1 * 15) * pitch + fc;
+#pragma unroll
+          for (int v = 0; v < 7; ++v) { fs[v * pitch] = wl[v]; fs[(7 + v) * pitch] = wr[v]; }
+          fs[14 * pitch] = bn;
+        }
       }
       // ---- z-face (i, j, k-1/2): frame (rho, vz, vx, vy, p, Bx, By)
       if (k >= 0) {
@@ -250,8 +207,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1)
           recon_var<RECON>([&](int off) { return q[v][off + RL]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[7 * pitch + fc] : R(0);
-        hlld(gamma, wl, wr, bn, fx);
-        store_face<2>(sb, pitch, fc, fx);
+        if (SOLVER == 0) {
+          hlld(gamma, wl, wr, bn, fx);
+          store_face<2>(sb, pitch, fc, fx);
+        } else {
+          R* fs = P.fstate + (2 * 15) * pitch + fc;
+#pragma unroll
+          for (int v = 0; v < 7; ++v) { fs[v * pitch] = wl[v]; fs[(7 + v) * pitch] = wr[v]; }
+          fs[14 * pitch] = bn;
+        }
       }
       // ---- cell-centred reference EMF, E = -v x B
       if (MHD) {
@@ -516,20 +480,36 @@ static void launch_fill_all(aeth_ctx* c, int reg, int nv, int block) {
   c->n_launch += 3;
 }
 
-template <typename R, bool P64, int RECON, bool MHD>
+template <typename R, bool P64, int RECON, bool MHD, int SOLVER = 0>
 static void launch_flux3(aeth_ctx* c, int src, int block) {
   const int per_sm = sizeof(R) == 4 ? 2 : 1;
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
-    k_flux3<R, P64, RECON, MHD><<<grid, NT, 0, c->stream>>>(
+    k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER><<<grid, NT, 0, c->stream>>>(
         S, r.t0, r.t1, src, (R)c->cfg.gamma, (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk,
         c->d_floor);
   });
   c->n_launch += 1;
 }
 
+template <typename R>
+void mlp_flux_pass(aeth_ctx* c, int block);
+
 template <typename R, bool P64, bool MHD>
 static void flux_pass(aeth_ctx* c, int recon, int src, int block) {
+  if (c->cfg.riemann == AETH_RIEMANN_MLP && c->d_mlp) {
+    // learned flux: dump the face states, then the tensor-core network
+    // (with HLLD fallback) solves them block by block
+    if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD, 1>(c, src, block);
+    else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD, 1>(c, src, block);
+    else launch_flux3<R, P64, 2, MHD, 1>(c, src, block);
+    if (block >= 0) {
+      mlp_flux_pass<R>(c, block);
+    } else {
+      for (int b = 0; b < (int)c->blocks.size(); ++b) mlp_flux_pass<R>(c, b);
+    }
+    return;
+  }
   if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD>(c, src, block);
   else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD>(c, src, block);
   else launch_flux3<R, P64, 2, MHD>(c, src, block);
@@ -573,6 +553,8 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
 template <typename R, bool P64, bool MHD>
 static aeth_status step_fused_T(aeth_ctx* c) {
   const int recon = c->cfg.recon;
+  if (c->cfg.riemann == AETH_RIEMANN_MLP && !c->d_mlp)
+    return fail(c, AETH_ERR_STATE, "learned flux selected: call aeth_load_mlp first");
   if (c->cfg.integrator == AETH_INT_VL2) {
     // predictor: U^{n+1/2} = U^n - dt/2 L_donor(U^n)   (register A -> B)
     stage_fused<R, P64, MHD>(c, AETH_RECON_DONOR, 0, R(1), R(0), R(0.5), 1);

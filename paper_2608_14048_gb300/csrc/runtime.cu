@@ -77,6 +77,10 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
     delete c;
     return AETH_ERR_UNSUPPORTED;
   }
+  if (cfg->riemann == AETH_RIEMANN_MLP && (cfg->precision == AETH_FP64 || cfg->n_dust > 0)) {
+    delete c;
+    return AETH_ERR_UNSUPPORTED;   // the learned flux runs with FP32 states, gas only
+  }
   c->elem = cfg->precision == AETH_FP64 ? 8 : 4;
   c->g = ghost_width(cfg->recon);
   *out = c;
@@ -168,6 +172,10 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
       }
       B.off_dflux = off;
       off += align256((size_t)12 * c->cfg.n_dust * sz * c->elem);
+    }
+    if (c->cfg.riemann == AETH_RIEMANN_MLP) {
+      B.off_fstate = off;
+      off += 45 * arr;
     }
     B.geo_len = geometry_len(B.L);
     B.off_geo = off;

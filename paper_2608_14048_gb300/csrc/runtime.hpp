@@ -24,6 +24,7 @@ struct BlockPtrs {
   R* edge[3];          // corner EMFs by component
   R* dust[2];          // dust registers: [species][4] arrays each (IMEX2P)
   R* dflux;            // dust fluxes: [direction][species][4] arrays
+  R* fstate;           // learned flux: face states [direction][wl 7, wr 7, bn]
   long long pitch;     // elements between consecutive arrays of a register
                        // and of the scratch (w, f, e, edge in that order)
 };
@@ -37,6 +38,7 @@ struct BlockInfo {
   size_t off_geo;         // geometry tables (R)
   size_t off_dust[2];     // dust registers (n_dust * 4 arrays each)
   size_t off_dflux;       // dust face fluxes [3][n_dust][4] arrays
+  size_t off_fstate;      // learned flux: face states [3][15] arrays
   size_t geo_len;         // number of R entries in the geometry tables
   int dt_blocks;          // CUDA blocks of this block's dt/diag reductions
   int dt_offset;          // their first slot in the partials array

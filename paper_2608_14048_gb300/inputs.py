@@ -489,3 +489,22 @@ def batched_boxes(nblocks: int, seed: int, sizes=(16, 24, 32, 48, 64), sph_every
         with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
             return list(ex.map(_one_box, jobs, chunksize=4))
     return [_one_box(j) for j in jobs]
+
+
+# ---------------------------------------------------------------------------
+# learned-flux network: seeded initial parameters
+# ---------------------------------------------------------------------------
+
+MLP_DIMS = (14, 128, 128, 128, 7)
+
+
+def mlp_init_params(seed: int, dims=MLP_DIMS, bias_scale=0.0):
+    """Layer-wise N(0, 1/fan_in) weights and (optionally small) biases,
+    packed per layer as W[out][in] then b[out] (FP32)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l in range(len(dims) - 1):
+        nin, nout = dims[l], dims[l + 1]
+        parts.append(rng.normal(size=(nout, nin)) / math.sqrt(nin))
+        parts.append(rng.normal(size=nout) * bias_scale)
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)

@@ -1,0 +1,162 @@
+"""Learned Riemann flux on the GPU against the FP64 references.
+
+* Gradients of the project's FP32 training kernels equal the FP64
+  backpropagation of the oracle (relative L2 1e-4: FP32 accumulation over
+  <= 128-wide sums and 96 samples).
+* The BF16 tensor-core forward pass equals the FP64 forward within the BF16
+  bound: 8 significant bits (rounding 2^-9 ~ 2e-3) applied to the inputs,
+  weights and three hidden activations gives a few 1e-3 relative error per
+  output; the test allows 2e-2 of the output scale.
+* A network trained on the solver's own interface states (HLLD targets)
+  replaces HLLD on most faces, keeps div B at round-off and conserves mass,
+  and stays close to the FP64 HLLD oracle; an untrained network is rejected
+  by the checks on nearly every face.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_14048_gb300 import aether as A
+from paper_2608_14048_gb300 import inputs as I
+from tests.gpu_helpers import oracle_run, rel_l1
+
+pytestmark = pytest.mark.gpu
+DIMS = list(I.MLP_DIMS)
+
+
+def _t(x, dtype=None):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dtype or torch.float32).cuda()
+
+
+def test_training_gradients_match_fp64_backprop():
+    import torch
+    rng = np.random.default_rng(5)
+    p = I.mlp_init_params(11, bias_scale=0.1)
+    n = 96
+    X = np.zeros((n, 16), np.float32); X[:, :14] = rng.normal(size=(n, 14))
+    Y = np.zeros((n, 8), np.float32); Y[:, :7] = rng.normal(size=(n, 7))
+    dp, dX, dY = _t(p), _t(X), _t(Y)
+    grad = torch.zeros_like(dp)
+    wf = A.aeth_mlp_work_floats(n)
+    work = torch.zeros(wf, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    A.aeth_mlp_grad(dp.data_ptr(), dX.data_ptr(), dY.data_ptr(), n, grad.data_ptr(),
+                    work.data_ptr(), wf, loss.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    l_ref, g_ref = O.mlp_grad(DIMS, p.astype(np.float64), X[:, :14].astype(np.float64),
+                              Y[:, :7].astype(np.float64))
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - l_ref) <= 1e-5 * abs(l_ref)
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+
+
+def _solver_mlp(n=(8, 8, 8), tau=0.0):
+    import torch
+    cfg = A.make_config(precision=A.FP32, riemann=A.MLP, mlp_tau=tau)
+    return A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+
+
+def test_bf16_tensor_core_forward_matches_fp64():
+    import torch
+    rng = np.random.default_rng(6)
+    p = I.mlp_init_params(12, bias_scale=0.1)
+    n = 1000   # not a multiple of 32: ragged last warp
+    X = np.zeros((n, 16), np.float32); X[:, :14] = rng.normal(size=(n, 14))
+    sv = _solver_mlp()
+    try:
+        A.aeth_load_mlp(sv.ctx, p)
+        dX = _t(X)
+        dY = torch.zeros((n, 8), dtype=torch.float32, device="cuda")
+        A.aeth_mlp_infer(sv.ctx, dX.data_ptr(), dY.data_ptr(), n)
+        torch.cuda.synchronize()
+        y = dY.cpu().numpy()
+    finally:
+        sv.close()
+    ref = O.mlp_forward(DIMS, p.astype(np.float64), X[:, :14].astype(np.float64))
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(y[:, :7] - ref)) <= 2e-2 * scale, np.max(np.abs(y[:, :7] - ref)) / scale
+    assert np.all(y[:, 7] == y[0, 7])   # padded output row carries only its bias (zero)
+
+
+def _train(samples_X, samples_Y, steps=4000, batch=8192, lr=2e-3, seed=13):
+    import math
+    import torch
+    p = _t(I.mlp_init_params(seed))
+    m = torch.zeros_like(p); v = torch.zeros_like(p); g = torch.zeros_like(p)
+    wf = A.aeth_mlp_work_floats(batch)
+    work = torch.zeros(wf, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda"); gen.manual_seed(seed)
+    N = samples_X.shape[0]
+    st = torch.cuda.current_stream().cuda_stream
+    losses = []
+    for it in range(1, steps + 1):
+        idx = torch.randint(0, N, (batch,), device="cuda", generator=gen)
+        xb = samples_X[idx].contiguous(); yb = samples_Y[idx].contiguous()
+        A.aeth_mlp_grad(p.data_ptr(), xb.data_ptr(), yb.data_ptr(), batch, g.data_ptr(),
+                        work.data_ptr(), wf, loss.data_ptr(), st)
+        lr_t = 5e-5 + 0.5 * (lr - 5e-5) * (1 + math.cos(math.pi * it / steps))   # cosine decay
+        A.aeth_mlp_adam(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), it,
+                        lr_t, stream=st)
+        if it == 1 or it % 1000 == 0:
+            torch.cuda.synchronize()
+            losses.append(loss.item())
+    return p.cpu().numpy(), losses
+
+
+@pytest.mark.slow
+def test_trained_network_replaces_hlld_on_most_faces():
+    import torch
+    n = 32
+    st = I.turbulence_box(n=n, seed=20260819, mach=2.0, beta=1.0, gamma=1.0001)
+    # interface states of the solver itself (HLLD path), a few steps apart
+    cfg = A.make_config(gamma=st.gamma, precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+    cap = 3 * n ** 3 * 4
+    X = torch.zeros((cap, 16), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")
+    got = 0
+    try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        for _ in range(4):
+            k = A.aeth_mlp_collect(sv.ctx, 1, X[got:].data_ptr(), Y[got:].data_ptr(), cap - got)
+            got += k
+            sv.run(3)
+    finally:
+        sv.close()
+    X, Y = X[:got], Y[:got]
+    params, losses = _train(X, Y)
+    print("samples", got, "losses", losses)
+    assert losses[-1] < 0.1 * losses[0]
+
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)
+
+    def run(p, tau=0.0):
+        cfg2 = A.make_config(gamma=st.gamma, precision=A.FP32, riemann=A.MLP, mlp_tau=tau)
+        s2 = A.Solver(cfg2, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+        try:
+            A.aeth_load_mlp(s2.ctx, p)
+            s2.set_state(0, st.cons, st.b1, st.b2, st.b3)
+            d0 = s2.diagnostics()
+            for dt in dts:
+                s2.step(dt)
+            out = s2.get_state(0)
+            d1 = s2.diagnostics()
+        finally:
+            s2.close()
+        return out, d0, d1
+
+    faces = 3 * (n + 1) * (n + 2) ** 2 * 2 * len(dts)   # face evaluations (approx.)
+    out, d0, d1 = run(params)
+    frac = d1["mlp_fallbacks"] / faces
+    errs = [rel_l1(out[0][v], ref.cons[v]) for v in range(5)]
+    print("trained: fallback fraction", frac, "rel L1", errs)
+    assert d1["max_divb_rel"] < 1e-5                      # CT stays exact
+    assert abs(d1["mass"] - d0["mass"]) < 1e-5 * d0["mass"]
+    assert frac < 0.5
+    assert max(errs) < 5e-2
+    out_r, _, d1r = run(I.mlp_init_params(99))
+    frac_r = d1r["mlp_fallbacks"] / faces
+    print("untrained: fallback fraction", frac_r)
+    assert frac_r > 0.9
