@@ -58,7 +58,7 @@ def dist_env():
     return ws, rank, local
 
 
-WORKLOADS = ("turb256", "batched512", "dust128", "wave32")
+WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512")
 
 
 def workload_config(a):
@@ -76,6 +76,15 @@ def workload_config(a):
                 "drag": f"closed-form arrowhead, {a.drag.upper()}", "precision": a.prec,
                 "seed": 20260817,
                 "l2": "inputs larger than L2 (128^3 x 37 vars x 2 registers)"}
+    if a.workload == "learned512":
+        n = a.n if a.n != 256 else 512
+        return {"workload": f"learned_flux_mhd_turbulence_{n}^3", "grid": [n, n, n],
+                "riemann": "BF16 MLP 14-128-128-128-7 (mma.sync) + HLLD fallback",
+                "recon": "PLM", "integrator": "VL2", "mach_rms": 4.0,
+                "beta": "0.1..10 (log10 beta = sin 2 pi y)", "gamma": 1.0001,
+                "precision": "fp32 state, bf16 network", "seed": 20260820,
+                "training": "interface states of a 128^3 HLLD run of the same generator",
+                "l2": "inputs larger than L2"}
     if a.workload == "wave32":
         return {"workload": "linear_fast_wave_32^3", "grid": [32, 32, 32], "recon": "PLM",
                 "riemann": "HLLD", "integrator": "VL2", "cfl": 0.3, "precision": a.prec,
@@ -165,6 +174,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def train_learned_flux(A, I, torch, dev, n=128, steps=4000, batch=8192, lr=2e-3):
+    """Train the learned flux on interface states of an HLLD run of the same
+    generator at n^3 (the project's own collection and training kernels)."""
+    import math
+    t0 = time.perf_counter()
+    st = I.turbulence_box(n=n, seed=20260821, mach=4.0, beta_modulated=True, gamma=1.0001)
+    cfg = A.make_config(gamma=st.gamma, precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream(dev))
+    cap = 3 * n ** 3 * 3 // 2
+    X = torch.zeros((cap, 16), dtype=torch.float32, device=dev)
+    Y = torch.zeros((cap, 8), dtype=torch.float32, device=dev)
+    got = 0
+    sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+    for _ in range(3):
+        got += A.aeth_mlp_collect(sv.ctx, 2, X[got:].data_ptr(), Y[got:].data_ptr(), cap - got)
+        sv.run(10)
+    sv.close()
+    X, Y = X[:got], Y[:got]
+    p = torch.from_numpy(I.mlp_init_params(13)).to(dev)
+    m, v, g = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    wf = A.aeth_mlp_work_floats(batch)
+    work = torch.zeros(wf, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(13)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    losses = []
+    for it in range(1, steps + 1):
+        idx = torch.randint(0, got, (batch,), device=dev, generator=gen)
+        xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+        A.aeth_mlp_grad(p.data_ptr(), xb.data_ptr(), yb.data_ptr(), batch, g.data_ptr(),
+                        work.data_ptr(), wf, loss.data_ptr(), s)
+        lr_t = 5e-5 + 0.5 * (lr - 5e-5) * (1 + math.cos(math.pi * it / steps))
+        A.aeth_mlp_adam(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), it,
+                        lr_t, stream=s)
+        if it == 1 or it == steps:
+            torch.cuda.synchronize(dev)
+            losses.append(loss.item())
+    return {"params": p.cpu().numpy(), "samples": got, "losses": losses,
+            "seconds": time.perf_counter() - t0}
+
+
 def make_input(a):
     from paper_2608_14048_gb300 import inputs as I
     return I.turbulence_box(n=a.n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
@@ -250,6 +301,14 @@ def main():
         cfg = A.make_config(gamma=gas.gamma, recon=rec, integrator=A.IMEX2P, cfl=0.3,
                             precision=prec, mhd=False, t_stop=ts,
                             drag_precision=A.FP64 if a.drag == "fp64" else A.FP32)
+    elif a.workload == "learned512":
+        from paper_2608_14048_gb300 import inputs as I
+        n = a.n if a.n != 256 else 512
+        learned = train_learned_flux(A, I, torch, dev)
+        states = [I.turbulence_box(n=n, seed=20260820, mach=4.0, beta_modulated=True,
+                                   gamma=1.0001)]
+        cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
+                            precision=A.FP32, path=path, riemann=A.MLP)
     elif a.workload == "wave32":
         from paper_2608_14048_gb300 import inputs as I
         states = [I.linear_fast_wave(32)]
@@ -264,6 +323,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sv = A.Solver(cfg, blocks, stream=stream)
     mhd_run = a.workload != "dust128"
+    if a.workload == "learned512":
+        A.aeth_load_mlp(sv.ctx, learned["params"])
 
     def upload(host=None):
         for q, s_ in enumerate(states):
@@ -277,7 +338,7 @@ def main():
 
     upload()
     kchunk = None
-    if not a.no_autotune and a.workload != "dust128":
+    if not a.no_autotune and a.workload not in ("dust128", "learned512"):
         # tile shape chosen by the autotuner on this workload's own state,
         # then the state is reloaded (the autotuner advances it)
         kchunk = A.aeth_autotune(sv.ctx)
@@ -323,6 +384,42 @@ def main():
     A.aeth_profile(sv.ctx, False)
     sv.sync()
     diag = sv.diagnostics()
+    extra = {}
+    if a.workload == "learned512":
+        # the same input and step count with plain HLLD on the same GPU
+        cfg_h = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
+                              precision=A.FP32, path=path)
+        svh = A.Solver(cfg_h, blocks, stream=stream)
+        svh.set_state(0, states[0].cons, states[0].b1, states[0].b2, states[0].b3)
+        for _ in range(a.warmup):
+            svh.run(1)
+        svh.sync()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        svh.run(a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_h = e0.elapsed_time(e1)
+        svh.close()
+        faces = 3 * (states[0].block.n[0] + 1) * (states[0].block.n[1] + 2) * \
+            (states[0].block.n[2] + 2) * 2 * a.steps
+        # the flux pass (state dump + three tensor-core MLP launches + HLLD
+        # fallbacks) against the sustained BF16 peak: 2 (16*128 + 2*128^2 +
+        # 128*8) = 71680 flop per face
+        nn = states[0].block.n
+        flops_pass = 3 * (nn[0] + 1) * (nn[1] + 2) * (nn[2] + 2) * 71680.0
+        tf = flops_pass * klaunch / (kms * 1e-3) / 1e12 if kms > 0 else None
+        peak_t = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1700.0
+        extra = {"roofline_tensor": {"bound": "tensor", "achieved": tf, "peak": peak_t,
+                                     "unit": "TFLOP/s", "frac": tf / peak_t if tf else None,
+                                     "kernel": "learned-flux pass (mma.sync BF16)",
+                                     "flop_per_face": 71680},
+                 "learned": {"hlld_value": cells * a.steps / (ms_h * 1e-3),
+                             "speedup_vs_hlld": ms_h / ms,
+                             "fallback_fraction": diag["mlp_fallbacks"] / faces,
+                             "train_samples": learned["samples"],
+                             "train_loss": learned["losses"], "train_s": learned["seconds"]}}
 
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -388,6 +485,7 @@ def main():
         "gpu_launches": all_launches,
         "diag_after": {"max_divb_rel": diag["max_divb_rel"], "floor_hits": diag["floor_hits"]},
         "flux_tile": {"tx": 32, "ty": 8, "kchunk": kchunk, "autotuned": kchunk is not None},
+        **extra,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
