@@ -29,6 +29,11 @@ void launch_fill(const BlockPtrs<R>& P, R* const* arrs, int nv, cudaStream_t st)
 constexpr int TX = 32;
 constexpr int TY = 8;
 constexpr int NT = TX * TY;
+// resident CTAs per SM requested for the FP32 flux pass (register budget
+// 65536 / (256 * FLUX_MINB) per thread)
+#ifndef AETH_FLUX_MINB
+#define AETH_FLUX_MINB 3
+#endif
 
 bool fused_supported(const aeth_ctx*) { return true; }
 
@@ -84,12 +89,12 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 
 // ------------------------------------------------------------------------
 // 1. flux pass.  Persistent: CTAs stride over the tiles of all blocks.
-//    Two CTAs per SM in FP32 (<= 128 registers); FP64 takes the full file.
+//    AETH_FLUX_MINB CTAs per SM in FP32; FP64 takes the full register file.
 // ------------------------------------------------------------------------
 // SOLVER 0: HLLD; 1: write the face states (wl, wr, bn) for the learned
 // flux instead of solving.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits) {
   constexpr int RL = RECON + 1, RH = RECON;
@@ -482,7 +487,7 @@ static void launch_fill_all(aeth_ctx* c, int reg, int nv, int block) {
 
 template <typename R, bool P64, int RECON, bool MHD, int SOLVER = 0>
 static void launch_flux3(aeth_ctx* c, int src, int block) {
-  const int per_sm = sizeof(R) == 4 ? 2 : 1;
+  const int per_sm = sizeof(R) == 4 ? AETH_FLUX_MINB : 1;
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
     k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER><<<grid, NT, 0, c->stream>>>(

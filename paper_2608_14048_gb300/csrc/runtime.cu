@@ -186,8 +186,8 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
     max_stage = std::max(max_stage, st * sizeof(double));
     npart += B.desc.ny * B.desc.nz;   // x-rows of this block
   }
-  // batched reductions: at most 4096 CTAs, each reducing whole x-rows
-  c->dt_grid = std::max(1, std::min(npart, 4096));
+  // batched reductions: at most 8192 CTAs, each reducing whole x-rows
+  c->dt_grid = std::max(1, std::min(npart, 8192));
   npart = c->dt_grid;
   // device block table and tile prefix sums of the batched passes
   const int nb = (int)c->blocks.size();
