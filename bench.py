@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--workload", default="turb256", choices=WORKLOADS)
     ap.add_argument("--drag", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--mlp-engine", default="tcgen05", choices=["tcgen05", "mma_sync"])
     return ap.parse_args()
 
 
@@ -79,7 +80,7 @@ def workload_config(a):
     if a.workload == "learned512":
         n = a.n if a.n != 256 else 512
         return {"workload": f"learned_flux_mhd_turbulence_{n}^3", "grid": [n, n, n],
-                "riemann": "BF16 MLP 14-128-128-128-7 (mma.sync) + HLLD fallback",
+                "riemann": f"BF16 MLP 14-128-128-128-7 ({a.mlp_engine}) + HLLD fallback",
                 "recon": "PLM", "integrator": "VL2", "mach_rms": 4.0,
                 "beta": "0.1..10 (log10 beta = sin 2 pi y)", "gamma": 1.0001,
                 "precision": "fp32 state, bf16 network", "seed": 20260820,
@@ -308,7 +309,8 @@ def main():
         states = [I.turbulence_box(n=n, seed=20260820, mach=4.0, beta_modulated=True,
                                    gamma=1.0001)]
         cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
-                            precision=A.FP32, path=path, riemann=A.MLP)
+                            precision=A.FP32, path=path, riemann=A.MLP,
+                            mlp_engine=A.TCGEN05 if a.mlp_engine == "tcgen05" else A.MMA_SYNC)
     elif a.workload == "wave32":
         from paper_2608_14048_gb300 import inputs as I
         states = [I.linear_fast_wave(32)]
@@ -386,21 +388,32 @@ def main():
     diag = sv.diagnostics()
     extra = {}
     if a.workload == "learned512":
-        # the same input and step count with plain HLLD on the same GPU
-        cfg_h = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
-                              precision=A.FP32, path=path)
-        svh = A.Solver(cfg_h, blocks, stream=stream)
-        svh.set_state(0, states[0].cons, states[0].b1, states[0].b2, states[0].b3)
-        for _ in range(a.warmup):
-            svh.run(1)
-        svh.sync()
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        svh.run(a.steps)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms_h = e0.elapsed_time(e1)
-        svh.close()
+        # the same input and step count with plain HLLD, and with the other
+        # tensor-core engine, on the same GPU
+        def other(cfg_o, params=None):
+            svh = A.Solver(cfg_o, blocks, stream=stream)
+            if params is not None:
+                A.aeth_load_mlp(svh.ctx, params)
+            svh.set_state(0, states[0].cons, states[0].b1, states[0].b2, states[0].b3)
+            for _ in range(a.warmup):
+                svh.run(1)
+            svh.sync()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            svh.run(a.steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_o = e0.elapsed_time(e1)
+            svh.close()
+            return ms_o
+
+        ms_h = other(A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
+                                   precision=A.FP32, path=path))
+        other_engine = "mma_sync" if a.mlp_engine == "tcgen05" else "tcgen05"
+        ms_e = other(A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
+                                   precision=A.FP32, path=path, riemann=A.MLP,
+                                   mlp_engine=A.TCGEN05 if other_engine == "tcgen05" else A.MMA_SYNC),
+                     learned["params"])
         faces = 3 * (states[0].block.n[0] + 1) * (states[0].block.n[1] + 2) * \
             (states[0].block.n[2] + 2) * 2 * a.steps
         # the flux pass (state dump + three tensor-core MLP launches + HLLD
@@ -413,10 +426,12 @@ def main():
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1700.0
         extra = {"roofline_tensor": {"bound": "tensor", "achieved": tf, "peak": peak_t,
                                      "unit": "TFLOP/s", "frac": tf / peak_t if tf else None,
-                                     "kernel": "learned-flux pass (mma.sync BF16)",
+                                     "kernel": f"learned-flux pass ({a.mlp_engine} BF16)",
                                      "flop_per_face": 71680},
                  "learned": {"hlld_value": cells * a.steps / (ms_h * 1e-3),
                              "speedup_vs_hlld": ms_h / ms,
+                             "engine": a.mlp_engine,
+                             f"{other_engine}_value": cells * a.steps / (ms_e * 1e-3),
                              "fallback_fraction": diag["mlp_fallbacks"] / faces,
                              "train_samples": learned["samples"],
                              "train_loss": learned["losses"], "train_s": learned["seconds"]}}

@@ -60,6 +60,9 @@ enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2 };
 /* Riemann solver (Sec. 2.4); AETH_RIEMANN_MLP = learned flux with HLLD
  * fallback */
 enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_MLP = 2 };
+/* tensor-core engine of the learned flux: tcgen05 MMAs with TMEM
+ * accumulators, or warp-level mma.sync */
+enum { AETH_MLP_TCGEN05 = 0, AETH_MLP_MMA_SYNC = 1 };
 /* time integrator (Sec. 2.6) */
 enum { AETH_INT_VL2 = 0, AETH_INT_RK2 = 1, AETH_INT_IMEX2P = 2 };
 /* working precision: all-FP64; FP32; FP32 with the pressure recovery of
@@ -90,6 +93,8 @@ typedef struct {
                          AETH_FP32: in FP32 (dust runs only) */
   double mlp_tau;     /* learned flux: residual-check tolerance (fraction of the
                          HLL dissipation bracket); <= 0 selects 0.25 */
+  int mlp_engine;     /* learned flux: AETH_MLP_TCGEN05 (default, 0) or
+                         AETH_MLP_MMA_SYNC */
 } aeth_config;
 
 typedef struct {
@@ -196,8 +201,11 @@ aeth_status aeth_get_dust(aeth_ctx* ctx, int block, int k, double* rho_mom);
 aeth_status aeth_load_mlp(aeth_ctx* ctx, const float* params, size_t n);
 
 /* Tensor-core forward pass of the loaded network on n dimensionless feature
- * rows (device d_X [n][16]) into device d_Y [n][8].  Asynchronous. */
+ * rows (device d_X [n][16]) into device d_Y [n][8].  aeth_mlp_infer: warp
+ * mma.sync (asynchronous); aeth_mlp_infer_tc: tcgen05 with TMEM
+ * accumulators (synchronises; AETH_ERR_TIMEOUT if an MMA wait ran out). */
 aeth_status aeth_mlp_infer(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
+aeth_status aeth_mlp_infer_tc(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 
 /* Training data from the solver itself: for every stride-th interior cell of
  * every block, the PLM states of its three lower faces (dimensionless

@@ -26,6 +26,7 @@ STATUS = {0: "AETH_OK", -1: "AETH_ERR_ARG", -2: "AETH_ERR_OOM", -3: "AETH_ERR_CU
 EOS_MHD, EOS_HYDRO = 0, 1
 DONOR, PLM, PPM = 0, 1, 2
 HLLD, MLP = 0, 2
+TCGEN05, MMA_SYNC = 0, 1          # tensor-core engine of the learned flux
 VL2, RK2, IMEX2P = 0, 1, 2
 FP64, FP32, FP32_P64 = 0, 1, 2
 CART, SPH = 0, 1
@@ -36,7 +37,7 @@ FUSED, UNFUSED = 0, 1
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
            "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
-           "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
+           "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
            "aeth_cfl_dt_noalloc",
            "aeth_last_error", "aeth_destroy"]
@@ -54,7 +55,7 @@ class aeth_config(C.Structure):
                 ("integrator", C.c_int), ("cfl", C.c_double), ("precision", C.c_int),
                 ("path", C.c_int), ("strict_floors", C.c_int), ("n_dust", C.c_int),
                 ("t_stop", C.POINTER(C.c_double)), ("drag_precision", C.c_int),
-                ("mlp_tau", C.c_double)]
+                ("mlp_tau", C.c_double), ("mlp_engine", C.c_int)]
 
 
 class aeth_block_desc(C.Structure):
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "aeth_get_dust": ([P, C.c_int, C.c_int, P], C.c_int),
         "aeth_load_mlp": ([P, P, C.c_size_t], C.c_int),
         "aeth_mlp_infer": ([P, P, P, C.c_int], C.c_int),
+        "aeth_mlp_infer_tc": ([P, P, P, C.c_int], C.c_int),
         "aeth_mlp_collect": ([P, C.c_int, P, P, C.c_longlong, C.POINTER(C.c_longlong)], C.c_int),
         "aeth_mlp_work_floats": ([C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "aeth_mlp_grad": ([P, P, P, C.c_int, P, P, C.c_size_t, P, P], C.c_int),
@@ -226,6 +228,10 @@ def aeth_mlp_infer(ctx, d_X: int, d_Y: int, n: int):
     _check(ctx, load_library().aeth_mlp_infer(ctx, C.c_void_p(d_X), C.c_void_p(d_Y), int(n)))
 
 
+def aeth_mlp_infer_tc(ctx, d_X: int, d_Y: int, n: int):
+    _check(ctx, load_library().aeth_mlp_infer_tc(ctx, C.c_void_p(d_X), C.c_void_p(d_Y), int(n)))
+
+
 def aeth_mlp_collect(ctx, stride: int, d_X: int, d_Y: int, capacity: int) -> int:
     n = C.c_longlong(0)
     _check(ctx, load_library().aeth_mlp_collect(ctx, int(stride), C.c_void_p(d_X), C.c_void_p(d_Y),
@@ -311,7 +317,7 @@ def _check(ctx, rc):
 
 def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=FP64, mhd=True,
                 path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
-                riemann=HLLD, drag_precision=FP64, mlp_tau=0.0):
+                riemann=HLLD, drag_precision=FP64, mlp_tau=0.0, mlp_engine=TCGEN05):
     cfg = aeth_config()
     cfg.eos = EOS_MHD if mhd else EOS_HYDRO
     cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
@@ -319,6 +325,7 @@ def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=F
     cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors
     cfg.drag_precision = drag_precision
     cfg.mlp_tau = mlp_tau
+    cfg.mlp_engine = mlp_engine
     if t_stop is not None and len(t_stop) > 0:
         arr = (C.c_double * len(t_stop))(*t_stop)
         cfg.n_dust = len(t_stop)

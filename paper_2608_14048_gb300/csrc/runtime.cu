@@ -60,6 +60,7 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (cfg->n_dust < 0 || cfg->n_dust > 32) bad = AETH_ERR_ARG;
   if (cfg->n_dust > 0 && !cfg->t_stop) bad = AETH_ERR_ARG;
   if (cfg->drag_precision != AETH_FP64 && cfg->drag_precision != AETH_FP32) bad = AETH_ERR_ARG;
+  if (cfg->mlp_engine != AETH_MLP_TCGEN05 && cfg->mlp_engine != AETH_MLP_MMA_SYNC) bad = AETH_ERR_ARG;
   if (bad != AETH_OK) {
     delete c;
     return bad;
@@ -505,6 +506,7 @@ void aeth_destroy(aeth_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->own_arena && c->arena) cudaFree(c->arena);
   if (c->d_mlp) cudaFree(c->d_mlp);
+  if (c->d_mlp_tc) cudaFree(c->d_mlp_tc);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   delete c;
 }

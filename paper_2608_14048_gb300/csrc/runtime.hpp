@@ -103,6 +103,7 @@ struct aeth_ctx {
   cudaGraphExec_t graph = nullptr;
   // MLP parameters (device, bf16/fp32) for the learned flux
   void* d_mlp = nullptr;
+  void* d_mlp_tc = nullptr;   // the same network, core-matrix image (tcgen05)
   size_t mlp_n = 0;
   // kernel timing (aeth_profile)
   bool profile = false;

@@ -79,6 +79,83 @@ def test_bf16_tensor_core_forward_matches_fp64():
     assert np.all(y[:, 7] == y[0, 7])   # padded output row carries only its bias (zero)
 
 
+@pytest.mark.parametrize("n", [0, 1, 1000, 152 * 128 * 2 + 77])
+def test_tcgen05_forward_matches_fp64_and_mma_sync(n):
+    """tcgen05 network (TMEM accumulators): ragged last tile (1000 = 7 x 128
+    + 104), more tiles than SMs (persistent loop), empty input.  Against the
+    FP64 forward: the BF16 bound above.  Against the mma.sync network (same
+    BF16 roundings, FP32 sums in another order): 5e-3 of the output scale."""
+    import torch
+    rng = np.random.default_rng(7)
+    p = I.mlp_init_params(14, bias_scale=0.1)
+    X = np.zeros((max(n, 1), 16), np.float32); X[:, :14] = rng.normal(size=(max(n, 1), 14))
+    sv = _solver_mlp()
+    try:
+        A.aeth_load_mlp(sv.ctx, p)
+        dX = _t(X)
+        y_tc = torch.full((max(n, 1), 8), 7.0, dtype=torch.float32, device="cuda")
+        y_ms = torch.zeros((max(n, 1), 8), dtype=torch.float32, device="cuda")
+        A.aeth_mlp_infer_tc(sv.ctx, dX.data_ptr(), y_tc.data_ptr(), n)
+        A.aeth_mlp_infer(sv.ctx, dX.data_ptr(), y_ms.data_ptr(), n)
+        torch.cuda.synchronize()
+        yt, ym = y_tc.cpu().numpy(), y_ms.cpu().numpy()
+    finally:
+        sv.close()
+    if n == 0:
+        assert np.all(yt == 7.0)            # nothing written
+        return
+    m = min(n, 4096)
+    ref = O.mlp_forward(DIMS, p.astype(np.float64), X[:m, :14].astype(np.float64))
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(yt[:m, :7] - ref)) <= 2e-2 * scale, np.max(np.abs(yt[:m, :7] - ref)) / scale
+    assert np.max(np.abs(yt[:, :7] - ym[:, :7])) <= 5e-3 * scale, np.max(np.abs(yt - ym)) / scale
+    assert np.all(yt[:, 7] == 0.0)
+
+
+def _zero_last_layer(p, b4):
+    """Network whose output is its last bias whatever the input: W4 = 0."""
+    q = p.copy()
+    o = A.MLP_NPARAM - (7 * 128 + 7)
+    q[o:o + 7 * 128] = 0.0
+    q[o + 7 * 128:] = b4
+    return q
+
+
+@pytest.mark.parametrize("mhd", [True, False])
+def test_learned_flux_engines_agree_bitwise(mhd):
+    """Both tensor-core engines inside the VL2 flux pass, on a network whose
+    output is exactly its last bias (W4 = 0, so neither engine rounds):
+    features, output scaling, the acceptance test, HLLD fallback and the
+    flux / EMF stores must give bit-identical states and equal fallback
+    counts.  Ragged tiles: 40 x 20 x 12 has 2 x 22 x 14 work units of 32
+    faces per direction, not a multiple of the 128-face tile."""
+    import torch
+    n = (40, 20, 12)
+    st = I.smooth_random_mhd(I.Block(n), 77, v_rms=0.5, b_rms=0.5 if mhd else 0.0, mhd=mhd)
+    p = _zero_last_layer(I.mlp_init_params(15, bias_scale=0.1),
+                         np.array([0.05, 0.3, -0.1, 0.08, 0.2, 0.01, -0.02], np.float32))
+    outs, fbs = [], []
+    for eng in (A.TCGEN05, A.MMA_SYNC):
+        cfg = A.make_config(precision=A.FP32, riemann=A.MLP, mlp_tau=50.0, mhd=mhd, mlp_engine=eng)
+        sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+        try:
+            A.aeth_load_mlp(sv.ctx, p)
+            sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+            sv.diagnostics()
+            sv.step(1e-3)
+            sv.step(1e-3)
+            outs.append(sv.get_state(0))
+            fbs.append(sv.diagnostics()["mlp_fallbacks"])
+        finally:
+            sv.close()
+    # hydro runs carry no face field: compare the conserved variables only
+    for a, b in list(zip(outs[0], outs[1]))[:4 if mhd else 1]:
+        assert np.array_equal(a, b)
+    assert fbs[0] == fbs[1]
+    faces = 3 * 41 * 22 * 14 * 2 * 2
+    assert 0 < fbs[0] < faces          # both branches taken
+
+
 def _train(samples_X, samples_Y, steps=4000, batch=8192, lr=2e-3, seed=13):
     import math
     import torch
@@ -132,8 +209,9 @@ def test_trained_network_replaces_hlld_on_most_faces():
 
     ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)
 
-    def run(p, tau=0.0):
-        cfg2 = A.make_config(gamma=st.gamma, precision=A.FP32, riemann=A.MLP, mlp_tau=tau)
+    def run(p, tau=0.0, engine=A.TCGEN05):
+        cfg2 = A.make_config(gamma=st.gamma, precision=A.FP32, riemann=A.MLP, mlp_tau=tau,
+                             mlp_engine=engine)
         s2 = A.Solver(cfg2, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
         try:
             A.aeth_load_mlp(s2.ctx, p)
@@ -148,14 +226,22 @@ def test_trained_network_replaces_hlld_on_most_faces():
         return out, d0, d1
 
     faces = 3 * (n + 1) * (n + 2) ** 2 * 2 * len(dts)   # face evaluations (approx.)
-    out, d0, d1 = run(params)
-    frac = d1["mlp_fallbacks"] / faces
-    errs = [rel_l1(out[0][v], ref.cons[v]) for v in range(5)]
-    print("trained: fallback fraction", frac, "rel L1", errs)
-    assert d1["max_divb_rel"] < 1e-5                      # CT stays exact
-    assert abs(d1["mass"] - d0["mass"]) < 1e-5 * d0["mass"]
-    assert frac < 0.5
-    assert max(errs) < 5e-2
+    outs = {}
+    for eng in (A.TCGEN05, A.MMA_SYNC):
+        out, d0, d1 = run(params, engine=eng)
+        frac = d1["mlp_fallbacks"] / faces
+        errs = [rel_l1(out[0][v], ref.cons[v]) for v in range(5)]
+        print("trained, engine", eng, ": fallback fraction", frac, "rel L1", errs)
+        assert d1["max_divb_rel"] < 1e-5                      # CT stays exact
+        assert abs(d1["mass"] - d0["mass"]) < 1e-5 * d0["mass"]
+        assert frac < 0.5
+        assert max(errs) < 5e-2
+        outs[eng] = out
+    # the two engines round the same BF16 network differently (SiLU form,
+    # FP32 summation order): their states stay close
+    agree = [rel_l1(outs[A.TCGEN05][0][v], outs[A.MMA_SYNC][0][v]) for v in range(5)]
+    print("engines rel L1", agree)
+    assert max(agree) < 1e-2
     out_r, _, d1r = run(I.mlp_init_params(99))
     frac_r = d1r["mlp_fallbacks"] / faces
     print("untrained: fallback fraction", frac_r)
