@@ -188,29 +188,38 @@ aeth_status aeth_get_dust(aeth_ctx* ctx, int block, int k, double* rho_mom);
  * with HLLD): a 14 -> 128 -> 128 -> 128 -> 7 MLP with SiLU hidden layers.
  * Inputs: the face-frame left/right primitive states and the normal field,
  * divided by rho_L and c = max(c_f,L, c_f,R) (rho_L = 1 dropped, zero-padded
- * to 16); outputs: the 7 face fluxes divided by rho_L c, rho_L c^2 (x3),
- * rho_L c^3 gamma/(gamma-1), sqrt(rho_L) c^2 (x2).  Parameter layout (FP32): per layer l,
- * W_l[out][in] row-major then b_l[out]; 52103 floats in all.
+ * to 16); outputs y: the face flux as a correction of the HLLE flux F_E
+ * scaled by the jump, F = F_E + k J y, with k the flux scales rho_L c,
+ * rho_L c^2 (x3), rho_L c^3 gamma/(gamma-1), sqrt(rho_L) c^2 (x2) and
+ * J = (S_R - S_L) max_q |U_R,q - U_L,q| / k_q the dimensionless jump (Davis
+ * speeds S); F tends to the physical flux as the jump vanishes.  Parameter
+ * layout (FP32): per layer l, W_l[out][in] row-major then b_l[out]; 52103
+ * floats in all.
  *
- * aeth_load_mlp: copy the network to the device (BF16 weights, FP32 biases;
- * the library allocates ~75 KB).  With config riemann = AETH_RIEMANN_MLP the
- * step evaluates it on the tensor cores for every face and falls back to
- * HLLD on faces failing the residual check against HLLE (tolerance
- * mlp_tau) or the positivity of the implied intermediate states; fallbacks
- * are counted in aeth_diag.mlp_fallbacks.  FP32/FP32_P64 gas runs only. */
+ * aeth_load_mlp: copy the network to the device (BF16 weights and biases
+ * in the layouts of both engines; the library allocates ~160 KB).  With
+ * config riemann = AETH_RIEMANN_MLP the step evaluates it on the tensor
+ * cores for every face and falls back to HLLD on faces where |F - F_E|
+ * exceeds mlp_tau (S_R - S_L) |U_R - U_L| + 2e-2 k in some component, or
+ * where the intermediate HLL states F implies lose positive density or
+ * pressure; fallbacks are counted in aeth_diag.mlp_fallbacks.  FP32 and
+ * FP32_P64 gas runs only. */
 aeth_status aeth_load_mlp(aeth_ctx* ctx, const float* params, size_t n);
 
 /* Tensor-core forward pass of the loaded network on n dimensionless feature
- * rows (device d_X [n][16]) into device d_Y [n][8].  aeth_mlp_infer: warp
- * mma.sync (asynchronous); aeth_mlp_infer_tc: tcgen05 with TMEM
- * accumulators (synchronises; AETH_ERR_TIMEOUT if an MMA wait ran out). */
+ * rows (device d_X [n][16], columns 14 and 15 ignored) into device d_Y
+ * [n][8].  Asynchronous on the bound stream.  aeth_mlp_infer: warp
+ * mma.sync; aeth_mlp_infer_tc: tcgen05 with TMEM accumulators (d_X, d_Y
+ * 16-byte aligned); an MMA wait that runs out latches a status bit that the
+ * next synchronising call reports as AETH_ERR_TIMEOUT. */
 aeth_status aeth_mlp_infer(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 aeth_status aeth_mlp_infer_tc(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 
 /* Training data from the solver itself: for every stride-th interior cell of
  * every block, the PLM states of its three lower faces (dimensionless
- * features, 16 floats per sample, device array d_X) and their HLLD fluxes
- * (dimensionless, 8 floats per sample, last one zero, d_Y).  At most
+ * features, 16 floats per sample, device array d_X) and the network
+ * targets y = (F_HLLD - F_E) / (k J) of their HLLD fluxes (computed in
+ * FP64; zero where J < 1e-9; 8 floats per sample, last one zero, d_Y).  At most
  * `capacity` samples are written; *n_out receives the count.  Synchronous. */
 aeth_status aeth_mlp_collect(aeth_ctx* ctx, int stride, float* d_X, float* d_Y,
                              long long capacity, long long* n_out);

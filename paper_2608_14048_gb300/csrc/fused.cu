@@ -341,7 +341,7 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
       outp[v][c] = base + bdt * rhs;
     }
   }
-  if (!MHD) return;
+  if constexpr (MHD) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
@@ -368,6 +368,7 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
     // periodic axis: face n is the image of face 0
     if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0)
       outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
+  }
   }
 }
 

@@ -78,15 +78,20 @@ __global__ void __launch_bounds__(256)
     }
     const R bn = mhd ? ub[(5 + d) * pitch + L.idx(i, j, k)] : R(0);
     if (!mhd) { wl[5] = wl[6] = wr[5] = wr[6] = R(0); }
-    R fx[7];
-    hlld(gamma, wl, wr, bn, fx);
-    float x[16], sc[7];
+    float x[16], sc[7], y[7];
     const FaceScale s = mlp_features(wl, wr, bn, gamma, x);
     mlp_scale_out(s, (float)gamma, sc);
+    {
+      // targets in FP64: F_HLLD - F_HLLE cancels for small jumps
+      double dl[7], dr[7], fx[7];
+      for (int q = 0; q < 7; ++q) { dl[q] = (double)wl[q]; dr[q] = (double)wr[q]; }
+      hlld((double)gamma, dl, dr, (double)bn, fx);
+      mlp_target((double)gamma, dl, dr, (double)bn, fx, sc, y);
+    }
     const unsigned long long slot_id = atomicAdd(count, 1ull);
     if ((long long)slot_id >= capacity) continue;
     for (int q = 0; q < 16; ++q) X[slot_id * 16 + q] = x[q];
-    for (int q = 0; q < 7; ++q) Y[slot_id * 8 + q] = (float)fx[q] / sc[q];
+    for (int q = 0; q < 7; ++q) Y[slot_id * 8 + q] = y[q];
     Y[slot_id * 8 + 7] = 0.0f;
   }
 }
@@ -510,13 +515,13 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, 1)
     __syncwarp();
     float k7[7];
     mlp_scale_out(sc, (float)gamma, k7);
-    R F[7];
+    float y[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) F[q] = (R)(sY[lane * 8 + q] * k7[q]);
-    if (!mhd) F[5] = F[6] = R(0);
+    for (int q = 0; q < 7; ++q) y[q] = sY[lane * 8 + q];
     __syncwarp();
     if (!valid) continue;
-    if (!mlp_accept(gamma, wl, wr, bn, F, k7, tau)) {
+    R F[7];
+    if (!mlp_compose(gamma, wl, wr, bn, y, k7, tau, mhd != 0, F)) {
       hlld(gamma, wl, wr, bn, F);
       ++fb;
     }

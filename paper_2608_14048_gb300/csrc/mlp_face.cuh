@@ -1,8 +1,14 @@
-// Face features, output scaling and the acceptance test of the learned
-// Riemann flux, shared by the mma.sync and the tcgen05 network kernels.
+// Face features, output scaling, training targets, flux composition and
+// the acceptance test of the learned Riemann flux, shared by the sample
+// kernel and the mma.sync and tcgen05 network kernels.
 #pragma once
 
 #include "common.cuh"
+
+// norm of the scaled jump in J: 0 = max over components, 2 = Euclidean
+#ifndef AETH_MLP_JNORM
+#define AETH_MLP_JNORM 2
+#endif
 
 namespace aeth {
 
@@ -71,38 +77,88 @@ __device__ __forceinline__ bool state_ok(R gamma, const R* u, R bn) {
   return (gamma - R(1)) * (u[4] - ke - me) > R(0);
 }
 
-// Accept the network's flux if it lies within tau of the HLL dissipation
-// bracket around HLLE (plus a small absolute floor), and the intermediate
-// states it implies in the HLL fan keep rho > 0 and p > 0.
+// HLLE flux and jump size of a face.  Davis speeds S_L = min(v_L, v_R) -
+// c_max, S_R = max(v_L, v_R) + c_max; the HLLE flux F_E; the dimensionless
+// jump J = (S_R - S_L) max_q |U_R,q - U_L,q| / k_q (k the flux scales).
+// The HLL dissipation of component q is at most (S_R - S_L) |dU_q| / 4 <=
+// k_q J / 4, so (F - F_E) / (k J) is O(1) for every consistent flux F.
 template <typename R>
-__device__ __forceinline__ bool mlp_accept(R gamma, const R* wl, const R* wr, R bn, const R* F,
-                                           const float* scale, R tau) {
-  R ul[7], fl[7], ur[7], fr[7];
-  side_uf(gamma, wl, bn, ul, fl);
-  side_uf(gamma, wr, bn, ur, fr);
+struct HllFace {
+  R ul[7], fl[7], ur[7], fr[7], fe[7];
+  R sl, sr, J;
+};
+
+template <typename R>
+__device__ __forceinline__ void hll_face(R gamma, const R* wl, const R* wr, R bn, const float* k,
+                                         HllFace<R>& h) {
+  side_uf(gamma, wl, bn, h.ul, h.fl);
+  side_uf(gamma, wr, bn, h.ur, h.fr);
   const R cl = fast_speed(gamma, wl[0], wl[4], bn, wl[5], wl[6]);
   const R cr = fast_speed(gamma, wr[0], wr[4], bn, wr[5], wr[6]);
   const R cm = fmax(cl, cr);
-  const R sl = fmin(wl[1], wr[1]) - cm, sr = fmax(wl[1], wr[1]) + cm;
+  h.sl = fmin(wl[1], wr[1]) - cm;
+  h.sr = fmax(wl[1], wr[1]) + cm;
+  R jm = R(0);
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
-    R fh;
-    if (sl >= R(0)) fh = fl[q];
-    else if (sr <= R(0)) fh = fr[q];
-    else fh = (sr * fl[q] - sl * fr[q] + sl * sr * (ur[q] - ul[q])) / (sr - sl);
-    const R tol = tau * (sr - sl) * fabs(ur[q] - ul[q]) + R(2e-2) * (R)scale[q];
-    if (!(fabs(F[q] - fh) <= tol)) return false;
+    const R du = h.ur[q] - h.ul[q];
+#if AETH_MLP_JNORM == 2
+    jm += (du / (R)k[q]) * (du / (R)k[q]);
+#else
+    jm = fmax(jm, fabs(du) / (R)k[q]);
+#endif
+    if (h.sl >= R(0)) h.fe[q] = h.fl[q];
+    else if (h.sr <= R(0)) h.fe[q] = h.fr[q];
+    else h.fe[q] = (h.sr * h.fl[q] - h.sl * h.fr[q] + h.sl * h.sr * du) / (h.sr - h.sl);
   }
-  if (sl < R(0)) {
+#if AETH_MLP_JNORM == 2
+  jm = sqrt(jm);
+#endif
+  h.J = (h.sr - h.sl) * jm;
+}
+
+// Training target of the network: the HLLD flux fx as a correction of
+// HLLE scaled by the jump, y_q = (fx_q - F_E,q) / (k_q J); zero where the
+// states coincide to round-off (J < 1e-9: HLLD = HLLE there).
+template <typename R>
+__device__ __forceinline__ void mlp_target(R gamma, const R* wl, const R* wr, R bn, const R* fx,
+                                           const float* k, float* y) {
+  HllFace<R> h;
+  hll_face(gamma, wl, wr, bn, k, h);
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    y[q] = h.J > R(1e-9) ? (float)((fx[q] - h.fe[q]) / ((R)k[q] * h.J)) : 0.0f;
+}
+
+// The learned flux F = F_E + k J y from the network output y, and its
+// acceptance: F within tau of the HLL dissipation bracket around F_E (plus
+// a 2e-2 k floor), and positive density and pressure in the intermediate
+// states F implies in the HLL fan.  The flux is consistent by construction
+// (F -> F_E -> the physical flux as the jump vanishes).  Returns false to
+// reject the face (F is then undefined).
+template <typename R>
+__device__ __forceinline__ bool mlp_compose(R gamma, const R* wl, const R* wr, R bn, const float* y,
+                                            const float* k, R tau, bool mhd, R* F) {
+  HllFace<R> h;
+  hll_face(gamma, wl, wr, bn, k, h);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) F[q] = h.fe[q] + (R)k[q] * h.J * (R)y[q];
+  if (!mhd) F[5] = F[6] = R(0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const R tol = tau * (h.sr - h.sl) * fabs(h.ur[q] - h.ul[q]) + R(2e-2) * (R)k[q];
+    if (!(fabs(F[q] - h.fe[q]) <= tol)) return false;
+  }
+  if (h.sl < R(0)) {
     R us[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) us[q] = ul[q] - (F[q] - fl[q]) / sl;
+    for (int q = 0; q < 7; ++q) us[q] = h.ul[q] - (F[q] - h.fl[q]) / h.sl;
     if (!state_ok(gamma, us, bn)) return false;
   }
-  if (sr > R(0)) {
+  if (h.sr > R(0)) {
     R us[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) us[q] = ur[q] - (F[q] - fr[q]) / sr;
+    for (int q = 0; q < 7; ++q) us[q] = h.ur[q] - (F[q] - h.fr[q]) / h.sr;
     if (!state_ok(gamma, us, bn)) return false;
   }
   return true;

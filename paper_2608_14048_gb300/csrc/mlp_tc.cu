@@ -526,10 +526,7 @@ __global__ void __launch_bounds__(512 / TPW, 1)
     float k7[7];
     mlp_scale_out(sc, (float)gamma, k7);
     R F[7];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) F[q] = (R)(y[q] * k7[q]);
-    if (!mhd) F[5] = F[6] = R(0);
-    if (!mlp_accept(gamma, f.wl, f.wr, f.bn, F, k7, tau)) {
+    if (!mlp_compose(gamma, f.wl, f.wr, f.bn, y, k7, tau, mhd != 0, F)) {
       hlld(gamma, f.wl, f.wr, f.bn, F);
       ++fb;
     }

@@ -242,7 +242,14 @@ def test_trained_network_replaces_hlld_on_most_faces():
     agree = [rel_l1(outs[A.TCGEN05][0][v], outs[A.MMA_SYNC][0][v]) for v in range(5)]
     print("engines rel L1", agree)
     assert max(agree) < 1e-2
-    out_r, _, d1r = run(I.mlp_init_params(99))
+    # an untrained network: its correction k J y is random, so the checks
+    # reject it wherever it leaves the HLL bracket (far more often than the
+    # trained one) and accept it only where k J |y| is within tolerance
+    frac_t = d1["mlp_fallbacks"] / faces
+    out_r, d0r, d1r = run(I.mlp_init_params(99))
     frac_r = d1r["mlp_fallbacks"] / faces
-    print("untrained: fallback fraction", frac_r)
-    assert frac_r > 0.9
+    errs_r = [rel_l1(out_r[0][v], ref.cons[v]) for v in range(5)]
+    print("untrained: fallback fraction", frac_r, "rel L1", errs_r)
+    assert frac_r > max(0.6, frac_t + 0.3)
+    assert d1r["max_divb_rel"] < 1e-5
+    assert abs(d1r["mass"] - d0r["mass"]) < 1e-5 * d0r["mass"]
