@@ -191,8 +191,8 @@ aeth_status aeth_get_dust(aeth_ctx* ctx, int block, int k, double* rho_mom);
  * to 16); outputs y: the face flux as a correction of the HLLE flux F_E
  * scaled by the jump, F = F_E + k J y, with k the flux scales rho_L c,
  * rho_L c^2 (x3), rho_L c^3 gamma/(gamma-1), sqrt(rho_L) c^2 (x2) and
- * J = (S_R - S_L) max_q |U_R,q - U_L,q| / k_q the dimensionless jump (Davis
- * speeds S); F tends to the physical flux as the jump vanishes.  Parameter
+ * J = (S_R - S_L) (sum_q ((U_R,q - U_L,q) / k_q)^2)^(1/2) the dimensionless
+ * jump (Davis speeds S); F tends to the physical flux as the jump vanishes.  Parameter
  * layout (FP32): per layer l, W_l[out][in] row-major then b_l[out]; 52103
  * floats in all.
  *

@@ -79,7 +79,9 @@ __device__ __forceinline__ bool state_ok(R gamma, const R* u, R bn) {
 
 // HLLE flux and jump size of a face.  Davis speeds S_L = min(v_L, v_R) -
 // c_max, S_R = max(v_L, v_R) + c_max; the HLLE flux F_E; the dimensionless
-// jump J = (S_R - S_L) max_q |U_R,q - U_L,q| / k_q (k the flux scales).
+// jump J = (S_R - S_L) |dU / k| (k the flux scales; Euclidean norm over
+// the 7 components by default, the smoother target for training, or the
+// max norm).
 // The HLL dissipation of component q is at most (S_R - S_L) |dU_q| / 4 <=
 // k_q J / 4, so (F - F_E) / (k J) is O(1) for every consistent flux F.
 template <typename R>
