@@ -106,7 +106,23 @@ def peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("fused.cu", "common.cuh")
+KERNEL_SOURCES = ("fused.cu", "common.cuh", "stage.cuh")
+
+
+def nvtx_push(name):
+    import torch
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    import torch
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
 
 
 def kernel_source_hash():
@@ -362,6 +378,9 @@ def main():
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # NVTX range "timed" around the timed steps: a profiler capture can be
+    # restricted to them (ncu --nvtx --nvtx-include timed/)
+    nvtx_push("timed")
     if flush is None:
         e0.record(stream)
         sv.run(a.steps)
@@ -378,6 +397,7 @@ def main():
             torch.cuda.synchronize(dev)
             ms_acc += e0.elapsed_time(e1)
     torch.cuda.synchronize(dev)
+    nvtx_pop()
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1) if flush is None else ms_acc

@@ -312,7 +312,7 @@ def solenoidal_gaussian_velocity(n: int, seed: int, kmin=2.0, kmax=8.0, slope=-2
     k2 = np.where(kk > 0, kk ** 2, 1.0)
     kd = (comps[0] * kx + comps[1] * ky + comps[2] * kz) / k2
     comps = [comps[0] - kd * kx, comps[1] - kd * ky, comps[2] - kd * kz]
-    v = [np.fft.irfftn(c, s=(n, n, n)) for c in comps]
+    v = [np.fft.irfftn(c, s=(n, n, n), axes=(0, 1, 2)) for c in comps]
     rms = math.sqrt(float(np.mean(v[0] ** 2 + v[1] ** 2 + v[2] ** 2)))
     return [np.ascontiguousarray(q / rms) for q in v]
 
