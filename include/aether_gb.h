@@ -215,6 +215,14 @@ aeth_status aeth_load_mlp(aeth_ctx* ctx, const float* params, size_t n);
 aeth_status aeth_mlp_infer(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 aeth_status aeth_mlp_infer_tc(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * warp waits, through the wait the tcgen05 network kernels use, on an
+ * mbarrier that never receives an arrival.  The wait gives up after its
+ * limit (~0.5 s) and the call returns AETH_ERR_TIMEOUT; the context's own
+ * status word is untouched and the context stays usable.  Synchronous;
+ * requires aeth_finalize. */
+aeth_status aeth_selftest_wait_timeout(aeth_ctx* ctx);
+
 /* Training data from the solver itself: for every stride-th interior cell of
  * every block, the PLM states of its three lower faces (dimensionless
  * features, 16 floats per sample, device array d_X) and the network

@@ -647,6 +647,41 @@ aeth_status mlp_tc_prepare(aeth_ctx* c) {
 
 }  // namespace aeth
 
+namespace aeth {
+
+// One warp waits, through the same bounded wait as the network kernels, on
+// an mbarrier that never receives an arrival; the wait gives up after its
+// wall-time limit and the kernel reports the time-out in *flag.
+__global__ void k_wait_selftest(int* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t a = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  const bool got = tc::wait_bar(a, 0u);
+  if (threadIdx.x == 0 && !got) atomicOr(flag, ST_TIMEOUT);
+}
+
+}  // namespace aeth
+
+extern "C" aeth_status aeth_selftest_wait_timeout(aeth_ctx* c) {
+  using namespace aeth;
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  int* flag = (int*)(c->arena + c->off_scalars + 512);
+  AETH_CK(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(flag);
+  AETH_CK(c, cudaGetLastError());
+  c->n_launch += 1;
+  int h = 0;
+  AETH_CK(c, cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  if (h & ST_TIMEOUT) return fail(c, AETH_ERR_TIMEOUT, "self-test: the bounded wait gave up as designed");
+  return AETH_OK;
+}
+
 extern "C" aeth_status aeth_mlp_infer_tc(aeth_ctx* c, const float* d_X, float* d_Y, int n) {
   using namespace aeth;
   if (!c || !d_X || !d_Y || n < 0) return AETH_ERR_ARG;

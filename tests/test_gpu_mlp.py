@@ -112,6 +112,31 @@ def test_tcgen05_forward_matches_fp64_and_mma_sync(n):
     assert np.all(yt[:, 7] == 0.0)
 
 
+def test_bounded_wait_gives_up_and_context_survives():
+    """The mbarrier wait of the tcgen05 kernels is bounded: on a barrier
+    that nothing arrives at it gives up (~0.5 s), the host reads
+    AETH_ERR_TIMEOUT, and the context keeps working (a step still runs and
+    its state stays finite)."""
+    import time
+    import torch
+    n = (16, 12, 10)
+    st = I.smooth_random_mhd(I.Block(n), 78, v_rms=0.5, b_rms=0.5)
+    cfg = A.make_config(precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+    try:
+        t0 = time.time()
+        code = A.aeth_selftest_wait_timeout(sv.ctx)
+        dt_wall = time.time() - t0
+        assert code == -6                       # AETH_ERR_TIMEOUT
+        assert dt_wall < 30.0
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        sv.step(1e-3)
+        out = sv.get_state(0)
+        assert np.all(np.isfinite(out[0]))
+    finally:
+        sv.close()
+
+
 def _zero_last_layer(p, b4):
     """Network whose output is its last bias whatever the input: W4 = 0."""
     q = p.copy()
