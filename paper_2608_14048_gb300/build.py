@@ -18,10 +18,13 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaether_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# FP32 division and square root use the hardware approximations (max 2 ulp);
-# FP64 arithmetic is unaffected by these two flags.
+# FP32 division and square root use the hardware approximations (max 2 ulp)
+# and FP32 denormals flush to zero (no input or intermediate of the method
+# is denormal: the flag removes the denormal fix-up instructions around the
+# approximations, -14% time in the flux pass); FP64 arithmetic is
+# unaffected by these flags.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-prec-div=false", "-prec-sqrt=false",
+              "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")] + ARCH
 
 

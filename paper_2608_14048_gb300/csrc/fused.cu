@@ -34,6 +34,12 @@ constexpr int NT = TX * TY;
 #ifndef AETH_FLUX_MINB
 #define AETH_FLUX_MINB 3
 #endif
+// resident CTAs per SM requested for the update pass (registers 65536 /
+// (256 * UPD_MINB)): the loads of a cell are hoisted above its stores, so
+// the register cap trades memory-level parallelism per thread for threads
+#ifndef AETH_UPD_MINB
+#define AETH_UPD_MINB 3
+#endif
 
 bool fused_supported(const aeth_ctx*) { return true; }
 
@@ -287,6 +293,70 @@ __global__ void __launch_bounds__(256) k_emf_ref(Src S, int t0, int t1) {
 // ------------------------------------------------------------------------
 // 3. update: out = w0*A + w1*B + beta*dt*L (Eq. 8 + Eq. 12), CT (Eq. 9)
 // ------------------------------------------------------------------------
+// CT inputs of the three lower faces of one cell (Eq. 9): circulation of
+// the corner EMFs around each face, face area, and the two register values.
+template <typename R>
+struct CtIn {
+  R circ[3], area[3], b0[3], b1[3];
+  bool on[3];
+};
+
+template <typename R, bool MHD, bool SPH>
+__device__ __forceinline__ CtIn<R> ct_gather(const BlockPtrs<R>& B, const int* P, long long c,
+                                             bool has_b) {
+  CtIn<R> t;
+  const Layout& L = B.L;
+  const Geometry<R>& geo = B.geo;
+  const int i = P[0], j = P[1], k = P[2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    t.on[d] = false;
+    t.circ[d] = t.area[d] = t.b0[d] = t.b1[d] = R(0);
+    if constexpr (MHD) {
+      const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+      const int hid = L.bc[d] == AETH_BC_OUTFLOW ? L.n[d] : L.n[d] - 1;
+      if (P[d] > hid || P[e1] >= L.n[e1] || P[e2] >= L.n[e2]) continue;
+      t.on[d] = true;
+      int Q1[3] = {i, j, k}, Q2[3] = {i, j, k};
+      Q1[e1] += 1; Q2[e2] += 1;
+      const long long q1 = c + L.stride(e1), q2 = c + L.stride(e2);
+      if (SPH) {
+        t.circ[d] = B.edge[e2][q1] * geo.edge[e2](Q1[0], Q1[1], Q1[2]) -
+                    B.edge[e2][c] * geo.edge[e2](i, j, k) -
+                    (B.edge[e1][q2] * geo.edge[e1](Q2[0], Q2[1], Q2[2]) -
+                     B.edge[e1][c] * geo.edge[e1](i, j, k));
+      } else {
+        const R l2 = geo.edge[e2](0, 0, 0), l1 = geo.edge[e1](0, 0, 0);
+        t.circ[d] = B.edge[e2][q1] * l2 - B.edge[e2][c] * l2 - (B.edge[e1][q2] * l1 - B.edge[e1][c] * l1);
+      }
+      t.area[d] = SPH ? geo.area[d](i, j, k) : geo.area[d](0, 0, 0);
+      t.b0[d] = B.reg[0][5 + d][c];
+      if (has_b) t.b1[d] = B.reg[1][5 + d][c];
+    }
+  }
+  return t;
+}
+
+template <typename R, bool MHD>
+__device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, long long c,
+                                         R* const* outp, const CtIn<R>& t, R w0, R w1, R bdt,
+                                         bool has_b) {
+  if constexpr (MHD) {
+    const Layout& L = B.L;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (!t.on[d]) continue;
+      R base = w0 * t.b0[d];
+      if (has_b) base += w1 * t.b1[d];
+      const R nb = base - bdt * t.circ[d] / t.area[d];
+      outp[5 + d][c] = nb;
+      // periodic axis: face n is the image of face 0
+      if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0)
+        outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
+    }
+  }
+}
+
 template <typename R, bool P64, bool MHD, bool SPH>
 __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P, int src, int out,
                                             R w0, R w1, R bdt, R gamma, R rho_floor, R p_floor) {
@@ -330,52 +400,44 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
       srcv[2] = T(2, 2) * ct - T(0, 1) * ir;
       srcv[3] = -T(2, 0) * ir - T(2, 1) * ct;
     }
+    // every input of the cell is loaded before the first store: the stores
+    // go through pointer arrays the compiler cannot prove disjoint from the
+    // loads, so interleaving them would serialise the memory round trips
+    R fm[3][5], fp[3][5], u0[5], u1[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        fp[d][v] = B.f[d][v][cp[d]];
+        fm[d][v] = B.f[d][v][c];
+      }
+      u0[v] = B.reg[0][v][c];
+      u1[v] = has_b ? B.reg[1][v][c] : R(0);
+    }
+    CtIn<R> ct = ct_gather<R, MHD, SPH>(B, P, c, has_b);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R div = R(0);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) div += Ap[d] * B.f[d][v][cp[d]] - Am[d] * B.f[d][v][c];
+      for (int d = 0; d < 3; ++d) div += Ap[d] * fp[d][v] - Am[d] * fm[d][v];
       const R rhs = -div / V + srcv[v];
-      R base = w0 * B.reg[0][v][c];
-      if (has_b) base += w1 * B.reg[1][v][c];
+      R base = w0 * u0[v];
+      if (has_b) base += w1 * u1[v];
       outp[v][c] = base + bdt * rhs;
     }
+    ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
+    return;
   }
-  if constexpr (MHD) {
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-    const int hid = L.bc[d] == AETH_BC_OUTFLOW ? L.n[d] : L.n[d] - 1;
-    if (P[d] > hid || P[e1] >= L.n[e1] || P[e2] >= L.n[e2]) continue;
-    int Q1[3] = {i, j, k}, Q2[3] = {i, j, k};
-    Q1[e1] += 1; Q2[e2] += 1;
-    const long long q1 = c + L.stride(e1), q2 = c + L.stride(e2);
-    R circ;
-    if (SPH) {
-      circ = B.edge[e2][q1] * geo.edge[e2](Q1[0], Q1[1], Q1[2]) -
-             B.edge[e2][c] * geo.edge[e2](i, j, k) -
-             (B.edge[e1][q2] * geo.edge[e1](Q2[0], Q2[1], Q2[2]) -
-              B.edge[e1][c] * geo.edge[e1](i, j, k));
-    } else {
-      const R l2 = geo.edge[e2](0, 0, 0), l1 = geo.edge[e1](0, 0, 0);
-      circ = B.edge[e2][q1] * l2 - B.edge[e2][c] * l2 - (B.edge[e1][q2] * l1 - B.edge[e1][c] * l1);
-    }
-    const R Af = SPH ? geo.area[d](i, j, k) : geo.area[d](0, 0, 0);
-    R base = w0 * B.reg[0][5 + d][c];
-    if (has_b) base += w1 * B.reg[1][5 + d][c];
-    const R nb = base - bdt * circ / Af;
-    outp[5 + d][c] = nb;
-    // periodic axis: face n is the image of face 0
-    if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0)
-      outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
-  }
-  }
+  // cells on the upper face layer (index n along some axis) update only the
+  // face field
+  CtIn<R> ct = ct_gather<R, MHD, SPH>(B, P, c, has_b);
+  ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
 }
 
 // COORD: 0 every block Cartesian, 1 every block spherical, 2 mixed (the
 // coordinate system is then read per tile).
 template <typename R, bool P64, bool MHD, int COORD, typename Src>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
     k_update_f(Src S, int t0, int t1, int src, int out, R w0, R w1, R beta,
                const double* __restrict__ dt, R gamma, R rho_floor, R p_floor) {
   const int add[3] = {1, 1, 1};
