@@ -45,30 +45,6 @@ bool fused_supported(const aeth_ctx*) { return true; }
 
 __host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
 
-// Where a tile's block comes from: the device block table (passes over
-// several blocks; binary search of the tile prefix sums), or the kernel's
-// parameter space (passes over one block: uniform constant-bank loads).
-template <typename R>
-struct TableSrc {
-  const BlockPtrs<R>* tab;
-  const int* pre;
-  int nb;
-  __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
-    const int b = find_block(pre, nb, t);
-    loc = t - pre[b];
-    return tab[b];
-  }
-};
-template <typename R>
-struct ParamSrc {
-  BlockPtrs<R> P;
-  int base;   // first tile of the block in the pass's numbering
-  __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
-    loc = t - base;
-    return P;
-  }
-};
-
 template <typename R>
 struct FluxOut {
   R* f[3][5];

@@ -170,6 +170,30 @@ __device__ __forceinline__ int find_block(const int* __restrict__ pre, int nb, i
   }
   return lo;
 }
+// Where a tile's block comes from: the device block table (passes over
+// several blocks; binary search of the tile prefix sums), or the kernel's
+// parameter space (passes over one block: uniform constant-bank loads).
+template <typename R>
+struct TableSrc {
+  const BlockPtrs<R>* tab;
+  const int* pre;
+  int nb;
+  __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
+    const int b = find_block(pre, nb, t);
+    loc = t - pre[b];
+    return tab[b];
+  }
+};
+template <typename R>
+struct ParamSrc {
+  BlockPtrs<R> P;
+  int base;   // first tile of the block in the pass's numbering
+  __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
+    loc = t - base;
+    return P;
+  }
+};
+
 inline int prefix_total(const aeth_ctx* c, int kind) {
   const int nb = (int)c->blocks.size();
   return c->h_prefix[kind * (nb + 1) + nb];
