@@ -124,11 +124,21 @@ __device__ __forceinline__ void recon_face(const R* s, R& wl, R& wr) {
 
 template <typename R>
 __device__ __forceinline__ R fast_speed(R gamma, R rho, R p, R bn, R bt1, R bt2) {
-  R a2 = gamma * p / rho;
-  R b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
-  R s = a2 + b2;
-  R disc = fmax(s * s - R(4) * a2 * bn * bn / rho, R(0));
-  return sqrt(R(0.5) * (s + sqrt(disc)));
+  if constexpr (sizeof(R) == 4) {
+    // one reciprocal of rho for the three quotients
+    const R ir = R(1) / rho;
+    const R a2 = gamma * p * ir;
+    const R b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) * ir;
+    const R s = a2 + b2;
+    const R disc = fmax(s * s - R(4) * a2 * bn * bn * ir, R(0));
+    return sqrt(R(0.5) * (s + sqrt(disc)));
+  } else {
+    R a2 = gamma * p / rho;
+    R b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
+    R s = a2 + b2;
+    R disc = fmax(s * s - R(4) * a2 * bn * bn / rho, R(0));
+    return sqrt(R(0.5) * (s + sqrt(disc)));
+  }
 }
 
 // Single-star state of one side (MK05): density, transverse velocity and
@@ -180,17 +190,8 @@ __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R b
   const R fl5 = byl * ul - bn * vl, fr5 = byr * ur - bn * vr;
   const R fl6 = bzl * ul - bn * wl, fr6 = bzr * ur - bn * wr;
   // fast speeds and outer waves
-  R cfl, cfr;
-  {
-    const R a2 = gamma * pl / rl, b2 = bb_l / rl, s = a2 + b2;
-    const R disc = fmax(s * s - R(4) * a2 * bn * bn / rl, R(0));
-    cfl = sqrt(R(0.5) * (s + sqrt(disc)));
-  }
-  {
-    const R a2 = gamma * pr / rr, b2 = bb_r / rr, s = a2 + b2;
-    const R disc = fmax(s * s - R(4) * a2 * bn * bn / rr, R(0));
-    cfr = sqrt(R(0.5) * (s + sqrt(disc)));
-  }
+  const R cfl = fast_speed(gamma, rl, pl, bn, byl, bzl);
+  const R cfr = fast_speed(gamma, rr, pr, bn, byr, bzr);
   const R cmax = fmax(cfl, cfr);
   const R sl = fmin(ul, ur) - cmax;
   const R sr = fmax(ul, ur) + cmax;
@@ -210,11 +211,22 @@ __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R b
   R rsr, v1sr, v2sr, b1sr, b2sr, esr;
   hlld_star(rl, ul, vl, wl, byl, bzl, el, ptl, sl, sm, pts, bn, rsl, v1sl, v2sl, b1sl, b2sl, esl);
   hlld_star(rr, ur, vr, wr, byr, bzr, er, ptr, sr, sm, pts, bn, rsr, v1sr, v2sr, b1sr, b2sr, esr);
-  const R sql = sqrt(rsl), sqr = sqrt(rsr);
   const R abn = fabs(bn);
   const bool degen = R(0.5) * bn * bn < Eps<R>::hlld * pts;
-  const R ssl = degen ? sm : sm - abn / sql;
-  const R ssr = degen ? sm : sm + abn / sqr;
+  R sql, sqr, ssl, ssr;
+  if constexpr (sizeof(R) == 4) {
+    // one reciprocal square root gives sqrt(rho*) and |Bn| / sqrt(rho*)
+    const R ql = rsqrtf(rsl), qr = rsqrtf(rsr);
+    sql = rsl * ql;
+    sqr = rsr * qr;
+    ssl = degen ? sm : sm - abn * ql;
+    ssr = degen ? sm : sm + abn * qr;
+  } else {
+    sql = sqrt(rsl);
+    sqr = sqrt(rsr);
+    ssl = degen ? sm : sm - abn / sql;
+    ssr = degen ? sm : sm + abn / sqr;
+  }
   int region;
   if (ssl >= R(0)) region = 1;
   else if (sm >= R(0)) region = 2;

@@ -32,7 +32,7 @@ constexpr int NT = TX * TY;
 // resident CTAs per SM requested for the FP32 flux pass (register budget
 // 65536 / (256 * FLUX_MINB) per thread)
 #ifndef AETH_FLUX_MINB
-#define AETH_FLUX_MINB 3
+#define AETH_FLUX_MINB 2
 #endif
 // resident CTAs per SM requested for the update pass (registers 65536 /
 // (256 * UPD_MINB)): the loads of a cell are hoisted above its stores, so
