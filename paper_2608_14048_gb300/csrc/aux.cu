@@ -378,98 +378,98 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// CFL time step (Eq. 11) over all blocks: one partial minimum per CTA.  A
-// CTA iteration takes RPI rows (x lines) of cells at once and loads all of
-// them before using any, so each thread keeps RPI independent load groups
-// in flight (the rows' block lookups included).
+// CFL time step (Eq. 11) over all blocks: one partial minimum per CTA.  The
+// work unit is the 32x4x2 cell tile of the elementwise passes (full warps
+// on every block size, one block lookup per 256 cells); a CTA iteration
+// takes TPI tiles and loads all of them before using any, so each thread
+// keeps TPI independent load groups in flight.
 template <typename R, bool P64, typename Src>
 __global__ void __launch_bounds__(256)
     k_dt(Src S, int total, int mhd, double gamma, double rho_floor, double p_floor, int nd,
          double* __restrict__ partial, int* status) {
-  constexpr int RPI = 4;
+  constexpr int TPI = 2;
   __shared__ double sm[8];
   R m = R(INFINITY);   // running minimum in the working precision
   bool bad = false;
-  for (int t0 = blockIdx.x * RPI; t0 < total; t0 += gridDim.x * RPI) {
-    for (int base = 0;; base += blockDim.x) {
-      const int i = base + (int)threadIdx.x;
-      R a[RPI][5], bf[RPI][6], wd[RPI][3];
-      bool on[RPI];
-      bool more = false;   // some row has cells beyond this chunk (CTA-uniform)
+  const int tx = (int)threadIdx.x % CELL_BX, ty = ((int)threadIdx.x / CELL_BX) % CELL_BY;
+  const int tz = (int)threadIdx.x / (CELL_BX * CELL_BY);
+  for (int t0 = blockIdx.x * TPI; t0 < total; t0 += gridDim.x * TPI) {
+    R a[TPI][5], bf[TPI][6], wd[TPI][3];
+    int ci[TPI][3];
+    bool on[TPI];
 #pragma unroll
-      for (int q = 0; q < RPI; ++q) {
-        on[q] = false;
-        const int t = t0 + q;
-        if (t >= total) continue;
-        int r;
-        const BlockPtrs<R>& P = S.get(t, r);
-        const Layout L = P.L;
-        more = more || L.n[0] > base + (int)blockDim.x;
-        if (i >= L.n[0]) continue;
-        on[q] = true;
-        const int j = r % L.n[1], k = r / L.n[1];
-        const long long c = L.idx(i, j, k);
-        const R* const* u = P.reg[0];
+    for (int q = 0; q < TPI; ++q) {
+      on[q] = false;
+      const int t = t0 + q;
+      if (t >= total) continue;
+      int loc;
+      const BlockPtrs<R>& P = S.get(t, loc);
+      const Layout L = P.L;
+      const int ntx = (L.n[0] + CELL_BX) / CELL_BX, nty = (L.n[1] + CELL_BY) / CELL_BY;
+      const int i = (loc % ntx) * CELL_BX + tx, j = ((loc / ntx) % nty) * CELL_BY + ty;
+      const int k = (loc / (ntx * nty)) * CELL_BZ + tz;
+      if (i >= L.n[0] || j >= L.n[1] || k >= L.n[2]) continue;
+      on[q] = true;
+      ci[q][0] = i; ci[q][1] = j; ci[q][2] = k;
+      const long long c = L.idx(i, j, k);
+      const R* const* u = P.reg[0];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) a[q][v] = u[v][c];
-        if (mhd) {
-          bf[q][0] = u[5][c]; bf[q][1] = u[5][c + 1];
-          bf[q][2] = u[6][c]; bf[q][3] = u[6][c + L.sx];
-          bf[q][4] = u[7][c]; bf[q][5] = u[7][c + L.sx * L.sy];
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) wd[q][d] = P.geo.width[d](i, j, k);
+      for (int v = 0; v < 5; ++v) a[q][v] = u[v][c];
+      if (mhd) {
+        bf[q][0] = u[5][c]; bf[q][1] = u[5][c + 1];
+        bf[q][2] = u[6][c]; bf[q][3] = u[6][c + L.sx];
+        bf[q][4] = u[7][c]; bf[q][5] = u[7][c + L.sx * L.sy];
       }
 #pragma unroll
-      for (int q = 0; q < RPI; ++q) {
-        if (!on[q]) continue;
-        R rho = a[q][0];
-        if (!(rho >= (R)rho_floor)) { if (!(rho == rho)) bad = true; rho = (R)rho_floor; }
-        const R v[3] = {a[q][1] / rho, a[q][2] / rho, a[q][3] / rho};
-        R bc[3] = {0, 0, 0};
-        if (mhd) {
-          bc[0] = R(0.5) * (bf[q][0] + bf[q][1]);
-          bc[1] = R(0.5) * (bf[q][2] + bf[q][3]);
-          bc[2] = R(0.5) * (bf[q][4] + bf[q][5]);
-        }
-        R pr;
-        if (P64) {
-          double ke = 0.5 * ((double)a[q][1] * a[q][1] + (double)a[q][2] * a[q][2] +
-                             (double)a[q][3] * a[q][3]) / (double)rho;
-          double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
-          pr = (R)((gamma - 1.0) * ((double)a[q][4] - ke - me));
-        } else {
-          pr = (R)(gamma - 1.0) * (a[q][4] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
-                                   R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
-        }
-        if (!(pr >= (R)p_floor)) { if (!(pr == pr)) bad = true; pr = (R)p_floor; }
+      for (int d = 0; d < 3; ++d) wd[q][d] = P.geo.width[d](i, j, k);
+    }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
-          const R dtd = wd[q][d] / (fabs(v[d]) + cf);
-          if (!(dtd > R(0))) bad = true;
-          m = fmin(m, dtd);
-        }
-        // pressureless dust species: c = 0 (Eq. 11)
-        if (nd > 0) {
-          int r;
-          const BlockPtrs<R>& P = S.get(t0 + q, r);
-          const Layout L = P.L;
-          const int j = r % L.n[1], k = r / L.n[1];
-          const long long c = L.idx(i, j, k);
-          const long long sz = L.size();
-          for (int sp = 0; sp < nd; ++sp) {
-            const R rk = P.dust[0][(long long)(4 * sp) * sz + c];
-            if (!(rk > R(0))) continue;
+    for (int q = 0; q < TPI; ++q) {
+      if (!on[q]) continue;
+      R rho = a[q][0];
+      if (!(rho >= (R)rho_floor)) { if (!(rho == rho)) bad = true; rho = (R)rho_floor; }
+      const R v[3] = {a[q][1] / rho, a[q][2] / rho, a[q][3] / rho};
+      R bc[3] = {0, 0, 0};
+      if (mhd) {
+        bc[0] = R(0.5) * (bf[q][0] + bf[q][1]);
+        bc[1] = R(0.5) * (bf[q][2] + bf[q][3]);
+        bc[2] = R(0.5) * (bf[q][4] + bf[q][5]);
+      }
+      R pr;
+      if (P64) {
+        double ke = 0.5 * ((double)a[q][1] * a[q][1] + (double)a[q][2] * a[q][2] +
+                           (double)a[q][3] * a[q][3]) / (double)rho;
+        double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
+        pr = (R)((gamma - 1.0) * ((double)a[q][4] - ke - me));
+      } else {
+        pr = (R)(gamma - 1.0) * (a[q][4] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
+                                 R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+      }
+      if (!(pr >= (R)p_floor)) { if (!(pr == pr)) bad = true; pr = (R)p_floor; }
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              const R vk = fabs(P.dust[0][(long long)(4 * sp + 1 + d) * sz + c] / rk);
-              if (vk > R(0)) m = fmin(m, wd[q][d] / vk);
-            }
+      for (int d = 0; d < 3; ++d) {
+        const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
+        const R dtd = wd[q][d] / (fabs(v[d]) + cf);
+        if (!(dtd > R(0))) bad = true;
+        m = fmin(m, dtd);
+      }
+      // pressureless dust species: c = 0 (Eq. 11)
+      if (nd > 0) {
+        int loc;
+        const BlockPtrs<R>& P = S.get(t0 + q, loc);
+        const Layout L = P.L;
+        const long long c = L.idx(ci[q][0], ci[q][1], ci[q][2]);
+        const long long sz = L.size();
+        for (int sp = 0; sp < nd; ++sp) {
+          const R rk = P.dust[0][(long long)(4 * sp) * sz + c];
+          if (!(rk > R(0))) continue;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const R vk = fabs(P.dust[0][(long long)(4 * sp + 1 + d) * sz + c] / rk);
+            if (vk > R(0)) m = fmin(m, wd[q][d] / vk);
           }
         }
       }
-      if (!more) break;
     }
   }
   const double md = warp_min((double)m);
@@ -501,16 +501,16 @@ __global__ void k_dt_final(const double* __restrict__ partial, int n, double sca
 template <typename R, bool P64>
 static aeth_status dt_T(aeth_ctx* c) {
   const int nb = (int)c->blocks.size();
-  const int total = prefix_total(c, PK_ROWS);
-  // 4 rows per CTA iteration; at most dt_grid partial minima
-  const int grid = std::max(1, std::min(c->dt_grid, (total + 3) / 4));
+  const int total = prefix_total(c, PK_CELL);
+  // 2 tiles per CTA iteration; at most dt_grid partial minima
+  const int grid = std::max(1, std::min(c->dt_grid, (total + 1) / 2));
   if (nb == 1) {
     const ParamSrc<R> src{block_ptrs<R>(c, 0), 0};
     k_dt<R, P64, ParamSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
         c->d_partials, c->d_status);
   } else {
-    const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_ROWS * (nb + 1), nb};
+    const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb};
     k_dt<R, P64, TableSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
         c->d_partials, c->d_status);
