@@ -446,18 +446,27 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
       else if (e == d) { lo[e] = 0; ext[e] = 2 * g + 1; }
       else { lo[e] = 0; ext[e] = L.n[e] + 1; }
     }
-    const int ntx = ceil_div_d(ext[0], CELL_BX), nty = ceil_div_d(ext[1], CELL_BY);
-    const int t0c = (loc % ntx) * CELL_BX + (int)(threadIdx.x % CELL_BX);
-    const int t1c = ((loc / ntx) % nty) * CELL_BY + (int)((threadIdx.x / CELL_BX) % CELL_BY);
-    const int t2c = (loc / (ntx * nty)) * CELL_BZ + (int)(threadIdx.x / (CELL_BX * CELL_BY));
-    if (t0c >= ext[0] || t1c >= ext[1] || t2c >= ext[2]) continue;
+    // threads run linearly over the slab (x fastest): every lane busy even
+    // where the slab is only 2g+1 cells thick along x
+    const long long el = (long long)loc * FILL_TILE + threadIdx.x;
+    if (el >= (long long)ext[0] * ext[1] * ext[2]) continue;
+    const int t0c = (int)(el % ext[0]);
+    const int t1c = (int)((el / ext[0]) % ext[1]);
+    const int t2c = (int)(el / ((long long)ext[0] * ext[1]));
     int c[3] = {t0c + lo[0], t1c + lo[1], t2c + lo[2]};
     const int n = L.n[d];
     const int tt = c[d];
     c[d] = tt < g ? tt - g : n + (tt - g);
     const int p = c[d];
     const long long dst = L.idx(c[0], c[1], c[2]);
-    for (int v = 0; v < nv; ++v) {
+    // every source is loaded before the first store (the stores go through
+    // pointer arrays the compiler cannot prove disjoint from the loads)
+    R val[NVAR];
+    bool on[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      on[v] = false;
+      if (v >= nv) continue;
       const bool face_d = (v == 5 + d);
       int s;
       if (L.bc[d] == AETH_BC_PERIODIC) {
@@ -470,9 +479,12 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
       }
       int sc[3] = {c[0], c[1], c[2]};
       sc[d] = s;
-      R* arr = B.reg[reg][v];
-      arr[dst] = arr[L.idx(sc[0], sc[1], sc[2])];
+      val[v] = B.reg[reg][v][L.idx(sc[0], sc[1], sc[2])];
+      on[v] = true;
     }
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v)
+      if (on[v]) B.reg[reg][v][dst] = val[v];
   }
 }
 

@@ -52,6 +52,7 @@ enum PassKind : int { PK_FLUX = 0, PK_CELL = 1, PK_FILL0 = 2, PK_FILL1 = 3, PK_F
 // Tile geometry of each pass kind (threads per tile fixed per kind).
 constexpr int FLUX_TX = 32, FLUX_TY = 8;
 constexpr int CELL_BX = 32, CELL_BY = 4, CELL_BZ = 2;
+constexpr int FILL_TILE = 256;   // ghost cells per tile of the fill pass
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -65,10 +66,12 @@ inline int tiles_of(const Layout& L, int kind, int kchunk) {
     return ceil_div(L.n[0] + 1, CELL_BX) * ceil_div(L.n[1] + 1, CELL_BY) *
            ceil_div(L.n[2] + 1, CELL_BZ);
   if (kind == PK_ROWS) return L.n[1] * L.n[2];
+  // ghost slab of axis d, threads mapped linearly over it (FILL_TILE cells
+  // per tile)
   const int d = kind - PK_FILL0;
-  int ext[3];
-  for (int e = 0; e < 3; ++e) ext[e] = e < d ? L.n[e] + 2 * g + 1 : (e == d ? 2 * g + 1 : L.n[e] + 1);
-  return ceil_div(ext[0], CELL_BX) * ceil_div(ext[1], CELL_BY) * ceil_div(ext[2], CELL_BZ);
+  long long cells = 1;
+  for (int e = 0; e < 3; ++e) cells *= e < d ? L.n[e] + 2 * g + 1 : (e == d ? 2 * g + 1 : L.n[e] + 1);
+  return (int)((cells + FILL_TILE - 1) / FILL_TILE);
 }
 
 }  // namespace aeth
