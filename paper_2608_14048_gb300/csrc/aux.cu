@@ -189,6 +189,17 @@ static aeth_status build_tables_T(aeth_ctx* c) {
                              cudaMemcpyHostToDevice, c->stream));
   AETH_CK(c, cudaMemcpyAsync(c->d_prefix, c->h_prefix.data(), c->h_prefix.size() * sizeof(int),
                              cudaMemcpyHostToDevice, c->stream));
+  std::vector<int2> maps[PK_N];
+  for (int kind = 0; kind < PK_N; ++kind) {
+    if (!c->d_tmap[kind]) continue;
+    const int* p = c->h_prefix.data() + kind * (nb + 1);
+    if (p[nb] != c->tmap_n[kind]) return fail(c, AETH_ERR_STATE, "tile map size mismatch");
+    maps[kind].resize((size_t)p[nb]);
+    for (int b = 0; b < nb; ++b)
+      for (int t = p[b]; t < p[b + 1]; ++t) maps[kind][t] = make_int2(b, t - p[b]);
+    AETH_CK(c, cudaMemcpyAsync(c->d_tmap[kind], maps[kind].data(), maps[kind].size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, c->stream));
+  }
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   return AETH_OK;
 }
@@ -510,7 +521,8 @@ static aeth_status dt_T(aeth_ctx* c) {
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
         c->d_partials, c->d_status);
   } else {
-    const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb};
+    const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb,
+                          c->d_tmap[PK_CELL]};
     k_dt<R, P64, TableSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
         c->d_partials, c->d_status);

@@ -521,7 +521,7 @@ static void with_src(aeth_ctx* c, int kind, int block, F launch) {
     const TileRange r = range_of(c, kind, b);
     launch(ParamSrc<R>{block_ptrs<R>(c, b), r.t0}, r);
   } else {
-    launch(TableSrc<R>{dtab<R>(c), dpre(c, kind), nb}, range_of(c, kind, -1));
+    launch(TableSrc<R>{dtab<R>(c), dpre(c, kind), nb, c->d_tmap[kind]}, range_of(c, kind, -1));
   }
 }
 

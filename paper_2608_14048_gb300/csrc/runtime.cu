@@ -196,6 +196,15 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
   off += align256((size_t)nb * sizeof(BlockPtrs<double>));
   c->off_prefix = off;
   off += align256((size_t)PK_N * (nb + 1) * sizeof(int));
+  for (int kind = 0; kind < PK_N; ++kind) {
+    c->tmap_n[kind] = 0;
+    if (nb < 2 || !(kind == PK_CELL || (kind >= PK_FILL0 && kind <= PK_FILL2))) continue;
+    long long tiles = 0;
+    for (const auto& B : c->blocks) tiles += tiles_of(B.L, kind, 0);
+    c->off_tmap[kind] = off;
+    c->tmap_n[kind] = tiles;
+    off += align256((size_t)tiles * sizeof(int2));
+  }
   c->off_stage = off;
   c->stage_bytes = align256(max_stage);
   off += c->stage_bytes;
@@ -243,6 +252,8 @@ aeth_status aeth_finalize(aeth_ctx* c, size_t* bytes) {
   AETH_CK(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
   c->d_tab = c->arena + c->off_tab;
   c->d_prefix = (int*)(c->arena + c->off_prefix);
+  for (int kind = 0; kind < PK_N; ++kind)
+    c->d_tmap[kind] = c->tmap_n[kind] > 0 ? (int2*)(c->arena + c->off_tmap[kind]) : nullptr;
   s = build_tables(c);
   if (s != AETH_OK) return s;
   AETH_CK(c, cudaStreamSynchronize(c->stream));

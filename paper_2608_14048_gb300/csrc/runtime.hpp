@@ -116,6 +116,11 @@ struct aeth_ctx {
   long long n_launch = 0;             // kernels launched (all kinds)
   // batched launches: device block table and tile prefix sums
   size_t off_tab = 0, off_prefix = 0;
+  // per pass kind, a tile -> (block, local tile) map for contexts of several
+  // blocks (cell and fill passes, whose tile counts are fixed at plan time)
+  size_t off_tmap[aeth::PK_N] = {};
+  int2* d_tmap[aeth::PK_N] = {};
+  long long tmap_n[aeth::PK_N] = {};
   void* d_tab = nullptr;              // BlockPtrs<R>[nb]
   int* d_prefix = nullptr;            // [PK_N][nb + 1]
   std::vector<int> h_prefix;          // host copy
@@ -181,7 +186,13 @@ struct TableSrc {
   const BlockPtrs<R>* tab;
   const int* pre;
   int nb;
+  const int2* map;   // tile -> (block, tile in block), or null: binary search
   __device__ __forceinline__ const BlockPtrs<R>& get(int t, int& loc) const {
+    if (map) {
+      const int2 e = map[t];
+      loc = e.y;
+      return tab[e.x];
+    }
     const int b = find_block(pre, nb, t);
     loc = t - pre[b];
     return tab[b];
