@@ -99,6 +99,21 @@ template <typename R, typename DT, int NDMAX>
 __global__ void __launch_bounds__(256)
     k_dust_update(Layout L, R idx1, R idx2, R idx3, DustUpd<R> A, int nd, int stage,
                   unsigned long long* floor_hits) {
+  // per-species drag constants of this stage, the same for every cell:
+  // a_k = h / t_k, 1 / (1 + a_k), w_k = a_k / (1 + a_k) with h = g dt
+  __shared__ DT s_ak[NDMAX], s_ia[NDMAX], s_wk[NDMAX];
+  {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid < nd && tid < NDMAX) {
+      const DT h = (DT)kImexG * (DT)(*A.dt);
+      const DT a = h * (DT)A.inv_t_stop[tid];
+      const DT ia = DT(1) / (DT(1) + a);
+      s_ak[tid] = a;
+      s_ia[tid] = ia;
+      s_wk[tid] = a * ia;
+    }
+    __syncthreads();
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -138,47 +153,75 @@ __global__ void __launch_bounds__(256)
   // closed-form implicit drag with h = g dt (Sec. 2.2).  With
   // a_k = h / t_k, w_k = a_k / (1 + a_k):
   //   rho_g v_g' = (M_g* + sum_k w_k M_k*) * rho_g / (rho_g + sum_k rho_k w_k)
-  //   v_k' = (v_k* + a_k v_g') / (1 + a_k)
-  // which needs only 1/rho_k, 1/(1 + a_k) per species and one 1/den.
-  const DT h = (DT)kImexG * (DT)(*A.dt);
+  //   M_k' = rho_k v_k' = (M_k* + rho_k a_k v_g') / (1 + a_k)
+  //   dKE_k = (M_k'^2 - M_k*^2) / (2 rho_k)
+  // 1/rho_k and 1/den come from one division (simultaneous inversion,
+  // Montgomery 1987: prefix products, one reciprocal, back-substitution).
   R gy[5], dy[NDMAX][4];
   const DT rg = gx[0];
   gy[0] = gx[0];
-  DT ak[NDMAX], ia[NDMAX], wk[NDMAX], ir[NDMAX];
+  DT rk[NDMAX], rak[NDMAX], ir[NDMAX];
   DT den = rg;
 #pragma unroll
   for (int s = 0; s < NDMAX; ++s) {
     if (s >= nd) break;
-    ak[s] = h * (DT)A.inv_t_stop[s];
-    ia[s] = DT(1) / (DT(1) + ak[s]);
-    wk[s] = ak[s] * ia[s];
-    const DT r = dx[s][0];
-    ir[s] = r > DT(0) ? DT(1) / r : DT(0);
-    den += r * wk[s];
+    rk[s] = dx[s][0];
+    rak[s] = rk[s] * s_ak[s];
+    den += rk[s] * s_wk[s];
     dy[s][0] = dx[s][0];
   }
-  const DT inv_den = DT(1) / den;
-  DT dke = 0;   // change of the dust kinetic energy
+  DT inv_den;
+  if constexpr (sizeof(DT) == 8 && NDMAX <= 8) {
+    // prefix products x_0 ... x_{s-1} of the densities (a non-positive
+    // density enters as 1 and gets 1/rho = 0); at most 8 factors of the
+    // density range stay far inside the FP64 exponent range
+    DT pre[NDMAX];
+    DT acc = DT(1);
+#pragma unroll
+    for (int s = 0; s < NDMAX; ++s) {
+      if (s >= nd) break;
+      pre[s] = acc;
+      acc *= rk[s] > DT(0) ? rk[s] : DT(1);
+    }
+    const DT q = DT(1) / (acc * den);   // the one division
+    inv_den = q * acc;
+    DT ip = q * den;                    // 1 / (x_0 ... x_{nd-1})
+#pragma unroll
+    for (int s = NDMAX - 1; s >= 0; --s) {
+      if (s >= nd) continue;
+      ir[s] = rk[s] > DT(0) ? ip * pre[s] : DT(0);
+      ip *= rk[s] > DT(0) ? rk[s] : DT(1);   // 1 / (x_0 ... x_{s-1})
+    }
+  } else {
+    inv_den = DT(1) / den;
+#pragma unroll
+    for (int s = 0; s < NDMAX; ++s) {
+      if (s >= nd) break;
+      ir[s] = rk[s] > DT(0) ? DT(1) / rk[s] : DT(0);
+    }
+  }
+  DT dke2 = 0;   // twice the change of the dust kinetic energy
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
+    DT m0[NDMAX];
     DT num = gx[1 + q];   // rho_g v_g* = M_g*
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
-      num += wk[s] * (DT)dx[s][1 + q];   // rho_k w_k v_k* = w_k M_k*
+      m0[s] = (DT)dx[s][1 + q];
+      num += s_wk[s] * m0[s];   // rho_k w_k v_k* = w_k M_k*
     }
     const DT vg = num * inv_den;
     gy[1 + q] = (R)(rg * vg);
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
-      const DT r = dx[s][0];
-      const DT v0 = (DT)dx[s][1 + q] * ir[s];
-      const DT v1 = (v0 + ak[s] * vg) * ia[s];
-      dy[s][1 + q] = (R)(r * v1);
-      dke += DT(0.5) * r * (v1 - v0) * (v1 + v0);
+      const DT m1 = (m0[s] + rak[s] * vg) * s_ia[s];
+      dy[s][1 + q] = (R)m1;
+      dke2 += (m1 - m0[s]) * (m1 + m0[s]) * ir[s];
     }
   }
+  const DT dke = DT(0.5) * dke2;
   // total energy conserved: drift energy becomes gas heat
   gy[4] = (R)((DT)gx[4] - dke);
   int hits = 0;
