@@ -506,7 +506,7 @@ def main():
         "data": "synthetic", "config": workload_config(a),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                     "kernel": "stage kernel" if a.path == "fused" else "k_flux",
+                     "kernel": "k_flux3 (fused prim + reconstruction + HLLD, 3 directions)" if a.path == "fused" else "k_flux",
                      "peak_kind": peak_kind,
                      "algo_bytes_per_launch": kbytes / max(klaunch, 1),
                      "kernel_ms_per_launch": kms / max(klaunch, 1),
