@@ -41,16 +41,23 @@ def _cut(arr_c, b1, b2, b3, lo, size, n):
     return [np.ascontiguousarray(x) for x in (cons, s1, s2, s3)]
 
 
-def test_turbulence_256_fp32_one_step_sampled():
+@pytest.mark.parametrize("recon", ["plm", "ppm"])
+def test_turbulence_256_fp32_one_step_sampled(recon):
+    """Both reconstructions of the 256^3 benchmark, with the tile shape the
+    autotuner picks as in bench.py (PPM's stencil of 3 keeps the dependency
+    radius at 6 <= HALO)."""
     import torch
     n = 256
     st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
     g = O.make_grid((n, n, n))
-    p = O.make_params(gamma=st.gamma, recon=O.PLM)
+    orec, arec = (O.PLM, A.PLM) if recon == "plm" else (O.PPM, A.PPM)
+    p = O.make_params(gamma=st.gamma, recon=orec)
     dt = O.compute_dt(g, p, O.State(st.cons, st.b1, st.b2, st.b3))
-    cfg = A.make_config(gamma=st.gamma, recon=A.PLM, precision=A.FP32, path=A.FUSED)
+    cfg = A.make_config(gamma=st.gamma, recon=arec, precision=A.FP32, path=A.FUSED)
     sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
     try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        A.aeth_autotune(sv.ctx)          # advances the state: reload it
         sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
         sv.step(dt)
         gc, g1, g2, g3 = sv.get_state(0)
@@ -116,3 +123,111 @@ def test_dust_128_eight_species_one_step_sampled():
         errs = [rel_l1(cen(gc)[v], sc[v, h, h, h]) for v in range(5)]
         errs += [rel_l1(cen(gd)[k, q], sd[k, q, h, h, h]) for k in range(8) for q in range(4)]
         assert max(errs) < 1e-5, (c0, max(errs))
+
+
+def test_batched_512_boxes_one_step_sampled():
+    """The 512-box configuration at full size, as bench.py runs it (same
+    generator and seed, autotuned tile, one launch per pass over all boxes):
+    the GPU advances every box one step with the oracle's CFL step over all
+    boxes; the oracle recomputes sampled boxes (spherical and Cartesian, the
+    smallest and the largest) element by element."""
+    import os
+    import torch
+    sts = I.batched_boxes(512, 20260818, gl=2, workers=min(16, os.cpu_count() or 1))
+    params = O.make_params(gamma=sts[0].gamma, recon=O.PLM)
+
+    def grid(st):
+        b = st.block
+        return O.make_grid(b.n, b.lo, b.hi, b.coord, b.bc)
+
+    dt = min(O.compute_dt(grid(st), params, O.State(st.cons, st.b1, st.b2, st.b3)) for st in sts)
+    cells = [int(np.prod(st.block.n)) for st in sts]
+    sph = [q for q, st in enumerate(sts) if st.block.coord == I.SPH]
+    cart = [q for q, st in enumerate(sts) if st.block.coord != I.SPH]
+    rng = np.random.default_rng(11)
+    pick = sorted({int(np.argmin(cells)), int(np.argmax(cells)), sph[0], sph[-1], cart[0],
+                   *rng.choice(len(sts), 3, replace=False).tolist()})
+    cfg = A.make_config(gamma=sts[0].gamma, recon=A.PLM, precision=A.FP32, path=A.FUSED)
+    blocks = [A.make_block(st.block.n, st.block.lo, st.block.hi, st.block.coord, st.block.bc)
+              for st in sts]
+    sv = A.Solver(cfg, blocks, stream=torch.cuda.current_stream())
+    try:
+        for q, st in enumerate(sts):
+            sv.set_state(q, st.cons, st.b1, st.b2, st.b3)
+        A.aeth_autotune(sv.ctx)          # advances the state: reload it
+        for q, st in enumerate(sts):
+            sv.set_state(q, st.cons, st.b1, st.b2, st.b3)
+        sv.step(dt)
+        outs = {q: sv.get_state(q) for q in pick}
+        diag = sv.diagnostics()
+    finally:
+        sv.close()
+    assert diag["max_divb_rel"] < 1e-5
+    for q in pick:
+        st = sts[q]
+        s = O.State(st.cons, st.b1, st.b2, st.b3)
+        O.step(grid(st), params, dt, s)
+        o = outs[q]
+        errs = [rel_l1(o[0][v], s.cons[v]) for v in range(5)]
+        bnorm = sum(np.sum(np.abs(x)) / x.size for x in (s.b1, s.b2, s.b3)) / 3
+        errs += [float(np.mean(np.abs(o[1 + d] - x))) / bnorm for d, x in enumerate((s.b1, s.b2, s.b3))]
+        assert max(errs) < 1e-5, (q, st.block.n, st.block.coord, errs)
+
+
+def test_learned_flux_512_one_step_properties():
+    """The 512^3 learned-flux configuration at full size (FP32 state, BF16
+    network on the tcgen05 engine).  The oracle has no learned flux, so the
+    step is checked by what holds at any size: div B stays at round-off
+    (CT), mass is conserved to FP32 round-off, no floor is hit, most faces
+    keep the network's flux, and the state stays within the acceptance
+    tolerance of an HLLD step from the same input with the oracle's dt."""
+    import torch
+    from tests.test_gpu_mlp import _train
+    # training data: interface states of a 64^3 HLLD run of the same generator
+    small = I.turbulence_box(n=64, seed=20260821, mach=4.0, beta_modulated=True, gamma=1.0001)
+    cfg = A.make_config(gamma=small.gamma, precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block((64, 64, 64))], stream=torch.cuda.current_stream())
+    cap = 3 * 64 ** 3 * 4
+    X = torch.zeros((cap, 16), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")
+    got = 0
+    try:
+        sv.set_state(0, small.cons, small.b1, small.b2, small.b3)
+        for _ in range(4):
+            got += A.aeth_mlp_collect(sv.ctx, 1, X[got:].data_ptr(), Y[got:].data_ptr(), cap - got)
+            sv.run(3)
+    finally:
+        sv.close()
+    params, losses = _train(X[:got], Y[:got], steps=2000)
+    assert losses[-1] < 0.1 * losses[0]
+    del X, Y
+    n = 512
+    st = I.turbulence_box(n=n, seed=20260820, mach=4.0, beta_modulated=True, gamma=1.0001)
+    dt = O.compute_dt(O.make_grid((n, n, n)), O.make_params(gamma=st.gamma, recon=O.PLM),
+                      O.State(st.cons, st.b1, st.b2, st.b3))
+    outs = {}
+    for riemann in (A.MLP, A.HLLD):
+        cfg = A.make_config(gamma=st.gamma, recon=A.PLM, precision=A.FP32, riemann=riemann)
+        sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+        try:
+            if riemann == A.MLP:
+                A.aeth_load_mlp(sv.ctx, params)
+            sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+            d0 = sv.diagnostics()
+            sv.step(dt)
+            d1 = sv.diagnostics()
+            outs[riemann] = (sv.get_state(0)[0], d0, d1)
+        finally:
+            sv.close()
+    cons, d0, d1 = outs[A.MLP]
+    faces = 3 * (n + 1) * (n + 2) ** 2 * 2
+    frac = d1["mlp_fallbacks"] / faces
+    assert np.all(np.isfinite(cons))
+    assert d1["max_divb_rel"] < 1e-5
+    assert abs(d1["mass"] - d0["mass"]) < 1e-6 * d0["mass"]
+    assert d1["floor_hits"] == 0
+    assert frac < 0.3, frac
+    ref = outs[A.HLLD][0]
+    errs = [rel_l1(cons[v], ref[v]) for v in range(5)]
+    print("512^3 learned vs HLLD one step: fallback", frac, "rel L1", errs)
+    assert max(errs) < 1e-2, errs
