@@ -344,7 +344,7 @@ def main():
     if a.workload == "learned512":
         A.aeth_load_mlp(sv.ctx, learned["params"])
 
-    def upload(host=None):
+    def upload(host=None, host_dust=None):
         for q, s_ in enumerate(states):
             if host is None:
                 sv.set_state(q, s_.cons, s_.b1, s_.b2, s_.b3)
@@ -352,7 +352,8 @@ def main():
                 A.aeth_set_state(sv.ctx, q, *host[q])
         if dust is not None:
             for k in range(dust.shape[0]):
-                A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]))
+                A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]) if host_dust is None
+                                else host_dust[k])
 
     upload()
     kchunk = None
@@ -475,14 +476,18 @@ def main():
         hout = [[h[0], None, None, None] for h in hout]
     nbytes = lambda lst: sum(x.numel() * 8 for h in lst for x in h if x is not None)
     h2d, d2h = nbytes(hin), nbytes(hout)
+    hdust = None
     if dust is not None:
         h2d += dust.nbytes
         d2h += dust.nbytes
-        dbuf = [np.empty(dust.shape[1:]) for _ in range(dust.shape[0])]
+        hdust = [torch.from_numpy(np.ascontiguousarray(dust[k])).pin_memory()
+                 for k in range(dust.shape[0])]
+        dbuf = [torch.empty(dust.shape[1:], dtype=torch.float64).pin_memory()
+                for _ in range(dust.shape[0])]
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(ke):
-        upload(hin)
+        upload(hin, hdust)
         sv.run(1)
         for q in range(len(states)):
             A.aeth_get_state(sv.ctx, q, *hout[q])

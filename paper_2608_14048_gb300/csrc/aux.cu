@@ -270,7 +270,9 @@ template void launch_fill<double>(const BlockPtrs<double>&, double* const*, int,
 // ------------------------------------------------------------------------
 
 template <typename R>
-__global__ void k_load(Layout L, Arr8<R> a, int mhd, const double* __restrict__ s) {
+__global__ void k_load(Layout L, Arr8<R> a, int mhd, const double* __restrict__ sc,
+                       const double* __restrict__ b1, const double* __restrict__ b2,
+                       const double* __restrict__ b3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -280,19 +282,17 @@ __global__ void k_load(Layout L, Arr8<R> a, int mhd, const double* __restrict__ 
   const long long d = L.idx(i, j, k);
   if (i < nx && j < ny && k < nz) {
     const long long c = ((long long)k * ny + j) * nx + i;
-    for (int v = 0; v < 5; ++v) a.p[v][d] = (R)s[v * nc + c];
+    for (int v = 0; v < 5; ++v) a.p[v][d] = (R)sc[v * nc + c];
   }
   if (!mhd) return;
-  const double* b1 = s + 5 * nc;
-  const double* b2 = b1 + (long long)nz * ny * (nx + 1);
-  const double* b3 = b2 + (long long)nz * (ny + 1) * nx;
   if (j < ny && k < nz) a.p[5][d] = (R)b1[((long long)k * ny + j) * (nx + 1) + i];
   if (i < nx && k < nz) a.p[6][d] = (R)b2[((long long)k * (ny + 1) + j) * nx + i];
   if (i < nx && j < ny) a.p[7][d] = (R)b3[((long long)k * ny + j) * nx + i];
 }
 
 template <typename R>
-__global__ void k_store(Layout L, Arr8<R> a, int mhd, double* __restrict__ s) {
+__global__ void k_store(Layout L, Arr8<R> a, int mhd, double* __restrict__ sc,
+                        double* __restrict__ b1, double* __restrict__ b2, double* __restrict__ b3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -302,12 +302,9 @@ __global__ void k_store(Layout L, Arr8<R> a, int mhd, double* __restrict__ s) {
   if (i < nx && j < ny && k < nz) {
     const long long c = ((long long)k * ny + j) * nx + i;
     const long long d = L.idx(i, j, k);
-    for (int v = 0; v < 5; ++v) s[v * nc + c] = (double)a.p[v][d];
+    for (int v = 0; v < 5; ++v) sc[v * nc + c] = (double)a.p[v][d];
   }
   if (!mhd) return;
-  double* b1 = s + 5 * nc;
-  double* b2 = b1 + (long long)nz * ny * (nx + 1);
-  double* b3 = b2 + (long long)nz * (ny + 1) * nx;
   // periodic axes: the last face is the image of the first
   const int i1 = (i == nx && L.bc[0] == AETH_BC_PERIODIC) ? 0 : i;
   const int j2 = (j == ny && L.bc[1] == AETH_BC_PERIODIC) ? 0 : j;
@@ -318,24 +315,24 @@ __global__ void k_store(Layout L, Arr8<R> a, int mhd, double* __restrict__ s) {
 }
 
 template <typename R>
-static aeth_status load_store_T(aeth_ctx* c, int b, bool load) {
+static aeth_status load_store_T(aeth_ctx* c, int b, bool load, double* const* io) {
   BlockPtrs<R> P = block_ptrs<R>(c, b);
   Arr8<R> a{};
   for (int v = 0; v < NVAR; ++v) a.p[v] = P.reg[0][v];
   const Layout& L = P.L;
   dim3 blk(32, 4, 2);
   dim3 grd((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 3) / 4, (L.n[2] + 1 + 1) / 2);
-  if (load) k_load<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), c->d_stage);
-  else k_store<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), c->d_stage);
+  if (load) k_load<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), io[0], io[1], io[2], io[3]);
+  else k_store<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), io[0], io[1], io[2], io[3]);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }
 
-aeth_status enqueue_load(aeth_ctx* c, int b) {
-  return c->elem == 8 ? load_store_T<double>(c, b, true) : load_store_T<float>(c, b, true);
+aeth_status enqueue_load(aeth_ctx* c, int b, double* const* io) {
+  return c->elem == 8 ? load_store_T<double>(c, b, true, io) : load_store_T<float>(c, b, true, io);
 }
-aeth_status enqueue_store(aeth_ctx* c, int b) {
-  return c->elem == 8 ? load_store_T<double>(c, b, false) : load_store_T<float>(c, b, false);
+aeth_status enqueue_store(aeth_ctx* c, int b, double* const* io) {
+  return c->elem == 8 ? load_store_T<double>(c, b, false, io) : load_store_T<float>(c, b, false, io);
 }
 
 // dust species k: rho_mom[4][nz][ny][nx] <-> register A
@@ -359,20 +356,20 @@ __global__ void k_dust_io(Layout L, R* __restrict__ dreg, int k, int load,
 }
 
 template <typename R>
-static aeth_status dust_io_T(aeth_ctx* c, int b, int k, bool load) {
+static aeth_status dust_io_T(aeth_ctx* c, int b, int k, bool load, double* io) {
   BlockPtrs<R> P = block_ptrs<R>(c, b);
   const Layout& L = P.L;
   dim3 blk(32, 4, 2);
   dim3 grd((L.n[0] + 31) / 32, (L.n[1] + 3) / 4, (L.n[2] + 1) / 2);
-  k_dust_io<R><<<grd, blk, 0, c->stream>>>(L, P.dust[0], k, load ? 1 : 0, c->d_stage);
+  k_dust_io<R><<<grd, blk, 0, c->stream>>>(L, P.dust[0], k, load ? 1 : 0, io);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }
-aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k) {
-  return c->elem == 8 ? dust_io_T<double>(c, b, k, true) : dust_io_T<float>(c, b, k, true);
+aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k, double* io) {
+  return c->elem == 8 ? dust_io_T<double>(c, b, k, true, io) : dust_io_T<float>(c, b, k, true, io);
 }
-aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k) {
-  return c->elem == 8 ? dust_io_T<double>(c, b, k, false) : dust_io_T<float>(c, b, k, false);
+aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k, double* io) {
+  return c->elem == 8 ? dust_io_T<double>(c, b, k, false, io) : dust_io_T<float>(c, b, k, false, io);
 }
 
 // ------------------------------------------------------------------------

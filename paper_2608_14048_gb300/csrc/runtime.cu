@@ -1,5 +1,7 @@
 // C-ABI entry points of include/aether_gb.h: context, block table, device
 // arena, host<->device state transfer, step sequencing and CUDA graphs.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -278,6 +280,42 @@ static aeth_status read_status(aeth_ctx* c) {
   return AETH_OK;
 }
 
+// Device address of a caller's host array of `bytes`, or null.  Only memory
+// the CUDA runtime has pinned and mapped (cudaHostAlloc, cudaHostRegister)
+// qualifies, and only when its allocation range covers the whole array:
+// the transfer kernels then read or write it directly over NVLink-C2C.
+// Anything else (pageable memory, a failed query) goes through the staging
+// buffer and cudaMemcpy.
+static void* mapped_host(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  using GetAttr = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static GetAttr get = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (GetAttr) nullptr;
+    }
+    return (GetAttr)f;
+  }();
+  if (!get) return nullptr;
+  const CUdeviceptr dp = (CUdeviceptr)(uintptr_t)at.devicePointer;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS) return nullptr;
+  if (get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS) return nullptr;
+  if (dp < start || dp + bytes > start + size) return nullptr;
+  return at.devicePointer;
+}
+
 aeth_status aeth_set_state(aeth_ctx* c, int b, const double* cons, const double* b1,
                            const double* b2, const double* b3) {
   aeth_status s = check_block(c, b);
@@ -285,18 +323,26 @@ aeth_status aeth_set_state(aeth_ctx* c, int b, const double* cons, const double*
   if (!cons) return fail(c, AETH_ERR_ARG, "cons is NULL");
   const auto& B = c->blocks[b];
   const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz, nc = nx * ny * nz;
-  double* d = c->d_stage;
-  AETH_CK(c, cudaMemcpyAsync(d, cons, 5 * nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  if (is_mhd(c)) {
-    if (!b1 || !b2 || !b3) return fail(c, AETH_ERR_ARG, "face fields are NULL");
-    double* p1 = d + 5 * nc;
-    double* p2 = p1 + nz * ny * (nx + 1);
-    double* p3 = p2 + nz * (ny + 1) * nx;
-    AETH_CK(c, cudaMemcpyAsync(p1, b1, nz * ny * (nx + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    AETH_CK(c, cudaMemcpyAsync(p2, b2, nz * (ny + 1) * nx * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    AETH_CK(c, cudaMemcpyAsync(p3, b3, (nz + 1) * ny * nx * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const bool mhd = is_mhd(c);
+  if (mhd && (!b1 || !b2 || !b3)) return fail(c, AETH_ERR_ARG, "face fields are NULL");
+  const size_t bytes[4] = {5 * nc * sizeof(double), nz * ny * (nx + 1) * sizeof(double),
+                           nz * (ny + 1) * nx * sizeof(double), (nz + 1) * ny * nx * sizeof(double)};
+  const double* host[4] = {cons, b1, b2, b3};
+  double* io[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool direct = true;
+  for (int q = 0; q < (mhd ? 4 : 1); ++q) {
+    io[q] = (double*)mapped_host(host[q], bytes[q]);
+    direct = direct && io[q];
   }
-  s = enqueue_load(c, b);
+  if (!direct) {
+    double* d = c->d_stage;
+    for (int q = 0; q < (mhd ? 4 : 1); ++q) {
+      io[q] = d;
+      AETH_CK(c, cudaMemcpyAsync(d, host[q], bytes[q], cudaMemcpyHostToDevice, c->stream));
+      d += bytes[q] / sizeof(double);
+    }
+  }
+  s = enqueue_load(c, b, io);
   if (s != AETH_OK) return s;
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   return AETH_OK;
@@ -306,19 +352,39 @@ aeth_status aeth_get_state(aeth_ctx* c, int b, double* cons, double* b1, double*
   aeth_status s = check_block(c, b);
   if (s != AETH_OK) return s;
   if (!cons) return fail(c, AETH_ERR_ARG, "cons is NULL");
-  s = enqueue_store(c, b);
-  if (s != AETH_OK) return s;
   const auto& B = c->blocks[b];
   const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz, nc = nx * ny * nz;
-  double* d = c->d_stage;
-  AETH_CK(c, cudaMemcpyAsync(cons, d, 5 * nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (is_mhd(c) && b1 && b2 && b3) {
-    double* p1 = d + 5 * nc;
-    double* p2 = p1 + nz * ny * (nx + 1);
-    double* p3 = p2 + nz * (ny + 1) * nx;
-    AETH_CK(c, cudaMemcpyAsync(b1, p1, nz * ny * (nx + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    AETH_CK(c, cudaMemcpyAsync(b2, p2, nz * (ny + 1) * nx * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    AETH_CK(c, cudaMemcpyAsync(b3, p3, (nz + 1) * ny * nx * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const bool faces = is_mhd(c) && b1 && b2 && b3;
+  const size_t bytes[4] = {5 * nc * sizeof(double), nz * ny * (nx + 1) * sizeof(double),
+                           nz * (ny + 1) * nx * sizeof(double), (nz + 1) * ny * nx * sizeof(double)};
+  double* host[4] = {cons, b1, b2, b3};
+  double* io[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool direct = true;
+  for (int q = 0; q < (faces ? 4 : 1); ++q) {
+    io[q] = (double*)mapped_host(host[q], bytes[q]);
+    direct = direct && io[q];
+  }
+  if (!direct) {
+    double* d = c->d_stage;
+    for (int q = 0; q < 4; ++q) {
+      io[q] = d;
+      d += bytes[q] / sizeof(double);
+    }
+  } else if (!faces) {
+    // the store kernel writes the face fields of an MHD state: into staging
+    double* d = c->d_stage;
+    for (int q = 1; q < 4; ++q) {
+      io[q] = d;
+      d += bytes[q] / sizeof(double);
+    }
+  }
+  s = enqueue_store(c, b, io);
+  if (s != AETH_OK) return s;
+  if (!direct) {
+    AETH_CK(c, cudaMemcpyAsync(cons, io[0], bytes[0], cudaMemcpyDeviceToHost, c->stream));
+    if (faces)
+      for (int q = 1; q < 4; ++q)
+        AETH_CK(c, cudaMemcpyAsync(host[q], io[q], bytes[q], cudaMemcpyDeviceToHost, c->stream));
   }
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   return read_status(c);
@@ -329,8 +395,13 @@ aeth_status aeth_set_dust(aeth_ctx* c, int b, int k, const double* rm) {
   if (s != AETH_OK) return s;
   if (k < 0 || k >= c->cfg.n_dust || !rm) return fail(c, AETH_ERR_ARG, "bad dust species or NULL");
   const auto& B = c->blocks[b];
-  AETH_CK(c, cudaMemcpyAsync(c->d_stage, rm, 4 * B.ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  s = enqueue_dust_load(c, b, k);
+  const size_t bytes = 4 * B.ncell * sizeof(double);
+  double* io = (double*)mapped_host(rm, bytes);
+  if (!io) {
+    io = c->d_stage;
+    AETH_CK(c, cudaMemcpyAsync(io, rm, bytes, cudaMemcpyHostToDevice, c->stream));
+  }
+  s = enqueue_dust_load(c, b, k, io);
   if (s != AETH_OK) return s;
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   return AETH_OK;
@@ -340,10 +411,13 @@ aeth_status aeth_get_dust(aeth_ctx* c, int b, int k, double* rm) {
   aeth_status s = check_block(c, b);
   if (s != AETH_OK) return s;
   if (k < 0 || k >= c->cfg.n_dust || !rm) return fail(c, AETH_ERR_ARG, "bad dust species or NULL");
-  s = enqueue_dust_store(c, b, k);
-  if (s != AETH_OK) return s;
   const auto& B = c->blocks[b];
-  AETH_CK(c, cudaMemcpyAsync(rm, c->d_stage, 4 * B.ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const size_t bytes = 4 * B.ncell * sizeof(double);
+  double* mapped = (double*)mapped_host(rm, bytes);
+  s = enqueue_dust_store(c, b, k, mapped ? mapped : c->d_stage);
+  if (s != AETH_OK) return s;
+  if (!mapped)
+    AETH_CK(c, cudaMemcpyAsync(rm, c->d_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   return read_status(c);
 }

@@ -160,11 +160,14 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b);
 aeth_status enqueue_step(aeth_ctx* c, bool cfl_on_device);
 aeth_status enqueue_dt(aeth_ctx* c);
 aeth_status enqueue_diag(aeth_ctx* c);
-aeth_status enqueue_load(aeth_ctx* c, int b);
-aeth_status enqueue_store(aeth_ctx* c, int b);
+// state / dust transfer kernels; io = the FP64 arrays (cons, b1, b2, b3) in
+// device-accessible memory: the staging buffer, or the caller's host arrays
+// where they are pinned and mapped (read and written over NVLink-C2C)
+aeth_status enqueue_load(aeth_ctx* c, int b, double* const* io);
+aeth_status enqueue_store(aeth_ctx* c, int b, double* const* io);
 aeth_status enqueue_set_dt(aeth_ctx* c, double dt);
-aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k);
-aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k);
+aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k, double* io);
+aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k, double* io);
 aeth_status build_geometry(aeth_ctx* c);
 aeth_status build_tables(aeth_ctx* c);
 

@@ -235,3 +235,65 @@ def test_batched_uneven_blocks_one_launch_per_pass(prec, tol):
         assert max(errs) < tol, (q, sts[q].block.n, sts[q].block.coord, errs)
     if prec == "fp64":
         assert diag["max_divb_rel"] < 1e-12
+
+
+def test_pinned_host_arrays_take_the_direct_path_bit_for_bit():
+    """set_state / get_state (and the dust twins) with pinned host arrays,
+    which the transfer kernels read and write directly, give exactly the
+    state of the staged path with pageable numpy arrays."""
+    import torch
+    n = (20, 12, 10)
+    st = I.smooth_random_mhd(I.Block(n), 91, v_rms=0.6, b_rms=0.5)
+    outs = []
+    for pinned in (False, True):
+        cfg = A.make_config(gamma=st.gamma, precision=A.FP32)
+        sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+        try:
+            arrs = [st.cons, st.b1, st.b2, st.b3]
+            if pinned:
+                arrs = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in arrs]
+            A.aeth_set_state(sv.ctx, 0, *arrs)
+            sv.step(1e-3)
+            if pinned:
+                res = [torch.empty(s, dtype=torch.float64).pin_memory() for s in sv.shapes(0)]
+                A.aeth_get_state(sv.ctx, 0, *res)
+                res = [r.numpy().copy() for r in res]
+            else:
+                res = sv.get_state(0)
+        finally:
+            sv.close()
+        outs.append(res)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_pinned_dust_arrays_take_the_direct_path_bit_for_bit():
+    import torch
+    n = (16, 12, 8)
+    gas, dust, ts = I.dust_box(I.Block(n), 92, nd=3)
+    outs = []
+    for pinned in (False, True):
+        cfg = A.make_config(gamma=gas.gamma, precision=A.FP32, mhd=False, integrator=A.IMEX2P,
+                            t_stop=ts)
+        sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+        try:
+            sv.set_state(0, gas.cons)
+            for k in range(dust.shape[0]):
+                x = np.ascontiguousarray(dust[k])
+                A.aeth_set_dust(sv.ctx, 0, k, torch.from_numpy(x).pin_memory() if pinned else x)
+            sv.step(1e-3)
+            res = []
+            for k in range(dust.shape[0]):
+                if pinned:
+                    r = torch.empty(dust.shape[1:], dtype=torch.float64).pin_memory()
+                    A.aeth_get_dust(sv.ctx, 0, k, r)
+                    res.append(r.numpy().copy())
+                else:
+                    r = np.empty(dust.shape[1:])
+                    A.aeth_get_dust(sv.ctx, 0, k, r)
+                    res.append(r)
+        finally:
+            sv.close()
+        outs.append(res)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
