@@ -33,7 +33,7 @@ METRIC = "cell-updates/s on 1 GB300 (FP32/learned vs FP64 plain) at stated L1; %
 UNIT = "cell-updates/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--drag", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--mlp-engine", default="tcgen05", choices=["tcgen05", "mma_sync"])
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -263,6 +263,24 @@ def cpu_baseline(a, st_full):
                       f"({el:.1f} s), OpenMP over {cores} host threads"}
 
 
+def max_over_ranks(x, ws, device=None):
+    """The maximum over all ranks of a per-rank float (the slowest rank sets
+    a multi-GPU time); the value itself at one rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput: the units every rank processed over the
+    (max-over-ranks) time."""
+    return units_per_rank * ws / seconds
+
+
 def run_reference(a):
     ws, rank, local = dist_env()
     if ws > 1 and rank != 0:
@@ -457,12 +475,8 @@ def main():
                              "train_samples": learned["samples"],
                              "train_loss": learned["losses"], "train_s": learned["seconds"]}}
 
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-
-    value = cells * a.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(ms, ws, device=dev)
+    value = whole_job_rate(cells * a.steps, ws, ms * 1e-3)
 
     # end to end through the public API with host buffers: every step copies
     # the state in from pinned host memory and reads it back
@@ -494,8 +508,8 @@ def main():
         if dust is not None:
             for k in range(dust.shape[0]):
                 A.aeth_get_dust(sv.ctx, 0, k, dbuf[k])
-    e2e_s = time.perf_counter() - t0
-    e2e_val = cells * ke * ws / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, device=dev)
+    e2e_val = whole_job_rate(cells * ke, ws, e2e_s)
     sv.close()
 
     hbm, peak_kind = peaks()
