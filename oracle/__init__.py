@@ -27,6 +27,7 @@ CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 DONOR, PLM, PPM = 0, 1, 2
 VL2, RK2 = 0, 1
+HLLD, HLLE = 0, 1
 
 
 class Grid(C.Structure):
@@ -38,7 +39,8 @@ class Grid(C.Structure):
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("recon", C.c_int),
-                ("integrator", C.c_int), ("cfl", C.c_double), ("mhd", C.c_int)]
+                ("integrator", C.c_int), ("cfl", C.c_double), ("mhd", C.c_int),
+                ("riemann", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -87,6 +89,8 @@ def lib():
             L.orc_mhd_diag.restype = None
             L.orc_hlld.argtypes = [C.c_double, dp, dp, C.c_double, dp]
             L.orc_hlld.restype = C.c_int
+            L.orc_hlle.argtypes = [C.c_double, dp, dp, C.c_double, dp]
+            L.orc_hlle.restype = None
             L.orc_recon_line.argtypes = [C.c_int, C.c_int, dp, dp, dp]
             L.orc_recon_line.restype = None
             L.orc_corner_emf.argtypes = [C.c_double] * 4 + [dp] + [C.c_double] * 4
@@ -123,8 +127,8 @@ def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), coord=CART, bc=(PERIODI
 
 
 def make_params(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, mhd=True,
-                rho_floor=1e-12, p_floor=1e-10) -> Params:
-    return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0)
+                rho_floor=1e-12, p_floor=1e-10, riemann=HLLD) -> Params:
+    return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0, riemann)
 
 
 class State:
@@ -174,6 +178,15 @@ def hlld(gamma: float, wl, wr, bn: float):
     f = np.zeros(7)
     reg = lib().orc_hlld(float(gamma), _dp(wl), _dp(wr), float(bn), _dp(f))
     return f, reg
+
+
+def hlle(gamma: float, wl, wr, bn: float):
+    """Face-frame HLLE flux[7] (orc_hlle)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.zeros(7)
+    lib().orc_hlle(float(gamma), _dp(wl), _dp(wr), float(bn), _dp(f))
+    return f
 
 
 def recon_line(recon: int, w):

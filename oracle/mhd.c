@@ -274,6 +274,22 @@ static void side_flux(double gamma, const double* w, double bn, double* u,
   *pt_out = pt;
 }
 
+void orc_hlle(double gamma, const double* wl, const double* wr, double bn, double* flux) {
+  double ul[7], ur[7], fl[7], fr[7], ptl, ptr;
+  side_flux(gamma, wl, bn, ul, fl, &ptl);
+  side_flux(gamma, wr, bn, ur, fr, &ptr);
+  double cfl = fast_speed(gamma, wl[0], wl[4], bn, wl[5], wl[6]);
+  double cfr = fast_speed(gamma, wr[0], wr[4], bn, wr[5], wr[6]);
+  double cmax = cfl > cfr ? cfl : cfr;
+  double sl = (wl[1] < wr[1] ? wl[1] : wr[1]) - cmax;
+  double sr = (wl[1] > wr[1] ? wl[1] : wr[1]) + cmax;
+  double bm = sl < 0.0 ? sl : 0.0;
+  double bp = sr > 0.0 ? sr : 0.0;
+  /* the HLL state integrates the conservation law over the fan [b-, b+] */
+  for (int q = 0; q < 7; ++q)
+    flux[q] = (bp * fl[q] - bm * fr[q] + bp * bm * (ur[q] - ul[q])) / (bp - bm);
+}
+
 #define HLLD_EPS 1e-12
 
 int orc_hlld(double gamma, const double* wl, const double* wr, double bn,
@@ -499,7 +515,8 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
           /* the normal field is the stored face value on both sides */
           double bn = mhd ? src_b[d][fc] : 0.0;
           double fx[7];
-          orc_hlld(p->gamma, wl, wr, bn, fx);
+          if (p->riemann == ORC_HLLE) orc_hlle(p->gamma, wl, wr, bn, fx);
+          else orc_hlld(p->gamma, wl, wr, bn, fx);
           wk->f[d][0][fc] = fx[0];
           wk->f[d][1 + d][fc] = fx[1];
           wk->f[d][1 + t1][fc] = fx[2];

@@ -31,6 +31,7 @@ enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_PERIODIC = 0, ORC_OUTFLOW = 1 };
 enum { ORC_DONOR = 0, ORC_PLM = 1, ORC_PPM = 2 };
 enum { ORC_VL2 = 0, ORC_RK2 = 1 };
+enum { ORC_HLLD = 0, ORC_HLLE = 1 };
 
 typedef struct {
   int nx, ny, nz;     /* interior cells along x1, x2, x3 */
@@ -46,6 +47,7 @@ typedef struct {
   int integrator;     /* ORC_VL2 or ORC_RK2 */
   double cfl;         /* Courant factor C of Eq. 11 */
   int mhd;            /* 1: MHD; 0: hydro (face arrays ignored, B = 0) */
+  int riemann;        /* ORC_HLLD (Sec. 2.4 default) or ORC_HLLE */
 } orc_params;
 
 typedef struct {
@@ -75,6 +77,15 @@ void orc_mhd_diag(const orc_grid* g, const orc_params* p, const double* cons,
  * 0..5 (L, *L, **L, **R, *R, R) that supplied the flux. */
 int orc_hlld(double gamma, const double* wl, const double* wr, double bn,
              double* flux);
+
+/* Single-face HLLE flux (Harten, Lax & van Leer 1983; Einfeldt 1988;
+ * Sec. 2.4), same frames as orc_hlld: the flux of the single averaged state
+ * of the HLL fan between the outer wave-speed estimates
+ *   S_L = min(vn_L, vn_R) - max(c_f,L, c_f,R),
+ *   S_R = max(vn_L, vn_R) + max(c_f,L, c_f,R)
+ * (the estimates the HLLD solver uses), with b- = min(S_L, 0) and
+ * b+ = max(S_R, 0) so that a supersonic face takes the upwind flux. */
+void orc_hlle(double gamma, const double* wl, const double* wr, double bn, double* flux);
 
 /* Reconstruction of one 1-D line: w[0..n-1] -> left/right states at the
  * n-1 interior faces (face f lies between cells f and f+1; faces whose

@@ -6,6 +6,10 @@ a wrong sign or index, a transposed operand) fails at least one of them:
 * HLLD: physical flux on equal states (consistency); exact hydro limit = the
   textbook HLLC; exact resolution of a stationary contact with B_n != 0;
   invariance under rotations of the transverse plane.
+* HLLE: consistency; upwind flux on supersonic faces; the closed-form
+  Rusanov reduction on a stationary contact; mirror/rotation symmetry;
+  positive density and pressure of the implied HLL state; Sod against the
+  exact solution; second order of PLM + HLLE + RK2 on a smooth wave.
 * Reconstruction: linear data exact (PLM, PPM); the fourth-order PPM
   interface value exact for cubic cell averages; first order at extrema.
 * Corner EMF (Gardiner & Stone 2005): plane-parallel data along either
@@ -155,6 +159,128 @@ def test_hlld_mirror_symmetry():
         np.testing.assert_allclose(fm, exp, rtol=1e-9, atol=1e-11)
 
 
+# --------------------------------------------------------------------- HLLE
+
+def _cons(g, w, bn):
+    rho, vn, v1, v2, p, b1, b2 = w
+    bb = bn * bn + b1 * b1 + b2 * b2
+    e = p / (g - 1) + 0.5 * rho * (vn * vn + v1 * v1 + v2 * v2) + 0.5 * bb
+    return np.array([rho, rho * vn, rho * v1, rho * v2, e, b1, b2])
+
+
+def _cf(g, w, bn):
+    """Fast magnetosonic speed along the normal."""
+    rho, p = w[0], w[4]
+    a2 = g * p / rho
+    b2 = (bn * bn + w[5] ** 2 + w[6] ** 2) / rho
+    s = a2 + b2
+    return math.sqrt(0.5 * (s + math.sqrt(max(s * s - 4 * a2 * bn * bn / rho, 0.0))))
+
+
+def test_hlle_consistency_equal_states():
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        w = rand_state(rng)
+        bn = rng.normal()
+        np.testing.assert_allclose(O.hlle(5 / 3, w, w, bn), physical_flux(5 / 3, w, bn),
+                                   rtol=1e-12, atol=1e-12)
+
+
+def test_hlle_supersonic_faces_take_the_upwind_flux():
+    rng = np.random.default_rng(22)
+    for _ in range(100):
+        wl = rand_state(rng); wr = rand_state(rng); bn = rng.normal()
+        c = max(_cf(5 / 3, wl, bn), _cf(5 / 3, wr, bn))
+        wl[1] = wr[1] = 0.0
+        wl[1] += c + 0.1 + rng.uniform(0, 1); wr[1] += c + 0.1 + rng.uniform(0, 1)
+        np.testing.assert_allclose(O.hlle(5 / 3, wl, wr, bn), physical_flux(5 / 3, wl, bn),
+                                   rtol=1e-13, atol=1e-13)
+        wl[1], wr[1] = -wl[1], -wr[1]
+        np.testing.assert_allclose(O.hlle(5 / 3, wl, wr, bn), physical_flux(5 / 3, wr, bn),
+                                   rtol=1e-13, atol=1e-13)
+
+
+def test_hlle_stationary_contact_is_rusanov_with_the_fast_speed():
+    # u = 0 on both sides, p, v_t and B continuous, rho jumps: the two
+    # physical fluxes agree and S_R = -S_L = c_max, so HLLE reduces to
+    # F_L - (c_max / 2)(U_R - U_L): a diffusive contact (HLLD's is exact)
+    wl = np.array([1.0, 0.0, 0.3, -0.2, 0.7, 0.4, 0.9])
+    wr = wl.copy(); wr[0] = 0.25
+    for bn in (0.8, -0.5, 0.0):
+        c = max(_cf(5 / 3, wl, bn), _cf(5 / 3, wr, bn))
+        ex = physical_flux(5 / 3, wl, bn) - 0.5 * c * (_cons(5 / 3, wr, bn) - _cons(5 / 3, wl, bn))
+        np.testing.assert_allclose(O.hlle(5 / 3, wl, wr, bn), ex, rtol=1e-13, atol=1e-14)
+        assert O.hlle(5 / 3, wl, wr, bn)[0] > 0.1     # mass diffuses toward the light side
+
+
+def test_hlle_mirror_and_rotation_symmetry():
+    rng = np.random.default_rng(23)
+    for _ in range(100):
+        wl = rand_state(rng); wr = rand_state(rng); bn = rng.normal()
+
+        def mir(w):
+            w = w.copy(); w[1] = -w[1]
+            return w
+
+        f = O.hlle(5 / 3, wl, wr, bn)
+        fm = O.hlle(5 / 3, mir(wr), mir(wl), -bn)
+        np.testing.assert_allclose(fm, [-f[0], f[1], -f[2], -f[3], -f[4], -f[5], -f[6]],
+                                   rtol=1e-9, atol=1e-11)
+        th = rng.uniform(0, 2 * math.pi)
+        c, s_ = math.cos(th), math.sin(th)
+
+        def rot(w):
+            w = w.copy()
+            w[2], w[3] = c * w[2] - s_ * w[3], s_ * w[2] + c * w[3]
+            w[5], w[6] = c * w[5] - s_ * w[6], s_ * w[5] + c * w[6]
+            return w
+
+        fr = O.hlle(5 / 3, rot(wl), rot(wr), bn)
+        exp = f.copy()
+        exp[2], exp[3] = c * f[2] - s_ * f[3], s_ * f[2] + c * f[3]
+        exp[5], exp[6] = c * f[5] - s_ * f[6], s_ * f[5] + c * f[6]
+        np.testing.assert_allclose(fr, exp, rtol=1e-9, atol=1e-11)
+
+
+def test_hlle_hll_state_keeps_density_and_pressure_positive():
+    # Einfeldt's property of HLLE with outer speed bounds: the intermediate
+    # state U* = U_L + (F - F_L) / S_L implied by the flux stays physical,
+    # here on strong hydro rarefactions (states moving apart)
+    rng = np.random.default_rng(24)
+    g = 1.4
+    for _ in range(300):
+        wl = rand_state(rng); wr = rand_state(rng)
+        wl[5:] = wr[5:] = 0.0
+        wl[1] = -abs(wl[1]) - rng.uniform(0, 3); wr[1] = abs(wr[1]) + rng.uniform(0, 3)
+        f = O.hlle(g, wl, wr, 0.0)
+        c = max(_cf(g, wl, 0.0), _cf(g, wr, 0.0))
+        sl = min(wl[1], wr[1]) - c
+        us = _cons(g, wl, 0.0) + (f - physical_flux(g, wl, 0.0)) / sl
+        assert us[0] > 0
+        pstar = (g - 1) * (us[4] - 0.5 * (us[1] ** 2 + us[2] ** 2 + us[3] ** 2) / us[0])
+        assert pstar > 0, (wl, wr, us)
+
+
+def test_sod_shock_tube_hlle_against_exact():
+    errs = []
+    for n in (128, 256):
+        st = I.riemann_1d(0, n, I.SOD_LEFT, I.SOD_RIGHT, 1.4)
+        s = _run_1d(st, 0.25, riemann=O.HLLE)
+        x = st.block.centers(0)
+        ex = ER.sample(x, 0.25, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+        errs.append(np.mean(np.abs(s.cons[0, 0, 0, :] - ex[0])))
+    assert errs[1] < 8e-3
+    order = math.log2(errs[0] / errs[1])
+    assert 0.6 < order < 1.3, (errs, order)
+
+
+def test_plm_hlle_rk2_fast_wave_second_order():
+    # the paper's throughput combination (PLM + HLLE + RK2) on a smooth wave
+    e64 = _aligned_wave_error(64, riemann=O.HLLE, integ=O.RK2)
+    e128 = _aligned_wave_error(128, riemann=O.HLLE, integ=O.RK2)
+    assert math.log2(e64 / e128) > 1.9, (e64, e128)
+
+
 # ------------------------------------------------------------ reconstruction
 
 @pytest.mark.parametrize("recon", [O.DONOR, O.PLM, O.PPM])
@@ -242,11 +368,11 @@ def test_corner_emf_upwind_selection():
 
 # ---------------------------------------------------------- whole-scheme pins
 
-def _run_1d(st, t_end, recon=O.PLM, integ=O.VL2, cfl=0.3):
+def _run_1d(st, t_end, recon=O.PLM, integ=O.VL2, cfl=0.3, riemann=O.HLLD):
     b = st.block
     g = O.make_grid(b.n, b.lo, b.hi, b.coord, b.bc)
     p = O.make_params(gamma=st.gamma, recon=recon, integrator=integ, cfl=cfl,
-                      mhd=bool(np.any(st.b1) or np.any(st.b2) or np.any(st.b3)))
+                      mhd=bool(np.any(st.b1) or np.any(st.b2) or np.any(st.b3)), riemann=riemann)
     s = O.State(st.cons, st.b1, st.b2, st.b3)
     O.run(g, p, s, t_end=t_end)
     return s
@@ -327,7 +453,7 @@ def _wave_error(n):
     return math.sqrt(err) / st.meta["amp"]
 
 
-def _aligned_wave_error(n, amp=1e-6, ntrans=4):
+def _aligned_wave_error(n, amp=1e-6, ntrans=4, riemann=O.HLLD, integ=O.VL2):
     """Fast wave along x in a thin 3-D periodic box (B = (1, sqrt2, 0.5),
     rho = 1, P = 1/gamma): L1 error of rho after one period."""
     g_ = 5 / 3
@@ -345,7 +471,7 @@ def _aligned_wave_error(n, amp=1e-6, ntrans=4):
     cons = np.stack([1 + amp * r[0] * cavg, amp * r[1] * cavg, amp * r[2] * cavg, amp * r[3] * cavg,
                      (1 / g_ + amp * r[4] * cavg) / (g_ - 1) + 0.5 * (1 + by ** 2 + bz ** 2)])
     g = O.make_grid((n, ntrans, ntrans))
-    p = O.make_params()
+    p = O.make_params(riemann=riemann, integrator=integ)
     s = O.State(cons, b1, b2, b3)
     O.run(g, p, s, t_end=1.0 / lam)
     return np.mean(np.abs(s.cons[0] - cons[0])) / amp
