@@ -39,7 +39,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fp32_p64"],
+                    help="working precision (default: fp64 for wave512, the paper's, else fp32)")
     ap.add_argument("--recon", default="plm", choices=["plm", "ppm"])
     ap.add_argument("--path", default="fused", choices=["fused", "unfused"])
     ap.add_argument("--n", type=int, default=256)
@@ -49,7 +50,11 @@ def parse(argv=None):
     ap.add_argument("--drag", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--mlp-engine", default="tcgen05", choices=["tcgen05", "mma_sync"])
-    return ap.parse_args(argv)
+    ap.add_argument("--hydro", action="store_true", help="wave512: the hydro column (B = 0)")
+    a = ap.parse_args(argv)
+    if a.prec is None:
+        a.prec = "fp64" if a.workload == "wave512" else "fp32"
+    return a
 
 
 def dist_env():
@@ -59,7 +64,11 @@ def dist_env():
     return ws, rank, local
 
 
-WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512")
+WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512", "wave512")
+# the paper's single-device throughput table (Sec. 6.1): PLM + HLLE + RK2,
+# FP64, 3-D linear wave at 512 x 512 x 256, NVIDIA A100 40 GB, in cells per
+# second per device
+PAPER_WAVE512 = {"mhd": 300e6, "hydro": 709e6}
 
 
 def workload_config(a):
@@ -85,6 +94,16 @@ def workload_config(a):
                 "beta": "0.1..10 (log10 beta = sin 2 pi y)", "gamma": 1.0001,
                 "precision": "fp32 state, bf16 network", "seed": 20260820,
                 "training": "interface states of a 128^3 HLLD run of the same generator",
+                "l2": "inputs larger than L2"}
+    if a.workload == "wave512":
+        kind = "hydro" if a.hydro else "mhd"
+        return {"workload": f"linear_wave_512x512x256_{kind}", "grid": [512, 512, 256],
+                "box": [2.0, 2.0, 1.0], "recon": "PLM", "riemann": "HLLE", "integrator": "RK2",
+                "ct": "upwind corner EMF (GS05)" if not a.hydro else None, "cfl": 0.3,
+                "gamma": 5.0 / 3.0, "precision": a.prec, "path": a.path, "amplitude": 1e-6,
+                "blocks": "one 512x512x256 block (the paper tiles it into 128^3 blocks)",
+                "paper_reference": f"{PAPER_WAVE512[kind] / 1e6:.0f} Mzcps, NVIDIA A100 40GB, FP64 "
+                                   "(paper Sec. 6.1 table)",
                 "l2": "inputs larger than L2"}
     if a.workload == "wave32":
         return {"workload": "linear_fast_wave_32^3", "grid": [32, 32, 32], "recon": "PLM",
@@ -240,13 +259,24 @@ def make_input(a):
 
 def cpu_baseline(a, st_full):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    same generator on a 64^3 box, stepped until ~10 s of CPU work."""
+    same generator on a 64^3 box (64 x 64 x 32 of the 2 x 2 x 1 box for the
+    linear wave), stepped until ~10 s of CPU work."""
     import oracle as O
     from paper_2608_14048_gb300 import inputs as I
     n = 64
-    st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
-    g = O.make_grid((n, n, n))
-    p = O.make_params(gamma=st.gamma, recon=O.PLM if a.recon == "plm" else O.PPM)
+    if a.workload == "wave512":
+        st = I.linear_wave_box((64, 64, 32), (2.0, 2.0, 1.0), mhd=not a.hydro)
+        g = O.make_grid((64, 64, 32), hi=(2.0, 2.0, 1.0))
+        p = O.make_params(gamma=st.gamma, recon=O.PLM, integrator=O.RK2, riemann=O.HLLE,
+                          mhd=not a.hydro)
+        cells = 64 * 64 * 32
+        what = f"{'hydro' if a.hydro else 'MHD'} linear wave 64x64x32 (PLM+HLLE+RK2)"
+    else:
+        st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
+        g = O.make_grid((n, n, n))
+        p = O.make_params(gamma=st.gamma, recon=O.PLM if a.recon == "plm" else O.PPM)
+        cells = n ** 3
+        what = f"{n}^3 box of the same turbulence generator"
     s = O.State(st.cons, st.b1, st.b2, st.b3)
     dt = O.compute_dt(g, p, s)
     t0 = time.perf_counter()
@@ -258,9 +288,24 @@ def cpu_baseline(a, st_full):
         O.step(g, p, dt, s)
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n ** 3 * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, {n}^3 box of the same turbulence generator, {k} VL2 steps "
-                      f"({el:.1f} s), OpenMP over {cores} host threads"}
+    return {"value": cells * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {what}, {k} steps ({el:.1f} s), OpenMP over {cores} "
+                      f"host threads"}
+
+
+def vs_paper(a, value):
+    """value / the paper's number for this exact workload, metric and
+    precision (only the FP64 linear-wave benchmark has one), else None."""
+    if a.workload == "wave512" and a.prec == "fp64":
+        return value / PAPER_WAVE512["hydro" if a.hydro else "mhd"]
+    return None
+
+
+def bytes_per_cell_update(a):
+    """HBM bytes per cell-update of the two-stage step at the state's
+    precision: 40 words for MHD, 25 for hydro, ~185 for 8 dust species."""
+    words = 185.0 if a.workload == "dust128" else (25.0 if a.workload == "wave512" and a.hydro else 40.0)
+    return words * (8.0 if a.prec == "fp64" else 4.0)
 
 
 def max_over_ranks(x, ws, device=None):
@@ -290,7 +335,8 @@ def run_reference(a):
     steps = a.steps
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
             "n_gpus": a.gpus, "steps": steps, "warmup": a.warmup,
-            "ms_per_step": 64 ** 3 / base["value"] * 1e3, "higher_is_better": True,
+            "ms_per_step": (64 * 64 * 32 if a.workload == "wave512" else 64 ** 3) / base["value"] * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(a), "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -317,7 +363,7 @@ def main():
 
     # CPU baseline first (rank 0, N = 1), before the GPU work starts
     base = None
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload == "turb256":
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload in ("turb256", "wave512"):
         base = cpu_baseline(a, None)
 
     prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]
@@ -345,6 +391,11 @@ def main():
         cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.VL2, cfl=0.3,
                             precision=A.FP32, path=path, riemann=A.MLP,
                             mlp_engine=A.TCGEN05 if a.mlp_engine == "tcgen05" else A.MMA_SYNC)
+    elif a.workload == "wave512":
+        from paper_2608_14048_gb300 import inputs as I
+        states = [I.linear_wave_box((512, 512, 256), (2.0, 2.0, 1.0), mhd=not a.hydro)]
+        cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.RK2, cfl=0.3,
+                            precision=prec, path=path, riemann=A.HLLE, mhd=not a.hydro)
     elif a.workload == "wave32":
         from paper_2608_14048_gb300 import inputs as I
         states = [I.linear_fast_wave(32)]
@@ -358,7 +409,7 @@ def main():
               for s_ in states]
     stream = torch.cuda.current_stream(dev)
     sv = A.Solver(cfg, blocks, stream=stream)
-    mhd_run = a.workload != "dust128"
+    mhd_run = a.workload != "dust128" and not (a.workload == "wave512" and a.hydro)
     if a.workload == "learned512":
         A.aeth_load_mlp(sv.ctx, learned["params"])
 
@@ -520,7 +571,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "weak", "vs_baseline": vs_paper(a, value),
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32+f64"}[a.prec],
         "data": "synthetic", "config": workload_config(a),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -530,8 +581,7 @@ def main():
                      "algo_bytes_per_launch": kbytes / max(klaunch, 1),
                      "kernel_ms_per_launch": kms / max(klaunch, 1),
                      "kernel_share_of_step": (kms / ms) if ms > 0 else None,
-                     "cell_rate_hbm_frac": value / ws * (160.0 if a.prec != "fp64" else 320.0)
-                     / (hbm * 1e9) if mhd_run else value / ws * 740.0 / (hbm * 1e9)},
+                     "cell_rate_hbm_frac": value / ws * bytes_per_cell_update(a) / (hbm * 1e9)},
         "cpu_baseline": base,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": ke},

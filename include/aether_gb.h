@@ -57,9 +57,11 @@ typedef enum {
 enum { AETH_EOS_ADIABATIC_MHD = 0, AETH_EOS_ADIABATIC_HYDRO = 1 };
 /* reconstruction (Sec. 2.4) */
 enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2 };
-/* Riemann solver (Sec. 2.4); AETH_RIEMANN_MLP = learned flux with HLLD
- * fallback */
-enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_MLP = 2 };
+/* Riemann solver (Sec. 2.4): HLLD (Miyoshi & Kusano 2005); HLLE (Harten,
+ * Lax & van Leer 1983; Einfeldt 1988) with the outer speed estimates of the
+ * HLLD solver, the paper's throughput-benchmark solver; AETH_RIEMANN_MLP =
+ * learned flux with HLLD fallback */
+enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_HLLE = 1, AETH_RIEMANN_MLP = 2 };
 /* tensor-core engine of the learned flux: tcgen05 MMAs with TMEM
  * accumulators, or warp-level mma.sync */
 enum { AETH_MLP_TCGEN05 = 0, AETH_MLP_MMA_SYNC = 1 };

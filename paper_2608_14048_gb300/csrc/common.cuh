@@ -283,6 +283,38 @@ __device__ __forceinline__ int hlld(R gamma, const R* wl, const R* wr, R bn, R* 
                 wr[3], wr[4], wr[5], wr[6], bn, flux);
 }
 
+// HLLE (Harten, Lax & van Leer 1983; Einfeldt 1988; Sec. 2.4): the flux of
+// the single averaged state of the HLL fan between the outer speeds of the
+// HLLD solver, S_L = min(vn) - max(c_f), S_R = max(vn) + max(c_f), with
+// b- = min(S_L, 0), b+ = max(S_R, 0) (a supersonic face takes the upwind
+// flux without a branch).  Same frames as hlld; returns 0.
+template <typename R>
+__device__ __forceinline__ int hlle(R gamma, const R* wl, const R* wr, R bn, R* f) {
+  const R gm1 = gamma - R(1);
+  auto side = [&](const R* w, R* u, R* fx) {
+    const R rho = w[0], vn = w[1], v1 = w[2], v2 = w[3], p = w[4], b1 = w[5], b2 = w[6];
+    const R bb = bn * bn + b1 * b1 + b2 * b2;
+    const R pt = p + R(0.5) * bb;
+    const R e = p / gm1 + R(0.5) * rho * (vn * vn + v1 * v1 + v2 * v2) + R(0.5) * bb;
+    const R vb = vn * bn + v1 * b1 + v2 * b2;
+    u[0] = rho; u[1] = rho * vn; u[2] = rho * v1; u[3] = rho * v2; u[4] = e; u[5] = b1; u[6] = b2;
+    fx[0] = rho * vn; fx[1] = rho * vn * vn + pt - bn * bn; fx[2] = rho * vn * v1 - bn * b1;
+    fx[3] = rho * vn * v2 - bn * b2; fx[4] = (e + pt) * vn - bn * vb;
+    fx[5] = b1 * vn - bn * v1; fx[6] = b2 * vn - bn * v2;
+  };
+  R ul[7], ur[7], fl[7], fr[7];
+  side(wl, ul, fl);
+  side(wr, ur, fr);
+  const R cm = fmax(fast_speed(gamma, wl[0], wl[4], bn, wl[5], wl[6]),
+                    fast_speed(gamma, wr[0], wr[4], bn, wr[5], wr[6]));
+  const R bm = fmin(fmin(wl[1], wr[1]) - cm, R(0));
+  const R bp = fmax(fmax(wl[1], wr[1]) + cm, R(0));
+  const R inv = R(1) / (bp - bm);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) f[q] = (bp * fl[q] - bm * fr[q] + bp * bm * (ur[q] - ul[q])) * inv;
+  return 0;
+}
+
 // Upwind selection of Gardiner & Stone (2005): lower-index value for a
 // positive mass flux, upper for negative, mean for zero.
 template <typename R>

@@ -73,7 +73,7 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // 1. flux pass.  Persistent: CTAs stride over the tiles of all blocks.
 //    AETH_FLUX_MINB CTAs per SM in FP32; FP64 takes the full register file.
 // ------------------------------------------------------------------------
-// SOLVER 0: HLLD; 1: write the face states (wl, wr, bn) for the learned
+// SOLVER 0: HLLD; 2: HLLE; 1: write the face states (wl, wr, bn) for the learned
 // flux instead of solving.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
@@ -157,8 +157,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
           recon_var<RECON>([&](int off) { return sw[slot[v]][sy][sx + off]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[5 * pitch + fc] : R(0);
-        if (SOLVER == 0) {
-          hlld(gamma, wl, wr, bn, fx);
+        if (SOLVER != 1) {
+          if (SOLVER == 2) hlle(gamma, wl, wr, bn, fx);
+          else hlld(gamma, wl, wr, bn, fx);
           store_face<0>(sb, pitch, fc, fx);
         } else {
           R* fs = P.fstate + (0 * 15) * pitch + fc;
@@ -176,8 +177,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
           recon_var<RECON>([&](int off) { return sw[slot[v]][sy + off][sx]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[6 * pitch + fc] : R(0);
-        if (SOLVER == 0) {
-          hlld(gamma, wl, wr, bn, fx);
+        if (SOLVER != 1) {
+          if (SOLVER == 2) hlle(gamma, wl, wr, bn, fx);
+          else hlld(gamma, wl, wr, bn, fx);
           store_face<1>(sb, pitch, fc, fx);
         } else {
           R* fs = P.fstate + (1 * 15) * pitch + fc;
@@ -194,8 +196,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
           recon_var<RECON>([&](int off) { return q[v][off + RL]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[7 * pitch + fc] : R(0);
-        if (SOLVER == 0) {
-          hlld(gamma, wl, wr, bn, fx);
+        if (SOLVER != 1) {
+          if (SOLVER == 2) hlle(gamma, wl, wr, bn, fx);
+          else hlld(gamma, wl, wr, bn, fx);
           store_face<2>(sb, pitch, fc, fx);
         } else {
           R* fs = P.fstate + (2 * 15) * pitch + fc;
@@ -564,6 +567,12 @@ static void flux_pass(aeth_ctx* c, int recon, int src, int block) {
     } else {
       for (int b = 0; b < (int)c->blocks.size(); ++b) mlp_flux_pass<R>(c, b);
     }
+    return;
+  }
+  if (c->cfg.riemann == AETH_RIEMANN_HLLE) {
+    if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD, 2>(c, src, block);
+    else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD, 2>(c, src, block);
+    else launch_flux3<R, P64, 2, MHD, 2>(c, src, block);
     return;
   }
   if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD>(c, src, block);

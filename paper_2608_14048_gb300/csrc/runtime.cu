@@ -54,7 +54,9 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (cfg->eos != AETH_EOS_ADIABATIC_MHD && cfg->eos != AETH_EOS_ADIABATIC_HYDRO) bad = AETH_ERR_ARG;
   if (!(cfg->gamma > 1.0)) bad = AETH_ERR_ARG;
   if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM) bad = AETH_ERR_ARG;
-  if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_MLP) bad = AETH_ERR_ARG;
+  if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_HLLE &&
+      cfg->riemann != AETH_RIEMANN_MLP)
+    bad = AETH_ERR_ARG;
   if (cfg->integrator < AETH_INT_VL2 || cfg->integrator > AETH_INT_IMEX2P) bad = AETH_ERR_ARG;
   if (cfg->precision < AETH_FP64 || cfg->precision > AETH_FP32_P64) bad = AETH_ERR_ARG;
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) bad = AETH_ERR_ARG;

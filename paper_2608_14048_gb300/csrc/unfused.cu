@@ -53,7 +53,7 @@ __global__ void k_prim(Layout L, ConstArr8<R> u, Arr8<R> w, int mhd, double gamm
 // ------------------------------------------------------------------------
 template <typename R, int RECON>
 __global__ void k_flux(Layout L, ConstArr8<R> w, const R* __restrict__ bface, int d, int mhd,
-                       R gamma, R* f0, R* f1, R* f2, R* f3, R* f4, R* e0, R* e1) {
+                       int solver, R gamma, R* f0, R* f1, R* f2, R* f3, R* f4, R* e0, R* e1) {
   int c[3];
   c[0] = blockIdx.x * blockDim.x + threadIdx.x;
   c[1] = blockIdx.y * blockDim.y + threadIdx.y;
@@ -83,7 +83,8 @@ __global__ void k_flux(Layout L, ConstArr8<R> w, const R* __restrict__ bface, in
   }
   const R bn = mhd ? bface[fc] : R(0);
   R fx[7];
-  hlld(gamma, wl, wr, bn, fx);
+  if (solver == AETH_RIEMANN_HLLE) hlle(gamma, wl, wr, bn, fx);
+  else hlld(gamma, wl, wr, bn, fx);
   R* fo[5] = {f0, f1, f2, f3, f4};
   fo[0][fc] = fx[0];
   fo[1 + d][fc] = fx[1];
@@ -243,13 +244,13 @@ static void stage_unfused(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src
     const double faces = (double)ext[0] * ext[1] * ext[2];
     prof_begin(c);
     if (recon == AETH_RECON_DONOR)
-      k_flux<R, 0><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+      k_flux<R, 0><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, c->cfg.riemann, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     else if (recon == AETH_RECON_PLM)
-      k_flux<R, 1><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+      k_flux<R, 1><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, c->cfg.riemann, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     else
-      k_flux<R, 2><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+      k_flux<R, 2><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, c->cfg.riemann, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     prof_end(c, faces * (mhd ? 15 : 10) * sizeof(R));
   }

@@ -227,6 +227,58 @@ def linear_fast_wave(n=32, amp=1e-6, gamma=5.0 / 3.0) -> InitialState:
                         {"speed": lam, "period": period, "amp": amp, "B0": B0})
 
 
+def linear_wave_box(shape=(512, 512, 256), lengths=(2.0, 2.0, 1.0), amp=1e-6,
+                    gamma=5.0 / 3.0, mhd=True, gl=2) -> InitialState:
+    """The 3-D linear-wave throughput problem (paper Sec. 6.1) on a periodic
+    box of uniform spacing: rho = 1, P = 1/gamma, one right-moving fast
+    (MHD, B = (1, sqrt2, 0.5) in the wave frame) or sound (hydro) eigenmode
+    of amplitude amp with wave vector 2 pi (1/Lx, 1/Ly, 1/Lz), periodic on
+    every axis (along (1,1,2) for the default 2 x 2 x 1 box).  Cell averages
+    of the perturbation are exact (one sinc factor per axis); face B comes
+    from edge integrals of a vector potential (Gauss-Legendre order gl), so
+    div B = 0 to round-off whatever gl."""
+    b = Block(tuple(shape), hi=tuple(float(x) for x in lengths))
+    kvec = 2 * math.pi * np.array([1.0 / lengths[0], 1.0 / lengths[1], 1.0 / lengths[2]])
+    khat = kvec / np.linalg.norm(kvec)
+    t1 = np.array([-khat[1], khat[0], 0.0]); t1 /= np.linalg.norm(t1)
+    t2 = np.cross(khat, t1)
+    bpar, bt1, bt2 = (1.0, math.sqrt(2.0), 0.5) if mhd else (0.0, 0.0, 0.0)
+    B0 = bpar * khat + bt1 * t1 + bt2 * t2
+    p0 = 1.0 / gamma
+    lam, r = fast_eigenvector(gamma, 1.0, p0, bpar, bt1, bt2)
+    X, Y, Z = _cell_mesh(b)
+    h = [lengths[d] / shape[d] for d in range(3)]
+    sinc = np.prod([math.sin(kvec[d] * h[d] / 2) / (kvec[d] * h[d] / 2) for d in range(3)])
+    cavg = np.cos(kvec[0] * X + kvec[1] * Y + kvec[2] * Z) * sinc
+    del X, Y, Z
+    dv = amp * (r[1] * khat + r[2] * t1 + r[3] * t2)
+    dp = amp * r[4]
+    if mhd:
+        db = amp * (r[5] * t1 + r[6] * t2)
+        avec = -np.cross(kvec, db) / float(kvec @ kvec)
+
+        def A(x1, x2, x3):
+            sn = np.sin(kvec[0] * x1 + kvec[1] * x2 + kvec[2] * x3)
+            return (avec[0] * sn, avec[1] * sn, avec[2] * sn)
+
+        b1, b2, b3 = face_field_from_potential(b, A, B0, gl=gl)
+        eb = 0.5 * ((0.5 * (b1[:, :, 1:] + b1[:, :, :-1])) ** 2 +
+                    (0.5 * (b2[:, 1:, :] + b2[:, :-1, :])) ** 2 +
+                    (0.5 * (b3[1:, :, :] + b3[:-1, :, :])) ** 2)
+    else:
+        nz, ny, nx = shape[2], shape[1], shape[0]
+        b1 = np.zeros((nz, ny, nx + 1)); b2 = np.zeros((nz, ny + 1, nx)); b3 = np.zeros((nz + 1, ny, nx))
+        eb = 0.0
+    cons = np.empty((5,) + cavg.shape)
+    cons[0] = 1.0 + amp * r[0] * cavg
+    for d in range(3):
+        cons[1 + d] = dv[d] * cavg
+    cons[4] = (p0 + dp * cavg) / (gamma - 1.0) + eb
+    period = (1.0 / float(np.linalg.norm(kvec / (2 * math.pi)))) / lam
+    return InitialState(b, cons, b1, b2, b3, gamma,
+                        {"speed": lam, "period": period, "amp": amp, "B0": B0})
+
+
 # ---------------------------------------------------------------------------
 # random smooth periodic fields
 # ---------------------------------------------------------------------------

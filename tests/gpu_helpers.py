@@ -9,6 +9,7 @@ from paper_2608_14048_gb300 import aether as A
 RECON = {"donor": (O.DONOR, A.DONOR), "plm": (O.PLM, A.PLM), "ppm": (O.PPM, A.PPM)}
 INTEG = {"vl2": (O.VL2, A.VL2), "rk2": (O.RK2, A.RK2)}
 PREC = {"fp64": A.FP64, "fp32": A.FP32, "fp32_p64": A.FP32_P64}
+RIEMANN = {"hlld": (O.HLLD, A.HLLD), "hlle": (O.HLLE, A.HLLE)}
 
 
 def rel_l1(a, b):
@@ -16,23 +17,25 @@ def rel_l1(a, b):
     return float(np.sum(np.abs(a - b)) / den) if den > 0 else float(np.sum(np.abs(a)))
 
 
-def oracle_run(st, recon="plm", integ="vl2", nsteps=4, mhd=True, dts=None, cfl=0.3):
+def oracle_run(st, recon="plm", integ="vl2", nsteps=4, mhd=True, dts=None, cfl=0.3,
+               riemann="hlld"):
     b = st.block
     g = O.make_grid(b.n, b.lo, b.hi, b.coord, b.bc)
     p = O.make_params(gamma=st.gamma, recon=RECON[recon][0], integrator=INTEG[integ][0],
-                      mhd=mhd, cfl=cfl)
+                      mhd=mhd, cfl=cfl, riemann=RIEMANN[riemann][0])
     s = O.State(st.cons, st.b1, st.b2, st.b3)
     used = O.run(g, p, s, nsteps=None if dts is not None else nsteps, dts=dts)
     return s, used
 
 
 def gpu_run(states, dts, recon="plm", integ="vl2", prec="fp64", mhd=True, path=A.FUSED,
-            use_run=False, cfl=0.3):
+            use_run=False, cfl=0.3, riemann="hlld"):
     """Advance one or several blocks (list of InitialState) with the given dt
     sequence; returns a list of (cons, b1, b2, b3) per block."""
     import torch
     cfg = A.make_config(gamma=states[0].gamma, recon=RECON[recon][1], integrator=INTEG[integ][1],
-                        precision=PREC[prec], mhd=mhd, path=path, cfl=cfl)
+                        precision=PREC[prec], mhd=mhd, path=path, cfl=cfl,
+                        riemann=RIEMANN[riemann][1])
     blocks = [A.make_block(s.block.n, s.block.lo, s.block.hi, s.block.coord, s.block.bc)
               for s in states]
     sv = A.Solver(cfg, blocks, stream=torch.cuda.current_stream())

@@ -297,3 +297,37 @@ def test_pinned_dust_arrays_take_the_direct_path_bit_for_bit():
         outs.append(res)
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+# ----------------------------------------------------------------- HLLE
+@pytest.mark.parametrize("path", [A.FUSED, A.UNFUSED])
+@pytest.mark.parametrize("recon,integ", [("plm", "rk2"), ("plm", "vl2"), ("ppm", "rk2")])
+def test_hlle_fp64_parity_random_box(recon, integ, path):
+    """HLLE (Sec. 2.4) on both kernel paths, with the paper's throughput
+    combination PLM + HLLE + RK2 among the cases."""
+    st = _state(seed=13)
+    ref, dts = oracle_run(st, recon, integ, nsteps=5, riemann="hlle")
+    (out,), diag = gpu_run([st], dts, recon, integ, "fp64", path=path, riemann="hlle")
+    errs = compare(out, ref)
+    assert max(errs) < FP64_TOL, errs
+    assert diag["max_divb_rel"] < 1e-12
+
+
+@pytest.mark.parametrize("mhd", [True, False])
+def test_hlle_fp32_parity(mhd):
+    st = _state(seed=14, mhd=mhd)
+    ref, dts = oracle_run(st, "plm", "rk2", nsteps=5, mhd=mhd, riemann="hlle")
+    (out,), _ = gpu_run([st], dts, "plm", "rk2", "fp32", mhd=mhd, riemann="hlle")
+    errs = compare(out, ref, mhd=mhd)
+    assert max(errs) < FP32_TOL, errs
+
+
+def test_hlle_differs_from_hlld():
+    """The solver switch reaches the kernels: HLLE is more diffusive, so the
+    two GPU runs differ well beyond round-off while each matches its own
+    oracle (above)."""
+    st = _state(seed=15)
+    _, dts = oracle_run(st, "plm", "rk2", nsteps=3)
+    (a,), _ = gpu_run([st], dts, "plm", "rk2", "fp64", riemann="hlld")
+    (b,), _ = gpu_run([st], dts, "plm", "rk2", "fp64", riemann="hlle")
+    assert max(rel_l1(a[0][v], b[0][v]) for v in range(5)) > 1e-6
