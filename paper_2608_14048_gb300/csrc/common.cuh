@@ -124,21 +124,13 @@ __device__ __forceinline__ void recon_face(const R* s, R& wl, R& wr) {
 
 template <typename R>
 __device__ __forceinline__ R fast_speed(R gamma, R rho, R p, R bn, R bt1, R bt2) {
-  if constexpr (sizeof(R) == 4) {
-    // one reciprocal of rho for the three quotients
-    const R ir = R(1) / rho;
-    const R a2 = gamma * p * ir;
-    const R b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) * ir;
-    const R s = a2 + b2;
-    const R disc = fmax(s * s - R(4) * a2 * bn * bn * ir, R(0));
-    return sqrt(R(0.5) * (s + sqrt(disc)));
-  } else {
-    R a2 = gamma * p / rho;
-    R b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) / rho;
-    R s = a2 + b2;
-    R disc = fmax(s * s - R(4) * a2 * bn * bn / rho, R(0));
-    return sqrt(R(0.5) * (s + sqrt(disc)));
-  }
+  // one reciprocal of rho for the three quotients
+  const R ir = R(1) / rho;
+  const R a2 = gamma * p * ir;
+  const R b2 = (bn * bn + bt1 * bt1 + bt2 * bt2) * ir;
+  const R s = a2 + b2;
+  const R disc = fmax(s * s - R(4) * a2 * bn * bn * ir, R(0));
+  return sqrt(R(0.5) * (s + sqrt(disc)));
 }
 
 // Single-star state of one side (MK05): density, transverse velocity and
@@ -174,12 +166,24 @@ template <typename R>
 __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R byl, R bzl,
                                       R rr, R ur, R vr, R wr, R pr, R byr, R bzr, R bn,
                                       R* f) {
-  const R gm1 = gamma - R(1);
+  // internal energies p / (gamma - 1): FP64 shares one division (a long
+  // instruction sequence at the FP64 rate); FP32 keeps the single
+  // approximate division, whose rounding the learned flux's engines rely on
+  R eil, eir;
+  if constexpr (sizeof(R) == 8) {
+    const R igm1 = R(1) / (gamma - R(1));
+    eil = pl * igm1;
+    eir = pr * igm1;
+  } else {
+    const R gm1 = gamma - R(1);
+    eil = pl / gm1;
+    eir = pr / gm1;
+  }
   const R bb_l = bn * bn + byl * byl + bzl * bzl;
   const R bb_r = bn * bn + byr * byr + bzr * bzr;
   const R ptl = pl + R(0.5) * bb_l, ptr = pr + R(0.5) * bb_r;
-  const R el = pl / gm1 + R(0.5) * rl * (ul * ul + vl * vl + wl * wl) + R(0.5) * bb_l;
-  const R er = pr / gm1 + R(0.5) * rr * (ur * ur + vr * vr + wr * wr) + R(0.5) * bb_r;
+  const R el = eil + R(0.5) * rl * (ul * ul + vl * vl + wl * wl) + R(0.5) * bb_l;
+  const R er = eir + R(0.5) * rr * (ur * ur + vr * vr + wr * wr) + R(0.5) * bb_r;
   // physical fluxes
   const R vbl = ul * bn + vl * byl + wl * bzl, vbr = ur * bn + vr * byr + wr * bzr;
   const R fl0 = rl * ul, fr0 = rr * ur;
@@ -213,20 +217,11 @@ __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R b
   hlld_star(rr, ur, vr, wr, byr, bzr, er, ptr, sr, sm, pts, bn, rsr, v1sr, v2sr, b1sr, b2sr, esr);
   const R abn = fabs(bn);
   const bool degen = R(0.5) * bn * bn < Eps<R>::hlld * pts;
-  R sql, sqr, ssl, ssr;
-  if constexpr (sizeof(R) == 4) {
-    // one reciprocal square root gives sqrt(rho*) and |Bn| / sqrt(rho*)
-    const R ql = rsqrtf(rsl), qr = rsqrtf(rsr);
-    sql = rsl * ql;
-    sqr = rsr * qr;
-    ssl = degen ? sm : sm - abn * ql;
-    ssr = degen ? sm : sm + abn * qr;
-  } else {
-    sql = sqrt(rsl);
-    sqr = sqrt(rsr);
-    ssl = degen ? sm : sm - abn / sql;
-    ssr = degen ? sm : sm + abn / sqr;
-  }
+  // one reciprocal square root gives sqrt(rho*) and |Bn| / sqrt(rho*)
+  const R ql = rsqrt(rsl), qr = rsqrt(rsr);
+  const R sql = rsl * ql, sqr = rsr * qr;
+  const R ssl = degen ? sm : sm - abn * ql;
+  const R ssr = degen ? sm : sm + abn * qr;
   int region;
   if (ssl >= R(0)) region = 1;
   else if (sm >= R(0)) region = 2;
@@ -290,12 +285,12 @@ __device__ __forceinline__ int hlld(R gamma, const R* wl, const R* wr, R bn, R* 
 // flux without a branch).  Same frames as hlld; returns 0.
 template <typename R>
 __device__ __forceinline__ int hlle(R gamma, const R* wl, const R* wr, R bn, R* f) {
-  const R gm1 = gamma - R(1);
+  const R igm1 = R(1) / (gamma - R(1));
   auto side = [&](const R* w, R* u, R* fx) {
     const R rho = w[0], vn = w[1], v1 = w[2], v2 = w[3], p = w[4], b1 = w[5], b2 = w[6];
     const R bb = bn * bn + b1 * b1 + b2 * b2;
     const R pt = p + R(0.5) * bb;
-    const R e = p / gm1 + R(0.5) * rho * (vn * vn + v1 * v1 + v2 * v2) + R(0.5) * bb;
+    const R e = p * igm1 + R(0.5) * rho * (vn * vn + v1 * v1 + v2 * v2) + R(0.5) * bb;
     const R vb = vn * bn + v1 * b1 + v2 * b2;
     u[0] = rho; u[1] = rho * vn; u[2] = rho * v1; u[3] = rho * v2; u[4] = e; u[5] = b1; u[6] = b2;
     fx[0] = rho * vn; fx[1] = rho * vn * vn + pt - bn * bn; fx[2] = rho * vn * v1 - bn * b1;
