@@ -26,7 +26,7 @@ _lib = None
 CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 DONOR, PLM, PPM = 0, 1, 2
-VL2, RK2 = 0, 1
+VL2, RK2, RK3 = 0, 1, 2
 HLLD, HLLE = 0, 1
 
 

@@ -720,6 +720,21 @@ int orc_mhd_step(const orc_grid* g, const orc_params* p, double dt,
                   0.5, dt, B, Bb);
     hits += stage(&m, p, p->recon, &wk, B, Bb, 1.0, A, Ab, 0.0, NULL, NULL,
                   1.0, dt, A, Ab);
+  } else if (p->integrator == ORC_RK3) {
+    /* SSP-RK3 (Shu & Osher 1988; Sec. 2.6): u1 = u + dt L(u);
+     * u2 = 3/4 u + 1/4 u1 + 1/4 dt L(u1); u' = 1/3 u + 2/3 u2 + 2/3 dt L(u2),
+     * with a third register for u2 */
+    double *C[5], *Cb[3];
+    for (int v = 0; v < 5; ++v) C[v] = zalloc(m.size);
+    for (int d = 0; d < 3; ++d) Cb[d] = zalloc(m.size);
+    hits += stage(&m, p, p->recon, &wk, A, Ab, 1.0, A, Ab, 0.0, NULL, NULL,
+                  1.0, dt, B, Bb);
+    hits += stage(&m, p, p->recon, &wk, B, Bb, 0.75, A, Ab, 0.25, B, Bb, 0.25,
+                  dt, C, Cb);
+    hits += stage(&m, p, p->recon, &wk, C, Cb, 1.0 / 3.0, A, Ab, 2.0 / 3.0, C, Cb,
+                  2.0 / 3.0, dt, A, Ab);
+    for (int v = 0; v < 5; ++v) free(C[v]);
+    for (int d = 0; d < 3; ++d) free(Cb[d]);
   } else {
     /* two-register SSP-RK2 (Eq. 10): u2 <- u1; u1 <- u1 + dt L(u1);
      * u1 <- 1/2 u2 + 1/2 u1 + 1/2 dt L(u1) */

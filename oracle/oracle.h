@@ -30,7 +30,7 @@ extern "C" {
 enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_PERIODIC = 0, ORC_OUTFLOW = 1 };
 enum { ORC_DONOR = 0, ORC_PLM = 1, ORC_PPM = 2 };
-enum { ORC_VL2 = 0, ORC_RK2 = 1 };
+enum { ORC_VL2 = 0, ORC_RK2 = 1, ORC_RK3 = 2 };
 enum { ORC_HLLD = 0, ORC_HLLE = 1 };
 
 typedef struct {
@@ -44,7 +44,7 @@ typedef struct {
   double gamma;
   double rho_floor, p_floor;
   int recon;          /* reconstruction of the final (or only) stage */
-  int integrator;     /* ORC_VL2 or ORC_RK2 */
+  int integrator;     /* ORC_VL2, ORC_RK2 or ORC_RK3 */
   double cfl;         /* Courant factor C of Eq. 11 */
   int mhd;            /* 1: MHD; 0: hydro (face arrays ignored, B = 0) */
   int riemann;        /* ORC_HLLD (Sec. 2.4 default) or ORC_HLLE */

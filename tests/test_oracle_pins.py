@@ -14,6 +14,8 @@ a wrong sign or index, a transposed operand) fails at least one of them:
   interface value exact for cubic cell averages; first order at extrema.
 * Corner EMF (Gardiner & Stone 2005): plane-parallel data along either
   transverse axis reduces the corner value to the face value.
+* Time integrators: temporal order 3 (SSP-RK3) and 2 (SSP-RK2) at fixed
+  grid on a smooth wave.
 * Whole scheme: Sod shock tube (paper Sec. 5.1 set-up) against the exact
   Riemann solution; second-order convergence of the 3-D linear fast wave;
   div B at round-off; conservation to round-off; bitwise symmetry of a 1-D
@@ -492,6 +494,33 @@ def test_linear_fast_wave_second_order():
     assert math.log2(e32 / e64) > 1.9, (e32, e64)
 
 
+def _temporal_error(integ, m, t_end, ref):
+    """rho after m equal steps of the 16^3 fast wave with donor-cell states
+    and HLLE: a smooth semi-discrete operator (no limiter; HLLD would switch
+    between its ** states where S_M crosses zero around a fluid at rest,
+    which caps the observable temporal order), against `ref`."""
+    st = I.linear_fast_wave(16)
+    g = O.make_grid((16, 16, 16))
+    p = O.make_params(gamma=st.gamma, recon=O.DONOR, integrator=integ, riemann=O.HLLE)
+    s = O.State(st.cons, st.b1, st.b2, st.b3)
+    O.run(g, p, s, dts=[t_end / m] * m)
+    if ref is None:
+        return s.cons[0].copy()
+    return float(np.mean(np.abs(s.cons[0] - ref))) / st.meta["amp"]
+
+
+@pytest.mark.parametrize("integ,order", [(O.RK3, 3.0), (O.RK2, 2.0)])
+def test_runge_kutta_temporal_order(integ, order):
+    # same grid, step halved twice: the difference to a fine-step reference
+    # falls as dt^order (a wrong stage weight drops SSP-RK3 to first or
+    # second order)
+    t_end = 0.25 * I.linear_fast_wave(16).meta["period"]
+    ref = _temporal_error(integ, 1024, t_end, None)
+    e8, e16, e32 = (_temporal_error(integ, m, t_end, ref) for m in (8, 16, 32))
+    assert math.log2(e8 / e16) > order - 0.3, (e8, e16)
+    assert math.log2(e16 / e32) > order - 0.3, (e16, e32)
+
+
 def _random_periodic(n=12, seed=7, recon=O.PLM, integ=O.VL2, steps=6):
     st = I.smooth_random_mhd(I.Block((n, n + 2, n - 2)), seed, v_rms=0.8, b_rms=0.7,
                              B0=(0.3, -0.2, 0.1))
@@ -504,7 +533,8 @@ def _random_periodic(n=12, seed=7, recon=O.PLM, integ=O.VL2, steps=6):
     return st, s, d0, d1, g, p
 
 
-@pytest.mark.parametrize("recon,integ", [(O.PLM, O.VL2), (O.PPM, O.VL2), (O.PLM, O.RK2)])
+@pytest.mark.parametrize("recon,integ", [(O.PLM, O.VL2), (O.PPM, O.VL2), (O.PLM, O.RK2),
+                                         (O.PLM, O.RK3)])
 def test_conservation_and_divb(recon, integ):
     st, s, d0, d1, g, p = _random_periodic(recon=recon, integ=integ)
     assert d0["max_divb_rel"] < 1e-14
