@@ -65,8 +65,10 @@ enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_HLLE = 1, AETH_RIEMANN_MLP = 2 };
 /* tensor-core engine of the learned flux: tcgen05 MMAs with TMEM
  * accumulators, or warp-level mma.sync */
 enum { AETH_MLP_TCGEN05 = 0, AETH_MLP_MMA_SYNC = 1 };
-/* time integrator (Sec. 2.6) */
-enum { AETH_INT_VL2 = 0, AETH_INT_RK2 = 1, AETH_INT_IMEX2P = 2 };
+/* time integrator (Sec. 2.6): VL2, SSP-RK2, IMEX2P (dust runs), SSP-RK3
+ * (three stages in the two registers; Cartesian blocks only, since its
+ * middle stage updates the stage register in place) */
+enum { AETH_INT_VL2 = 0, AETH_INT_RK2 = 1, AETH_INT_IMEX2P = 2, AETH_INT_RK3 = 3 };
 /* working precision: all-FP64; FP32; FP32 with the pressure recovery of
  * Eq. 5 (E minus kinetic minus magnetic energy) evaluated in FP64 */
 enum { AETH_FP64 = 0, AETH_FP32 = 1, AETH_FP32_P64 = 2 };

@@ -27,7 +27,7 @@ EOS_MHD, EOS_HYDRO = 0, 1
 DONOR, PLM, PPM = 0, 1, 2
 HLLD, HLLE, MLP = 0, 1, 2
 TCGEN05, MMA_SYNC = 0, 1          # tensor-core engine of the learned flux
-VL2, RK2, IMEX2P = 0, 1, 2
+VL2, RK2, IMEX2P, RK3 = 0, 1, 2, 3
 FP64, FP32, FP32_P64 = 0, 1, 2
 CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1

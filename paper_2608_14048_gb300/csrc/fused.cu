@@ -628,6 +628,13 @@ static aeth_status step_fused_T(aeth_ctx* c) {
   } else if (c->cfg.integrator == AETH_INT_RK2) {
     stage_fused<R, P64, MHD>(c, recon, 0, R(1), R(0), R(1), 1);
     stage_fused<R, P64, MHD>(c, recon, 1, R(0.5), R(0.5), R(0.5), 0);
+  } else if (c->cfg.integrator == AETH_INT_RK3) {
+    // SSP-RK3 in two registers: B = A + dt L(A); B = 3/4 A + 1/4 B +
+    // 1/4 dt L(B) (in place: every cell reads only its own A and B);
+    // A = 1/3 A + 2/3 B + 2/3 dt L(B)
+    stage_fused<R, P64, MHD>(c, recon, 0, R(1), R(0), R(1), 1);
+    stage_fused<R, P64, MHD>(c, recon, 1, R(0.75), R(0.25), R(0.25), 1);
+    stage_fused<R, P64, MHD>(c, recon, 1, R(1.0 / 3.0), R(2.0 / 3.0), R(2.0 / 3.0), 0);
   } else {
     return fail(c, AETH_ERR_UNSUPPORTED, "integrator %d not available", c->cfg.integrator);
   }

@@ -57,7 +57,7 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_HLLE &&
       cfg->riemann != AETH_RIEMANN_MLP)
     bad = AETH_ERR_ARG;
-  if (cfg->integrator < AETH_INT_VL2 || cfg->integrator > AETH_INT_IMEX2P) bad = AETH_ERR_ARG;
+  if (cfg->integrator < AETH_INT_VL2 || cfg->integrator > AETH_INT_RK3) bad = AETH_ERR_ARG;
   if (cfg->precision < AETH_FP64 || cfg->precision > AETH_FP32_P64) bad = AETH_ERR_ARG;
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) bad = AETH_ERR_ARG;
   if (cfg->path != AETH_PATH_FUSED && cfg->path != AETH_PATH_UNFUSED) bad = AETH_ERR_ARG;
@@ -128,6 +128,8 @@ aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
   for (int q = 0; q < 3; ++q)
     if (d->bc[q] == AETH_BC_PERIODIC && nn[q] < g && nn[q] != 1)
       return fail(c, AETH_ERR_ARG, "periodic axis %d needs n >= ghost width %d (or n == 1)", q, g);
+  if (d->coord == AETH_COORD_SPH && c->cfg.integrator == AETH_INT_RK3)
+    return fail(c, AETH_ERR_UNSUPPORTED, "SSP-RK3 runs on Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH && c->cfg.n_dust > 0)
     return fail(c, AETH_ERR_UNSUPPORTED, "dust runs support Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH) {

@@ -302,6 +302,15 @@ aeth_status step_unfused(aeth_ctx* c) {
       stage_unfused<R, P64>(c, block_ptrs<R>(c, b), recon, 0, R(1), 0, R(0), R(1), 1);
     for (int b = 0; b < nb; ++b)
       stage_unfused<R, P64>(c, block_ptrs<R>(c, b), recon, 1, R(0.5), 1, R(0.5), R(0.5), 0);
+  } else if (c->cfg.integrator == AETH_INT_RK3) {
+    // SSP-RK3 in two registers (the middle stage updates B in place)
+    for (int b = 0; b < nb; ++b)
+      stage_unfused<R, P64>(c, block_ptrs<R>(c, b), recon, 0, R(1), 0, R(0), R(1), 1);
+    for (int b = 0; b < nb; ++b)
+      stage_unfused<R, P64>(c, block_ptrs<R>(c, b), recon, 1, R(0.75), 1, R(0.25), R(0.25), 1);
+    for (int b = 0; b < nb; ++b)
+      stage_unfused<R, P64>(c, block_ptrs<R>(c, b), recon, 1, R(1.0 / 3.0), 1, R(2.0 / 3.0),
+                            R(2.0 / 3.0), 0);
   } else {
     return fail(c, AETH_ERR_UNSUPPORTED, "integrator %d not available on the unfused path",
                 c->cfg.integrator);

@@ -331,3 +331,33 @@ def test_hlle_differs_from_hlld():
     (a,), _ = gpu_run([st], dts, "plm", "rk2", "fp64", riemann="hlld")
     (b,), _ = gpu_run([st], dts, "plm", "rk2", "fp64", riemann="hlle")
     assert max(rel_l1(a[0][v], b[0][v]) for v in range(5)) > 1e-6
+
+
+# ------------------------------------------------------------- SSP-RK3
+@pytest.mark.parametrize("path", [A.FUSED, A.UNFUSED])
+@pytest.mark.parametrize("recon,riemann", [("plm", "hlld"), ("ppm", "hlld"), ("plm", "hlle")])
+def test_rk3_fp64_parity(recon, riemann, path):
+    st = _state(seed=16)
+    ref, dts = oracle_run(st, recon, "rk3", nsteps=4, riemann=riemann)
+    (out,), diag = gpu_run([st], dts, recon, "rk3", "fp64", path=path, riemann=riemann)
+    errs = compare(out, ref)
+    assert max(errs) < FP64_TOL, errs
+    assert diag["max_divb_rel"] < 1e-12
+
+
+def test_rk3_fp32_parity_and_device_cfl_run():
+    st = _state(seed=17)
+    ref, dts = oracle_run(st, "plm", "rk3", nsteps=4)
+    (out,), _ = gpu_run([st], dts, "plm", "rk3", "fp32", use_run=True)
+    errs = compare(out, ref)
+    assert max(errs) < FP32_TOL, errs
+
+
+def test_rk3_rejects_spherical_blocks():
+    import torch
+    cfg = A.make_config(integrator=A.RK3)
+    b = A.make_block((8, 8, 8), lo=(1.0, 0.8, 0.0), hi=(2.0, 2.3, 1.0), coord=A.SPH,
+                     bc=(A.OUTFLOW, A.OUTFLOW, A.PERIODIC))
+    with pytest.raises(Exception) as e:
+        A.Solver(cfg, [b], stream=torch.cuda.current_stream())
+    assert "Cartesian" in str(e.value) or "UNSUPPORTED" in str(e.value)
