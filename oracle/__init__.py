@@ -40,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("recon", C.c_int),
                 ("integrator", C.c_int), ("cfl", C.c_double), ("mhd", C.c_int),
-                ("riemann", C.c_int)]
+                ("riemann", C.c_int), ("iso", C.c_int), ("cs_iso", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -91,6 +91,9 @@ def lib():
             L.orc_hlld.restype = C.c_int
             L.orc_hlle.argtypes = [C.c_double, dp, dp, C.c_double, dp]
             L.orc_hlle.restype = None
+            for fn in ("orc_hlld_iso", "orc_hlle_iso"):
+                getattr(L, fn).argtypes = [C.c_double, dp, dp, C.c_double, dp]
+                getattr(L, fn).restype = None
             L.orc_recon_line.argtypes = [C.c_int, C.c_int, dp, dp, dp]
             L.orc_recon_line.restype = None
             L.orc_corner_emf.argtypes = [C.c_double] * 4 + [dp] + [C.c_double] * 4
@@ -127,8 +130,10 @@ def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), coord=CART, bc=(PERIODI
 
 
 def make_params(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, mhd=True,
-                rho_floor=1e-12, p_floor=1e-10, riemann=HLLD) -> Params:
-    return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0, riemann)
+                rho_floor=1e-12, p_floor=1e-10, riemann=HLLD, iso=False, cs=1.0) -> Params:
+    """iso=True: the isothermal closure p = cs^2 rho (gamma unused)."""
+    return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0, riemann,
+                  1 if iso else 0, cs)
 
 
 class State:
@@ -178,6 +183,23 @@ def hlld(gamma: float, wl, wr, bn: float):
     f = np.zeros(7)
     reg = lib().orc_hlld(float(gamma), _dp(wl), _dp(wr), float(bn), _dp(f))
     return f, reg
+
+
+def hlld_iso(cs: float, wl, wr, bn: float):
+    """Face-frame isothermal HLLD flux[7] (orc_hlld_iso; energy entry 0)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.zeros(7)
+    lib().orc_hlld_iso(float(cs), _dp(wl), _dp(wr), float(bn), _dp(f))
+    return f
+
+
+def hlle_iso(cs: float, wl, wr, bn: float):
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.zeros(7)
+    lib().orc_hlle_iso(float(cs), _dp(wl), _dp(wr), float(bn), _dp(f))
+    return f
 
 
 def hlle(gamma: float, wl, wr, bn: float):

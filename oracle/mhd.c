@@ -159,8 +159,13 @@ static long cons_to_prim(const Mesh* m, const orc_params* p, double** u,
         }
         double ke = 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3);
         double me = 0.5 * (bc1 * bc1 + bc2 * bc2 + bc3 * bc3);
-        double pr = (p->gamma - 1.0) * (u[4][c] - ke - me);
-        if (pr < p->p_floor) { pr = p->p_floor; ++hits; }
+        double pr;
+        if (p->iso) {
+          pr = p->cs_iso * p->cs_iso * rho;
+        } else {
+          pr = (p->gamma - 1.0) * (u[4][c] - ke - me);
+          if (pr < p->p_floor) { pr = p->p_floor; ++hits; }
+        }
         w[0][c] = rho; w[1][c] = v1; w[2][c] = v2; w[3][c] = v3;
         w[4][c] = pr;  w[5][c] = bc1; w[6][c] = bc2; w[7][c] = bc3;
       }
@@ -272,6 +277,103 @@ static void side_flux(double gamma, const double* w, double bn, double* u,
   f[5] = b1 * vn - bn * v1;
   f[6] = b2 * vn - bn * v2;
   *pt_out = pt;
+}
+
+/* Physical flux and conserved vector of one isothermal side (p = a2 rho),
+ * face frame; the energy entries are zero. */
+static void side_flux_iso(double a2, const double* w, double bn, double* u, double* f) {
+  double rho = w[0], vn = w[1], v1 = w[2], v2 = w[3], b1 = w[5], b2 = w[6];
+  double pt = a2 * rho + 0.5 * (bn * bn + b1 * b1 + b2 * b2);
+  u[0] = rho; u[1] = rho * vn; u[2] = rho * v1; u[3] = rho * v2; u[4] = 0.0;
+  u[5] = b1; u[6] = b2;
+  f[0] = rho * vn;
+  f[1] = rho * vn * vn + pt - bn * bn;
+  f[2] = rho * vn * v1 - bn * b1;
+  f[3] = rho * vn * v2 - bn * b2;
+  f[4] = 0.0;
+  f[5] = b1 * vn - bn * v1;
+  f[6] = b2 * vn - bn * v2;
+}
+
+/* outer wave-speed estimates of both solvers: the fast speed with gamma = 1
+ * and p = a2 rho is the isothermal fast speed */
+static void iso_speeds(double a2, const double* wl, const double* wr, double bn, double* sl,
+                       double* sr) {
+  double cfl = fast_speed(1.0, wl[0], a2 * wl[0], bn, wl[5], wl[6]);
+  double cfr = fast_speed(1.0, wr[0], a2 * wr[0], bn, wr[5], wr[6]);
+  double cmax = cfl > cfr ? cfl : cfr;
+  *sl = (wl[1] < wr[1] ? wl[1] : wr[1]) - cmax;
+  *sr = (wl[1] > wr[1] ? wl[1] : wr[1]) + cmax;
+}
+
+void orc_hlle_iso(double cs, const double* wl, const double* wr, double bn, double* flux) {
+  double a2 = cs * cs, ul[7], ur[7], fl[7], fr[7], sl, sr;
+  side_flux_iso(a2, wl, bn, ul, fl);
+  side_flux_iso(a2, wr, bn, ur, fr);
+  iso_speeds(a2, wl, wr, bn, &sl, &sr);
+  double bm = sl < 0.0 ? sl : 0.0, bp = sr > 0.0 ? sr : 0.0;
+  for (int q = 0; q < 7; ++q)
+    flux[q] = (bp * fl[q] - bm * fr[q] + bp * bm * (ur[q] - ul[q])) / (bp - bm);
+}
+
+#define HLLD_ISO_EPS 1e-12
+
+void orc_hlld_iso(double cs, const double* wl, const double* wr, double bn, double* flux) {
+  double a2 = cs * cs, ul[7], ur[7], fl[7], fr[7], sl, sr;
+  side_flux_iso(a2, wl, bn, ul, fl);
+  side_flux_iso(a2, wr, bn, ur, fr);
+  iso_speeds(a2, wl, wr, bn, &sl, &sr);
+  if (sl >= 0.0) { for (int q = 0; q < 7; ++q) flux[q] = fl[q]; return; }
+  if (sr <= 0.0) { for (int q = 0; q < 7; ++q) flux[q] = fr[q]; return; }
+  /* density and normal momentum are uniform inside the fan (no contact
+   * wave): their fluxes there are the HLL fluxes, rho* is the HLL average
+   * and the normal velocity of the transverse jump conditions is
+   * u* = F_rho^HLL / rho* */
+  double rs = (sr * ur[0] - sl * ul[0] - (fr[0] - fl[0])) / (sr - sl);
+  double fm = (sr * fl[0] - sl * fr[0] + sl * sr * (ur[0] - ul[0])) / (sr - sl);
+  double fmn = (sr * fl[1] - sl * fr[1] + sl * sr * (ur[1] - ul[1])) / (sr - sl);
+  double us = fm / rs;
+  double sq = sqrt(rs);
+  double sgn = bn > 0.0 ? 1.0 : (bn < 0.0 ? -1.0 : 0.0);
+  double ssl = us - fabs(bn) / sq, ssr = us + fabs(bn) / sq;
+  /* outer star states: Rankine-Hugoniot conditions across S_L and S_R for
+   * the transverse momentum and field, with rho* and u* fixed */
+  double st[2][7], fs[2][7];
+  const double* w[2] = {wl, wr};
+  const double* uu[2] = {ul, ur};
+  const double* ff[2] = {fl, fr};
+  double s[2] = {sl, sr};
+  for (int k = 0; k < 2; ++k) {
+    double rho = w[k][0], vn = w[k][1];
+    double den = rho * (s[k] - vn) * (s[k] - us) - bn * bn;
+    double vt1 = w[k][2], vt2 = w[k][3], bt1 = w[k][5], bt2 = w[k][6];
+    if (fabs(den) >= HLLD_ISO_EPS * (rho * (s[k] - vn) * (s[k] - vn) + bn * bn)) {
+      double fv = bn * (us - vn) / den;
+      double fb = (rho * (s[k] - vn) * (s[k] - vn) - bn * bn) / den;
+      vt1 = w[k][2] - w[k][5] * fv;
+      vt2 = w[k][3] - w[k][6] * fv;
+      bt1 = w[k][5] * fb;
+      bt2 = w[k][6] * fb;
+    }
+    st[k][0] = rs; st[k][1] = rs * us; st[k][2] = rs * vt1; st[k][3] = rs * vt2; st[k][4] = 0.0;
+    st[k][5] = bt1; st[k][6] = bt2;
+    for (int q = 2; q < 7; ++q) fs[k][q] = ff[k][q] + s[k] * (st[k][q] - uu[k][q]);
+    fs[k][0] = fm;
+    fs[k][1] = fmn;
+    fs[k][4] = 0.0;
+  }
+  if (ssl >= 0.0) { for (int q = 0; q < 7; ++q) flux[q] = fs[0][q]; return; }
+  if (ssr <= 0.0) { for (int q = 0; q < 7; ++q) flux[q] = fs[1][q]; return; }
+  /* central state between the Alfven waves (equal densities on both sides) */
+  double vl1 = st[0][2] / rs, vl2 = st[0][3] / rs, vr1 = st[1][2] / rs, vr2 = st[1][3] / rs;
+  double vc1 = 0.5 * (vl1 + vr1) + 0.5 * (st[1][5] - st[0][5]) * sgn / sq;
+  double vc2 = 0.5 * (vl2 + vr2) + 0.5 * (st[1][6] - st[0][6]) * sgn / sq;
+  double bc1 = 0.5 * (st[0][5] + st[1][5]) + 0.5 * sq * (vr1 - vl1) * sgn;
+  double bc2 = 0.5 * (st[0][6] + st[1][6]) + 0.5 * sq * (vr2 - vl2) * sgn;
+  double uc[7] = {rs, rs * us, rs * vc1, rs * vc2, 0.0, bc1, bc2};
+  for (int q = 0; q < 7; ++q) flux[q] = fs[0][q];
+  for (int q = 2; q < 7; ++q) flux[q] += ssl * (uc[q] - st[0][q]);
+  flux[4] = 0.0;
 }
 
 void orc_hlle(double gamma, const double* wl, const double* wr, double bn, double* flux) {
@@ -515,8 +617,14 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
           /* the normal field is the stored face value on both sides */
           double bn = mhd ? src_b[d][fc] : 0.0;
           double fx[7];
-          if (p->riemann == ORC_HLLE) orc_hlle(p->gamma, wl, wr, bn, fx);
-          else orc_hlld(p->gamma, wl, wr, bn, fx);
+          if (p->iso) {
+            if (p->riemann == ORC_HLLE) orc_hlle_iso(p->cs_iso, wl, wr, bn, fx);
+            else orc_hlld_iso(p->cs_iso, wl, wr, bn, fx);
+          } else if (p->riemann == ORC_HLLE) {
+            orc_hlle(p->gamma, wl, wr, bn, fx);
+          } else {
+            orc_hlld(p->gamma, wl, wr, bn, fx);
+          }
           wk->f[d][0][fc] = fx[0];
           wk->f[d][1 + d][fc] = fx[1];
           wk->f[d][1 + t1][fc] = fx[2];
@@ -777,16 +885,22 @@ double orc_mhd_dt(const orc_grid* g, const orc_params* p, const double* cons,
           bc[2] = 0.5 * (b3[((long)k * ny + j) * nx + i] +
                          b3[((long)(k + 1) * ny + j) * nx + i]);
         }
-        double pr = (p->gamma - 1.0) *
-                    (cons[4 * ncell + c] -
-                     0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
-                     0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
-        if (pr < p->p_floor) pr = p->p_floor;
+        double pr, gam = p->gamma;
+        if (p->iso) {
+          /* isothermal: the fast speed with gamma = 1 and p = cs^2 rho */
+          pr = p->cs_iso * p->cs_iso * rho;
+          gam = 1.0;
+        } else {
+          pr = (p->gamma - 1.0) *
+               (cons[4 * ncell + c] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
+                0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+          if (pr < p->p_floor) pr = p->p_floor;
+        }
         double w[3];
         orc_widths(&m, i, j, k, w);
         for (int d = 0; d < 3; ++d) {
           int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-          double cf = fast_speed(p->gamma, rho, pr, bc[d], bc[t1], bc[t2]);
+          double cf = fast_speed(gam, rho, pr, bc[d], bc[t1], bc[t2]);
           double dtd = w[d] / (fabs(v[d]) + cf);
           if (dtd < dtmin) dtmin = dtd;
         }

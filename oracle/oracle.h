@@ -48,6 +48,9 @@ typedef struct {
   double cfl;         /* Courant factor C of Eq. 11 */
   int mhd;            /* 1: MHD; 0: hydro (face arrays ignored, B = 0) */
   int riemann;        /* ORC_HLLD (Sec. 2.4 default) or ORC_HLLE */
+  int iso;            /* 1: isothermal closure p = cs_iso^2 rho (Sec. 2.1): no
+                         energy equation (the energy slot is carried, unused) */
+  double cs_iso;      /* isothermal sound speed */
 } orc_params;
 
 typedef struct {
@@ -86,6 +89,17 @@ int orc_hlld(double gamma, const double* wl, const double* wr, double bn,
  * (the estimates the HLLD solver uses), with b- = min(S_L, 0) and
  * b+ = max(S_R, 0) so that a supersonic face takes the upwind flux. */
 void orc_hlle(double gamma, const double* wl, const double* wr, double bn, double* flux);
+
+/* Isothermal solvers (p = cs^2 rho; Sec. 2.1, 2.4), same frames with the
+ * pressure slot of w unused and a zero energy flux.
+ * orc_hlld_iso: the isothermal HLLD of Mignone (2007): density and normal
+ * momentum are uniform inside the fan (no contact wave), with the HLL
+ * fluxes there; rho* = the HLL average and u* = F_rho^HLL / rho*; outer
+ * transverse states across the fast waves, a central state between the
+ * Alfven waves S*_L,R = u* -+ |Bn|/sqrt(rho*).
+ * orc_hlle_iso: HLLE with the same outer speeds. */
+void orc_hlld_iso(double cs, const double* wl, const double* wr, double bn, double* flux);
+void orc_hlle_iso(double cs, const double* wl, const double* wr, double bn, double* flux);
 
 /* Reconstruction of one 1-D line: w[0..n-1] -> left/right states at the
  * n-1 interior faces (face f lies between cells f and f+1; faces whose

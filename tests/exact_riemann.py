@@ -93,3 +93,72 @@ def sample(x, t, left, right, g, x0=0.0):
                     w = (r, u, pr * (c / cr) ** (2 * g / (g - 1)))
         out[:, n] = w
     return out
+
+
+# ------------------------------------------------------------- isothermal
+# Isothermal gas (p = c^2 rho): across a shock into state k the velocity
+# changes by c (rho* - rho_k) / sqrt(rho* rho_k); across a rarefaction by
+# c ln(rho* / rho_k); inside a left (right) fan u -+ c = x/t and
+# rho = rho_k exp(-+(u - u_k)/c).
+
+def _iso_f(rs, rk, c):
+    if rs > rk:
+        return c * (rs - rk) / math.sqrt(rs * rk), c * (rs + rk) / (2 * rs * math.sqrt(rs * rk))
+    return c * math.log(rs / rk), c / rs
+
+
+def iso_star(rl, ul, rr, ur, c):
+    """Star density and velocity of the isothermal Riemann problem (Newton
+    on f_L(rho*) + f_R(rho*) + u_R - u_L = 0)."""
+    rs = math.sqrt(rl * rr)
+    for _ in range(100):
+        fl, dfl = _iso_f(rs, rl, c)
+        fr, dfr = _iso_f(rs, rr, c)
+        g = fl + fr + ur - ul
+        step = g / (dfl + dfr)
+        rs_new = max(rs - step, 1e-3 * rs)
+        if abs(rs_new - rs) < 1e-14 * rs:
+            rs = rs_new
+            break
+        rs = rs_new
+    fl, _ = _iso_f(rs, rl, c)
+    return rs, ul - fl
+
+
+def iso_sample(x, t, left, right, c, x0=0.0):
+    """rho(x, t), u(x, t) of the isothermal Riemann problem; left/right =
+    (rho, u)."""
+    rl, ul = left
+    rr, ur = right
+    rs, us = iso_star(rl, ul, rr, ur, c)
+    xi = (np.asarray(x, dtype=float) - x0) / t
+    rho = np.empty_like(xi)
+    u = np.empty_like(xi)
+    for q, s in enumerate(xi):
+        if s <= us:   # left of the contact-free middle: left wave
+            if rs > rl:
+                sh = ul - c * math.sqrt(rs / rl)
+                rho[q], u[q] = (rl, ul) if s < sh else (rs, us)
+            else:
+                head, tail = ul - c, us - c
+                if s < head:
+                    rho[q], u[q] = rl, ul
+                elif s > tail:
+                    rho[q], u[q] = rs, us
+                else:
+                    u[q] = s + c
+                    rho[q] = rl * math.exp(-(u[q] - ul) / c)
+        else:
+            if rs > rr:
+                sh = ur + c * math.sqrt(rs / rr)
+                rho[q], u[q] = (rr, ur) if s > sh else (rs, us)
+            else:
+                head, tail = ur + c, us + c
+                if s > head:
+                    rho[q], u[q] = rr, ur
+                elif s < tail:
+                    rho[q], u[q] = rs, us
+                else:
+                    u[q] = s - c
+                    rho[q] = rr * math.exp((u[q] - ur) / c)
+    return rho, u
