@@ -53,8 +53,17 @@ typedef enum {
   AETH_ERR_UNSUPPORTED = -8  /* option combination not built */
 } aeth_status;
 
-/* equation of state (Sec. 2.1) */
-enum { AETH_EOS_ADIABATIC_MHD = 0, AETH_EOS_ADIABATIC_HYDRO = 1 };
+/* equation of state (Sec. 2.1): ideal gas p = (gamma - 1) e, or the
+ * isothermal closure p = cs_iso^2 rho (no energy equation: the energy slot
+ * of the state is carried with zero flux; the isothermal HLLD of Mignone
+ * (2007) or the isothermal HLLE solves the faces; Cartesian blocks, gas
+ * only) */
+enum {
+  AETH_EOS_ADIABATIC_MHD = 0,
+  AETH_EOS_ADIABATIC_HYDRO = 1,
+  AETH_EOS_ISOTHERMAL_MHD = 2,
+  AETH_EOS_ISOTHERMAL_HYDRO = 3
+};
 /* reconstruction (Sec. 2.4) */
 enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2 };
 /* Riemann solver (Sec. 2.4): HLLD (Miyoshi & Kusano 2005); HLLE (Harten,
@@ -81,7 +90,8 @@ enum { AETH_PATH_FUSED = 0, AETH_PATH_UNFUSED = 1 };
 
 typedef struct {
   int eos;            /* AETH_EOS_* */
-  double gamma;       /* adiabatic index of the ideal-gas closure */
+  double gamma;       /* adiabatic index of the ideal-gas closure (> 1; not
+                         read by the isothermal closure) */
   double rho_floor;   /* density floor of the cons->prim conversion */
   double p_floor;     /* pressure floor */
   int recon;          /* AETH_RECON_* of the final stage */
@@ -99,6 +109,8 @@ typedef struct {
                          HLL dissipation bracket); <= 0 selects 0.25 */
   int mlp_engine;     /* learned flux: AETH_MLP_TCGEN05 (default, 0) or
                          AETH_MLP_MMA_SYNC */
+  double cs_iso;      /* isothermal sound speed (> 0, finite) of the
+                         AETH_EOS_ISOTHERMAL_* closures; ignored otherwise */
 } aeth_config;
 
 typedef struct {

@@ -23,7 +23,7 @@ AETH_OK = 0
 STATUS = {0: "AETH_OK", -1: "AETH_ERR_ARG", -2: "AETH_ERR_OOM", -3: "AETH_ERR_CUDA",
           -4: "AETH_ERR_NONFINITE", -5: "AETH_ERR_FLOOR", -6: "AETH_ERR_TIMEOUT",
           -7: "AETH_ERR_STATE", -8: "AETH_ERR_UNSUPPORTED"}
-EOS_MHD, EOS_HYDRO = 0, 1
+EOS_MHD, EOS_HYDRO, EOS_ISO_MHD, EOS_ISO_HYDRO = 0, 1, 2, 3
 DONOR, PLM, PPM = 0, 1, 2
 HLLD, HLLE, MLP = 0, 1, 2
 TCGEN05, MMA_SYNC = 0, 1          # tensor-core engine of the learned flux
@@ -55,7 +55,7 @@ class aeth_config(C.Structure):
                 ("integrator", C.c_int), ("cfl", C.c_double), ("precision", C.c_int),
                 ("path", C.c_int), ("strict_floors", C.c_int), ("n_dust", C.c_int),
                 ("t_stop", C.POINTER(C.c_double)), ("drag_precision", C.c_int),
-                ("mlp_tau", C.c_double), ("mlp_engine", C.c_int)]
+                ("mlp_tau", C.c_double), ("mlp_engine", C.c_int), ("cs_iso", C.c_double)]
 
 
 class aeth_block_desc(C.Structure):
@@ -323,9 +323,15 @@ def _check(ctx, rc):
 
 def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=FP64, mhd=True,
                 path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
-                riemann=HLLD, drag_precision=FP64, mlp_tau=0.0, mlp_engine=TCGEN05):
+                riemann=HLLD, drag_precision=FP64, mlp_tau=0.0, mlp_engine=TCGEN05, iso=False,
+                cs=1.0):
+    """iso=True selects the isothermal closure p = cs^2 rho (gamma unused)."""
     cfg = aeth_config()
-    cfg.eos = EOS_MHD if mhd else EOS_HYDRO
+    if iso:
+        cfg.eos = EOS_ISO_MHD if mhd else EOS_ISO_HYDRO
+    else:
+        cfg.eos = EOS_MHD if mhd else EOS_HYDRO
+    cfg.cs_iso = cs
     cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
     cfg.recon, cfg.riemann, cfg.integrator, cfg.cfl = recon, riemann, integrator, cfl
     cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors

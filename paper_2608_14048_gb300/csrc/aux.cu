@@ -394,7 +394,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename R, bool P64, typename Src>
 __global__ void __launch_bounds__(256)
     k_dt(Src S, int total, int mhd, double gamma, double rho_floor, double p_floor, int nd,
-         double* __restrict__ partial, int* status) {
+         double cs2, double* __restrict__ partial, int* status) {
+  // cs2 > 0: isothermal closure p = cs2 rho, fast speed with gamma = 1
+  const bool iso = cs2 > 0.0;
   constexpr int TPI = 2;
   __shared__ double sm[8];
   R m = R(INFINITY);   // running minimum in the working precision
@@ -444,7 +446,9 @@ __global__ void __launch_bounds__(256)
         bc[2] = R(0.5) * (bf[q][4] + bf[q][5]);
       }
       R pr;
-      if (P64) {
+      if (iso) {
+        pr = (R)cs2 * rho;
+      } else if (P64) {
         double ke = 0.5 * ((double)a[q][1] * a[q][1] + (double)a[q][2] * a[q][2] +
                            (double)a[q][3] * a[q][3]) / (double)rho;
         double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
@@ -456,7 +460,8 @@ __global__ void __launch_bounds__(256)
       if (!(pr >= (R)p_floor)) { if (!(pr == pr)) bad = true; pr = (R)p_floor; }
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const R cf = fast_speed((R)gamma, rho, pr, bc[d], bc[(d + 1) % 3], bc[(d + 2) % 3]);
+        const R cf = fast_speed(iso ? R(1) : (R)gamma, rho, pr, bc[d], bc[(d + 1) % 3],
+                                bc[(d + 2) % 3]);
         const R dtd = wd[q][d] / (fabs(v[d]) + cf);
         if (!(dtd > R(0))) bad = true;
         m = fmin(m, dtd);
@@ -512,17 +517,18 @@ static aeth_status dt_T(aeth_ctx* c) {
   const int total = prefix_total(c, PK_CELL);
   // 2 tiles per CTA iteration; at most dt_grid partial minima
   const int grid = std::max(1, std::min(c->dt_grid, (total + 1) / 2));
+  const double cs2 = is_iso(c) ? c->cfg.cs_iso * c->cfg.cs_iso : 0.0;
   if (nb == 1) {
     const ParamSrc<R> src{block_ptrs<R>(c, 0), 0};
     k_dt<R, P64, ParamSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
-        c->d_partials, c->d_status);
+        cs2, c->d_partials, c->d_status);
   } else {
     const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb,
                           c->d_tmap[PK_CELL]};
     k_dt<R, P64, TableSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
-        c->d_partials, c->d_status);
+        cs2, c->d_partials, c->d_status);
   }
   c->n_launch += 2;
   const double scale = c->cfg.cfl * cmax_of(c->cfg.integrator);

@@ -310,6 +310,117 @@ __device__ __forceinline__ int hlle(R gamma, const R* wl, const R* wr, R bn, R* 
   return 0;
 }
 
+// ------------------------------------------------------------------------
+// Isothermal closure p = cs^2 rho (Sec. 2.1): physical flux of one side
+// (energy entries zero) and the outer speeds (the fast speed with gamma = 1
+// and p = cs^2 rho).
+// ------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void side_iso(R a2, const R* w, R bn, R* u, R* f) {
+  const R rho = w[0], vn = w[1], v1 = w[2], v2 = w[3], b1 = w[5], b2 = w[6];
+  const R pt = a2 * rho + R(0.5) * (bn * bn + b1 * b1 + b2 * b2);
+  u[0] = rho; u[1] = rho * vn; u[2] = rho * v1; u[3] = rho * v2; u[4] = R(0); u[5] = b1; u[6] = b2;
+  f[0] = rho * vn; f[1] = rho * vn * vn + pt - bn * bn; f[2] = rho * vn * v1 - bn * b1;
+  f[3] = rho * vn * v2 - bn * b2; f[4] = R(0); f[5] = b1 * vn - bn * v1; f[6] = b2 * vn - bn * v2;
+}
+
+template <typename R>
+__device__ __forceinline__ void iso_speeds(R a2, const R* wl, const R* wr, R bn, R& sl, R& sr) {
+  const R cm = fmax(fast_speed(R(1), wl[0], a2 * wl[0], bn, wl[5], wl[6]),
+                    fast_speed(R(1), wr[0], a2 * wr[0], bn, wr[5], wr[6]));
+  sl = fmin(wl[1], wr[1]) - cm;
+  sr = fmax(wl[1], wr[1]) + cm;
+}
+
+// Isothermal HLLE: HLL average between the outer speeds (branch-free form).
+template <typename R>
+__device__ __forceinline__ int hlle_iso(R cs, const R* wl, const R* wr, R bn, R* f) {
+  const R a2 = cs * cs;
+  R ul[7], ur[7], fl[7], fr[7], sl, sr;
+  side_iso(a2, wl, bn, ul, fl);
+  side_iso(a2, wr, bn, ur, fr);
+  iso_speeds(a2, wl, wr, bn, sl, sr);
+  const R bm = fmin(sl, R(0)), bp = fmax(sr, R(0));
+  const R inv = R(1) / (bp - bm);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) f[q] = (bp * fl[q] - bm * fr[q] + bp * bm * (ur[q] - ul[q])) * inv;
+  return 0;
+}
+
+// Isothermal HLLD (Mignone 2007): no contact wave, so density and normal
+// momentum are uniform inside the fan with the HLL fluxes there; rho* is
+// the HLL average and u* = F_rho^HLL / rho* enters the jump conditions of
+// the transverse components across the fast waves; a central state lies
+// between the Alfven waves S*_L,R = u* -+ |Bn| / sqrt(rho*).
+template <typename R>
+__device__ __forceinline__ int hlld_iso(R cs, const R* wl, const R* wr, R bn, R* f) {
+  const R a2 = cs * cs;
+  R ul[7], ur[7], fl[7], fr[7], sl, sr;
+  side_iso(a2, wl, bn, ul, fl);
+  side_iso(a2, wr, bn, ur, fr);
+  iso_speeds(a2, wl, wr, bn, sl, sr);
+  if (sl >= R(0)) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) f[q] = fl[q];
+    return 0;
+  }
+  if (sr <= R(0)) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) f[q] = fr[q];
+    return 5;
+  }
+  const R idn = R(1) / (sr - sl);
+  const R rs = (sr * ur[0] - sl * ul[0] - (fr[0] - fl[0])) * idn;
+  const R fm = (sr * fl[0] - sl * fr[0] + sl * sr * (ur[0] - ul[0])) * idn;
+  const R fmn = (sr * fl[1] - sl * fr[1] + sl * sr * (ur[1] - ul[1])) * idn;
+  const R us = fm / rs;
+  const R sq = sqrt(rs);
+  const R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
+  const R ssl = us - fabs(bn) / sq, ssr = us + fabs(bn) / sq;
+  // transverse star state of one side across its fast wave (speed s)
+  auto star = [&](const R* w, R s, R* t) {
+    const R rho = w[0], vn = w[1];
+    const R den = rho * (s - vn) * (s - us) - bn * bn;
+    R vt1 = w[2], vt2 = w[3], bt1 = w[5], bt2 = w[6];
+    if (fabs(den) >= Eps<R>::hlld * (rho * (s - vn) * (s - vn) + bn * bn)) {
+      const R fv = bn * (us - vn) / den;
+      const R fb = (rho * (s - vn) * (s - vn) - bn * bn) / den;
+      vt1 = w[2] - w[5] * fv;
+      vt2 = w[3] - w[6] * fv;
+      bt1 = w[5] * fb;
+      bt2 = w[6] * fb;
+    }
+    t[0] = vt1; t[1] = vt2; t[2] = bt1; t[3] = bt2;
+  };
+  R tl[4], tr[4];
+  star(wl, sl, tl);
+  star(wr, sr, tr);
+  const bool right = ssl < R(0) && ssr <= R(0);
+  const bool central = ssl < R(0) && ssr > R(0);
+  // outer star flux of the selected side, transverse entries
+  const R* uk = right ? ur : ul;
+  const R* fk = right ? fr : fl;
+  const R* tk = right ? tr : tl;
+  const R sk = right ? sr : sl;
+  R g2 = fk[2] + sk * (rs * tk[0] - uk[2]);
+  R g3 = fk[3] + sk * (rs * tk[1] - uk[3]);
+  R g5 = fk[5] + sk * (tk[2] - uk[5]);
+  R g6 = fk[6] + sk * (tk[3] - uk[6]);
+  if (central) {
+    // central state between the Alfven waves (equal densities both sides)
+    const R vc1 = R(0.5) * (tl[0] + tr[0]) + R(0.5) * (tr[2] - tl[2]) * sgn / sq;
+    const R vc2 = R(0.5) * (tl[1] + tr[1]) + R(0.5) * (tr[3] - tl[3]) * sgn / sq;
+    const R bc1 = R(0.5) * (tl[2] + tr[2]) + R(0.5) * sq * (tr[0] - tl[0]) * sgn;
+    const R bc2 = R(0.5) * (tl[3] + tr[3]) + R(0.5) * sq * (tr[1] - tl[1]) * sgn;
+    g2 += ssl * (rs * vc1 - rs * tl[0]);
+    g3 += ssl * (rs * vc2 - rs * tl[1]);
+    g5 += ssl * (bc1 - tl[2]);
+    g6 += ssl * (bc2 - tl[3]);
+  }
+  f[0] = fm; f[1] = fmn; f[2] = g2; f[3] = g3; f[4] = R(0); f[5] = g5; f[6] = g6;
+  return central ? 2 : (right ? 4 : 1);
+}
+
 // Upwind selection of Gardiner & Stone (2005): lower-index value for a
 // positive mass flux, upper for negative, mean for zero.
 template <typename R>

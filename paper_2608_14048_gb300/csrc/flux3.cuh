@@ -1,0 +1,269 @@
+// Flux pass of the fused stage (Sec. 2.4): conserved->primitive,
+// reconstruction and the Riemann solver for all three face directions of
+// every cell in one sweep.  A CTA owns a TX x TY column tile and marches
+// along z: each x-y plane of primitives (with the reconstruction halo) is
+// staged in shared memory for the x- and y-faces, while every thread keeps
+// the z-stencil of its own column in a register queue for the z-faces.
+// Each face is solved exactly once.  Outputs: hydro fluxes, face EMFs (the
+// transverse induction fluxes) and the cell-centred reference EMF of the
+// upwind CT scheme.
+//
+// The kernel template lives here so that its instantiations (one per
+// Riemann solver family) compile in separate translation units.
+#pragma once
+#include "runtime.hpp"
+#include "stage.cuh"
+
+namespace aeth {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NT = TX * TY;
+// resident CTAs per SM requested for the FP32 flux pass (register budget
+// 65536 / (256 * FLUX_MINB) per thread)
+#ifndef AETH_FLUX_MINB
+#define AETH_FLUX_MINB 2
+#endif
+
+__host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
+
+// Riemann solver family SOLVER (numbering of k_flux3 below) on one face.
+template <int SOLVER, typename R>
+__device__ __forceinline__ void solve_face(R g, const R* wl, const R* wr, R bn, R* fx) {
+  if constexpr (SOLVER == 2) hlle(g, wl, wr, bn, fx);
+  else if constexpr (SOLVER == 3) hlld_iso(g, wl, wr, bn, fx);
+  else if constexpr (SOLVER == 4) hlle_iso(g, wl, wr, bn, fx);
+  else hlld(g, wl, wr, bn, fx);
+}
+
+// Store the outputs of one face of direction D.  Scratch arrays sit at
+// sb + slot * pitch: E_ref 0..2, fluxes 8 + 5 D + v, face EMFs 23 + 2 D + q.
+template <int D, typename R>
+__device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, long long fc,
+                                           const R* fx) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  R* f = sb + (8 + 5 * D) * pitch + fc;
+  f[0] = fx[0];
+  f[(1 + D) * pitch] = fx[1];
+  f[(1 + T1) * pitch] = fx[2];
+  f[(1 + T2) * pitch] = fx[3];
+  f[4 * pitch] = fx[4];
+  R* e = sb + (23 + 2 * D) * pitch + fc;
+  e[0] = fx[6];        // E_t1 =  F(B_t2)
+  e[pitch] = -fx[5];   // E_t2 = -F(B_t1)
+}
+
+// ------------------------------------------------------------------------
+// 1. flux pass.  Persistent: CTAs stride over the tiles of all blocks.
+//    AETH_FLUX_MINB CTAs per SM in FP32; FP64 takes the full register file.
+// ------------------------------------------------------------------------
+// SOLVER 0: HLLD; 2: HLLE; 1: write the face states (wl, wr, bn) for the learned
+// flux instead of solving; 3: isothermal HLLD; 4: isothermal HLLE.  For the
+// isothermal solvers the `gamma` argument carries the sound speed cs, the
+// primitive pressure is cs^2 rho and is not reconstructed (the isothermal
+// fluxes take the pressure from the reconstructed density).
+template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
+    k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
+            unsigned long long* floor_hits) {
+  constexpr int RL = RECON + 1, RH = RECON;
+  constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
+  constexpr int QN = RL + RH + 1;
+  __shared__ R sw[NPRIM][WY][WX];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  constexpr bool ISO = SOLVER >= 3;
+  const R gm1 = ISO ? gamma * gamma : gamma - R(1);   // cs^2 for ISO
+  int hits = 0;
+
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    int loc;
+    const BlockPtrs<R>& P = S.get(t, loc);
+    const Layout L = P.L;
+    const int ntx = ceil_div_d(L.n[0] + 2, TX), nty = ceil_div_d(L.n[1] + 2, TY);
+    const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
+    const R* __restrict__ ub = P.reg[src][0];   // state arrays at ub + v * pitch
+    R* __restrict__ sb = P.w[0];                 // scratch arrays at sb + slot * pitch
+    const long long pitch = P.pitch;
+    const int i0 = -1 + bx * TX, j0 = -1 + by * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int k0 = -1 + bz * kchunk;
+    const int k1 = min(nz, k0 + kchunk - 1);
+    const bool active = i <= nx && j <= ny;
+
+    // z register queue of the own column: planes k-RL .. k+RH, 7 variables
+    // (the z-face normal field comes from the face array)
+    R q[7][QN];
+    auto load_q = [&](int slot, int kk) {
+      R w[8];
+      if (active && in_prim_range(L, i, j, kk)) {
+        prim_cell_s<R, P64, MHD, ISO>(L, ub, pitch, L.idx(i, j, kk), gm1, rho_floor, p_floor, w);
+      } else {
+        w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
+      }
+      // z-face frame order: rho, vz, vx, vy, p, Bx, By
+      q[0][slot] = w[0]; q[1][slot] = w[3]; q[2][slot] = w[1]; q[3][slot] = w[2];
+      q[4][slot] = w[4]; q[5][slot] = w[5]; q[6][slot] = w[6];
+    };
+#pragma unroll
+    for (int s = 0; s < QN - 1; ++s) load_q(s + 1, k0 - RL + s);
+
+    for (int k = k0; k <= k1; ++k) {
+      __syncthreads();
+      // stage plane k (tile + halo) in shared memory
+      for (int s = threadIdx.x; s < WX * WY; s += NT) {
+        const int rx = s % WX, ry = s / WX;
+        const int ci = i0 - RL + rx, cj = j0 - RL + ry;
+        R w[8];
+        if (in_prim_range(L, ci, cj, k)) {
+          hits += prim_cell_s<R, P64, MHD, ISO>(L, ub, pitch, L.idx(ci, cj, k), gm1, rho_floor,
+                                           p_floor, w);
+        } else {
+          w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
+        }
+#pragma unroll
+        for (int v = 0; v < NPRIM; ++v) sw[v][ry][rx] = w[v];
+      }
+      // advance the z queue: drop plane k-RL-1, add plane k+RH
+#pragma unroll
+      for (int v = 0; v < 7; ++v)
+#pragma unroll
+        for (int s = 0; s < QN - 1; ++s) q[v][s] = q[v][s + 1];
+      load_q(QN - 1, k + RH);
+      __syncthreads();
+      if (!active) continue;
+
+      const long long fc = L.idx(i, j, k);
+      const int sx = tx + RL, sy = ty + RL;
+      R wl[7], wr[7], fx[7];
+      // ---- x-face (i-1/2, j, k): frame (rho, vx, vy, vz, p, By, Bz)
+      if (i >= 0) {
+        const int slot[7] = {0, 1, 2, 3, 4, 6, 7};
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
+          recon_var<RECON>([&](int off) { return sw[slot[v]][sy][sx + off]; }, wl[v], wr[v]);
+        }
+        const R bn = MHD ? ub[5 * pitch + fc] : R(0);
+        if (SOLVER != 1) {
+          solve_face<SOLVER>(gamma, wl, wr, bn, fx);
+          store_face<0>(sb, pitch, fc, fx);
+        } else {
+          R* fs = P.fstate + (0 * 15) * pitch + fc;
+#pragma unroll
+          for (int v = 0; v < 7; ++v) { fs[v * pitch] = wl[v]; fs[(7 + v) * pitch] = wr[v]; }
+          fs[14 * pitch] = bn;
+        }
+      }
+      // ---- y-face (i, j-1/2, k): frame (rho, vy, vz, vx, p, Bz, Bx)
+      if (j >= 0) {
+        const int slot[7] = {0, 2, 3, 1, 4, 7, 5};
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
+          recon_var<RECON>([&](int off) { return sw[slot[v]][sy + off][sx]; }, wl[v], wr[v]);
+        }
+        const R bn = MHD ? ub[6 * pitch + fc] : R(0);
+        if (SOLVER != 1) {
+          solve_face<SOLVER>(gamma, wl, wr, bn, fx);
+          store_face<1>(sb, pitch, fc, fx);
+        } else {
+          R* fs = P.fstate + (1 * 15) * pitch + fc;
+#pragma unroll
+          for (int v = 0; v < 7; ++v) { fs[v * pitch] = wl[v]; fs[(7 + v) * pitch] = wr[v]; }
+          fs[14 * pitch] = bn;
+        }
+      }
+      // ---- z-face (i, j, k-1/2): frame (rho, vz, vx, vy, p, Bx, By)
+      if (k >= 0) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
+          recon_var<RECON>([&](int off) { return q[v][off + RL]; }, wl[v], wr[v]);
+        }
+        const R bn = MHD ? ub[7 * pitch + fc] : R(0);
+        if (SOLVER != 1) {
+          solve_face<SOLVER>(gamma, wl, wr, bn, fx);
+          store_face<2>(sb, pitch, fc, fx);
+        } else {
+          R* fs = P.fstate + (2 * 15) * pitch + fc;
+#pragma unroll
+          for (int v = 0; v < 7; ++v) { fs[v * pitch] = wl[v]; fs[(7 + v) * pitch] = wr[v]; }
+          fs[14 * pitch] = bn;
+        }
+      }
+      // ---- cell-centred reference EMF, E = -v x B
+      if (MHD) {
+        const R vx = sw[1][sy][sx], vy = sw[2][sy][sx], vz = sw[3][sy][sx];
+        const R bx_ = sw[5][sy][sx], by_ = sw[6][sy][sx], bz_ = sw[7][sy][sx];
+        sb[fc] = -(vy * bz_ - vz * by_);
+        sb[pitch + fc] = -(vz * bx_ - vx * bz_);
+        sb[2 * pitch + fc] = -(vx * by_ - vy * bx_);
+      }
+    }
+  }
+  if (hits) atomicAdd(floor_hits, (unsigned long long)hits);
+}
+
+// ------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------
+struct TileRange {
+  int t0, t1;
+};
+
+static TileRange range_of(const aeth_ctx* c, int kind, int block) {
+  const int nb = (int)c->blocks.size();
+  const int* p = c->h_prefix.data() + kind * (nb + 1);
+  if (block < 0) return {0, p[nb]};
+  return {p[block], p[block + 1]};
+}
+
+template <typename R>
+static const BlockPtrs<R>* dtab(const aeth_ctx* c) {
+  return (const BlockPtrs<R>*)c->d_tab;
+}
+
+static const int* dpre(const aeth_ctx* c, int kind) {
+  return c->d_prefix + kind * ((int)c->blocks.size() + 1);
+}
+
+// Launch a pass either from the device table (several blocks) or with the
+// block's pointers in the kernel parameters (one block).
+template <typename R, typename F>
+static void with_src(aeth_ctx* c, int kind, int block, F launch) {
+  const int nb = (int)c->blocks.size();
+  if (nb == 1 || block >= 0) {
+    const int b = block >= 0 ? block : 0;
+    const TileRange r = range_of(c, kind, b);
+    launch(ParamSrc<R>{block_ptrs<R>(c, b), r.t0}, r);
+  } else {
+    launch(TableSrc<R>{dtab<R>(c), dpre(c, kind), nb, c->d_tmap[kind]}, range_of(c, kind, -1));
+  }
+}
+
+template <typename R, bool P64, int RECON, bool MHD, int SOLVER>
+static void launch_flux3(aeth_ctx* c, int src, int block) {
+  const int per_sm = sizeof(R) == 4 ? AETH_FLUX_MINB : 1;
+  with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
+    const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
+    k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER><<<grid, NT, 0, c->stream>>>(
+        S, r.t0, r.t1, src, (R)(SOLVER >= 3 ? c->cfg.cs_iso : c->cfg.gamma), (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk,
+        c->d_floor);
+  });
+  c->n_launch += 1;
+}
+
+// One flux pass with the solver family SOLVER and the reconstruction of the
+// context (explicitly instantiated per family in flux_*.cu).
+template <typename R, bool P64, bool MHD, int SOLVER>
+void flux_pass_solver(aeth_ctx* c, int recon, int src, int block);
+
+template <typename R, bool P64, bool MHD, int SOLVER>
+void flux_pass_solver_impl(aeth_ctx* c, int recon, int src, int block) {
+  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD, SOLVER>(c, src, block);
+  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD, SOLVER>(c, src, block);
+  else launch_flux3<R, P64, 2, MHD, SOLVER>(c, src, block);
+}
+
+}  // namespace aeth

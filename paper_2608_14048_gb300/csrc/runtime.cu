@@ -51,8 +51,10 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (!c) return AETH_ERR_OOM;
   c->cfg = *cfg;
   aeth_status bad = AETH_OK;
-  if (cfg->eos != AETH_EOS_ADIABATIC_MHD && cfg->eos != AETH_EOS_ADIABATIC_HYDRO) bad = AETH_ERR_ARG;
-  if (!(cfg->gamma > 1.0)) bad = AETH_ERR_ARG;
+  if (cfg->eos < AETH_EOS_ADIABATIC_MHD || cfg->eos > AETH_EOS_ISOTHERMAL_HYDRO) bad = AETH_ERR_ARG;
+  const bool iso = cfg->eos == AETH_EOS_ISOTHERMAL_MHD || cfg->eos == AETH_EOS_ISOTHERMAL_HYDRO;
+  if (!iso && !(cfg->gamma > 1.0)) bad = AETH_ERR_ARG;
+  if (iso && !(cfg->cs_iso > 0.0 && cfg->cs_iso < INFINITY)) bad = AETH_ERR_ARG;
   if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM) bad = AETH_ERR_ARG;
   if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_HLLE &&
       cfg->riemann != AETH_RIEMANN_MLP)
@@ -82,9 +84,9 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
     delete c;
     return AETH_ERR_UNSUPPORTED;
   }
-  if (cfg->riemann == AETH_RIEMANN_MLP && (cfg->precision == AETH_FP64 || cfg->n_dust > 0)) {
+  if (cfg->riemann == AETH_RIEMANN_MLP && (cfg->precision == AETH_FP64 || cfg->n_dust > 0 || iso)) {
     delete c;
-    return AETH_ERR_UNSUPPORTED;   // the learned flux runs with FP32 states, gas only
+    return AETH_ERR_UNSUPPORTED;   // the learned flux runs with FP32 adiabatic states, gas only
   }
   c->elem = cfg->precision == AETH_FP64 ? 8 : 4;
   c->g = ghost_width(cfg->recon);
@@ -130,6 +132,8 @@ aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
       return fail(c, AETH_ERR_ARG, "periodic axis %d needs n >= ghost width %d (or n == 1)", q, g);
   if (d->coord == AETH_COORD_SPH && c->cfg.integrator == AETH_INT_RK3)
     return fail(c, AETH_ERR_UNSUPPORTED, "SSP-RK3 runs on Cartesian blocks only");
+  if (d->coord == AETH_COORD_SPH && is_iso(c))
+    return fail(c, AETH_ERR_UNSUPPORTED, "the isothermal closure runs on Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH && c->cfg.n_dust > 0)
     return fail(c, AETH_ERR_UNSUPPORTED, "dust runs support Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH) {

@@ -242,6 +242,16 @@ inline double cmax_of(int integrator) {
   return integrator == AETH_INT_IMEX2P ? 1.0 / (1.0 + 1.0 / 1.4142135623730951) : 1.0;
 }
 
-inline bool is_mhd(const aeth_ctx* c) { return c->cfg.eos == AETH_EOS_ADIABATIC_MHD; }
+inline bool is_mhd(const aeth_ctx* c) {
+  return c->cfg.eos == AETH_EOS_ADIABATIC_MHD || c->cfg.eos == AETH_EOS_ISOTHERMAL_MHD;
+}
+// isothermal closure p = cs_iso^2 rho (Sec. 2.1): the energy slot is carried
+// with zero flux
+inline bool is_iso(const aeth_ctx* c) {
+  return c->cfg.eos == AETH_EOS_ISOTHERMAL_MHD || c->cfg.eos == AETH_EOS_ISOTHERMAL_HYDRO;
+}
+// internal solver codes of the face kernels beyond AETH_RIEMANN_*
+constexpr int SOLVER_ISO_HLLD = 3;
+constexpr int SOLVER_ISO_HLLE = 4;
 
 }  // namespace aeth

@@ -7,7 +7,9 @@ namespace aeth {
 
 // Primitive variables of cell (i,j,k) (Eq. 5 with the floors of Sec. 2.1):
 // w = (rho, v1, v2, v3, p, Bc1, Bc2, Bc3).  Returns the number of floors hit.
-template <typename R, bool P64, bool MHD>
+// ISO: isothermal closure, p = gm1 * rho with gm1 holding cs^2 (the energy
+// entry is not read and no pressure floor applies).
+template <typename R, bool P64, bool MHD, bool ISO = false>
 __device__ __forceinline__ int prim_cell(const Layout& L, const ConstArr8<R>& u, long long c,
                                          R gm1, R rho_floor, R p_floor, R* w) {
   int hits = 0;
@@ -22,7 +24,9 @@ __device__ __forceinline__ int prim_cell(const Layout& L, const ConstArr8<R>& u,
     b3 = R(0.5) * (u.p[7][c] + u.p[7][c + L.sx * L.sy]);
   }
   R pr;
-  if (P64) {
+  if (ISO) {
+    pr = gm1 * rho;
+  } else if (P64) {
     const double m1 = u.p[1][c], m2 = u.p[2][c], m3 = u.p[3][c];
     const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / (double)rho;
     const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
@@ -31,20 +35,20 @@ __device__ __forceinline__ int prim_cell(const Layout& L, const ConstArr8<R>& u,
     pr = gm1 * (u.p[4][c] - R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3) -
                 R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3));
   }
-  if (pr < p_floor) { pr = p_floor; ++hits; }
+  if (!ISO && pr < p_floor) { pr = p_floor; ++hits; }
   w[0] = rho; w[1] = v1; w[2] = v2; w[3] = v3; w[4] = pr; w[5] = b1; w[6] = b2; w[7] = b3;
   return hits;
 }
 
 // Same, with the 8 state arrays at base + v * pitch.
-template <typename R, bool P64, bool MHD>
+template <typename R, bool P64, bool MHD, bool ISO = false>
 __device__ __forceinline__ int prim_cell_s(const Layout& L, const R* __restrict__ base,
                                            long long pitch, long long c, R gm1, R rho_floor,
                                            R p_floor, R* w) {
   ConstArr8<R> u;
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) u.p[v] = base + v * pitch;
-  return prim_cell<R, P64, MHD>(L, u, c, gm1, rho_floor, p_floor, w);
+  return prim_cell<R, P64, MHD, ISO>(L, u, c, gm1, rho_floor, p_floor, w);
 }
 
 __device__ __forceinline__ bool in_prim_range(const Layout& L, int i, int j, int k) {

@@ -14,7 +14,7 @@ void launch_fill(const BlockPtrs<R>& P, R* const* arrs, int nv, cudaStream_t st)
 // ------------------------------------------------------------------------
 template <typename R, bool P64>
 __global__ void k_prim(Layout L, ConstArr8<R> u, Arr8<R> w, int mhd, double gamma,
-                       R rho_floor, R p_floor, unsigned long long* floor_hits) {
+                       R rho_floor, R p_floor, double cs2, unsigned long long* floor_hits) {
   const int g = L.g;
   const int i = blockIdx.x * blockDim.x + threadIdx.x - g;
   const int j = blockIdx.y * blockDim.y + threadIdx.y - g;
@@ -32,7 +32,9 @@ __global__ void k_prim(Layout L, ConstArr8<R> u, Arr8<R> w, int mhd, double gamm
     b3 = R(0.5) * (u.p[7][c] + u.p[7][c + L.sx * L.sy]);
   }
   R pr;
-  if (P64) {
+  if (cs2 > 0.0) {
+    pr = (R)cs2 * rho;   // isothermal closure: no energy, no pressure floor
+  } else if (P64) {
     const double r = rho;
     const double ke = 0.5 * r * ((double)v1 * v1 + (double)v2 * v2 + (double)v3 * v3);
     const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
@@ -42,7 +44,7 @@ __global__ void k_prim(Layout L, ConstArr8<R> u, Arr8<R> w, int mhd, double gamm
     const R me = R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3);
     pr = (R)(gamma - 1.0) * (u.p[4][c] - ke - me);
   }
-  if (pr < p_floor) { pr = p_floor; ++hits; }
+  if (cs2 <= 0.0 && pr < p_floor) { pr = p_floor; ++hits; }
   w.p[0][c] = rho; w.p[1][c] = v1; w.p[2][c] = v2; w.p[3][c] = v3;
   w.p[4][c] = pr; w.p[5][c] = b1; w.p[6][c] = b2; w.p[7][c] = b3;
   if (hits) atomicAdd(floor_hits, (unsigned long long)hits);
@@ -83,7 +85,11 @@ __global__ void k_flux(Layout L, ConstArr8<R> w, const R* __restrict__ bface, in
   }
   const R bn = mhd ? bface[fc] : R(0);
   R fx[7];
+  // solver: AETH_RIEMANN_HLLD / _HLLE, or SOLVER_ISO_HLLD / _HLLE with
+  // `gamma` holding the isothermal sound speed
   if (solver == AETH_RIEMANN_HLLE) hlle(gamma, wl, wr, bn, fx);
+  else if (solver == SOLVER_ISO_HLLD) hlld_iso(gamma, wl, wr, bn, fx);
+  else if (solver == SOLVER_ISO_HLLE) hlle_iso(gamma, wl, wr, bn, fx);
   else hlld(gamma, wl, wr, bn, fx);
   R* fo[5] = {f0, f1, f2, f3, f4};
   fo[0][fc] = fx[0];
@@ -228,29 +234,33 @@ static void stage_unfused(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src
   for (int v = 0; v < NVAR; ++v) { u.p[v] = P.reg[src][v]; w.p[v] = P.w[v]; wo.p[v] = P.w[v]; }
   const int g = L.g;
   dim3 blk(32, 4, 2);
+  const bool iso = is_iso(c);
+  const double cs2 = iso ? c->cfg.cs_iso * c->cfg.cs_iso : 0.0;
+  const int solver = !iso ? c->cfg.riemann
+                          : (c->cfg.riemann == AETH_RIEMANN_HLLE ? SOLVER_ISO_HLLE : SOLVER_ISO_HLLD);
   {
     const int ex = L.n[0] + 2 * g, ey = L.n[1] + 2 * g, ez = L.n[2] + 2 * g;
     dim3 grd((ex + 31) / 32, (ey + 3) / 4, (ez + 1) / 2);
     k_prim<R, P64><<<grd, blk, 0, st>>>(L, u, wo, mhd, c->cfg.gamma, (R)c->cfg.rho_floor,
-                                        (R)c->cfg.p_floor, c->d_floor);
+                                        (R)c->cfg.p_floor, cs2, c->d_floor);
   }
   for (int d = 0; d < 3; ++d) {
     int ext[3];
     for (int e = 0; e < 3; ++e) ext[e] = e == d ? L.n[e] + 1 : L.n[e] + 2;
     dim3 grd((ext[0] + 31) / 32, (ext[1] + 3) / 4, (ext[2] + 1) / 2);
     const R* bf = P.reg[src][5 + d];
-    R gm = (R)c->cfg.gamma;
+    R gm = (R)(iso ? c->cfg.cs_iso : c->cfg.gamma);
     // algorithmic traffic: 7 primitives read and 7 outputs written per face
     const double faces = (double)ext[0] * ext[1] * ext[2];
     prof_begin(c);
     if (recon == AETH_RECON_DONOR)
-      k_flux<R, 0><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, c->cfg.riemann, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+      k_flux<R, 0><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, solver, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     else if (recon == AETH_RECON_PLM)
-      k_flux<R, 1><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, c->cfg.riemann, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+      k_flux<R, 1><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, solver, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     else
-      k_flux<R, 2><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, c->cfg.riemann, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+      k_flux<R, 2><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, solver, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     prof_end(c, faces * (mhd ? 15 : 10) * sizeof(R));
   }

@@ -18,24 +18,24 @@ def rel_l1(a, b):
 
 
 def oracle_run(st, recon="plm", integ="vl2", nsteps=4, mhd=True, dts=None, cfl=0.3,
-               riemann="hlld"):
+               riemann="hlld", iso=False, cs=1.0):
     b = st.block
     g = O.make_grid(b.n, b.lo, b.hi, b.coord, b.bc)
     p = O.make_params(gamma=st.gamma, recon=RECON[recon][0], integrator=INTEG[integ][0],
-                      mhd=mhd, cfl=cfl, riemann=RIEMANN[riemann][0])
+                      mhd=mhd, cfl=cfl, riemann=RIEMANN[riemann][0], iso=iso, cs=cs)
     s = O.State(st.cons, st.b1, st.b2, st.b3)
     used = O.run(g, p, s, nsteps=None if dts is not None else nsteps, dts=dts)
     return s, used
 
 
 def gpu_run(states, dts, recon="plm", integ="vl2", prec="fp64", mhd=True, path=A.FUSED,
-            use_run=False, cfl=0.3, riemann="hlld"):
+            use_run=False, cfl=0.3, riemann="hlld", iso=False, cs=1.0):
     """Advance one or several blocks (list of InitialState) with the given dt
     sequence; returns a list of (cons, b1, b2, b3) per block."""
     import torch
     cfg = A.make_config(gamma=states[0].gamma, recon=RECON[recon][1], integrator=INTEG[integ][1],
                         precision=PREC[prec], mhd=mhd, path=path, cfl=cfl,
-                        riemann=RIEMANN[riemann][1])
+                        riemann=RIEMANN[riemann][1], iso=iso, cs=cs)
     blocks = [A.make_block(s.block.n, s.block.lo, s.block.hi, s.block.coord, s.block.bc)
               for s in states]
     sv = A.Solver(cfg, blocks, stream=torch.cuda.current_stream())
