@@ -51,9 +51,14 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--mlp-engine", default="tcgen05", choices=["tcgen05", "mma_sync"])
     ap.add_argument("--hydro", action="store_true", help="wave512: the hydro column (B = 0)")
+    ap.add_argument("--iso", action="store_true",
+                    help="turb256: isothermal closure p = cs^2 rho with cs = 1 (the sound "
+                         "speed of the generator) and the isothermal HLLD")
     a = ap.parse_args(argv)
     if a.prec is None:
         a.prec = "fp64" if a.workload == "wave512" else "fp32"
+    if a.iso and a.workload != "turb256":
+        ap.error("--iso applies to the turb256 workload")
     return a
 
 
@@ -110,6 +115,13 @@ def workload_config(a):
                 "riemann": "HLLD", "integrator": "VL2", "cfl": 0.3, "precision": a.prec,
                 "amplitude": 1e-6,
                 "l2": "inputs smaller than L2; L2 is flushed between timed steps"}
+    if a.iso:
+        return {"workload": f"mhd_decaying_turbulence_{a.n}^3_isothermal",
+                "grid": [a.n, a.n, a.n], "recon": a.recon.upper(),
+                "riemann": "isothermal HLLD (Mignone 2007)", "ct": "upwind corner EMF (GS05)",
+                "integrator": "VL2", "cfl": 0.3, "eos": "isothermal, c_s = 1", "mach_rms": 2.0,
+                "beta": 1.0, "precision": a.prec, "path": a.path, "seed": 20260816,
+                "l2": f"inputs larger than L2 (state {a.n}^3 x 8 vars x 2 registers)"}
     return {"workload": f"mhd_decaying_turbulence_{a.n}^3", "grid": [a.n, a.n, a.n],
             "recon": a.recon.upper(), "riemann": "HLLD", "ct": "upwind corner EMF (GS05)",
             "integrator": "VL2", "cfl": 0.3, "gamma": 1.0001, "mach_rms": 2.0, "beta": 1.0,
@@ -125,7 +137,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("fused.cu", "common.cuh", "stage.cuh")
+KERNEL_SOURCES = ("flux3.cuh", "common.cuh", "stage.cuh")
 
 
 def nvtx_push(name):
@@ -274,9 +286,10 @@ def cpu_baseline(a, st_full):
     else:
         st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
         g = O.make_grid((n, n, n))
-        p = O.make_params(gamma=st.gamma, recon=O.PLM if a.recon == "plm" else O.PPM)
+        p = O.make_params(gamma=st.gamma, recon=O.PLM if a.recon == "plm" else O.PPM,
+                          iso=a.iso, cs=1.0)
         cells = n ** 3
-        what = f"{n}^3 box of the same turbulence generator"
+        what = f"{n}^3 box of the same turbulence generator" + (", isothermal" if a.iso else "")
     s = O.State(st.cons, st.b1, st.b2, st.b3)
     dt = O.compute_dt(g, p, s)
     t0 = time.perf_counter()
@@ -291,6 +304,14 @@ def cpu_baseline(a, st_full):
     return {"value": cells * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, {what}, {k} steps ({el:.1f} s), OpenMP over {cores} "
                       f"host threads"}
+
+
+def solver_label(a):
+    if a.workload == "learned512":
+        return "face-state dump"
+    if a.workload == "wave512":
+        return "HLLE"
+    return "isothermal HLLD" if a.iso else "HLLD"
 
 
 def vs_paper(a, value):
@@ -404,7 +425,7 @@ def main():
     else:
         states = [make_input(a)]
         cfg = A.make_config(gamma=states[0].gamma, recon=rec, integrator=A.VL2, cfl=0.3,
-                            precision=prec, path=path)
+                            precision=prec, path=path, iso=a.iso, cs=1.0)
     blocks = [A.make_block(s_.block.n, s_.block.lo, s_.block.hi, s_.block.coord, s_.block.bc)
               for s_ in states]
     stream = torch.cuda.current_stream(dev)
@@ -565,7 +586,8 @@ def main():
 
     hbm, peak_kind = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None
-    kernel_key = f"{a.path}_{a.prec}_{a.recon}" if a.workload == "turb256" else None
+    kernel_key = (f"{a.path}_{a.prec}_{a.recon}" + ("_iso" if a.iso else "")
+                  if a.workload == "turb256" else None)
     traffic = ncu_traffic(kernel_key) if kernel_key else None
     launches_per_step = klaunch / max(a.steps, 1)
     line = {
@@ -576,7 +598,8 @@ def main():
         "data": "synthetic", "config": workload_config(a),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                     "kernel": "k_flux3 (fused prim + reconstruction + HLLD, 3 directions)" if a.path == "fused" else "k_flux",
+                     "kernel": (f"k_flux3 (fused prim + reconstruction + {solver_label(a)}, "
+                                "3 directions)") if a.path == "fused" else "k_flux",
                      "peak_kind": peak_kind,
                      "algo_bytes_per_launch": kbytes / max(klaunch, 1),
                      "kernel_ms_per_launch": kms / max(klaunch, 1),

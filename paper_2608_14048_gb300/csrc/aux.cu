@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256)
       const long long c = L.idx(i, j, k);
       const R* const* u = P.reg[0];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a[q][v] = u[v][c];
+      for (int v = 0; v < 5; ++v) a[q][v] = (v == 4 && iso) ? R(0) : u[v][c];   // no energy
       if (mhd) {
         bf[q][0] = u[5][c]; bf[q][1] = u[5][c + 1];
         bf[q][2] = u[6][c]; bf[q][3] = u[6][c + L.sx];
