@@ -25,7 +25,7 @@ _lib = None
 
 CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1
-DONOR, PLM, PPM = 0, 1, 2
+DONOR, PLM, PPM, PPM5 = 0, 1, 2, 3
 VL2, RK2, RK3 = 0, 1, 2
 HLLD, HLLE = 0, 1
 

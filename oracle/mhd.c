@@ -207,6 +207,25 @@ static void ppm_limit(double w, double* al, double* ar) {
   *al = l; *ar = r;
 }
 
+/* PPM5 (Sec. 2.4): the interface value of a cell from the quartic through
+ * the five cell averages centred on it (upwind-biased toward that cell),
+ * exact for cell averages of polynomials up to degree 4.  q[0..4] = cells
+ * c-2..c+2; right: the value at c+1/2, left: at c-1/2. */
+static double ppm5_right(const double* q) {
+  return (2.0 * q[0] - 13.0 * q[1] + 47.0 * q[2] + 27.0 * q[3] - 3.0 * q[4]) / 60.0;
+}
+static double ppm5_left(const double* q) {
+  return (-3.0 * q[0] + 27.0 * q[1] + 47.0 * q[2] - 13.0 * q[3] + 2.0 * q[4]) / 60.0;
+}
+
+/* clip an interface value into the range of the two cells it separates */
+static double clip_pair(double a, double u0, double u1) {
+  double lo = u0 < u1 ? u0 : u1, hi = u0 < u1 ? u1 : u0;
+  if (a < lo) a = lo;
+  if (a > hi) a = hi;
+  return a;
+}
+
 /* s[0..5] = cells f-3..f+2 around face f (between s[2] and s[3]). */
 static void recon_face(int recon, const double* s, double* wl, double* wr) {
   if (recon == ORC_DONOR) {
@@ -214,6 +233,16 @@ static void recon_face(int recon, const double* s, double* wl, double* wr) {
   } else if (recon == ORC_PLM) {
     *wl = s[2] + 0.5 * vl_slope(s[1], s[2], s[3]);
     *wr = s[3] - 0.5 * vl_slope(s[2], s[3], s[4]);
+  } else if (recon == ORC_PPM5) {
+    /* cell s[2]: its two interface values from s[0..4]; cell s[3]: from
+     * s[1..5]; each clipped into its face's neighbour range, then the
+     * CW84 parabola limiter as in PPM */
+    double l1 = clip_pair(ppm5_left(s), s[1], s[2]), r1 = clip_pair(ppm5_right(s), s[2], s[3]);
+    double l2 = clip_pair(ppm5_left(s + 1), s[2], s[3]);
+    double r2 = clip_pair(ppm5_right(s + 1), s[3], s[4]);
+    ppm_limit(s[2], &l1, &r1);
+    ppm_limit(s[3], &l2, &r2);
+    *wl = r1; *wr = l2;
   } else {
     double im = ppm_iface(s[0], s[1], s[2], s[3]);   /* face f-1 */
     double i0 = ppm_iface(s[1], s[2], s[3], s[4]);   /* face f   */
@@ -227,7 +256,7 @@ static void recon_face(int recon, const double* s, double* wl, double* wr) {
 
 void orc_recon_line(int recon, int n, const double* w, double* wl,
                     double* wr) {
-  int reach = recon == ORC_DONOR ? 0 : (recon == ORC_PLM ? 1 : 2);
+  int reach = recon == ORC_DONOR ? 0 : (recon == ORC_PLM ? 1 : 2);   /* PPM, PPM5: 2 */
   for (int f = 0; f + 1 < n; ++f) {
     /* face between cells f and f+1: stencil cells f-2..f+3 */
     if (f - reach < 0 || f + 1 + reach > n - 1) {
@@ -745,7 +774,7 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
 /* ------------------------------------------------------------------ */
 
 int orc_ghost_width(int recon) {
-  return recon == ORC_PPM ? 3 : (recon == ORC_PLM ? 2 : 1);
+  return (recon == ORC_PPM || recon == ORC_PPM5) ? 3 : (recon == ORC_PLM ? 2 : 1);
 }
 
 void orc_load(const Mesh* m, const double* cons, const double* b1,

@@ -29,7 +29,7 @@ extern "C" {
 
 enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_PERIODIC = 0, ORC_OUTFLOW = 1 };
-enum { ORC_DONOR = 0, ORC_PLM = 1, ORC_PPM = 2 };
+enum { ORC_DONOR = 0, ORC_PLM = 1, ORC_PPM = 2, ORC_PPM5 = 3 };
 enum { ORC_VL2 = 0, ORC_RK2 = 1, ORC_RK3 = 2 };
 enum { ORC_HLLD = 0, ORC_HLLE = 1 };
 

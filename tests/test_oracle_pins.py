@@ -455,7 +455,7 @@ def _wave_error(n):
     return math.sqrt(err) / st.meta["amp"]
 
 
-def _aligned_wave_error(n, amp=1e-6, ntrans=4, riemann=O.HLLD, integ=O.VL2):
+def _aligned_wave_error(n, amp=1e-6, ntrans=4, riemann=O.HLLD, integ=O.VL2, recon=O.PLM):
     """Fast wave along x in a thin 3-D periodic box (B = (1, sqrt2, 0.5),
     rho = 1, P = 1/gamma): L1 error of rho after one period."""
     g_ = 5 / 3
@@ -473,7 +473,7 @@ def _aligned_wave_error(n, amp=1e-6, ntrans=4, riemann=O.HLLD, integ=O.VL2):
     cons = np.stack([1 + amp * r[0] * cavg, amp * r[1] * cavg, amp * r[2] * cavg, amp * r[3] * cavg,
                      (1 / g_ + amp * r[4] * cavg) / (g_ - 1) + 0.5 * (1 + by ** 2 + bz ** 2)])
     g = O.make_grid((n, ntrans, ntrans))
-    p = O.make_params(riemann=riemann, integrator=integ)
+    p = O.make_params(riemann=riemann, integrator=integ, recon=recon)
     s = O.State(cons, b1, b2, b3)
     O.run(g, p, s, t_end=1.0 / lam)
     return np.mean(np.abs(s.cons[0] - cons[0])) / amp
