@@ -41,7 +41,7 @@ def parse(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fp32_p64"],
                     help="working precision (default: fp64 for wave512, the paper's, else fp32)")
-    ap.add_argument("--recon", default="plm", choices=["plm", "ppm"])
+    ap.add_argument("--recon", default="plm", choices=["plm", "ppm", "ppm5"])
     ap.add_argument("--path", default="fused", choices=["fused", "unfused"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -286,7 +286,7 @@ def cpu_baseline(a, st_full):
     else:
         st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
         g = O.make_grid((n, n, n))
-        p = O.make_params(gamma=st.gamma, recon=O.PLM if a.recon == "plm" else O.PPM,
+        p = O.make_params(gamma=st.gamma, recon={"plm": O.PLM, "ppm": O.PPM, "ppm5": O.PPM5}[a.recon],
                           iso=a.iso, cs=1.0)
         cells = n ** 3
         what = f"{n}^3 box of the same turbulence generator" + (", isothermal" if a.iso else "")
@@ -388,7 +388,7 @@ def main():
         base = cpu_baseline(a, None)
 
     prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]
-    rec = A.PLM if a.recon == "plm" else A.PPM
+    rec = {"plm": A.PLM, "ppm": A.PPM, "ppm5": A.PPM5}[a.recon]
     path = A.FUSED if a.path == "fused" else A.UNFUSED
     dust = None
     if a.workload == "batched512":

@@ -64,8 +64,11 @@ enum {
   AETH_EOS_ISOTHERMAL_MHD = 2,
   AETH_EOS_ISOTHERMAL_HYDRO = 3
 };
-/* reconstruction (Sec. 2.4) */
-enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2 };
+/* reconstruction (Sec. 2.4): donor cell, PLM (van Leer 1974 limiter), PPM
+ * (Colella & Woodward 1984), PPM5 (interface values from the quartic
+ * through the five cell averages centred on each cell, with the PPM
+ * limiter; 3 ghost layers like PPM) */
+enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2, AETH_RECON_PPM5 = 3 };
 /* Riemann solver (Sec. 2.4): HLLD (Miyoshi & Kusano 2005); HLLE (Harten,
  * Lax & van Leer 1983; Einfeldt 1988) with the outer speed estimates of the
  * HLLD solver, the paper's throughput-benchmark solver; AETH_RIEMANN_MLP =

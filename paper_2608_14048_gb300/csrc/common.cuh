@@ -97,7 +97,31 @@ __device__ __forceinline__ void ppm_limit(R w, R& l, R& r) {
   }
 }
 
-// Face states from s[0..5] = cells f-3..f+2 around face f.
+// PPM5 (Sec. 2.4): interface values of a cell from the quartic through the
+// five cell averages q[0..4] centred on it (upwind-biased toward the cell):
+// at its upper face (right) and its lower face (left).
+template <typename R>
+__device__ __forceinline__ R ppm5_right(const R* q) {
+  return (R(2) * q[0] - R(13) * q[1] + R(47) * q[2] + R(27) * q[3] - R(3) * q[4]) *
+         R(1.0 / 60.0);
+}
+template <typename R>
+__device__ __forceinline__ R ppm5_left(const R* q) {
+  return (R(-3) * q[0] + R(27) * q[1] + R(47) * q[2] - R(13) * q[3] + R(2) * q[4]) *
+         R(1.0 / 60.0);
+}
+template <typename R>
+__device__ __forceinline__ R clip_pair(R a, R u0, R u1) {
+  return fmin(fmax(a, fmin(u0, u1)), fmax(u0, u1));
+}
+
+// Cells a reconstruction reads on each side of a face beyond its two
+// adjacent cells: donor 0, PLM 1, PPM and PPM5 2.
+template <int RECON>
+__host__ __device__ constexpr int recon_reach() { return RECON == 3 ? 2 : RECON; }
+
+// Face states from s[0..5] = cells f-3..f+2 around face f.  RECON: 0 donor,
+// 1 PLM, 2 PPM, 3 PPM5.
 template <int RECON, typename R>
 __device__ __forceinline__ void recon_face(const R* s, R& wl, R& wr) {
   if (RECON == 0) {
@@ -105,6 +129,14 @@ __device__ __forceinline__ void recon_face(const R* s, R& wl, R& wr) {
   } else if (RECON == 1) {
     wl = s[2] + R(0.5) * vl_slope(s[1], s[2], s[3]);
     wr = s[3] - R(0.5) * vl_slope(s[2], s[3], s[4]);
+  } else if (RECON == 3) {
+    // each interface value clipped into its face's neighbour range, then
+    // the CW84 parabola limiter as in PPM
+    R l1 = clip_pair(ppm5_left(s), s[1], s[2]), r1 = clip_pair(ppm5_right(s), s[2], s[3]);
+    R l2 = clip_pair(ppm5_left(s + 1), s[2], s[3]), r2 = clip_pair(ppm5_right(s + 1), s[3], s[4]);
+    ppm_limit(s[2], l1, r1);
+    ppm_limit(s[3], l2, r2);
+    wl = r1; wr = l2;
   } else {
     R im = ppm_iface(s[0], s[1], s[2], s[3]);
     R i0 = ppm_iface(s[1], s[2], s[3], s[4]);

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int e = 0; e < 3; ++e)
     if (c3[e] > L.n[e] || (e != D && c3[e] == L.n[e])) return;
-  constexpr int RL = RECON + 1, RH = RECON;
+  constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   const long long sz = L.size();
   const long long fc = L.idx(c3[0], c3[1], c3[2]);
   const long long sd = L.stride(D);
@@ -330,6 +330,11 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
       k_dust_flux<R, 1, 0><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);
       k_dust_flux<R, 1, 1><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);
       k_dust_flux<R, 1, 2><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);
+      break;
+    case AETH_RECON_PPM5:
+      k_dust_flux<R, 3, 0><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);
+      k_dust_flux<R, 3, 1><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);
+      k_dust_flux<R, 3, 2><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);
       break;
     default:
       k_dust_flux<R, 2, 0><<<grd, blk, 0, s>>>(L, dsrc, P.dflux, nd, dfl);

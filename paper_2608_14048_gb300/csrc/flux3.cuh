@@ -66,7 +66,7 @@ template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits) {
-  constexpr int RL = RECON + 1, RH = RECON;
+  constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
   constexpr int QN = RL + RH + 1;
   __shared__ R sw[NPRIM][WY][WX];
@@ -263,6 +263,7 @@ template <typename R, bool P64, bool MHD, int SOLVER>
 void flux_pass_solver_impl(aeth_ctx* c, int recon, int src, int block) {
   if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD, SOLVER>(c, src, block);
   else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD, SOLVER>(c, src, block);
+  else if (recon == AETH_RECON_PPM5) launch_flux3<R, P64, 3, MHD, SOLVER>(c, src, block);
   else launch_flux3<R, P64, 2, MHD, SOLVER>(c, src, block);
 }
 

@@ -1,5 +1,4 @@
-// Flux pass instantiations: adiabatic HLLE with the HLLD outer speeds, and
-// the face-state dump of the learned flux.
+// Flux pass instantiations: adiabatic HLLE with the HLLD outer speeds.
 #include "flux3.cuh"
 
 namespace aeth {
@@ -15,9 +14,6 @@ void flux_pass_solver(aeth_ctx* c, int recon, int src, int block) {
 AETH_FLUX_INST(float, false, 2)
 AETH_FLUX_INST(float, true, 2)
 AETH_FLUX_INST(double, false, 2)
-AETH_FLUX_INST(float, false, 1)
-AETH_FLUX_INST(float, true, 1)
-AETH_FLUX_INST(double, false, 1)
 #undef AETH_FLUX_INST
 
 }  // namespace aeth

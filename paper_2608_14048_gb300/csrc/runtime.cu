@@ -55,7 +55,7 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   const bool iso = cfg->eos == AETH_EOS_ISOTHERMAL_MHD || cfg->eos == AETH_EOS_ISOTHERMAL_HYDRO;
   if (!iso && !(cfg->gamma > 1.0)) bad = AETH_ERR_ARG;
   if (iso && !(cfg->cs_iso > 0.0 && cfg->cs_iso < INFINITY)) bad = AETH_ERR_ARG;
-  if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM) bad = AETH_ERR_ARG;
+  if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM5) bad = AETH_ERR_ARG;
   if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_HLLE &&
       cfg->riemann != AETH_RIEMANN_MLP)
     bad = AETH_ERR_ARG;

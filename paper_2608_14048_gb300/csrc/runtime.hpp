@@ -235,7 +235,9 @@ inline void prof_end(aeth_ctx* c, double algo_bytes) {
   c->prof_bytes += algo_bytes;
 }
 
-inline int ghost_width(int recon) { return recon == AETH_RECON_PPM ? 3 : (recon == AETH_RECON_PLM ? 2 : 1); }
+inline int ghost_width(int recon) {
+  return (recon == AETH_RECON_PPM || recon == AETH_RECON_PPM5) ? 3 : (recon == AETH_RECON_PLM ? 2 : 1);
+}
 
 inline double cmax_of(int integrator) {
   // IMEX2P: explicit Courant fraction 1/lambda, lambda = 1 + 1/sqrt(2)

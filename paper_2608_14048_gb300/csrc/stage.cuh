@@ -59,12 +59,12 @@ __device__ __forceinline__ bool in_prim_range(const Layout& L, int i, int j, int
 // Reconstruct face states of one variable from a stencil with stride.
 template <int RECON, typename R, typename Get>
 __device__ __forceinline__ void recon_var(Get get, R& wl, R& wr) {
-  constexpr int RL = RECON + 1;
+  constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   R s[6];
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
     const int off = t - 3;   // cell offset from the face's right cell
-    s[t] = (off >= -RL && off <= RECON) ? get(off) : R(0);
+    s[t] = (off >= -RL && off <= RH) ? get(off) : R(0);
   }
   recon_face<RECON>(s, wl, wr);
 }

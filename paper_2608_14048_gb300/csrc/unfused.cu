@@ -78,7 +78,7 @@ __global__ void k_flux(Layout L, ConstArr8<R> w, const R* __restrict__ bface, in
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       const int off = t - 3;
-      const bool need = RECON == 2 || (RECON == 1 && t >= 1 && t <= 4) || (RECON == 0 && (t == 2 || t == 3));
+      const bool need = RECON >= 2 || (RECON == 1 && t >= 1 && t <= 4) || (RECON == 0 && (t == 2 || t == 3));
       s[t] = need ? a[fc + off * sd] : R(0);
     }
     recon_face<RECON>(s, wl[q], wr[q]);
@@ -258,6 +258,9 @@ static void stage_unfused(aeth_ctx* c, const BlockPtrs<R>& P, int recon, int src
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     else if (recon == AETH_RECON_PLM)
       k_flux<R, 1><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, solver, gm, P.f[d][0], P.f[d][1], P.f[d][2],
+                                        P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
+    else if (recon == AETH_RECON_PPM5)
+      k_flux<R, 3><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, solver, gm, P.f[d][0], P.f[d][1], P.f[d][2],
                                         P.f[d][3], P.f[d][4], P.e[d][0], P.e[d][1]);
     else
       k_flux<R, 2><<<grd, blk, 0, st>>>(L, w, bf, d, mhd, solver, gm, P.f[d][0], P.f[d][1], P.f[d][2],

@@ -72,6 +72,14 @@ def test_dust_parity_three_species(prec, tol):
     assert max(errs) < tol, errs
 
 
+def test_dust_parity_ppm5():
+    # gas and dust share the reconstruction: PPM5 on both
+    gas, dust, ts = I.dust_box(I.Block((14, 12, 9)), 84, nd=3, t_stop=[0.003, 0.05, 1.0])
+    rc, rd, dts = _oracle(gas, dust, ts, 3, recon=O.PPM5)
+    cons, d, _ = _gpu(gas, dust, ts, dts, A.FP64, recon=A.PPM5)
+    assert max(_errs(cons, d, rc, rd)) < 1e-12
+
+
 def test_dust_parity_eight_species_stiff():
     # the 128^3 recipe at 16^3: t_s log-spaced 1e-4..1, dt/t_s,min ~ 10
     gas, dust, ts = I.dust_box(I.Block((16, 16, 16)), 82, nd=8)

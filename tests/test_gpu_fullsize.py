@@ -41,17 +41,19 @@ def _cut(arr_c, b1, b2, b3, lo, size, n):
     return [np.ascontiguousarray(x) for x in (cons, s1, s2, s3)]
 
 
-@pytest.mark.parametrize("recon,iso", [("plm", False), ("ppm", False), ("plm", True)])
+@pytest.mark.parametrize("recon,iso", [("plm", False), ("ppm", False), ("ppm5", False),
+                                       ("plm", True)])
 def test_turbulence_256_fp32_one_step_sampled(recon, iso):
-    """Both reconstructions of the 256^3 benchmark, and its isothermal
-    variant (p = c_s^2 rho with the generator's c_s = 1, isothermal HLLD),
-    with the tile shape the autotuner picks as in bench.py (PPM's stencil of
-    3 keeps the dependency radius at 6 <= HALO)."""
+    """The reconstructions of the 256^3 benchmark (PLM, PPM, PPM5), and its
+    isothermal variant (p = c_s^2 rho with the generator's c_s = 1,
+    isothermal HLLD), with the tile shape the autotuner picks as in bench.py
+    (the 3-cell stencils of PPM and PPM5 keep the dependency radius at
+    6 <= HALO)."""
     import torch
     n = 256
     st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
     g = O.make_grid((n, n, n))
-    orec, arec = (O.PLM, A.PLM) if recon == "plm" else (O.PPM, A.PPM)
+    orec, arec = {"plm": (O.PLM, A.PLM), "ppm": (O.PPM, A.PPM), "ppm5": (O.PPM5, A.PPM5)}[recon]
     p = O.make_params(gamma=st.gamma, recon=orec, iso=iso, cs=1.0)
     dt = O.compute_dt(g, p, O.State(st.cons, st.b1, st.b2, st.b3))
     cfg = A.make_config(gamma=st.gamma, recon=arec, precision=A.FP32, path=A.FUSED, iso=iso,

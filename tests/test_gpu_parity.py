@@ -361,3 +361,57 @@ def test_rk3_rejects_spherical_blocks():
     with pytest.raises(Exception) as e:
         A.Solver(cfg, [b], stream=torch.cuda.current_stream())
     assert "Cartesian" in str(e.value) or "UNSUPPORTED" in str(e.value)
+
+
+# ----------------------------------------------------------------- PPM5
+@pytest.mark.parametrize("path", [A.FUSED, A.UNFUSED])
+@pytest.mark.parametrize("integ,riemann", [("vl2", "hlld"), ("rk2", "hlle"), ("rk3", "hlld")])
+def test_ppm5_fp64_parity(integ, riemann, path):
+    """PPM5 (Sec. 2.4) on both kernel paths: three ghost layers, the
+    5-point interface values and the PPM limiter."""
+    st = _state(seed=61)
+    ref, dts = oracle_run(st, "ppm5", integ, nsteps=5, riemann=riemann)
+    (out,), diag = gpu_run([st], dts, "ppm5", integ, "fp64", path=path, riemann=riemann)
+    errs = compare(out, ref)
+    assert max(errs) < FP64_TOL, errs
+    assert diag["max_divb_rel"] < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_p64"])
+@pytest.mark.parametrize("mhd", [True, False])
+def test_ppm5_fp32_parity(prec, mhd):
+    st = _state(seed=62, mhd=mhd)
+    ref, dts = oracle_run(st, "ppm5", "vl2", nsteps=5, mhd=mhd)
+    (out,), _ = gpu_run([st], dts, "ppm5", "vl2", prec, mhd=mhd)
+    errs = compare(out, ref, mhd=mhd)
+    assert max(errs) < FP32_TOL, errs
+
+
+def test_ppm5_uneven_blocks_and_ragged_shapes():
+    """Several blocks of different (ragged, thin) sizes in one context: the
+    device-table launches with the 3-layer halo of PPM5."""
+    sts = [_state(n=(12, 10, 9), seed=63), _state(n=(33, 5, 7), seed=64),
+           _state(n=(8, 8, 1), seed=65)]
+    r0, dts = oracle_run(sts[0], "ppm5", "vl2", nsteps=3)
+    refs = [r0] + [oracle_run(s, "ppm5", "vl2", dts=dts)[0] for s in sts[1:]]
+    outs, _ = gpu_run(sts, dts, "ppm5", "vl2", "fp64")
+    for o, r in zip(outs, refs):
+        errs = compare(o, r)
+        assert all(e < FP64_TOL for e in errs if np.isfinite(e)), errs
+
+
+def test_ppm5_differs_from_ppm():
+    st = _state(seed=66)
+    _, dts = oracle_run(st, "ppm", "vl2", nsteps=3)
+    (a,), _ = gpu_run([st], dts, "ppm", "vl2", "fp64")
+    (b,), _ = gpu_run([st], dts, "ppm5", "vl2", "fp64")
+    assert max(rel_l1(a[0][v], b[0][v]) for v in range(5)) > 1e-7
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_ppm5_brio_wu_outflow_parity(axis):
+    st = I.brio_wu(axis, 48)
+    ref, dts = oracle_run(st, "ppm5", "rk3", nsteps=15)
+    (out,), _ = gpu_run([st], dts, "ppm5", "rk3", "fp64")
+    errs = compare(out, ref)
+    assert all(e < FP64_TOL for e in errs if np.isfinite(e)), errs
