@@ -27,7 +27,7 @@ CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 DONOR, PLM, PPM, PPM5 = 0, 1, 2, 3
 VL2, RK2, RK3 = 0, 1, 2
-HLLD, HLLE = 0, 1
+HLLD, HLLE, LHLLD = 0, 1, 2
 
 
 class Grid(C.Structure):
@@ -89,6 +89,8 @@ def lib():
             L.orc_mhd_diag.restype = None
             L.orc_hlld.argtypes = [C.c_double, dp, dp, C.c_double, dp]
             L.orc_hlld.restype = C.c_int
+            L.orc_lhlld.argtypes = [C.c_double, dp, dp, C.c_double, dp]
+            L.orc_lhlld.restype = C.c_int
             L.orc_hlle.argtypes = [C.c_double, dp, dp, C.c_double, dp]
             L.orc_hlle.restype = None
             for fn in ("orc_hlld_iso", "orc_hlle_iso"):
@@ -182,6 +184,15 @@ def hlld(gamma: float, wl, wr, bn: float):
     wr = np.ascontiguousarray(wr, dtype=np.float64)
     f = np.zeros(7)
     reg = lib().orc_hlld(float(gamma), _dp(wl), _dp(wr), float(bn), _dp(f))
+    return f, reg
+
+
+def lhlld(gamma: float, wl, wr, bn: float):
+    """Face-frame low-dissipation HLLD flux (orc_lhlld); returns (flux[7], region)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.zeros(7)
+    reg = lib().orc_lhlld(float(gamma), _dp(wl), _dp(wr), float(bn), _dp(f))
     return f, reg
 
 

@@ -523,6 +523,32 @@ int orc_hlld(double gamma, const double* wl, const double* wr, double bn,
   return region;
 }
 
+int orc_lhlld(double gamma, const double* wl, const double* wr, double bn, double* flux) {
+  int region = orc_hlld(gamma, wl, wr, bn, flux);
+  if (region == 0 || region == 5) return region;   /* supersonic: no contact */
+  /* the HLLD quantities the correction needs, recomputed as in orc_hlld */
+  double ul[7], ur[7], fl[7], fr[7], ptl, ptr;
+  side_flux(gamma, wl, bn, ul, fl, &ptl);
+  side_flux(gamma, wr, bn, ur, fr, &ptr);
+  double cfl = fast_speed(gamma, wl[0], wl[4], bn, wl[5], wl[6]);
+  double cfr = fast_speed(gamma, wr[0], wr[4], bn, wr[5], wr[6]);
+  double cmax = cfl > cfr ? cfl : cfr;
+  double sl = (wl[1] < wr[1] ? wl[1] : wr[1]) - cmax;
+  double sr = (wl[1] > wr[1] ? wl[1] : wr[1]) + cmax;
+  double sul = sl - wl[1], sur = sr - wr[1];
+  double den = sur * wr[0] - sul * wl[0];
+  double sm = (sur * wr[0] * wr[1] - sul * wl[0] * wl[1] - ptr + ptl) / den;
+  double d = wl[0] * wr[0] * sur * sul * (wr[1] - wl[1]) / den;
+  /* local Mach number: the larger flow speed over the larger fast speed */
+  double vl = sqrt(wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  double vr = sqrt(wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  double mach = (vl > vr ? vl : vr) / cmax;
+  double phi = mach < 1.0 ? mach : 1.0;
+  flux[1] += (phi - 1.0) * d;
+  flux[4] += (phi - 1.0) * d * sm;
+  return region;
+}
+
 /* ------------------------------------------------------------------ */
 /* Upwind corner EMF (Gardiner & Stone 2005), Sec. 2.5                   */
 /* ------------------------------------------------------------------ */
@@ -651,6 +677,8 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
             else orc_hlld_iso(p->cs_iso, wl, wr, bn, fx);
           } else if (p->riemann == ORC_HLLE) {
             orc_hlle(p->gamma, wl, wr, bn, fx);
+          } else if (p->riemann == ORC_LHLLD) {
+            orc_lhlld(p->gamma, wl, wr, bn, fx);
           } else {
             orc_hlld(p->gamma, wl, wr, bn, fx);
           }

@@ -31,7 +31,7 @@ enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_PERIODIC = 0, ORC_OUTFLOW = 1 };
 enum { ORC_DONOR = 0, ORC_PLM = 1, ORC_PPM = 2, ORC_PPM5 = 3 };
 enum { ORC_VL2 = 0, ORC_RK2 = 1, ORC_RK3 = 2 };
-enum { ORC_HLLD = 0, ORC_HLLE = 1 };
+enum { ORC_HLLD = 0, ORC_HLLE = 1, ORC_LHLLD = 2 };
 
 typedef struct {
   int nx, ny, nz;     /* interior cells along x1, x2, x3 */
@@ -47,7 +47,7 @@ typedef struct {
   int integrator;     /* ORC_VL2, ORC_RK2 or ORC_RK3 */
   double cfl;         /* Courant factor C of Eq. 11 */
   int mhd;            /* 1: MHD; 0: hydro (face arrays ignored, B = 0) */
-  int riemann;        /* ORC_HLLD (Sec. 2.4 default) or ORC_HLLE */
+  int riemann;        /* ORC_HLLD (Sec. 2.4 default), ORC_HLLE or ORC_LHLLD */
   int iso;            /* 1: isothermal closure p = cs_iso^2 rho (Sec. 2.1): no
                          energy equation (the energy slot is carried, unused) */
   double cs_iso;      /* isothermal sound speed */
@@ -80,6 +80,18 @@ void orc_mhd_diag(const orc_grid* g, const orc_params* p, const double* cons,
  * 0..5 (L, *L, **L, **R, *R, R) that supplied the flux. */
 int orc_hlld(double gamma, const double* wl, const double* wr, double bn,
              double* flux);
+
+/* Single-face low-dissipation HLLD (LHLLD; Sec. 2.4 after Minoshima &
+ * Miyoshi 2021, as read here): the HLLD flux with the pressure dissipation
+ * at the contact scaled by the local Mach number.  HLLD's star total
+ * pressure is p_T* = pbar + D, pbar the average of p_TL and p_TR weighted
+ * by rho_a (S_a - u_a), and D = rho_L rho_R (S_R - u_R)(S_L - u_L)(u_R - u_L)
+ * / den the term that grows with the sound speed.  Inside the fan the
+ * normal-momentum flux carries D and the energy flux S_M D; LHLLD replaces
+ * them with phi D and phi S_M D, phi = min(1, max(|v_L|, |v_R|) /
+ * max(c_f,L, c_f,R)).  phi = 1 (local Mach >= 1) gives HLLD exactly; with
+ * B = 0 it is the low-dissipation HLLC (LHLLC).  Returns the region. */
+int orc_lhlld(double gamma, const double* wl, const double* wr, double bn, double* flux);
 
 /* Single-face HLLE flux (Harten, Lax & van Leer 1983; Einfeldt 1988;
  * Sec. 2.4), same frames as orc_hlld: the flux of the single averaged state

@@ -396,6 +396,22 @@ def turbulence_box(n=256, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001,
 # 1-D Riemann problems embedded in 3-D
 # ---------------------------------------------------------------------------
 
+def taylor_green(n: int, mach: float, gamma=5.0 / 3.0, v0=1.0) -> InitialState:
+    """Taylor-Green vortex (the low-Mach dissipation test of Sec. 5): periodic
+    [0, 2 pi]^3, rho = 1, v = v0 (sin x cos y cos z, -cos x sin y cos z, 0),
+    p = p0 + (v0^2 / 16)(cos 2x + cos 2y)(cos 2z + 2) with p0 = v0^2 /
+    (gamma mach^2), so that v0 / c_s = mach; B = 0.  Cell-centre values."""
+    b = Block((n, n, n), (0.0, 0.0, 0.0), (2 * math.pi,) * 3)
+    X, Y, Z = _cell_mesh(b)
+    rho = np.ones_like(X)
+    v = (v0 * np.sin(X) * np.cos(Y) * np.cos(Z), -v0 * np.cos(X) * np.sin(Y) * np.cos(Z),
+         np.zeros_like(X))
+    p0 = v0 * v0 / (gamma * mach * mach)
+    p = p0 + (v0 * v0 / 16.0) * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    z1 = np.zeros((n, n, n + 1)); z2 = np.zeros((n, n + 1, n)); z3 = np.zeros((n + 1, n, n))
+    return _assemble(b, gamma, rho, v, p, z1, z2, z3, {"mach": mach})
+
+
 def riemann_1d(axis: int, n: int, left: dict, right: dict, gamma: float, x0=0.0,
                lo=-0.5, hi=0.5, ntrans=1) -> InitialState:
     """Discontinuity at x_axis = x0 between primitive states `left` and
