@@ -51,6 +51,8 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--mlp-engine", default="tcgen05", choices=["tcgen05", "mma_sync"])
     ap.add_argument("--hydro", action="store_true", help="wave512: the hydro column (B = 0)")
+    ap.add_argument("--riemann", default="lhlld", choices=["lhlld", "hlld"],
+                    help="tgv128: the gas solver (LHLLC / HLLC in hydro)")
     ap.add_argument("--iso", action="store_true",
                     help="turb256: isothermal closure p = cs^2 rho with cs = 1 (the sound "
                          "speed of the generator) and the isothermal HLLD")
@@ -69,7 +71,7 @@ def dist_env():
     return ws, rank, local
 
 
-WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512", "wave512")
+WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512", "wave512", "tgv128")
 # the paper's single-device throughput table (Sec. 6.1): PLM + HLLE + RK2,
 # FP64, 3-D linear wave at 512 x 512 x 256, NVIDIA A100 40 GB, in cells per
 # second per device
@@ -110,6 +112,15 @@ def workload_config(a):
                 "paper_reference": f"{PAPER_WAVE512[kind] / 1e6:.0f} Mzcps, NVIDIA A100 40GB, FP64 "
                                    "(paper Sec. 6.1 table)",
                 "l2": "inputs larger than L2"}
+    if a.workload == "tgv128":
+        return {"workload": "taylor_green_128^3_mach0.01", "grid": [128, 128, 128],
+                "box": "[0, 2 pi]^3", "recon": "PLM", "riemann": f"{a.riemann.upper()} (hydro)",
+                "integrator": "RK2", "cfl": 0.3, "gamma": 5.0 / 3.0, "mach": 0.01,
+                "precision": a.prec, "path": a.path,
+                "paper_test": "low-Mach Taylor-Green vortex (Sec. 5): 128^3, PLM + RK2, "
+                              "HLLC vs LHLLC at Mach 0.1 / 0.01",
+                "l2": "inputs larger than L2 (128^3 x 5 vars x 2 registers x fp32 = 84 MB "
+                      "state + 170 MB scratch)"}
     if a.workload == "wave32":
         return {"workload": "linear_fast_wave_32^3", "grid": [32, 32, 32], "recon": "PLM",
                 "riemann": "HLLD", "integrator": "VL2", "cfl": 0.3, "precision": a.prec,
@@ -283,6 +294,13 @@ def cpu_baseline(a, st_full):
                           mhd=not a.hydro)
         cells = 64 * 64 * 32
         what = f"{'hydro' if a.hydro else 'MHD'} linear wave 64x64x32 (PLM+HLLE+RK2)"
+    elif a.workload == "tgv128":
+        st = I.taylor_green(n, 0.01)
+        g = O.make_grid((n, n, n), hi=(2 * math.pi,) * 3)
+        p = O.make_params(gamma=st.gamma, recon=O.PLM, integrator=O.RK2, mhd=False,
+                          riemann=O.LHLLD if a.riemann == "lhlld" else O.HLLD)
+        cells = n ** 3
+        what = f"Taylor-Green vortex {n}^3 at Mach 0.01 (PLM + {solver_label(a)} + RK2)"
     else:
         st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
         g = O.make_grid((n, n, n))
@@ -311,6 +329,8 @@ def solver_label(a):
         return "face-state dump"
     if a.workload == "wave512":
         return "HLLE"
+    if a.workload == "tgv128":
+        return "LHLLC" if a.riemann == "lhlld" else "HLLC"
     return "isothermal HLLD" if a.iso else "HLLD"
 
 
@@ -325,7 +345,8 @@ def vs_paper(a, value):
 def bytes_per_cell_update(a):
     """HBM bytes per cell-update of the two-stage step at the state's
     precision: 40 words for MHD, 25 for hydro, ~185 for 8 dust species."""
-    words = 185.0 if a.workload == "dust128" else (25.0 if a.workload == "wave512" and a.hydro else 40.0)
+    hydro = (a.workload == "wave512" and a.hydro) or a.workload == "tgv128"
+    words = 185.0 if a.workload == "dust128" else (25.0 if hydro else 40.0)
     return words * (8.0 if a.prec == "fp64" else 4.0)
 
 
@@ -384,7 +405,8 @@ def main():
 
     # CPU baseline first (rank 0, N = 1), before the GPU work starts
     base = None
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload in ("turb256", "wave512"):
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload in ("turb256", "wave512",
+                                                                         "tgv128"):
         base = cpu_baseline(a, None)
 
     prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]
@@ -417,6 +439,12 @@ def main():
         states = [I.linear_wave_box((512, 512, 256), (2.0, 2.0, 1.0), mhd=not a.hydro)]
         cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.RK2, cfl=0.3,
                             precision=prec, path=path, riemann=A.HLLE, mhd=not a.hydro)
+    elif a.workload == "tgv128":
+        from paper_2608_14048_gb300 import inputs as I
+        states = [I.taylor_green(128, 0.01)]
+        cfg = A.make_config(gamma=states[0].gamma, recon=A.PLM, integrator=A.RK2, cfl=0.3,
+                            precision=prec, path=path, mhd=False,
+                            riemann=A.LHLLD if a.riemann == "lhlld" else A.HLLD)
     elif a.workload == "wave32":
         from paper_2608_14048_gb300 import inputs as I
         states = [I.linear_fast_wave(32)]
@@ -430,7 +458,7 @@ def main():
               for s_ in states]
     stream = torch.cuda.current_stream(dev)
     sv = A.Solver(cfg, blocks, stream=stream)
-    mhd_run = a.workload != "dust128" and not (a.workload == "wave512" and a.hydro)
+    mhd_run = a.workload not in ("dust128", "tgv128") and not (a.workload == "wave512" and a.hydro)
     if a.workload == "learned512":
         A.aeth_load_mlp(sv.ctx, learned["params"])
 

@@ -72,8 +72,12 @@ enum { AETH_RECON_DONOR = 0, AETH_RECON_PLM = 1, AETH_RECON_PPM = 2, AETH_RECON_
 /* Riemann solver (Sec. 2.4): HLLD (Miyoshi & Kusano 2005); HLLE (Harten,
  * Lax & van Leer 1983; Einfeldt 1988) with the outer speed estimates of the
  * HLLD solver, the paper's throughput-benchmark solver; AETH_RIEMANN_MLP =
- * learned flux with HLLD fallback */
-enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_HLLE = 1, AETH_RIEMANN_MLP = 2 };
+ * learned flux with HLLD fallback; AETH_RIEMANN_LHLLD = low-dissipation HLLD
+ * (after Minoshima & Miyoshi 2021): HLLD with the pressure dissipation at the
+ * contact (normal-momentum and energy flux) scaled by the local Mach number
+ * phi = min(1, max|v| / max c_f); LHLLC in hydro mode; adiabatic closures */
+enum { AETH_RIEMANN_HLLD = 0, AETH_RIEMANN_HLLE = 1, AETH_RIEMANN_MLP = 2,
+       AETH_RIEMANN_LHLLD = 3 };
 /* tensor-core engine of the learned flux: tcgen05 MMAs with TMEM
  * accumulators, or warp-level mma.sync */
 enum { AETH_MLP_TCGEN05 = 0, AETH_MLP_MMA_SYNC = 1 };

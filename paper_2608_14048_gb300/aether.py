@@ -25,7 +25,7 @@ STATUS = {0: "AETH_OK", -1: "AETH_ERR_ARG", -2: "AETH_ERR_OOM", -3: "AETH_ERR_CU
           -7: "AETH_ERR_STATE", -8: "AETH_ERR_UNSUPPORTED"}
 EOS_MHD, EOS_HYDRO, EOS_ISO_MHD, EOS_ISO_HYDRO = 0, 1, 2, 3
 DONOR, PLM, PPM, PPM5 = 0, 1, 2, 3
-HLLD, HLLE, MLP = 0, 1, 2
+HLLD, HLLE, MLP, LHLLD = 0, 1, 2, 3
 TCGEN05, MMA_SYNC = 0, 1          # tensor-core engine of the learned flux
 VL2, RK2, IMEX2P, RK3 = 0, 1, 2, 3
 FP64, FP32, FP32_P64 = 0, 1, 2

@@ -194,7 +194,13 @@ __device__ __forceinline__ void hlld_star(R rho, R un, R v1, R v2, R b1, R b2, R
 // HLLD flux.  Left/right states as scalars; all intermediate values stay in
 // registers (no runtime-indexed arrays).  Returns the solver region
 // 0..5 (L, *L, **L, **R, *R, R).
-template <typename R>
+// LD: the low-dissipation variant LHLLD (Sec. 2.4, after Minoshima & Miyoshi
+// 2021): HLLD's star total pressure is a weighted average of p_TL, p_TR plus
+// D = rho_L rho_R (S_R - u_R)(S_L - u_L)(u_R - u_L) / den, the pressure
+// dissipation that scales with the sound speed; inside the fan the flux
+// carries D in the normal momentum and S_M D in the energy, and LHLLD
+// scales both by phi = min(1, max(|v_L|, |v_R|) / max(c_f,L, c_f,R)).
+template <bool LD = false, typename R>
 __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R byl, R bzl,
                                       R rr, R ur, R vr, R wr, R pr, R byr, R bzr, R bn,
                                       R* f) {
@@ -277,6 +283,13 @@ __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R b
   R g4 = F4 + s_a * (es - u4);
   R g5 = F5 + s_a * (b1s - b1);
   R g6 = F6 + s_a * (b2s - b2);
+  if constexpr (LD) {
+    const R d = rl * rr * sur * sul * (ur - ul) * inv_den;
+    const R vml = sqrt(ul * ul + vl * vl + wl * wl), vmr = sqrt(ur * ur + vr * vr + wr * wr);
+    const R phi = fmin(R(1), fmax(vml, vmr) / cmax);
+    g1 += (phi - R(1)) * d;
+    g4 += (phi - R(1)) * d * sm;
+  }
   if (region == 2 || region == 3) {
     // double-star states: shared velocity and field, sqrt(rho*) weighted
     const R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
@@ -304,9 +317,9 @@ __device__ __forceinline__ int hlld_s(R gamma, R rl, R ul, R vl, R wl, R pl, R b
 
 // Array form: W = (rho, vn, vt1, vt2, p, Bt1, Bt2), flux (rho, Mn, Mt1, Mt2,
 // E, Bt1, Bt2).
-template <typename R>
+template <bool LD = false, typename R>
 __device__ __forceinline__ int hlld(R gamma, const R* wl, const R* wr, R bn, R* flux) {
-  return hlld_s(gamma, wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6], wr[0], wr[1], wr[2],
+  return hlld_s<LD>(gamma, wl[0], wl[1], wl[2], wl[3], wl[4], wl[5], wl[6], wr[0], wr[1], wr[2],
                 wr[3], wr[4], wr[5], wr[6], bn, flux);
 }
 

@@ -27,12 +27,16 @@ constexpr int NT = TX * TY;
 
 __host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
 
+// Solver families 3 and 4 are the isothermal ones.
+constexpr bool iso_solver(int solver) { return solver == 3 || solver == 4; }
+
 // Riemann solver family SOLVER (numbering of k_flux3 below) on one face.
 template <int SOLVER, typename R>
 __device__ __forceinline__ void solve_face(R g, const R* wl, const R* wr, R bn, R* fx) {
   if constexpr (SOLVER == 2) hlle(g, wl, wr, bn, fx);
   else if constexpr (SOLVER == 3) hlld_iso(g, wl, wr, bn, fx);
   else if constexpr (SOLVER == 4) hlle_iso(g, wl, wr, bn, fx);
+  else if constexpr (SOLVER == 5) hlld<true>(g, wl, wr, bn, fx);
   else hlld(g, wl, wr, bn, fx);
 }
 
@@ -58,7 +62,8 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 //    AETH_FLUX_MINB CTAs per SM in FP32; FP64 takes the full register file.
 // ------------------------------------------------------------------------
 // SOLVER 0: HLLD; 2: HLLE; 1: write the face states (wl, wr, bn) for the learned
-// flux instead of solving; 3: isothermal HLLD; 4: isothermal HLLE.  For the
+// flux instead of solving; 3: isothermal HLLD; 4: isothermal HLLE; 5: the
+// low-dissipation HLLD (LHLLD).  For the
 // isothermal solvers the `gamma` argument carries the sound speed cs, the
 // primitive pressure is cs^2 rho and is not reconstructed (the isothermal
 // fluxes take the pressure from the reconstructed density).
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
   constexpr int QN = RL + RH + 1;
   __shared__ R sw[NPRIM][WY][WX];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  constexpr bool ISO = SOLVER >= 3;
+  constexpr bool ISO = iso_solver(SOLVER);
   const R gm1 = ISO ? gamma * gamma : gamma - R(1);   // cs^2 for ISO
   int hits = 0;
 
@@ -248,7 +253,8 @@ static void launch_flux3(aeth_ctx* c, int src, int block) {
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
     k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER><<<grid, NT, 0, c->stream>>>(
-        S, r.t0, r.t1, src, (R)(SOLVER >= 3 ? c->cfg.cs_iso : c->cfg.gamma), (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk,
+        S, r.t0, r.t1, src, (R)(iso_solver(SOLVER) ? c->cfg.cs_iso : c->cfg.gamma),
+        (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk,
         c->d_floor);
   });
   c->n_launch += 1;

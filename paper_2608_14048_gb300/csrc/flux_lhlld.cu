@@ -1,0 +1,20 @@
+// Flux pass instantiations: the low-dissipation HLLD (LHLLD, after Minoshima
+// & Miyoshi 2021).
+#include "flux3.cuh"
+
+namespace aeth {
+
+template <typename R, bool P64, bool MHD, int SOLVER>
+void flux_pass_solver(aeth_ctx* c, int recon, int src, int block) {
+  flux_pass_solver_impl<R, P64, MHD, SOLVER>(c, recon, src, block);
+}
+
+#define AETH_FLUX_INST(R, P64)                                               \
+  template void flux_pass_solver<R, P64, true, 5>(aeth_ctx*, int, int, int); \
+  template void flux_pass_solver<R, P64, false, 5>(aeth_ctx*, int, int, int);
+AETH_FLUX_INST(float, false)
+AETH_FLUX_INST(float, true)
+AETH_FLUX_INST(double, false)
+#undef AETH_FLUX_INST
+
+}  // namespace aeth

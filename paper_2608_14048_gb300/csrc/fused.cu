@@ -337,6 +337,8 @@ static void flux_pass(aeth_ctx* c, int recon, int src, int block) {
     else flux_pass_solver<R, false, MHD, 3>(c, recon, src, block);
   } else if (hlle) {
     flux_pass_solver<R, P64, MHD, 2>(c, recon, src, block);
+  } else if (c->cfg.riemann == AETH_RIEMANN_LHLLD) {
+    flux_pass_solver<R, P64, MHD, 5>(c, recon, src, block);
   } else {
     flux_pass_solver<R, P64, MHD, 0>(c, recon, src, block);
   }

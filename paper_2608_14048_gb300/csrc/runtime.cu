@@ -56,9 +56,7 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (!iso && !(cfg->gamma > 1.0)) bad = AETH_ERR_ARG;
   if (iso && !(cfg->cs_iso > 0.0 && cfg->cs_iso < INFINITY)) bad = AETH_ERR_ARG;
   if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM5) bad = AETH_ERR_ARG;
-  if (cfg->riemann != AETH_RIEMANN_HLLD && cfg->riemann != AETH_RIEMANN_HLLE &&
-      cfg->riemann != AETH_RIEMANN_MLP)
-    bad = AETH_ERR_ARG;
+  if (cfg->riemann < AETH_RIEMANN_HLLD || cfg->riemann > AETH_RIEMANN_LHLLD) bad = AETH_ERR_ARG;
   if (cfg->integrator < AETH_INT_VL2 || cfg->integrator > AETH_INT_RK3) bad = AETH_ERR_ARG;
   if (cfg->precision < AETH_FP64 || cfg->precision > AETH_FP32_P64) bad = AETH_ERR_ARG;
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) bad = AETH_ERR_ARG;
@@ -83,6 +81,10 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   } else if (cfg->integrator == AETH_INT_IMEX2P) {
     delete c;
     return AETH_ERR_UNSUPPORTED;
+  }
+  if (iso && cfg->riemann == AETH_RIEMANN_LHLLD) {
+    delete c;
+    return AETH_ERR_UNSUPPORTED;   // isothermal solvers: HLLD and HLLE
   }
   if (cfg->riemann == AETH_RIEMANN_MLP && (cfg->precision == AETH_FP64 || cfg->n_dust > 0 || iso)) {
     delete c;

@@ -252,8 +252,9 @@ inline bool is_mhd(const aeth_ctx* c) {
 inline bool is_iso(const aeth_ctx* c) {
   return c->cfg.eos == AETH_EOS_ISOTHERMAL_MHD || c->cfg.eos == AETH_EOS_ISOTHERMAL_HYDRO;
 }
-// internal solver codes of the face kernels beyond AETH_RIEMANN_*
-constexpr int SOLVER_ISO_HLLD = 3;
-constexpr int SOLVER_ISO_HLLE = 4;
+// internal solver codes of the unfused face kernel, distinct from every
+// AETH_RIEMANN_* value
+constexpr int SOLVER_ISO_HLLD = 16;
+constexpr int SOLVER_ISO_HLLE = 17;
 
 }  // namespace aeth

@@ -85,11 +85,12 @@ __global__ void k_flux(Layout L, ConstArr8<R> w, const R* __restrict__ bface, in
   }
   const R bn = mhd ? bface[fc] : R(0);
   R fx[7];
-  // solver: AETH_RIEMANN_HLLD / _HLLE, or SOLVER_ISO_HLLD / _HLLE with
+  // solver: AETH_RIEMANN_HLLD / _HLLE / _LHLLD, or SOLVER_ISO_HLLD / _HLLE with
   // `gamma` holding the isothermal sound speed
   if (solver == AETH_RIEMANN_HLLE) hlle(gamma, wl, wr, bn, fx);
   else if (solver == SOLVER_ISO_HLLD) hlld_iso(gamma, wl, wr, bn, fx);
   else if (solver == SOLVER_ISO_HLLE) hlle_iso(gamma, wl, wr, bn, fx);
+  else if (solver == AETH_RIEMANN_LHLLD) hlld<true>(gamma, wl, wr, bn, fx);
   else hlld(gamma, wl, wr, bn, fx);
   R* fo[5] = {f0, f1, f2, f3, f4};
   fo[0][fc] = fx[0];

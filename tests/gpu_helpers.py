@@ -10,7 +10,7 @@ RECON = {"donor": (O.DONOR, A.DONOR), "plm": (O.PLM, A.PLM), "ppm": (O.PPM, A.PP
          "ppm5": (O.PPM5, A.PPM5)}
 INTEG = {"vl2": (O.VL2, A.VL2), "rk2": (O.RK2, A.RK2), "rk3": (O.RK3, A.RK3)}
 PREC = {"fp64": A.FP64, "fp32": A.FP32, "fp32_p64": A.FP32_P64}
-RIEMANN = {"hlld": (O.HLLD, A.HLLD), "hlle": (O.HLLE, A.HLLE)}
+RIEMANN = {"hlld": (O.HLLD, A.HLLD), "hlle": (O.HLLE, A.HLLE), "lhlld": (O.LHLLD, A.LHLLD)}
 
 
 def rel_l1(a, b):
