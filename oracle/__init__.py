@@ -40,7 +40,8 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("recon", C.c_int),
                 ("integrator", C.c_int), ("cfl", C.c_double), ("mhd", C.c_int),
-                ("riemann", C.c_int), ("iso", C.c_int), ("cs_iso", C.c_double)]
+                ("riemann", C.c_int), ("iso", C.c_int), ("cs_iso", C.c_double),
+                ("dual", C.c_int), ("alpha_switch", C.c_double), ("alpha_sync", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -91,6 +92,8 @@ def lib():
             L.orc_hlld.restype = C.c_int
             L.orc_lhlld.argtypes = [C.c_double, dp, dp, C.c_double, dp]
             L.orc_lhlld.restype = C.c_int
+            L.orc_dual_init.argtypes = [C.POINTER(Grid), C.POINTER(Params), dp, dp, dp, dp]
+            L.orc_dual_init.restype = None
             L.orc_hlle.argtypes = [C.c_double, dp, dp, C.c_double, dp]
             L.orc_hlle.restype = None
             for fn in ("orc_hlld_iso", "orc_hlle_iso"):
@@ -132,10 +135,13 @@ def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), coord=CART, bc=(PERIODI
 
 
 def make_params(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, mhd=True,
-                rho_floor=1e-12, p_floor=1e-10, riemann=HLLD, iso=False, cs=1.0) -> Params:
-    """iso=True: the isothermal closure p = cs^2 rho (gamma unused)."""
+                rho_floor=1e-12, p_floor=1e-10, riemann=HLLD, iso=False, cs=1.0, dual=False,
+                alpha_switch=1e-3, alpha_sync=1e-1) -> Params:
+    """iso=True: the isothermal closure p = cs^2 rho (gamma unused).
+    dual=True: the dual-energy formalism (Sec. 2.7); the state's cons then
+    has six variables, the sixth the entropy S (see dual_init)."""
     return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0, riemann,
-                  1 if iso else 0, cs)
+                  1 if iso else 0, cs, 1 if dual else 0, alpha_switch, alpha_sync)
 
 
 class State:
@@ -153,6 +159,18 @@ class State:
 
     def copy(self) -> "State":
         return State(self.cons.copy(), self.b1.copy(), self.b2.copy(), self.b3.copy())
+
+
+def dual_init(grid: Grid, params: Params, s: State) -> State:
+    """A copy of ``s`` with the entropy S = p / rho^(gamma-1) appended as the
+    sixth cell variable (orc_dual_init), for dual-energy runs."""
+    out = s.copy()
+    cons6 = np.zeros((6,) + out.cons.shape[1:])
+    cons6[:5] = out.cons[:5]
+    out.cons = np.ascontiguousarray(cons6)
+    lib().orc_dual_init(C.byref(grid), C.byref(params), _dp(out.cons), _dp(out.b1),
+                        _dp(out.b2), _dp(out.b3))
+    return out
 
 
 def step(grid: Grid, params: Params, dt: float, s: State) -> int:

@@ -137,8 +137,48 @@ void orc_fill_ghosts(const Mesh* m, double** u, int nu, double** b) {
 /* Conserved -> primitive (Sec. 2.1, Eq. 5) with floors                 */
 /* ------------------------------------------------------------------ */
 
+/* Dual-energy selection (Sec. 2.7): the internal energy from the total,
+ * eint = E - kinetic - magnetic, is untrusted when it is below alpha_switch
+ * times the kinetic plus magnetic energy (written as a product so that a
+ * fluid at rest without field compares eint with 0). */
+static int dual_use_entropy(const orc_params* p, double eint, double kin_mag) {
+  return eint < p->alpha_switch * kin_mag;
+}
+
+/* Dual-energy synchronisation of the interior cells of a stage state
+ * (Sec. 2.7), before its ghost fill: where eint is untrusted, E is
+ * rewritten from S (eint = S rho^(gamma-1) / (gamma-1)); where eint exceeds
+ * alpha_sync times the kinetic plus magnetic energy, S is resynchronised
+ * from E; in between neither changes. */
+static void dual_sync(const Mesh* m, const orc_params* p, double** u, double** b) {
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k < m->n[2]; ++k)
+    for (int j = 0; j < m->n[1]; ++j)
+      for (int i = 0; i < m->n[0]; ++i) {
+        long c = IDX(m, i, j, k);
+        double rho = u[0][c];
+        if (rho < p->rho_floor) rho = p->rho_floor;
+        double v1 = u[1][c] / rho, v2 = u[2][c] / rho, v3 = u[3][c] / rho;
+        double bc1 = 0, bc2 = 0, bc3 = 0;
+        if (p->mhd) {
+          bc1 = 0.5 * (b[0][c] + b[0][IDX(m, i + 1, j, k)]);
+          bc2 = 0.5 * (b[1][c] + b[1][IDX(m, i, j + 1, k)]);
+          bc3 = 0.5 * (b[2][c] + b[2][IDX(m, i, j, k + 1)]);
+        }
+        double km = 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3) +
+                    0.5 * (bc1 * bc1 + bc2 * bc2 + bc3 * bc3);
+        double eint = u[4][c] - km;
+        double rg = pow(rho, p->gamma - 1.0);
+        if (dual_use_entropy(p, eint, km)) {
+          u[4][c] = u[5][c] * rg / (p->gamma - 1.0) + km;
+        } else if (eint > p->alpha_sync * km) {
+          u[5][c] = (p->gamma - 1.0) * eint / rg;
+        }
+      }
+}
+
 /* W = (rho, v1, v2, v3, p, B1, B2, B3) with cell-centred B the mean of the
- * two bounding face values (Sec. 2.5). */
+ * two bounding face values (Sec. 2.5); with dual energy also w[8] = S/rho. */
 static long cons_to_prim(const Mesh* m, const orc_params* p, double** u,
                          double** b, double** w) {
   long hits = 0;
@@ -162,12 +202,18 @@ static long cons_to_prim(const Mesh* m, const orc_params* p, double** u,
         double pr;
         if (p->iso) {
           pr = p->cs_iso * p->cs_iso * rho;
+        } else if (p->dual && dual_use_entropy(p, u[4][c] - ke - me, ke + me)) {
+          /* dual energy (Sec. 2.7): the subtraction is untrusted, the
+           * pressure comes from the advected entropy */
+          pr = u[5][c] * pow(rho, p->gamma - 1.0);
+          if (pr < p->p_floor) { pr = p->p_floor; ++hits; }
         } else {
           pr = (p->gamma - 1.0) * (u[4][c] - ke - me);
           if (pr < p->p_floor) { pr = p->p_floor; ++hits; }
         }
         w[0][c] = rho; w[1][c] = v1; w[2][c] = v2; w[3][c] = v3;
         w[4][c] = pr;  w[5][c] = bc1; w[6][c] = bc2; w[7][c] = bc3;
+        if (p->dual) w[8][c] = u[5][c] / rho;   /* specific entropy */
       }
   return hits;
 }
@@ -580,8 +626,8 @@ double orc_corner_emf(double ea_m, double ea_p, double eb_m, double eb_p,
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-  double* w[8];      /* primitives */
-  double* f[3][5];   /* hydro fluxes per direction */
+  double* w[9];      /* primitives (+ specific entropy with dual energy) */
+  double* f[3][6];   /* hydro fluxes per direction (+ entropy flux) */
   double* e[3][2];   /* face EMFs per direction: component t1, t2 */
   double* edge[3];   /* corner EMFs, by component */
 } Work;
@@ -590,9 +636,9 @@ static double* zalloc(long n) { return (double*)calloc((size_t)n, sizeof(double)
 
 static int work_alloc(Work* wk, const Mesh* m) {
   memset(wk, 0, sizeof *wk);
-  for (int v = 0; v < 8; ++v) if (!(wk->w[v] = zalloc(m->size))) return -1;
+  for (int v = 0; v < 9; ++v) if (!(wk->w[v] = zalloc(m->size))) return -1;
   for (int d = 0; d < 3; ++d) {
-    for (int v = 0; v < 5; ++v) if (!(wk->f[d][v] = zalloc(m->size))) return -1;
+    for (int v = 0; v < 6; ++v) if (!(wk->f[d][v] = zalloc(m->size))) return -1;
     for (int v = 0; v < 2; ++v) if (!(wk->e[d][v] = zalloc(m->size))) return -1;
     if (!(wk->edge[d] = zalloc(m->size))) return -1;
   }
@@ -600,9 +646,9 @@ static int work_alloc(Work* wk, const Mesh* m) {
 }
 
 static void work_free(Work* wk) {
-  for (int v = 0; v < 8; ++v) free(wk->w[v]);
+  for (int v = 0; v < 9; ++v) free(wk->w[v]);
   for (int d = 0; d < 3; ++d) {
-    for (int v = 0; v < 5; ++v) free(wk->f[d][v]);
+    for (int v = 0; v < 6; ++v) free(wk->f[d][v]);
     for (int v = 0; v < 2; ++v) free(wk->e[d][v]);
     free(wk->edge[d]);
   }
@@ -638,7 +684,9 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
                   double** a_b, double w1, double** b_u, double** b_b,
                   double beta, double dt, double** out_u, double** out_b) {
   int mhd = p->mhd;
-  orc_fill_ghosts(m, src_u, 5, mhd ? src_b : NULL);
+  int nu = p->dual ? 6 : 5;
+  if (p->dual) dual_sync(m, p, src_u, src_b);
+  orc_fill_ghosts(m, src_u, nu, mhd ? src_b : NULL);
   long hits = cons_to_prim(m, p, src_u, src_b, wk->w);
 
   /* --- fluxes along each direction (Sec. 2.4), cyclic face frame --- */
@@ -691,6 +739,19 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
            * F(Bt2) = +E_t1 */
           wk->e[d][0][fc] = fx[6];
           wk->e[d][1][fc] = -fx[5];
+          if (p->dual) {
+            /* entropy flux (Sec. 2.7): mass flux times the specific entropy
+             * of the upwind side, reconstructed like the primitives */
+            double s6[6], sl, sr;
+            for (int t = 0; t < 6; ++t) {
+              int cc[3] = {c[0], c[1], c[2]};
+              cc[d] = c[d] - 3 + t;
+              if (cc[d] < -m->ng || cc[d] >= m->n[d] + m->ng) { s6[t] = NAN; continue; }
+              s6[t] = wk->w[8][IDX(m, cc[0], cc[1], cc[2])];
+            }
+            recon_face(recon, s6, &sl, &sr);
+            wk->f[d][5][fc] = fx[0] >= 0.0 ? fx[0] * sl : fx[0] * sr;
+          }
         }
   }
 
@@ -753,11 +814,11 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
           sph_source(m, i, j, k, wc, mhd, s);
           src[1] = s[0]; src[2] = s[1]; src[3] = s[2];
         }
-        for (int v = 0; v < 5; ++v) {
+        for (int v = 0; v < nu; ++v) {
           double div = 0.0;
           for (int d = 0; d < 3; ++d)
             div += Ap[d] * wk->f[d][v][cp[d]] - Am[d] * wk->f[d][v][c];
-          double rhs = -div / V + src[v];
+          double rhs = -div / V + (v < 5 ? src[v] : 0.0);
           double base = w0 * a_u[v][c];
           if (w1 != 0.0) base += w1 * b_u[v][c];
           out_u[v][c] = base + beta * dt * rhs;
@@ -861,6 +922,36 @@ void orc_store(const Mesh* m, double** u, int nu, double** b, double* cons,
       }
 }
 
+void orc_dual_init(const orc_grid* g, const orc_params* p, double* cons, const double* b1,
+                   const double* b2, const double* b3) {
+  Mesh m;
+  if (orc_mesh_init(&m, g, 1) != 0) return;
+  int nx = m.n[0], ny = m.n[1], nz = m.n[2];
+  long ncell = (long)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = ((long)k * ny + j) * nx + i;
+        double rho = cons[c];
+        if (rho < p->rho_floor) rho = p->rho_floor;
+        double m1 = cons[ncell + c], m2 = cons[2 * ncell + c], m3 = cons[3 * ncell + c];
+        double bc[3] = {0, 0, 0};
+        if (p->mhd) {
+          bc[0] = 0.5 * (b1[((long)k * ny + j) * (nx + 1) + i] +
+                         b1[((long)k * ny + j) * (nx + 1) + i + 1]);
+          bc[1] = 0.5 * (b2[((long)k * (ny + 1) + j) * nx + i] +
+                         b2[((long)k * (ny + 1) + j + 1) * nx + i]);
+          bc[2] = 0.5 * (b3[((long)k * ny + j) * nx + i] +
+                         b3[((long)(k + 1) * ny + j) * nx + i]);
+        }
+        double km = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rho +
+                    0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+        double pr = (p->gamma - 1.0) * (cons[4 * ncell + c] - km);
+        if (pr < p->p_floor) pr = p->p_floor;
+        cons[5 * ncell + c] = pr / pow(rho, p->gamma - 1.0);
+      }
+}
+
 /* ------------------------------------------------------------------ */
 /* Public: one step (Sec. 2.6)                                           */
 /* ------------------------------------------------------------------ */
@@ -870,12 +961,13 @@ int orc_mhd_step(const orc_grid* g, const orc_params* p, double dt,
                  long* floor_hits) {
   Mesh m;
   if (orc_mesh_init(&m, g, orc_ghost_width(p->recon)) != 0) return -1;
-  double *A[5], *Ab[3], *B[5], *Bb[3];
-  for (int v = 0; v < 5; ++v) { A[v] = zalloc(m.size); B[v] = zalloc(m.size); }
+  int nu = p->dual ? 6 : 5;   /* dual energy: S is the sixth cell variable */
+  double *A[6] = {0}, *Ab[3], *B[6] = {0}, *Bb[3];
+  for (int v = 0; v < nu; ++v) { A[v] = zalloc(m.size); B[v] = zalloc(m.size); }
   for (int d = 0; d < 3; ++d) { Ab[d] = zalloc(m.size); Bb[d] = zalloc(m.size); }
   Work wk;
   if (work_alloc(&wk, &m) != 0) return -2;
-  orc_load(&m, cons, b1, b2, b3, A, 5, p->mhd ? Ab : NULL);
+  orc_load(&m, cons, b1, b2, b3, A, nu, p->mhd ? Ab : NULL);
 
   long hits = 0;
   if (p->integrator == ORC_VL2) {
@@ -889,8 +981,8 @@ int orc_mhd_step(const orc_grid* g, const orc_params* p, double dt,
     /* SSP-RK3 (Shu & Osher 1988; Sec. 2.6): u1 = u + dt L(u);
      * u2 = 3/4 u + 1/4 u1 + 1/4 dt L(u1); u' = 1/3 u + 2/3 u2 + 2/3 dt L(u2),
      * with a third register for u2 */
-    double *C[5], *Cb[3];
-    for (int v = 0; v < 5; ++v) C[v] = zalloc(m.size);
+    double *C[6] = {0}, *Cb[3];
+    for (int v = 0; v < nu; ++v) C[v] = zalloc(m.size);
     for (int d = 0; d < 3; ++d) Cb[d] = zalloc(m.size);
     hits += stage(&m, p, p->recon, &wk, A, Ab, 1.0, A, Ab, 0.0, NULL, NULL,
                   1.0, dt, B, Bb);
@@ -898,7 +990,7 @@ int orc_mhd_step(const orc_grid* g, const orc_params* p, double dt,
                   dt, C, Cb);
     hits += stage(&m, p, p->recon, &wk, C, Cb, 1.0 / 3.0, A, Ab, 2.0 / 3.0, C, Cb,
                   2.0 / 3.0, dt, A, Ab);
-    for (int v = 0; v < 5; ++v) free(C[v]);
+    for (int v = 0; v < nu; ++v) free(C[v]);
     for (int d = 0; d < 3; ++d) free(Cb[d]);
   } else {
     /* two-register SSP-RK2 (Eq. 10): u2 <- u1; u1 <- u1 + dt L(u1);
@@ -908,11 +1000,11 @@ int orc_mhd_step(const orc_grid* g, const orc_params* p, double dt,
     hits += stage(&m, p, p->recon, &wk, B, Bb, 0.5, A, Ab, 0.5, B, Bb, 0.5,
                   dt, A, Ab);
   }
-  if (p->mhd) orc_fill_ghosts(&m, A, 5, Ab);
-  orc_store(&m, A, 5, p->mhd ? Ab : NULL, cons, b1, b2, b3);
+  if (p->mhd) orc_fill_ghosts(&m, A, nu, Ab);
+  orc_store(&m, A, nu, p->mhd ? Ab : NULL, cons, b1, b2, b3);
   if (floor_hits) *floor_hits = hits;
   work_free(&wk);
-  for (int v = 0; v < 5; ++v) { free(A[v]); free(B[v]); }
+  for (int v = 0; v < nu; ++v) { free(A[v]); free(B[v]); }
   for (int d = 0; d < 3; ++d) { free(Ab[d]); free(Bb[d]); }
   return 0;
 }
@@ -948,9 +1040,13 @@ double orc_mhd_dt(const orc_grid* g, const orc_params* p, const double* cons,
           pr = p->cs_iso * p->cs_iso * rho;
           gam = 1.0;
         } else {
-          pr = (p->gamma - 1.0) *
-               (cons[4 * ncell + c] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
-                0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+          double km = 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) +
+                      0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+          double eint = cons[4 * ncell + c] - km;
+          if (p->dual && dual_use_entropy(p, eint, km))
+            pr = cons[5 * ncell + c] * pow(rho, p->gamma - 1.0);
+          else
+            pr = (p->gamma - 1.0) * eint;
           if (pr < p->p_floor) pr = p->p_floor;
         }
         double w[3];

@@ -51,6 +51,9 @@ typedef struct {
   int iso;            /* 1: isothermal closure p = cs_iso^2 rho (Sec. 2.1): no
                          energy equation (the energy slot is carried, unused) */
   double cs_iso;      /* isothermal sound speed */
+  int dual;           /* 1: dual-energy formalism (Sec. 2.7): the state carries a
+                         sixth cell variable S = p / rho^(gamma-1) */
+  double alpha_switch, alpha_sync;  /* its thresholds (1e-3, 1e-1 by default) */
 } orc_params;
 
 typedef struct {
@@ -58,6 +61,12 @@ typedef struct {
   double max_divb_rel;          /* max |sum_f +-A_f B_f| / sum_f A_f |B_f| */
   long floor_hits;              /* cells where a floor was applied */
 } orc_diag;
+
+/* Dual-energy formalism (Sec. 2.7): the entropy S = p / rho^(gamma-1) of
+ * every interior cell from its conserved state (cons[5] of a 6-variable
+ * state; p from E with the floors of the cons->prim conversion). */
+void orc_dual_init(const orc_grid* g, const orc_params* p, double* cons, const double* b1,
+                   const double* b2, const double* b3);
 
 /* One full step of length dt (both stages), in place.  Returns 0 on
  * success, a negative value on bad arguments. */
