@@ -685,7 +685,14 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
                   double beta, double dt, double** out_u, double** out_b) {
   int mhd = p->mhd;
   int nu = p->dual ? 6 : 5;
-  if (p->dual) dual_sync(m, p, src_u, src_b);
+  if (p->dual) {
+    /* the sync reads each interior cell's bounding faces: on periodic axes
+     * the face at index n is the image of face 0, set by the ghost fill, so
+     * fill first, sync, then fill again to carry the synced E and S into
+     * the ghost cells */
+    orc_fill_ghosts(m, src_u, nu, mhd ? src_b : NULL);
+    dual_sync(m, p, src_u, src_b);
+  }
   orc_fill_ghosts(m, src_u, nu, mhd ? src_b : NULL);
   long hits = cons_to_prim(m, p, src_u, src_b, wk->w);
 
