@@ -118,6 +118,21 @@ typedef struct {
                          AETH_MLP_MMA_SYNC */
   double cs_iso;      /* isothermal sound speed (> 0, finite) of the
                          AETH_EOS_ISOTHERMAL_* closures; ignored otherwise */
+  int dual_energy;    /* 1: dual-energy formalism (Sec. 2.7, Bryan 1995 in the
+                         entropy form): the entropy S = p / rho^(gamma-1) is
+                         advected alongside the state (mass flux x S/rho of
+                         the upwind side); at every stage start a cell whose
+                         internal energy E - kinetic - magnetic is below
+                         alpha_switch x (kinetic + magnetic) takes its
+                         pressure from S and has E rewritten to match, one
+                         above alpha_sync x (kinetic + magnetic) has S
+                         resynchronised from E.  Adiabatic closures, fused
+                         path, AETH_FP64 or AETH_FP32 (it is the alternative
+                         to AETH_FP32_P64), HLLD / HLLE / LHLLD, no dust.
+                         S is initialised from the state by aeth_set_state
+                         and read back with aeth_get_entropy. */
+  double alpha_switch; /* <= 0 selects 1e-3 */
+  double alpha_sync;   /* <= 0 selects 1e-1 */
 } aeth_config;
 
 typedef struct {
@@ -176,6 +191,13 @@ aeth_status aeth_set_state(aeth_ctx* ctx, int block, const double* cons,
  * stream; returns any latched device error. */
 aeth_status aeth_get_state(aeth_ctx* ctx, int block, double* cons,
                            double* b1f, double* b2f, double* b3f);
+
+/* Dual-energy entropy S = p / rho^(gamma-1) of block `block` (register A,
+ * interior cells) into S[nz][ny][nx] (host FP64, caller-owned).  Pinned,
+ * mapped host memory is written directly, anything else through the
+ * library's staging buffer.  AETH_ERR_STATE when dual energy is off;
+ * synchronises the stream. */
+aeth_status aeth_get_entropy(aeth_ctx* ctx, int block, double* S);
 
 /* Eq. 11 over every block: dt = C * Cmax * min over cells and directions of
  * dx_d / (|v_d| + c_d), with c_d the directional fast speed (sound speed in

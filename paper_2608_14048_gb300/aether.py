@@ -39,7 +39,7 @@ EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
            "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
-           "aeth_cfl_dt_noalloc",
+           "aeth_cfl_dt_noalloc", "aeth_get_entropy",
            "aeth_last_error", "aeth_destroy"]
 
 
@@ -55,7 +55,9 @@ class aeth_config(C.Structure):
                 ("integrator", C.c_int), ("cfl", C.c_double), ("precision", C.c_int),
                 ("path", C.c_int), ("strict_floors", C.c_int), ("n_dust", C.c_int),
                 ("t_stop", C.POINTER(C.c_double)), ("drag_precision", C.c_int),
-                ("mlp_tau", C.c_double), ("mlp_engine", C.c_int), ("cs_iso", C.c_double)]
+                ("mlp_tau", C.c_double), ("mlp_engine", C.c_int), ("cs_iso", C.c_double),
+                ("dual_energy", C.c_int), ("alpha_switch", C.c_double),
+                ("alpha_sync", C.c_double)]
 
 
 class aeth_block_desc(C.Structure):
@@ -180,6 +182,10 @@ def aeth_set_state(ctx, block, cons, b1=None, b2=None, b3=None):
 
 def aeth_get_state(ctx, block, cons, b1=None, b2=None, b3=None):
     _check(ctx, load_library().aeth_get_state(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2), _ptr(b3)))
+
+
+def aeth_get_entropy(ctx, block, S):
+    _check(ctx, load_library().aeth_get_entropy(ctx, block, _ptr(S)))
 
 
 def aeth_compute_dt(ctx) -> float:
@@ -324,14 +330,17 @@ def _check(ctx, rc):
 def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=FP64, mhd=True,
                 path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
                 riemann=HLLD, drag_precision=FP64, mlp_tau=0.0, mlp_engine=TCGEN05, iso=False,
-                cs=1.0):
-    """iso=True selects the isothermal closure p = cs^2 rho (gamma unused)."""
+                cs=1.0, dual=False, alpha_switch=0.0, alpha_sync=0.0):
+    """iso=True selects the isothermal closure p = cs^2 rho (gamma unused);
+    dual=True the dual-energy formalism (alpha_* <= 0: the defaults)."""
     cfg = aeth_config()
     if iso:
         cfg.eos = EOS_ISO_MHD if mhd else EOS_ISO_HYDRO
     else:
         cfg.eos = EOS_MHD if mhd else EOS_HYDRO
     cfg.cs_iso = cs
+    cfg.dual_energy = 1 if dual else 0
+    cfg.alpha_switch, cfg.alpha_sync = alpha_switch, alpha_sync
     cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
     cfg.recon, cfg.riemann, cfg.integrator, cfg.cfl = recon, riemann, integrator, cfl
     cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors
@@ -411,6 +420,12 @@ class Solver:
         s = self.shapes(b)
         out = [np.empty(x) for x in s]
         aeth_get_state(self.ctx, b, *out)
+        return out
+
+    def get_entropy(self, b):
+        d = self.descs[b]
+        out = np.empty((d.nz, d.ny, d.nx))
+        aeth_get_entropy(self.ctx, b, out)
         return out
 
     def compute_dt(self):

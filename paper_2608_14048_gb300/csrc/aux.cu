@@ -38,6 +38,8 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
     P.dflux = (R*)(c->arena + B.off_dflux);
   }
   if (c->cfg.riemann == AETH_RIEMANN_MLP) P.fstate = (R*)(c->arena + B.off_fstate);
+  if (is_dual(c))
+    for (int r = 0; r < 2; ++r) P.ent[r] = (R*)(c->arena + B.off_ent[r]);
   // geometry tables: 12 separable factors x 3 axes
   const R* t = (const R*)(c->arena + B.off_geo);
   const int g = B.L.g;
@@ -269,10 +271,16 @@ template void launch_fill<double>(const BlockPtrs<double>&, double* const*, int,
 // host FP64 <-> device working precision (interior only)
 // ------------------------------------------------------------------------
 
+// Dual energy (ent != null): the entropy S = p / rho^(gamma-1) of each
+// interior cell from the FP64 input (p from E with the floors of Eq. 5).
+struct DualInit {
+  double gamma, rho_floor, p_floor;
+};
+
 template <typename R>
 __global__ void k_load(Layout L, Arr8<R> a, int mhd, const double* __restrict__ sc,
                        const double* __restrict__ b1, const double* __restrict__ b2,
-                       const double* __restrict__ b3) {
+                       const double* __restrict__ b3, R* __restrict__ ent, DualInit di) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z * blockDim.z + threadIdx.z;
@@ -283,6 +291,22 @@ __global__ void k_load(Layout L, Arr8<R> a, int mhd, const double* __restrict__ 
   if (i < nx && j < ny && k < nz) {
     const long long c = ((long long)k * ny + j) * nx + i;
     for (int v = 0; v < 5; ++v) a.p[v][d] = (R)sc[v * nc + c];
+    if (ent) {
+      const double rho = fmax(sc[c], di.rho_floor);
+      const double m1 = sc[nc + c], m2 = sc[2 * nc + c], m3 = sc[3 * nc + c];
+      double km = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rho;
+      if (mhd) {
+        const double x = 0.5 * (b1[((long long)k * ny + j) * (nx + 1) + i] +
+                                b1[((long long)k * ny + j) * (nx + 1) + i + 1]);
+        const double y = 0.5 * (b2[((long long)k * (ny + 1) + j) * nx + i] +
+                                b2[((long long)k * (ny + 1) + j + 1) * nx + i]);
+        const double z = 0.5 * (b3[((long long)k * ny + j) * nx + i] +
+                                b3[((long long)(k + 1) * ny + j) * nx + i]);
+        km += 0.5 * (x * x + y * y + z * z);
+      }
+      const double pr = fmax((di.gamma - 1.0) * (sc[4 * nc + c] - km), di.p_floor);
+      ent[d] = (R)(pr / pow(rho, di.gamma - 1.0));
+    }
   }
   if (!mhd) return;
   if (j < ny && k < nz) a.p[5][d] = (R)b1[((long long)k * ny + j) * (nx + 1) + i];
@@ -322,7 +346,10 @@ static aeth_status load_store_T(aeth_ctx* c, int b, bool load, double* const* io
   const Layout& L = P.L;
   dim3 blk(32, 4, 2);
   dim3 grd((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 3) / 4, (L.n[2] + 1 + 1) / 2);
-  if (load) k_load<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), io[0], io[1], io[2], io[3]);
+  const DualInit di{c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor};
+  if (load)
+    k_load<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), io[0], io[1], io[2], io[3], P.ent[0],
+                                          di);
   else k_store<R><<<grd, blk, 0, c->stream>>>(L, a, is_mhd(c), io[0], io[1], io[2], io[3]);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
@@ -365,6 +392,31 @@ static aeth_status dust_io_T(aeth_ctx* c, int b, int k, bool load, double* io) {
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }
+// dual-energy entropy of register A (interior) -> S[nz][ny][nx]
+template <typename R>
+__global__ void k_entropy_store(Layout L, const R* __restrict__ ent, double* __restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  if (i >= nx || j >= ny || k >= nz) return;
+  s[((long long)k * ny + j) * nx + i] = (double)ent[L.idx(i, j, k)];
+}
+
+template <typename R>
+static aeth_status entropy_store_T(aeth_ctx* c, int b, double* io) {
+  BlockPtrs<R> P = block_ptrs<R>(c, b);
+  const Layout& L = P.L;
+  dim3 blk(32, 4, 2);
+  dim3 grd((L.n[0] + 31) / 32, (L.n[1] + 3) / 4, (L.n[2] + 1) / 2);
+  k_entropy_store<R><<<grd, blk, 0, c->stream>>>(L, P.ent[0], io);
+  AETH_CK(c, cudaGetLastError());
+  return AETH_OK;
+}
+aeth_status enqueue_entropy_store(aeth_ctx* c, int b, double* io) {
+  return c->elem == 8 ? entropy_store_T<double>(c, b, io) : entropy_store_T<float>(c, b, io);
+}
+
 aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k, double* io) {
   return c->elem == 8 ? dust_io_T<double>(c, b, k, true, io) : dust_io_T<float>(c, b, k, true, io);
 }
@@ -394,7 +446,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename R, bool P64, typename Src>
 __global__ void __launch_bounds__(256)
     k_dt(Src S, int total, int mhd, double gamma, double rho_floor, double p_floor, int nd,
-         double cs2, double* __restrict__ partial, int* status) {
+         double cs2, double alpha_switch, double* __restrict__ partial, int* status) {
+  // alpha_switch > 0: dual energy, the pressure of an untrusted internal
+  // energy comes from the entropy (Sec. 2.7)
+  const bool dual = alpha_switch > 0.0;
   // cs2 > 0: isothermal closure p = cs2 rho, fast speed with gamma = 1
   const bool iso = cs2 > 0.0;
   constexpr int TPI = 2;
@@ -404,7 +459,7 @@ __global__ void __launch_bounds__(256)
   const int tx = (int)threadIdx.x % CELL_BX, ty = ((int)threadIdx.x / CELL_BX) % CELL_BY;
   const int tz = (int)threadIdx.x / (CELL_BX * CELL_BY);
   for (int t0 = blockIdx.x * TPI; t0 < total; t0 += gridDim.x * TPI) {
-    R a[TPI][5], bf[TPI][6], wd[TPI][3];
+    R a[TPI][5], bf[TPI][6], wd[TPI][3], sv[TPI];
     int ci[TPI][3];
     bool on[TPI];
 #pragma unroll
@@ -425,6 +480,7 @@ __global__ void __launch_bounds__(256)
       const R* const* u = P.reg[0];
 #pragma unroll
       for (int v = 0; v < 5; ++v) a[q][v] = (v == 4 && iso) ? R(0) : u[v][c];   // no energy
+      sv[q] = dual ? P.ent[0][c] : R(0);
       if (mhd) {
         bf[q][0] = u[5][c]; bf[q][1] = u[5][c + 1];
         bf[q][2] = u[6][c]; bf[q][3] = u[6][c + L.sx];
@@ -448,6 +504,12 @@ __global__ void __launch_bounds__(256)
       R pr;
       if (iso) {
         pr = (R)cs2 * rho;
+      } else if (dual) {
+        const R ke = R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const R me = R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+        const R eint = a[q][4] - ke - me;
+        pr = eint < (R)alpha_switch * (ke + me) ? sv[q] * pow(rho, (R)(gamma - 1.0))
+                                                : (R)(gamma - 1.0) * eint;
       } else if (P64) {
         double ke = 0.5 * ((double)a[q][1] * a[q][1] + (double)a[q][2] * a[q][2] +
                            (double)a[q][3] * a[q][3]) / (double)rho;
@@ -518,17 +580,18 @@ static aeth_status dt_T(aeth_ctx* c) {
   // 2 tiles per CTA iteration; at most dt_grid partial minima
   const int grid = std::max(1, std::min(c->dt_grid, (total + 1) / 2));
   const double cs2 = is_iso(c) ? c->cfg.cs_iso * c->cfg.cs_iso : 0.0;
+  const double dual_a = is_dual(c) ? c->cfg.alpha_switch : 0.0;
   if (nb == 1) {
     const ParamSrc<R> src{block_ptrs<R>(c, 0), 0};
     k_dt<R, P64, ParamSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
-        cs2, c->d_partials, c->d_status);
+        cs2, dual_a, c->d_partials, c->d_status);
   } else {
     const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb,
                           c->d_tmap[PK_CELL]};
     k_dt<R, P64, TableSrc<R>><<<grid, 256, 0, c->stream>>>(
         src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
-        cs2, c->d_partials, c->d_status);
+        cs2, dual_a, c->d_partials, c->d_status);
   }
   c->n_launch += 2;
   const double scale = c->cfg.cfl * cmax_of(c->cfg.integrator);

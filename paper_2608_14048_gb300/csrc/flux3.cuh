@@ -67,14 +67,21 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // isothermal solvers the `gamma` argument carries the sound speed cs, the
 // primitive pressure is cs^2 rho and is not reconstructed (the isothermal
 // fluxes take the pressure from the reconstructed density).
-template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0>
+// DUAL: dual energy (Sec. 2.7): the pressure of an untrusted internal energy
+// (below alpha_switch x kinetic + magnetic) comes from the entropy, and each
+// face also gets the entropy flux, its mass flux times the reconstructed
+// specific entropy S/rho of the upwind side, in scratch slot 3 + D.
+template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0,
+          bool DUAL = false>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
-            unsigned long long* floor_hits) {
+            unsigned long long* floor_hits, R alpha_switch) {
   constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
   constexpr int QN = RL + RH + 1;
-  __shared__ R sw[NPRIM][WY][WX];
+  constexpr int NW = NPRIM + (DUAL ? 1 : 0);   // staged planes (+ S/rho)
+  constexpr int NQ = 7 + (DUAL ? 1 : 0);       // z-queue variables (+ S/rho)
+  __shared__ R sw[NW][WY][WX];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   constexpr bool ISO = iso_solver(SOLVER);
   const R gm1 = ISO ? gamma * gamma : gamma - R(1);   // cs^2 for ISO
@@ -87,6 +94,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
     const int ntx = ceil_div_d(L.n[0] + 2, TX), nty = ceil_div_d(L.n[1] + 2, TY);
     const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
     const R* __restrict__ ub = P.reg[src][0];   // state arrays at ub + v * pitch
+    const R* __restrict__ eb = P.ent[src];       // entropy (DUAL)
     R* __restrict__ sb = P.w[0];                 // scratch arrays at sb + slot * pitch
     const long long pitch = P.pitch;
     const int i0 = -1 + bx * TX, j0 = -1 + by * TY;
@@ -96,19 +104,30 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
     const int k1 = min(nz, k0 + kchunk - 1);
     const bool active = i <= nx && j <= ny;
 
+    // primitives of cell cc (+ specific entropy sp with DUAL); returns floor hits
+    auto prim_at = [&](long long cc, R* w, R& sp) -> int {
+      if constexpr (DUAL) {
+        return prim_cell_dual<R, MHD>(L, ub, pitch, eb, cc, gm1, rho_floor, p_floor, alpha_switch,
+                                      w, sp);
+      } else {
+        sp = R(0);
+        return prim_cell_s<R, P64, MHD, ISO>(L, ub, pitch, cc, gm1, rho_floor, p_floor, w);
+      }
+    };
     // z register queue of the own column: planes k-RL .. k+RH, 7 variables
-    // (the z-face normal field comes from the face array)
-    R q[7][QN];
+    // (+ S/rho; the z-face normal field comes from the face array)
+    R q[NQ][QN];
     auto load_q = [&](int slot, int kk) {
-      R w[8];
+      R w[8], sp = R(1);
       if (active && in_prim_range(L, i, j, kk)) {
-        prim_cell_s<R, P64, MHD, ISO>(L, ub, pitch, L.idx(i, j, kk), gm1, rho_floor, p_floor, w);
+        prim_at(L.idx(i, j, kk), w, sp);
       } else {
         w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
       }
       // z-face frame order: rho, vz, vx, vy, p, Bx, By
       q[0][slot] = w[0]; q[1][slot] = w[3]; q[2][slot] = w[1]; q[3][slot] = w[2];
       q[4][slot] = w[4]; q[5][slot] = w[5]; q[6][slot] = w[6];
+      if constexpr (DUAL) q[NQ - 1][slot] = sp;
     };
 #pragma unroll
     for (int s = 0; s < QN - 1; ++s) load_q(s + 1, k0 - RL + s);
@@ -119,19 +138,19 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
       for (int s = threadIdx.x; s < WX * WY; s += NT) {
         const int rx = s % WX, ry = s / WX;
         const int ci = i0 - RL + rx, cj = j0 - RL + ry;
-        R w[8];
+        R w[8], sp = R(1);
         if (in_prim_range(L, ci, cj, k)) {
-          hits += prim_cell_s<R, P64, MHD, ISO>(L, ub, pitch, L.idx(ci, cj, k), gm1, rho_floor,
-                                           p_floor, w);
+          hits += prim_at(L.idx(ci, cj, k), w, sp);
         } else {
           w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
         }
 #pragma unroll
         for (int v = 0; v < NPRIM; ++v) sw[v][ry][rx] = w[v];
+        if constexpr (DUAL) sw[NW - 1][ry][rx] = sp;
       }
       // advance the z queue: drop plane k-RL-1, add plane k+RH
 #pragma unroll
-      for (int v = 0; v < 7; ++v)
+      for (int v = 0; v < NQ; ++v)
 #pragma unroll
         for (int s = 0; s < QN - 1; ++s) q[v][s] = q[v][s + 1];
       load_q(QN - 1, k + RH);
@@ -153,6 +172,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
         if (SOLVER != 1) {
           solve_face<SOLVER>(gamma, wl, wr, bn, fx);
           store_face<0>(sb, pitch, fc, fx);
+          if constexpr (DUAL) {
+            R sl, sr;
+            recon_var<RECON>([&](int off) { return sw[NW - 1][sy][sx + off]; }, sl, sr);
+            sb[3 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
+          }
         } else {
           R* fs = P.fstate + (0 * 15) * pitch + fc;
 #pragma unroll
@@ -172,6 +196,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
         if (SOLVER != 1) {
           solve_face<SOLVER>(gamma, wl, wr, bn, fx);
           store_face<1>(sb, pitch, fc, fx);
+          if constexpr (DUAL) {
+            R sl, sr;
+            recon_var<RECON>([&](int off) { return sw[NW - 1][sy + off][sx]; }, sl, sr);
+            sb[4 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
+          }
         } else {
           R* fs = P.fstate + (1 * 15) * pitch + fc;
 #pragma unroll
@@ -190,6 +219,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
         if (SOLVER != 1) {
           solve_face<SOLVER>(gamma, wl, wr, bn, fx);
           store_face<2>(sb, pitch, fc, fx);
+          if constexpr (DUAL) {
+            R sl, sr;
+            recon_var<RECON>([&](int off) { return q[NQ - 1][off + RL]; }, sl, sr);
+            sb[5 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
+          }
         } else {
           R* fs = P.fstate + (2 * 15) * pitch + fc;
 #pragma unroll
@@ -247,30 +281,30 @@ static void with_src(aeth_ctx* c, int kind, int block, F launch) {
   }
 }
 
-template <typename R, bool P64, int RECON, bool MHD, int SOLVER>
+template <typename R, bool P64, int RECON, bool MHD, int SOLVER, bool DUAL>
 static void launch_flux3(aeth_ctx* c, int src, int block) {
   const int per_sm = sizeof(R) == 4 ? AETH_FLUX_MINB : 1;
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
-    k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER><<<grid, NT, 0, c->stream>>>(
+    k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL><<<grid, NT, 0, c->stream>>>(
         S, r.t0, r.t1, src, (R)(iso_solver(SOLVER) ? c->cfg.cs_iso : c->cfg.gamma),
-        (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk,
-        c->d_floor);
+        (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk, c->d_floor, (R)c->cfg.alpha_switch);
   });
   c->n_launch += 1;
 }
 
 // One flux pass with the solver family SOLVER and the reconstruction of the
-// context (explicitly instantiated per family in flux_*.cu).
-template <typename R, bool P64, bool MHD, int SOLVER>
+// context (explicitly instantiated per family in flux_*.cu; DUAL in
+// flux_dual_*.cu).
+template <typename R, bool P64, bool MHD, int SOLVER, bool DUAL = false>
 void flux_pass_solver(aeth_ctx* c, int recon, int src, int block);
 
-template <typename R, bool P64, bool MHD, int SOLVER>
+template <typename R, bool P64, bool MHD, int SOLVER, bool DUAL>
 void flux_pass_solver_impl(aeth_ctx* c, int recon, int src, int block) {
-  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD, SOLVER>(c, src, block);
-  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD, SOLVER>(c, src, block);
-  else if (recon == AETH_RECON_PPM5) launch_flux3<R, P64, 3, MHD, SOLVER>(c, src, block);
-  else launch_flux3<R, P64, 2, MHD, SOLVER>(c, src, block);
+  if (recon == AETH_RECON_DONOR) launch_flux3<R, P64, 0, MHD, SOLVER, DUAL>(c, src, block);
+  else if (recon == AETH_RECON_PLM) launch_flux3<R, P64, 1, MHD, SOLVER, DUAL>(c, src, block);
+  else if (recon == AETH_RECON_PPM5) launch_flux3<R, P64, 3, MHD, SOLVER, DUAL>(c, src, block);
+  else launch_flux3<R, P64, 2, MHD, SOLVER, DUAL>(c, src, block);
 }
 
 }  // namespace aeth

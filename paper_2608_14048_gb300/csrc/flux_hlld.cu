@@ -3,9 +3,9 @@
 
 namespace aeth {
 
-template <typename R, bool P64, bool MHD, int SOLVER>
+template <typename R, bool P64, bool MHD, int SOLVER, bool DUAL>
 void flux_pass_solver(aeth_ctx* c, int recon, int src, int block) {
-  flux_pass_solver_impl<R, P64, MHD, SOLVER>(c, recon, src, block);
+  flux_pass_solver_impl<R, P64, MHD, SOLVER, DUAL>(c, recon, src, block);
 }
 
 #define AETH_FLUX_INST(R, P64)                                               \

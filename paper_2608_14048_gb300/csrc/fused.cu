@@ -145,7 +145,7 @@ __device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, lo
   }
 }
 
-template <typename R, bool P64, bool MHD, bool SPH>
+template <typename R, bool P64, bool MHD, bool SPH, bool DUAL = false>
 __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P, int src, int out,
                                             R w0, R w1, R bdt, R gamma, R rho_floor, R p_floor) {
   const Layout& L = B.L;
@@ -202,6 +202,17 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
       u0[v] = B.reg[0][v][c];
       u1[v] = has_b ? B.reg[1][v][c] : R(0);
     }
+    // dual energy: the entropy and its face fluxes (scratch slots 3..5)
+    R sfm[3], sfp[3], s0 = R(0), s1 = R(0);
+    if constexpr (DUAL) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        sfp[d] = B.w[3 + d][cp[d]];
+        sfm[d] = B.w[3 + d][c];
+      }
+      s0 = B.ent[0][c];
+      s1 = has_b ? B.ent[1][c] : R(0);
+    }
     CtIn<R> ct = ct_gather<R, MHD, SPH>(B, P, c, has_b);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -212,6 +223,14 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
       R base = w0 * u0[v];
       if (has_b) base += w1 * u1[v];
       outp[v][c] = base + bdt * rhs;
+    }
+    if constexpr (DUAL) {
+      R div = R(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) div += Ap[d] * sfp[d] - Am[d] * sfm[d];
+      R base = w0 * s0;
+      if (has_b) base += w1 * s1;
+      B.ent[out][c] = base + bdt * (-div / V);
     }
     ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
     return;
@@ -224,7 +243,7 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
 
 // COORD: 0 every block Cartesian, 1 every block spherical, 2 mixed (the
 // coordinate system is then read per tile).
-template <typename R, bool P64, bool MHD, int COORD, typename Src>
+template <typename R, bool P64, bool MHD, int COORD, typename Src, bool DUAL = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
     k_update_f(Src S, int t0, int t1, int src, int out, R w0, R w1, R beta,
                const double* __restrict__ dt, R gamma, R rho_floor, R p_floor) {
@@ -236,9 +255,50 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
     const CellTile ct = cell_tile(B, loc, add);
     if (ct.P[0] > B.L.n[0] || ct.P[1] > B.L.n[1] || ct.P[2] > B.L.n[2]) continue;
     if (COORD == 1 || (COORD == 2 && B.L.coord == AETH_COORD_SPH))
-      update_cell<R, P64, MHD, true>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor);
+      update_cell<R, P64, MHD, true, DUAL>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor,
+                                           p_floor);
     else
-      update_cell<R, P64, MHD, false>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor);
+      update_cell<R, P64, MHD, false, DUAL>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor,
+                                            p_floor);
+  }
+}
+
+// ------------------------------------------------------------------------
+// dual-energy synchronisation of the interior cells of register `reg` at a
+// stage start, before its ghost fill (Sec. 2.7): where the internal energy
+// from E is below alpha_switch x (kinetic + magnetic), E is rewritten from
+// the entropy, e = S rho^(gamma-1) / (gamma-1); above alpha_sync x
+// (kinetic + magnetic), S is resynchronised from E; in between neither
+// changes.  Each cell reads its own state and bounding faces only.
+// ------------------------------------------------------------------------
+template <typename R, bool MHD, typename Src>
+__global__ void __launch_bounds__(256) k_dual_sync(Src S, int t0, int t1, int reg, R gm1,
+                                                   R rho_floor, R a_switch, R a_sync) {
+  const int add[3] = {1, 1, 1};
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    int loc;
+    const BlockPtrs<R>& B = S.get(t, loc);
+    const CellTile ct = cell_tile(B, loc, add);
+    const Layout& L = B.L;
+    if (ct.P[0] >= L.n[0] || ct.P[1] >= L.n[1] || ct.P[2] >= L.n[2]) continue;
+    const long long c = L.idx(ct.P[0], ct.P[1], ct.P[2]);
+    R* const* u = B.reg[reg];
+    R* ent = B.ent[reg];
+    R rho = u[0][c];
+    if (rho < rho_floor) rho = rho_floor;
+    const R ir = R(1) / rho;
+    const R v1 = u[1][c] * ir, v2 = u[2][c] * ir, v3 = u[3][c] * ir;
+    R km = R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3);
+    if (MHD) {
+      const R b1 = R(0.5) * (u[5][c] + u[5][c + 1]);
+      const R b2 = R(0.5) * (u[6][c] + u[6][c + L.sx]);
+      const R b3 = R(0.5) * (u[7][c] + u[7][c + L.sx * L.sy]);
+      km += R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3);
+    }
+    const R eint = u[4][c] - km;
+    const R rg = pow(rho, gm1);
+    if (eint < a_switch * km) u[4][c] = ent[c] * rg / gm1 + km;
+    else if (eint > a_sync * km) ent[c] = gm1 * eint / rg;
   }
 }
 
@@ -297,6 +357,12 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
 #pragma unroll
     for (int v = 0; v < NVAR; ++v)
       if (on[v]) B.reg[reg][v][dst] = val[v];
+    // dual energy: the entropy is a cell variable like the density
+    if (R* e = B.ent[reg]) {
+      int sc[3] = {c[0], c[1], c[2]};
+      sc[d] = L.bc[d] == AETH_BC_PERIODIC ? ((p % n) + n) % n : (p < 0 ? 0 : n - 1);
+      e[dst] = e[L.idx(sc[0], sc[1], sc[2])];
+    }
   }
 }
 
@@ -331,6 +397,15 @@ static void flux_pass(aeth_ctx* c, int recon, int src, int block) {
     return;
   }
   const bool hlle = c->cfg.riemann == AETH_RIEMANN_HLLE;
+  if (is_dual(c)) {
+    // dual energy: FP64 or FP32 states (the pressure of untrusted cells
+    // comes from the entropy, not from an FP64 energy difference)
+    if (hlle) flux_pass_solver<R, false, MHD, 2, true>(c, recon, src, block);
+    else if (c->cfg.riemann == AETH_RIEMANN_LHLLD)
+      flux_pass_solver<R, false, MHD, 5, true>(c, recon, src, block);
+    else flux_pass_solver<R, false, MHD, 0, true>(c, recon, src, block);
+    return;
+  }
   if (is_iso(c)) {
     // the isothermal pressure cs^2 rho needs no FP64 energy difference
     if (hlle) flux_pass_solver<R, false, MHD, 4>(c, recon, src, block);
@@ -358,6 +433,15 @@ static double flux_algo_bytes(const aeth_ctx* c, bool mhd) {
 
 template <typename R, bool P64, bool MHD>
 static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int out) {
+  const bool dual = !P64 && is_dual(c);   // dual energy runs FP64 or FP32 states
+  if (dual) {
+    with_src<R>(c, PK_CELL, -1, [&](auto S, TileRange r) {
+      k_dual_sync<R, MHD><<<r.t1 - r.t0, 256, 0, c->stream>>>(
+          S, r.t0, r.t1, src, (R)(c->cfg.gamma - 1.0), (R)c->cfg.rho_floor,
+          (R)c->cfg.alpha_switch, (R)c->cfg.alpha_sync);
+    });
+    c->n_launch += 1;
+  }
   launch_fill_all<R>(c, src, MHD ? NVAR : 5, -1);
   prof_begin(c);
   flux_pass<R, P64, MHD>(c, recon, src, -1);
@@ -369,15 +453,21 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
     if (MHD) k_emf_ref<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1);
     const R g = (R)c->cfg.gamma, rf = (R)c->cfg.rho_floor, pf = (R)c->cfg.p_floor;
     const int n = r.t1 - r.t0;
-    if (mode == 0)
-      k_update_f<R, P64, MHD, 0><<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta,
-                                                          c->d_dt, g, rf, pf);
-    else if (mode == 1)
-      k_update_f<R, P64, MHD, 1><<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta,
-                                                          c->d_dt, g, rf, pf);
-    else
-      k_update_f<R, P64, MHD, 2><<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta,
-                                                          c->d_dt, g, rf, pf);
+    using Src = decltype(S);
+    auto upd = [&](auto kernel) {
+      kernel<<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta, c->d_dt, g, rf, pf);
+    };
+    if constexpr (!P64) {
+      if (dual) {
+        if (mode == 0) upd(k_update_f<R, P64, MHD, 0, Src, true>);
+        else if (mode == 1) upd(k_update_f<R, P64, MHD, 1, Src, true>);
+        else upd(k_update_f<R, P64, MHD, 2, Src, true>);
+        return;
+      }
+    }
+    if (mode == 0) upd(k_update_f<R, P64, MHD, 0, Src>);
+    else if (mode == 1) upd(k_update_f<R, P64, MHD, 1, Src>);
+    else upd(k_update_f<R, P64, MHD, 2, Src>);
   });
   c->n_launch += MHD ? 2 : 1;
 }

@@ -82,6 +82,17 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
     delete c;
     return AETH_ERR_UNSUPPORTED;
   }
+  if (cfg->dual_energy != 0) {
+    // dual energy: adiabatic gas, fused path, FP64 or FP32, a classical solver
+    const bool ok = !iso && cfg->path == AETH_PATH_FUSED && cfg->precision != AETH_FP32_P64 &&
+                    cfg->riemann != AETH_RIEMANN_MLP && cfg->n_dust == 0;
+    if (!ok) {
+      delete c;
+      return AETH_ERR_UNSUPPORTED;
+    }
+    if (!(c->cfg.alpha_switch > 0.0)) c->cfg.alpha_switch = 1e-3;
+    if (!(c->cfg.alpha_sync > 0.0)) c->cfg.alpha_sync = 1e-1;
+  }
   if (iso && cfg->riemann == AETH_RIEMANN_LHLLD) {
     delete c;
     return AETH_ERR_UNSUPPORTED;   // isothermal solvers: HLLD and HLLE
@@ -189,6 +200,12 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
     if (c->cfg.riemann == AETH_RIEMANN_MLP) {
       B.off_fstate = off;
       off += 45 * arr;
+    }
+    if (is_dual(c)) {
+      for (int r = 0; r < 2; ++r) {
+        B.off_ent[r] = off;
+        off += arr;
+      }
     }
     B.geo_len = geometry_len(B.L);
     B.off_geo = off;
@@ -396,6 +413,20 @@ aeth_status aeth_get_state(aeth_ctx* c, int b, double* cons, double* b1, double*
       for (int q = 1; q < 4; ++q)
         AETH_CK(c, cudaMemcpyAsync(host[q], io[q], bytes[q], cudaMemcpyDeviceToHost, c->stream));
   }
+  AETH_CK(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+aeth_status aeth_get_entropy(aeth_ctx* c, int b, double* S) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (!S) return fail(c, AETH_ERR_ARG, "S is NULL");
+  if (!is_dual(c)) return fail(c, AETH_ERR_STATE, "dual energy is off");
+  const size_t bytes = c->blocks[b].ncell * sizeof(double);
+  double* mapped = (double*)mapped_host(S, bytes);
+  s = enqueue_entropy_store(c, b, mapped ? mapped : c->d_stage);
+  if (s != AETH_OK) return s;
+  if (!mapped) AETH_CK(c, cudaMemcpyAsync(S, c->d_stage, bytes, cudaMemcpyDeviceToHost, c->stream));
   AETH_CK(c, cudaStreamSynchronize(c->stream));
   return read_status(c);
 }

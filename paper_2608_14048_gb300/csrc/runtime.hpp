@@ -25,6 +25,8 @@ struct BlockPtrs {
   R* dust[2];          // dust registers: [species][4] arrays each (IMEX2P)
   R* dflux;            // dust fluxes: [direction][species][4] arrays
   R* fstate;           // learned flux: face states [direction][wl 7, wr 7, bn]
+  R* ent[2];           // dual energy: entropy S of registers A and B (else null);
+                       // its face fluxes use scratch slots 3..5 (fused path)
   long long pitch;     // elements between consecutive arrays of a register
                        // and of the scratch (w, f, e, edge in that order)
 };
@@ -39,6 +41,7 @@ struct BlockInfo {
   size_t off_dust[2];     // dust registers (n_dust * 4 arrays each)
   size_t off_dflux;       // dust face fluxes [3][n_dust][4] arrays
   size_t off_fstate;      // learned flux: face states [3][15] arrays
+  size_t off_ent[2];      // dual energy: entropy array of each register
   size_t geo_len;         // number of R entries in the geometry tables
   int dt_blocks;          // CUDA blocks of this block's dt/diag reductions
   int dt_offset;          // their first slot in the partials array
@@ -168,6 +171,7 @@ aeth_status enqueue_store(aeth_ctx* c, int b, double* const* io);
 aeth_status enqueue_set_dt(aeth_ctx* c, double dt);
 aeth_status enqueue_dust_load(aeth_ctx* c, int b, int k, double* io);
 aeth_status enqueue_dust_store(aeth_ctx* c, int b, int k, double* io);
+aeth_status enqueue_entropy_store(aeth_ctx* c, int b, double* io);
 aeth_status build_geometry(aeth_ctx* c);
 aeth_status build_tables(aeth_ctx* c);
 
@@ -252,6 +256,9 @@ inline bool is_mhd(const aeth_ctx* c) {
 inline bool is_iso(const aeth_ctx* c) {
   return c->cfg.eos == AETH_EOS_ISOTHERMAL_MHD || c->cfg.eos == AETH_EOS_ISOTHERMAL_HYDRO;
 }
+// dual-energy formalism (Sec. 2.7) on
+inline bool is_dual(const aeth_ctx* c) { return c->cfg.dual_energy != 0; }
+
 // internal solver codes of the unfused face kernel, distinct from every
 // AETH_RIEMANN_* value
 constexpr int SOLVER_ISO_HLLD = 16;

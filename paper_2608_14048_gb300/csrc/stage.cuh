@@ -51,6 +51,41 @@ __device__ __forceinline__ int prim_cell_s(const Layout& L, const R* __restrict_
   return prim_cell<R, P64, MHD, ISO>(L, u, c, gm1, rho_floor, p_floor, w);
 }
 
+// Dual energy (Sec. 2.7): the primitives of cell c with the pressure from
+// the entropy S = ent[c] where the internal energy from E is below
+// alpha_switch times the kinetic plus magnetic energy, else from E; the
+// floors of Eq. 5; sp = S / rho, the specific entropy the faces
+// reconstruct.
+template <typename R, bool MHD>
+__device__ __forceinline__ int prim_cell_dual(const Layout& L, const R* __restrict__ base,
+                                              long long pitch, const R* __restrict__ ent,
+                                              long long c, R gm1, R rho_floor, R p_floor,
+                                              R alpha_switch, R* w, R& sp) {
+  int hits = 0;
+  const R* u0 = base;
+  R rho = u0[c];
+  if (rho < rho_floor) { rho = rho_floor; ++hits; }
+  const R ir = R(1) / rho;
+  const R v1 = u0[pitch + c] * ir, v2 = u0[2 * pitch + c] * ir, v3 = u0[3 * pitch + c] * ir;
+  R b1 = 0, b2 = 0, b3 = 0;
+  if (MHD) {
+    b1 = R(0.5) * (u0[5 * pitch + c] + u0[5 * pitch + c + 1]);
+    b2 = R(0.5) * (u0[6 * pitch + c] + u0[6 * pitch + c + L.sx]);
+    b3 = R(0.5) * (u0[7 * pitch + c] + u0[7 * pitch + c + L.sx * L.sy]);
+  }
+  // the internal energy in the same arithmetic as prim_cell, so that a run
+  // whose cells all trust E reproduces the plain run bit for bit
+  const R ke = R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3);
+  const R me = R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3);
+  const R eint = u0[4 * pitch + c] - ke - me;
+  const R S = ent[c];
+  R pr = eint < alpha_switch * (ke + me) ? S * pow(rho, gm1) : gm1 * eint;
+  if (pr < p_floor) { pr = p_floor; ++hits; }
+  w[0] = rho; w[1] = v1; w[2] = v2; w[3] = v3; w[4] = pr; w[5] = b1; w[6] = b2; w[7] = b3;
+  sp = S * ir;
+  return hits;
+}
+
 __device__ __forceinline__ bool in_prim_range(const Layout& L, int i, int j, int k) {
   return i >= -L.g && i < L.n[0] + L.g && j >= -L.g && j < L.n[1] + L.g && k >= -L.g &&
          k < L.n[2] + L.g;
