@@ -53,6 +53,9 @@ def parse(argv=None):
     ap.add_argument("--hydro", action="store_true", help="wave512: the hydro column (B = 0)")
     ap.add_argument("--riemann", default="lhlld", choices=["lhlld", "hlld"],
                     help="tgv128: the gas solver (LHLLC / HLLC in hydro)")
+    ap.add_argument("--dual", action="store_true",
+                    help="turb256: dual-energy formalism (entropy-based pressure where the "
+                         "internal energy is untrusted), FP32 or FP64")
     ap.add_argument("--iso", action="store_true",
                     help="turb256: isothermal closure p = cs^2 rho with cs = 1 (the sound "
                          "speed of the generator) and the isothermal HLLD")
@@ -61,6 +64,8 @@ def parse(argv=None):
         a.prec = "fp64" if a.workload == "wave512" else "fp32"
     if a.iso and a.workload != "turb256":
         ap.error("--iso applies to the turb256 workload")
+    if a.dual and (a.workload != "turb256" or a.iso or a.prec == "fp32_p64"):
+        ap.error("--dual applies to the adiabatic turb256 workload in fp32 or fp64")
     return a
 
 
@@ -133,6 +138,14 @@ def workload_config(a):
                 "integrator": "VL2", "cfl": 0.3, "eos": "isothermal, c_s = 1", "mach_rms": 2.0,
                 "beta": 1.0, "precision": a.prec, "path": a.path, "seed": 20260816,
                 "l2": f"inputs larger than L2 (state {a.n}^3 x 8 vars x 2 registers)"}
+    if a.dual:
+        return {"workload": f"mhd_decaying_turbulence_{a.n}^3_dual_energy",
+                "grid": [a.n, a.n, a.n], "recon": a.recon.upper(), "riemann": "HLLD",
+                "ct": "upwind corner EMF (GS05)", "integrator": "VL2", "cfl": 0.3,
+                "gamma": 1.0001, "mach_rms": 2.0, "beta": 1.0,
+                "dual_energy": "entropy S advected; alpha_switch 1e-3, alpha_sync 1e-1",
+                "precision": a.prec, "path": a.path, "seed": 20260816,
+                "l2": f"inputs larger than L2 (state {a.n}^3 x 9 vars x 2 registers)"}
     return {"workload": f"mhd_decaying_turbulence_{a.n}^3", "grid": [a.n, a.n, a.n],
             "recon": a.recon.upper(), "riemann": "HLLD", "ct": "upwind corner EMF (GS05)",
             "integrator": "VL2", "cfl": 0.3, "gamma": 1.0001, "mach_rms": 2.0, "beta": 1.0,
@@ -305,10 +318,14 @@ def cpu_baseline(a, st_full):
         st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
         g = O.make_grid((n, n, n))
         p = O.make_params(gamma=st.gamma, recon={"plm": O.PLM, "ppm": O.PPM, "ppm5": O.PPM5}[a.recon],
-                          iso=a.iso, cs=1.0)
+                          iso=a.iso, cs=1.0, dual=a.dual)
         cells = n ** 3
         what = f"{n}^3 box of the same turbulence generator" + (", isothermal" if a.iso else "")
+        if a.dual:
+            what += ", dual energy"
     s = O.State(st.cons, st.b1, st.b2, st.b3)
+    if getattr(a, "dual", False):
+        s = O.dual_init(g, p, s)
     dt = O.compute_dt(g, p, s)
     t0 = time.perf_counter()
     O.step(g, p, dt, s)
@@ -331,6 +348,8 @@ def solver_label(a):
         return "HLLE"
     if a.workload == "tgv128":
         return "LHLLC" if a.riemann == "lhlld" else "HLLC"
+    if a.dual:
+        return "HLLD + entropy flux (dual energy)"
     return "isothermal HLLD" if a.iso else "HLLD"
 
 
@@ -344,9 +363,12 @@ def vs_paper(a, value):
 
 def bytes_per_cell_update(a):
     """HBM bytes per cell-update of the two-stage step at the state's
-    precision: 40 words for MHD, 25 for hydro, ~185 for 8 dust species."""
+    precision: 40 words for MHD, 25 for hydro, ~185 for 8 dust species, +4
+    with dual energy."""
     hydro = (a.workload == "wave512" and a.hydro) or a.workload == "tgv128"
     words = 185.0 if a.workload == "dust128" else (25.0 if hydro else 40.0)
+    if getattr(a, "dual", False):
+        words += 4.0   # the entropy read and written in each of the two stages
     return words * (8.0 if a.prec == "fp64" else 4.0)
 
 
@@ -453,7 +475,7 @@ def main():
     else:
         states = [make_input(a)]
         cfg = A.make_config(gamma=states[0].gamma, recon=rec, integrator=A.VL2, cfl=0.3,
-                            precision=prec, path=path, iso=a.iso, cs=1.0)
+                            precision=prec, path=path, iso=a.iso, cs=1.0, dual=a.dual)
     blocks = [A.make_block(s_.block.n, s_.block.lo, s_.block.hi, s_.block.coord, s_.block.bc)
               for s_ in states]
     stream = torch.cuda.current_stream(dev)
@@ -615,6 +637,7 @@ def main():
     hbm, peak_kind = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None
     kernel_key = (f"{a.path}_{a.prec}_{a.recon}" + ("_iso" if a.iso else "")
+                  + ("_dual" if a.dual else "")
                   if a.workload == "turb256" else None)
     traffic = ncu_traffic(kernel_key) if kernel_key else None
     launches_per_step = klaunch / max(a.steps, 1)

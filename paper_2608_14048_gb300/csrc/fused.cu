@@ -422,13 +422,14 @@ static void flux_pass(aeth_ctx* c, int recon, int src, int block) {
 // Algorithmic HBM bytes of one flux pass: every cell's stage state read
 // once and its outputs (15 fluxes + 6 face EMFs + 3 E_ref) written once.
 // The isothermal closure needs neither the energy entry nor the energy
-// fluxes (the pass still writes those as zeros for the update pass).
+// fluxes (the pass still writes those as zeros for the update pass); dual
+// energy adds the entropy read and its three face fluxes.
 static double flux_algo_bytes(const aeth_ctx* c, bool mhd) {
   double cells = 0;
   for (const auto& B : c->blocks)
     cells += (double)(B.L.n[0] + 2) * (B.L.n[1] + 2) * (B.L.n[2] + 2);
-  const int e = is_iso(c) ? 1 : 0;
-  return cells * ((mhd ? 8 : 5) - e + (mhd ? 24 : 15) - 3 * e) * (double)c->elem;
+  const int e = is_iso(c) ? 1 : 0, s = is_dual(c) ? 1 : 0;
+  return cells * ((mhd ? 8 : 5) - e + s + (mhd ? 24 : 15) - 3 * e + 3 * s) * (double)c->elem;
 }
 
 template <typename R, bool P64, bool MHD>
