@@ -172,6 +172,21 @@ aeth_status aeth_bind_arena(aeth_ctx* ctx, void* dev_ptr, size_t bytes);
 aeth_status aeth_add_block(aeth_ctx* ctx, const aeth_block_desc* desc,
                            int* block_id);
 
+/* Mesh-block decomposition (Sec. 2.3): block `hi` lies beyond the upper
+ * face of block `lo` along `axis` (0, 1, 2), so the two share that face.
+ * Each block's ghost cells (and ghost faces) on a linked side are copied
+ * from the neighbour's cells, in one fill pass over all blocks per axis,
+ * which also supplies the edge and corner ghosts; the shared face's normal
+ * field is updated by the block above and mirrored into face n of the block
+ * below.  A linked side ignores the block's bc on that side; a block
+ * linked to itself is periodic along that axis.  Both blocks Cartesian,
+ * with equal cell counts across the face and >= ghost-width cells along
+ * `axis`; fused path, gas only.  Call after aeth_add_block, before
+ * aeth_plan.  AETH_ERR_ARG for bad indices, an already linked side or
+ * mismatched blocks; AETH_ERR_UNSUPPORTED for spherical blocks, the unfused
+ * path or dust. */
+aeth_status aeth_link_blocks(aeth_ctx* ctx, int lo, int axis, int hi);
+
 /* Compute the device-memory layout; *bytes_needed receives the arena size. */
 aeth_status aeth_plan(aeth_ctx* ctx, size_t* bytes_needed);
 

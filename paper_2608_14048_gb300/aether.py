@@ -39,7 +39,7 @@ EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
            "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
-           "aeth_cfl_dt_noalloc", "aeth_get_entropy",
+           "aeth_cfl_dt_noalloc", "aeth_get_entropy", "aeth_link_blocks",
            "aeth_last_error", "aeth_destroy"]
 
 
@@ -182,6 +182,47 @@ def aeth_set_state(ctx, block, cons, b1=None, b2=None, b3=None):
 
 def aeth_get_state(ctx, block, cons, b1=None, b2=None, b3=None):
     _check(ctx, load_library().aeth_get_state(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2), _ptr(b3)))
+
+
+def aeth_link_blocks(ctx, lo, axis, hi):
+    _check(ctx, load_library().aeth_link_blocks(ctx, int(lo), int(axis), int(hi)))
+
+
+def decompose(n, splits, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(PERIODIC,) * 3):
+    """Split the box [lo, hi] of n = (nx, ny, nz) cells into blocks with
+    splits[d] = the cell counts along axis d (summing to n[d]).  Returns the
+    block descriptors (x fastest), their links (lo, axis, hi) -- periodic
+    axes wrap around -- and each block's first cell (i0, j0, k0)."""
+    assert all(sum(splits[d]) == n[d] for d in range(3))
+    dx = [(hi[d] - lo[d]) / n[d] for d in range(3)]
+    starts = [np.concatenate([[0], np.cumsum(splits[d])[:-1]]).astype(int) for d in range(3)]
+    nb = [len(splits[d]) for d in range(3)]
+    descs, origin = [], []
+    idx = lambda a, b, c: (c * nb[1] + b) * nb[0] + a
+    for c in range(nb[2]):
+        for b in range(nb[1]):
+            for a in range(nb[0]):
+                p = (a, b, c)
+                cnt = [splits[d][p[d]] for d in range(3)]
+                o = [int(starts[d][p[d]]) for d in range(3)]
+                l3 = [lo[d] + o[d] * dx[d] for d in range(3)]
+                h3 = [lo[d] + (o[d] + cnt[d]) * dx[d] for d in range(3)]
+                descs.append(make_block(tuple(cnt), tuple(l3), tuple(h3), CART, bc))
+                origin.append(tuple(o))
+    links = []
+    for c in range(nb[2]):
+        for b in range(nb[1]):
+            for a in range(nb[0]):
+                p = [a, b, c]
+                for d in range(3):
+                    q = list(p)
+                    q[d] += 1
+                    if q[d] == nb[d]:
+                        if bc[d] != PERIODIC:
+                            continue
+                        q[d] = 0
+                    links.append((idx(*p), d, idx(*q)))
+    return descs, links, origin
 
 
 def aeth_get_entropy(ctx, block, S):
@@ -372,7 +413,7 @@ class Solver:
     """One library context with its blocks.  `arena="torch"` allocates the
     device arena as a torch uint8 tensor; `stream` binds a torch stream."""
 
-    def __init__(self, cfg: aeth_config, blocks, arena: str = "torch", stream=None):
+    def __init__(self, cfg: aeth_config, blocks, arena: str = "torch", stream=None, links=()):
         self.ctx = aeth_create(cfg)
         self.cfg = cfg
         self.blocks = []
@@ -382,6 +423,8 @@ class Solver:
                 aeth_bind_stream(self.ctx, stream.cuda_stream)
             for b in blocks:
                 self.blocks.append(aeth_add_block(self.ctx, b))
+            for lo_b, axis, hi_b in links:
+                aeth_link_blocks(self.ctx, lo_b, axis, hi_b)
             self.descs = list(blocks)
             if arena == "torch":
                 import torch

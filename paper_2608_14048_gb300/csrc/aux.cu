@@ -15,6 +15,7 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
   const BlockInfo& B = c->blocks[b];
   BlockPtrs<R> P{};
   P.L = B.L;
+  P.tab = (const BlockPtrs<R>*)c->d_tab;
   const long long sz = B.L.size();
   // every array starts on a 256-byte boundary
   const long long pitch = (sz * (long long)sizeof(R) + 255) / 256 * 256 / (long long)sizeof(R);
@@ -330,9 +331,11 @@ __global__ void k_store(Layout L, Arr8<R> a, int mhd, double* __restrict__ sc,
   }
   if (!mhd) return;
   // periodic axes: the last face is the image of the first
-  const int i1 = (i == nx && L.bc[0] == AETH_BC_PERIODIC) ? 0 : i;
-  const int j2 = (j == ny && L.bc[1] == AETH_BC_PERIODIC) ? 0 : j;
-  const int k3 = (k == nz && L.bc[2] == AETH_BC_PERIODIC) ? 0 : k;
+  // (a linked high side keeps its face n current: the neighbour's update
+  // writes it)
+  const int i1 = (i == nx && L.bc[0] == AETH_BC_PERIODIC && L.lnk[0][1] < 0) ? 0 : i;
+  const int j2 = (j == ny && L.bc[1] == AETH_BC_PERIODIC && L.lnk[1][1] < 0) ? 0 : j;
+  const int k3 = (k == nz && L.bc[2] == AETH_BC_PERIODIC && L.lnk[2][1] < 0) ? 0 : k;
   if (j < ny && k < nz) b1[((long long)k * ny + j) * (nx + 1) + i] = (double)a.p[5][L.idx(i1, j, k)];
   if (i < nx && k < nz) b2[((long long)k * (ny + 1) + j) * nx + i] = (double)a.p[6][L.idx(i, j2, k)];
   if (i < nx && j < ny) b3[((long long)k * ny + j) * nx + i] = (double)a.p[7][L.idx(i, j, k3)];

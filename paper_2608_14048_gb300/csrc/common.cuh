@@ -22,6 +22,10 @@ struct Layout {
   int g;           // ghost width
   int bc[3];       // 0 periodic, 1 outflow
   int coord;       // 0 Cartesian, 1 spherical-polar
+  int self;        // this block's index in its context
+  int lnk[3][2];   // per axis, low / high side: the block whose cells lie
+                   // beyond that side (its ghost cells are copied from
+                   // there and the side's bc is not used), or -1
   long long sx, sy, sz;   // padded extents (sx multiple of 4)
   __host__ __device__ long long idx(int i, int j, int k) const {
     return ((long long)(k + g) * sy + (j + g)) * sx + (i + OX);

@@ -102,7 +102,10 @@ __device__ __forceinline__ CtIn<R> ct_gather(const BlockPtrs<R>& B, const int* P
     t.circ[d] = t.area[d] = t.b0[d] = t.b1[d] = R(0);
     if constexpr (MHD) {
       const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-      const int hid = L.bc[d] == AETH_BC_OUTFLOW ? L.n[d] : L.n[d] - 1;
+      // faces 0..n-1 are this block's; face n too on an outflow side that
+      // is not linked (a linked or periodic side's face n is the image of
+      // the next block's face 0)
+      const int hid = (L.bc[d] == AETH_BC_OUTFLOW && L.lnk[d][1] < 0) ? L.n[d] : L.n[d] - 1;
       if (P[d] > hid || P[e1] >= L.n[e1] || P[e2] >= L.n[e2]) continue;
       t.on[d] = true;
       int Q1[3] = {i, j, k}, Q2[3] = {i, j, k};
@@ -127,8 +130,9 @@ __device__ __forceinline__ CtIn<R> ct_gather(const BlockPtrs<R>& B, const int* P
 
 template <typename R, bool MHD>
 __device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, long long c,
-                                         R* const* outp, const CtIn<R>& t, R w0, R w1, R bdt,
+                                         int out, const CtIn<R>& t, R w0, R w1, R bdt,
                                          bool has_b) {
+  R* const* outp = B.reg[out];
   if constexpr (MHD) {
     const Layout& L = B.L;
 #pragma unroll
@@ -138,9 +142,19 @@ __device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, lo
       if (has_b) base += w1 * t.b1[d];
       const R nb = base - bdt * t.circ[d] / t.area[d];
       outp[5 + d][c] = nb;
-      // periodic axis: face n is the image of face 0
-      if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0)
-        outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
+      if (P[d] == 0) {
+        const int lk = L.lnk[d][0];
+        if (lk >= 0) {
+          // linked low side: face 0 is also face n of the block below
+          const BlockPtrs<R>& A = lk == L.self ? B : B.tab[lk];
+          int Q[3] = {P[0], P[1], P[2]};
+          Q[d] = A.L.n[d];
+          A.reg[out][5 + d][A.L.idx(Q[0], Q[1], Q[2])] = nb;
+        } else if (L.bc[d] == AETH_BC_PERIODIC) {
+          // periodic axis: face n is the image of face 0
+          outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
+        }
+      }
     }
   }
 }
@@ -232,13 +246,13 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
       if (has_b) base += w1 * s1;
       B.ent[out][c] = base + bdt * (-div / V);
     }
-    ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
+    ct_store<R, MHD>(B, P, c, out, ct, w0, w1, bdt, has_b);
     return;
   }
   // cells on the upper face layer (index n along some axis) update only the
   // face field
   CtIn<R> ct = ct_gather<R, MHD, SPH>(B, P, c, has_b);
-  ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
+  ct_store<R, MHD>(B, P, c, out, ct, w0, w1, bdt, has_b);
 }
 
 // COORD: 0 every block Cartesian, 1 every block spherical, 2 mixed (the
@@ -331,6 +345,10 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
     c[d] = tt < g ? tt - g : n + (tt - g);
     const int p = c[d];
     const long long dst = L.idx(c[0], c[1], c[2]);
+    // a linked side copies from the neighbouring block's cells (and faces)
+    // beyond it: cells n_nb + p on the low side, p - n on the high side
+    const int lk = L.lnk[d][p < 0 ? 0 : 1];
+    const BlockPtrs<R>& SB = (lk < 0 || lk == L.self) ? B : B.tab[lk];
     // every source is loaded before the first store (the stores go through
     // pointer arrays the compiler cannot prove disjoint from the loads)
     R val[NVAR];
@@ -341,7 +359,9 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
       if (v >= nv) continue;
       const bool face_d = (v == 5 + d);
       int s;
-      if (L.bc[d] == AETH_BC_PERIODIC) {
+      if (lk >= 0) {
+        s = p < 0 ? SB.L.n[d] + p : p - n;
+      } else if (L.bc[d] == AETH_BC_PERIODIC) {
         s = ((p % n) + n) % n;
       } else if (face_d) {
         if (p >= 0 && p <= n) continue;
@@ -351,7 +371,7 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
       }
       int sc[3] = {c[0], c[1], c[2]};
       sc[d] = s;
-      val[v] = B.reg[reg][v][L.idx(sc[0], sc[1], sc[2])];
+      val[v] = SB.reg[reg][v][SB.L.idx(sc[0], sc[1], sc[2])];
       on[v] = true;
     }
 #pragma unroll
@@ -360,8 +380,9 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
     // dual energy: the entropy is a cell variable like the density
     if (R* e = B.ent[reg]) {
       int sc[3] = {c[0], c[1], c[2]};
-      sc[d] = L.bc[d] == AETH_BC_PERIODIC ? ((p % n) + n) % n : (p < 0 ? 0 : n - 1);
-      e[dst] = e[L.idx(sc[0], sc[1], sc[2])];
+      if (lk >= 0) sc[d] = p < 0 ? SB.L.n[d] + p : p - n;
+      else sc[d] = L.bc[d] == AETH_BC_PERIODIC ? ((p % n) + n) % n : (p < 0 ? 0 : n - 1);
+      e[dst] = SB.ent[reg][SB.L.idx(sc[0], sc[1], sc[2])];
     }
   }
 }

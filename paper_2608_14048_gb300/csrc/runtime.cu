@@ -163,12 +163,38 @@ aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
   L.g = g;
   for (int q = 0; q < 3; ++q) L.bc[q] = d->bc[q];
   L.coord = d->coord;
+  L.self = (int)c->blocks.size();
+  for (int q = 0; q < 3; ++q) L.lnk[q][0] = L.lnk[q][1] = -1;
   L.sx = ((long long)OX + d->nx + g + 1 + 3) / 4 * 4;
   L.sy = d->ny + 2 * g + 1;
   L.sz = d->nz + 2 * g + 1;
   B.ncell = (long long)d->nx * d->ny * d->nz;
   c->blocks.push_back(B);
   if (id) *id = (int)c->blocks.size() - 1;
+  return AETH_OK;
+}
+
+aeth_status aeth_link_blocks(aeth_ctx* c, int lo, int axis, int hi) {
+  if (!c) return AETH_ERR_ARG;
+  if (c->finalized || c->planned) return fail(c, AETH_ERR_STATE, "links must be set before plan/finalize");
+  const int nb = (int)c->blocks.size();
+  if (lo < 0 || lo >= nb || hi < 0 || hi >= nb || axis < 0 || axis > 2)
+    return fail(c, AETH_ERR_ARG, "bad block index or axis");
+  Layout& A = c->blocks[lo].L;
+  Layout& B = c->blocks[hi].L;
+  if (A.lnk[axis][1] >= 0 || B.lnk[axis][0] >= 0)
+    return fail(c, AETH_ERR_ARG, "side already linked");
+  if (A.coord != AETH_COORD_CART || B.coord != AETH_COORD_CART)
+    return fail(c, AETH_ERR_UNSUPPORTED, "linked blocks must be Cartesian");
+  for (int e = 0; e < 3; ++e)
+    if (e != axis && A.n[e] != B.n[e])
+      return fail(c, AETH_ERR_ARG, "linked blocks differ across the shared face (axis %d)", e);
+  if (A.n[axis] < c->g || B.n[axis] < c->g)
+    return fail(c, AETH_ERR_ARG, "linked blocks need >= %d cells along the link axis", c->g);
+  if (c->cfg.path != AETH_PATH_FUSED || c->cfg.n_dust > 0)
+    return fail(c, AETH_ERR_UNSUPPORTED, "linked blocks run on the fused gas path");
+  A.lnk[axis][1] = hi;
+  B.lnk[axis][0] = lo;
   return AETH_OK;
 }
 

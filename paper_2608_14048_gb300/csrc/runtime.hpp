@@ -25,6 +25,8 @@ struct BlockPtrs {
   R* dust[2];          // dust registers: [species][4] arrays each (IMEX2P)
   R* dflux;            // dust fluxes: [direction][species][4] arrays
   R* fstate;           // learned flux: face states [direction][wl 7, wr 7, bn]
+  const BlockPtrs* tab; // device table of every block of the context (linked
+                        // blocks reach their neighbours through it)
   R* ent[2];           // dual energy: entropy S of registers A and B (else null);
                        // its face fluxes use scratch slots 3..5 (fused path)
   long long pitch;     // elements between consecutive arrays of a register
