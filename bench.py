@@ -53,6 +53,9 @@ def parse(argv=None):
     ap.add_argument("--hydro", action="store_true", help="wave512: the hydro column (B = 0)")
     ap.add_argument("--riemann", default="lhlld", choices=["lhlld", "hlld"],
                     help="tgv128: the gas solver (LHLLC / HLLC in hydro)")
+    ap.add_argument("--block-size", type=int, default=0,
+                    help="turb256/wave512/tgv128: run the domain as linked blocks of this many "
+                         "cells per axis (the paper's mesh-block decomposition), 0: one block")
     ap.add_argument("--dual", action="store_true",
                     help="turb256: dual-energy formalism (entropy-based pressure where the "
                          "internal energy is untrusted), FP32 or FP64")
@@ -64,6 +67,8 @@ def parse(argv=None):
         a.prec = "fp64" if a.workload == "wave512" else "fp32"
     if a.iso and a.workload != "turb256":
         ap.error("--iso applies to the turb256 workload")
+    if a.block_size and a.workload not in ("turb256", "wave512", "tgv128"):
+        ap.error("--block-size applies to turb256, wave512 and tgv128")
     if a.dual and (a.workload != "turb256" or a.iso or a.prec == "fp32_p64"):
         ap.error("--dual applies to the adiabatic turb256 workload in fp32 or fp64")
     return a
@@ -84,6 +89,17 @@ PAPER_WAVE512 = {"mhd": 300e6, "hydro": 709e6}
 
 
 def workload_config(a):
+    cfg = _workload_config(a)
+    if a.block_size:
+        n = cfg["grid"]
+        nb = [g // a.block_size for g in n]
+        cfg["workload"] += f"_blocks{a.block_size}"
+        cfg["blocks"] = (f"{nb[0] * nb[1] * nb[2]} linked blocks of {a.block_size}^3 "
+                         f"({nb[0]}x{nb[1]}x{nb[2]}), ghost cells exchanged through the fill")
+    return cfg
+
+
+def _workload_config(a):
     if a.workload == "batched512":
         return {"workload": "batched_512_uneven_mhd_boxes", "blocks": 512,
                 "sides": [16, 24, 32, 48, 64], "spherical_every": 3, "recon": a.recon.upper(),
@@ -288,6 +304,31 @@ def train_learned_flux(A, I, torch, dev, n=128, steps=4000, batch=8192, lr=2e-3)
             "seconds": time.perf_counter() - t0}
 
 
+def split_into_blocks(A, st, bs):
+    """The whole-domain state as linked blocks of bs cells per axis: the
+    per-block states (cell and face arrays cut out of the domain's), their
+    descriptors and the links."""
+    import numpy as np
+
+    from paper_2608_14048_gb300 import inputs as I
+    n = st.block.n
+    if any(x % bs for x in n):
+        raise SystemExit(f"--block-size {bs} does not divide the grid {n}")
+    splits = tuple([bs] * (x // bs) for x in n)
+    descs, links, origin = A.decompose(n, splits, st.block.lo, st.block.hi, st.block.bc)
+    parts = []
+    for (i0, j0, k0), d in zip(origin, descs):
+        bx, by, bz = d.nx, d.ny, d.nz
+        blk = I.Block((bx, by, bz), (d.x1min, d.x2min, d.x3min), (d.x1max, d.x2max, d.x3max),
+                      st.block.coord, st.block.bc)
+        cut = lambda arr, ex: np.ascontiguousarray(
+            arr[..., k0:k0 + bz + ex[2], j0:j0 + by + ex[1], i0:i0 + bx + ex[0]])
+        parts.append(I.InitialState(blk, cut(st.cons, (0, 0, 0)), cut(st.b1, (1, 0, 0)),
+                                    cut(st.b2, (0, 1, 0)), cut(st.b3, (0, 0, 1)), st.gamma,
+                                    st.meta))
+    return parts, descs, links
+
+
 def make_input(a):
     from paper_2608_14048_gb300 import inputs as I
     return I.turbulence_box(n=a.n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
@@ -476,10 +517,14 @@ def main():
         states = [make_input(a)]
         cfg = A.make_config(gamma=states[0].gamma, recon=rec, integrator=A.VL2, cfl=0.3,
                             precision=prec, path=path, iso=a.iso, cs=1.0, dual=a.dual)
-    blocks = [A.make_block(s_.block.n, s_.block.lo, s_.block.hi, s_.block.coord, s_.block.bc)
-              for s_ in states]
+    links = ()
+    if a.block_size:
+        states, blocks, links = split_into_blocks(A, states[0], a.block_size)
+    else:
+        blocks = [A.make_block(s_.block.n, s_.block.lo, s_.block.hi, s_.block.coord, s_.block.bc)
+                  for s_ in states]
     stream = torch.cuda.current_stream(dev)
-    sv = A.Solver(cfg, blocks, stream=stream)
+    sv = A.Solver(cfg, blocks, stream=stream, links=links)
     mhd_run = a.workload not in ("dust128", "tgv128") and not (a.workload == "wave512" and a.hydro)
     if a.workload == "learned512":
         A.aeth_load_mlp(sv.ctx, learned["params"])
