@@ -18,7 +18,7 @@ BlockPtrs<R> block_ptrs(const aeth_ctx* c, int b) {
   P.tab = (const BlockPtrs<R>*)c->d_tab;
   const long long sz = B.L.size();
   // every array starts on a 256-byte boundary
-  const long long pitch = (sz * (long long)sizeof(R) + 255) / 256 * 256 / (long long)sizeof(R);
+  const long long pitch = (long long)(array_pitch_bytes(sz, (int)sizeof(R)) / sizeof(R));
   P.pitch = pitch;
   for (int r = 0; r < 2; ++r) {
     R* base = (R*)(c->arena + B.off_reg[r]);

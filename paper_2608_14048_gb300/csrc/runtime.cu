@@ -206,7 +206,7 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
   int npart = 0;
   for (auto& B : c->blocks) {
     const long long sz = B.L.size();
-    const size_t arr = align256((size_t)sz * c->elem);
+    const size_t arr = array_pitch_bytes(sz, c->elem);
     for (int r = 0; r < 2; ++r) {
       B.off_reg[r] = off;
       off += NVAR * arr;

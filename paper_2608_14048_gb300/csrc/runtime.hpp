@@ -258,6 +258,14 @@ inline bool is_mhd(const aeth_ctx* c) {
 inline bool is_iso(const aeth_ctx* c) {
   return c->cfg.eos == AETH_EOS_ISOTHERMAL_MHD || c->cfg.eos == AETH_EOS_ISOTHERMAL_HYDRO;
 }
+// Bytes between consecutive arrays of a block (registers and scratch): the
+// array rounded up to 256 bytes.  (Offsetting the array starts against
+// each other by extra multiples of 256 bytes was measured to change nothing:
+// the DRAM address hash already spreads the ~40 streams of a pass.)
+inline size_t array_pitch_bytes(long long cells, int elem) {
+  return ((size_t)cells * elem + 255) / 256 * 256;
+}
+
 // dual-energy formalism (Sec. 2.7) on
 inline bool is_dual(const aeth_ctx* c) { return c->cfg.dual_energy != 0; }
 
