@@ -1,0 +1,69 @@
+"""Host-side logic without a GPU: the mesh-block decomposition helper, the
+bench's block splitting and its option checks."""
+import numpy as np
+import pytest
+
+import bench
+from paper_2608_14048_gb300 import aether as A
+from paper_2608_14048_gb300 import inputs as I
+
+
+def test_decompose_counts_links_and_extents():
+    n = (24, 20, 14)
+    splits = ([9, 15], [8, 5, 7], [6, 8])
+    descs, links, origin = A.decompose(n, splits, (0.0, -1.0, 0.0), (2.4, 1.0, 1.4),
+                                       (A.PERIODIC, A.OUTFLOW, A.PERIODIC))
+    assert len(descs) == 12
+    # periodic x and z wrap (2 links per row / column), outflow y does not
+    assert len(links) == 12 + 8 + 12
+    assert len(set((lo, ax) for lo, ax, _ in links)) == len(links)   # each high side once
+    assert len(set((hi, ax) for _, ax, hi in links)) == len(links)   # each low side once
+    for q, (d, o) in enumerate(zip(descs, origin)):
+        # extents follow the cell offsets with the domain's uniform spacing
+        assert d.x1min == pytest.approx(0.1 * o[0])
+        assert d.x1max == pytest.approx(0.1 * (o[0] + d.nx))
+        assert d.x2min == pytest.approx(-1.0 + 0.1 * o[1])
+        assert d.x3max == pytest.approx(0.1 * (o[2] + d.nz))
+    for lo, ax, hi in links:
+        a, b = origin[lo], origin[hi]
+        na = (descs[lo].nx, descs[lo].ny, descs[lo].nz)
+        assert b[ax] == (a[ax] + na[ax]) % n[ax]
+        for e in range(3):
+            if e != ax:
+                assert a[e] == b[e]
+
+
+def test_decompose_single_block_links_itself_on_periodic_axes():
+    descs, links, origin = A.decompose((8, 8, 8), ([8], [8], [8]),
+                                       bc=(A.PERIODIC, A.OUTFLOW, A.PERIODIC))
+    assert links == [(0, 0, 0), (0, 2, 0)]
+    assert origin == [(0, 0, 0)]
+
+
+def test_bench_split_into_blocks_reassembles_the_state():
+    st = I.smooth_random_mhd(I.Block((16, 8, 8)), 3, v_rms=0.5, b_rms=0.5)
+    parts, descs, links = bench.split_into_blocks(A, st, 8)
+    assert len(parts) == 2 and len(links) == 6
+    whole = np.concatenate([parts[0].cons, parts[1].cons], axis=3)
+    np.testing.assert_array_equal(whole, st.cons)
+    # the shared x face appears in both blocks with the same values
+    np.testing.assert_array_equal(parts[0].b1[..., -1], parts[1].b1[..., 0])
+    with pytest.raises(SystemExit):
+        bench.split_into_blocks(A, st, 6)
+
+
+@pytest.mark.parametrize("argv", [["--dual", "--prec", "fp32_p64"], ["--iso", "--workload", "wave512"],
+                                  ["--block-size", "64", "--workload", "dust128"],
+                                  ["--dual", "--iso"]])
+def test_bench_rejects_option_combinations(argv):
+    with pytest.raises(SystemExit):
+        bench.parse(argv)
+
+
+def test_bench_workload_names():
+    assert bench.workload_config(bench.parse(["--dual"]))["workload"].endswith("_dual_energy")
+    a = bench.parse(["--workload", "wave512", "--block-size", "128"])
+    cfg = bench.workload_config(a)
+    assert cfg["workload"] == "linear_wave_512x512x256_mhd_blocks128"
+    assert cfg["blocks"].startswith("32 linked blocks")
+    assert bench.parse(["--workload", "wave512"]).prec == "fp64"
