@@ -446,13 +446,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // on every block size, one block lookup per 256 cells); a CTA iteration
 // takes TPI tiles and loads all of them before using any, so each thread
 // keeps TPI independent load groups in flight.
-template <typename R, bool P64, typename Src>
+// DUAL: dual energy, the pressure of an untrusted internal energy comes
+// from the entropy (Sec. 2.7)
+template <typename R, bool P64, typename Src, bool DUAL = false>
 __global__ void __launch_bounds__(256)
     k_dt(Src S, int total, int mhd, double gamma, double rho_floor, double p_floor, int nd,
          double cs2, double alpha_switch, double* __restrict__ partial, int* status) {
-  // alpha_switch > 0: dual energy, the pressure of an untrusted internal
-  // energy comes from the entropy (Sec. 2.7)
-  const bool dual = alpha_switch > 0.0;
+  constexpr bool dual = DUAL;
   // cs2 > 0: isothermal closure p = cs2 rho, fast speed with gamma = 1
   const bool iso = cs2 > 0.0;
   constexpr int TPI = 2;
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(256)
       const R* const* u = P.reg[0];
 #pragma unroll
       for (int v = 0; v < 5; ++v) a[q][v] = (v == 4 && iso) ? R(0) : u[v][c];   // no energy
-      sv[q] = dual ? P.ent[0][c] : R(0);
+      if constexpr (DUAL) sv[q] = P.ent[0][c];
       if (mhd) {
         bf[q][0] = u[5][c]; bf[q][1] = u[5][c + 1];
         bf[q][2] = u[6][c]; bf[q][3] = u[6][c + L.sx];
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(256)
       R pr;
       if (iso) {
         pr = (R)cs2 * rho;
-      } else if (dual) {
+      } else if constexpr (DUAL) {
         const R ke = R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         const R me = R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
         const R eint = a[q][4] - ke - me;
@@ -584,17 +584,18 @@ static aeth_status dt_T(aeth_ctx* c) {
   const int grid = std::max(1, std::min(c->dt_grid, (total + 1) / 2));
   const double cs2 = is_iso(c) ? c->cfg.cs_iso * c->cfg.cs_iso : 0.0;
   const double dual_a = is_dual(c) ? c->cfg.alpha_switch : 0.0;
+  auto launch = [&](auto src) {
+    using Src = decltype(src);
+    auto kernel = dual_a > 0.0 ? k_dt<R, P64, Src, true> : k_dt<R, P64, Src, false>;
+    kernel<<<grid, 256, 0, c->stream>>>(src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor,
+                                         c->cfg.p_floor, c->cfg.n_dust, cs2, dual_a,
+                                         c->d_partials, c->d_status);
+  };
   if (nb == 1) {
-    const ParamSrc<R> src{block_ptrs<R>(c, 0), 0};
-    k_dt<R, P64, ParamSrc<R>><<<grid, 256, 0, c->stream>>>(
-        src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
-        cs2, dual_a, c->d_partials, c->d_status);
+    launch(ParamSrc<R>{block_ptrs<R>(c, 0), 0});
   } else {
-    const TableSrc<R> src{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb,
-                          c->d_tmap[PK_CELL]};
-    k_dt<R, P64, TableSrc<R>><<<grid, 256, 0, c->stream>>>(
-        src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor, c->cfg.p_floor, c->cfg.n_dust,
-        cs2, dual_a, c->d_partials, c->d_status);
+    launch(TableSrc<R>{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb,
+                       c->d_tmap[PK_CELL]});
   }
   c->n_launch += 2;
   const double scale = c->cfg.cfl * cmax_of(c->cfg.integrator);

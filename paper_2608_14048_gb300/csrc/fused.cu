@@ -102,10 +102,10 @@ __device__ __forceinline__ CtIn<R> ct_gather(const BlockPtrs<R>& B, const int* P
     t.circ[d] = t.area[d] = t.b0[d] = t.b1[d] = R(0);
     if constexpr (MHD) {
       const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-      // faces 0..n-1 are this block's; face n too on an outflow side that
-      // is not linked (a linked or periodic side's face n is the image of
-      // the next block's face 0)
-      const int hid = (L.bc[d] == AETH_BC_OUTFLOW && L.lnk[d][1] < 0) ? L.n[d] : L.n[d] - 1;
+      // faces 0..n-1, and face n on an outflow axis (across a block link
+      // face n is also updated by the block above, from the same inputs,
+      // and the mirror pass then copies that value)
+      const int hid = L.bc[d] == AETH_BC_OUTFLOW ? L.n[d] : L.n[d] - 1;
       if (P[d] > hid || P[e1] >= L.n[e1] || P[e2] >= L.n[e2]) continue;
       t.on[d] = true;
       int Q1[3] = {i, j, k}, Q2[3] = {i, j, k};
@@ -130,9 +130,8 @@ __device__ __forceinline__ CtIn<R> ct_gather(const BlockPtrs<R>& B, const int* P
 
 template <typename R, bool MHD>
 __device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, long long c,
-                                         int out, const CtIn<R>& t, R w0, R w1, R bdt,
+                                         R* const* outp, const CtIn<R>& t, R w0, R w1, R bdt,
                                          bool has_b) {
-  R* const* outp = B.reg[out];
   if constexpr (MHD) {
     const Layout& L = B.L;
 #pragma unroll
@@ -142,19 +141,10 @@ __device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, lo
       if (has_b) base += w1 * t.b1[d];
       const R nb = base - bdt * t.circ[d] / t.area[d];
       outp[5 + d][c] = nb;
-      if (P[d] == 0) {
-        const int lk = L.lnk[d][0];
-        if (lk >= 0) {
-          // linked low side: face 0 is also face n of the block below
-          const BlockPtrs<R>& A = lk == L.self ? B : B.tab[lk];
-          int Q[3] = {P[0], P[1], P[2]};
-          Q[d] = A.L.n[d];
-          A.reg[out][5 + d][A.L.idx(Q[0], Q[1], Q[2])] = nb;
-        } else if (L.bc[d] == AETH_BC_PERIODIC) {
-          // periodic axis: face n is the image of face 0
-          outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
-        }
-      }
+      // periodic axis: face n is the image of face 0 (across a block link
+      // the mirror pass after the update writes face n from the block above)
+      if (L.bc[d] == AETH_BC_PERIODIC && P[d] == 0)
+        outp[5 + d][c + (long long)L.n[d] * L.stride(d)] = nb;
     }
   }
 }
@@ -246,13 +236,13 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
       if (has_b) base += w1 * s1;
       B.ent[out][c] = base + bdt * (-div / V);
     }
-    ct_store<R, MHD>(B, P, c, out, ct, w0, w1, bdt, has_b);
+    ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
     return;
   }
   // cells on the upper face layer (index n along some axis) update only the
   // face field
   CtIn<R> ct = ct_gather<R, MHD, SPH>(B, P, c, has_b);
-  ct_store<R, MHD>(B, P, c, out, ct, w0, w1, bdt, has_b);
+  ct_store<R, MHD>(B, P, c, outp, ct, w0, w1, bdt, has_b);
 }
 
 // COORD: 0 every block Cartesian, 1 every block spherical, 2 mixed (the
@@ -274,6 +264,32 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
     else
       update_cell<R, P64, MHD, false, DUAL>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor,
                                             p_floor);
+  }
+}
+
+// ------------------------------------------------------------------------
+// Block links (Sec. 2.3): after an update, face n along the link axis of the
+// block below takes the value of face 0 of the block above (both are the
+// shared face; the block above's CT owns it).  blockIdx.y = link, threads
+// over the face plane.
+// ------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_mirror_faces(const BlockPtrs<R>* __restrict__ tab,
+                                                      const int3* __restrict__ links, int reg) {
+  const int3 lk = links[blockIdx.y];   // (block below, axis, block above)
+  const BlockPtrs<R>& A = tab[lk.x];
+  const BlockPtrs<R>& B = tab[lk.z];
+  const int d = lk.y, e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+  const int n1 = A.L.n[e1], n2 = A.L.n[e2];
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < (long long)n1 * n2;
+       f += (long long)gridDim.x * blockDim.x) {
+    int Q[3];
+    Q[e1] = (int)(f % n1);
+    Q[e2] = (int)(f / n1);
+    Q[d] = 0;
+    const R v = B.reg[reg][5 + d][B.L.idx(Q[0], Q[1], Q[2])];
+    Q[d] = A.L.n[d];
+    A.reg[reg][5 + d][A.L.idx(Q[0], Q[1], Q[2])] = v;
   }
 }
 
@@ -491,6 +507,11 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
     else if (mode == 1) upd(k_update_f<R, P64, MHD, 1, Src>);
     else upd(k_update_f<R, P64, MHD, 2, Src>);
   });
+  if (MHD && !c->links.empty()) {
+    k_mirror_faces<R><<<dim3(64, (unsigned)c->links.size()), 256, 0, c->stream>>>(
+        dtab<R>(c), c->d_links, out);
+    c->n_launch += 1;
+  }
   c->n_launch += MHD ? 2 : 1;
 }
 

@@ -195,6 +195,7 @@ aeth_status aeth_link_blocks(aeth_ctx* c, int lo, int axis, int hi) {
     return fail(c, AETH_ERR_UNSUPPORTED, "linked blocks run on the fused gas path");
   A.lnk[axis][1] = hi;
   B.lnk[axis][0] = lo;
+  c->links.push_back(make_int3(lo, axis, hi));
   return AETH_OK;
 }
 
@@ -249,6 +250,8 @@ aeth_status aeth_plan(aeth_ctx* c, size_t* bytes) {
   const int nb = (int)c->blocks.size();
   c->off_tab = off;
   off += align256((size_t)nb * sizeof(BlockPtrs<double>));
+  c->off_links = off;
+  off += align256(std::max<size_t>(1, c->links.size()) * sizeof(int3));
   c->off_prefix = off;
   off += align256((size_t)PK_N * (nb + 1) * sizeof(int));
   for (int kind = 0; kind < PK_N; ++kind) {
@@ -307,6 +310,10 @@ aeth_status aeth_finalize(aeth_ctx* c, size_t* bytes) {
   AETH_CK(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
   c->d_tab = c->arena + c->off_tab;
   c->d_prefix = (int*)(c->arena + c->off_prefix);
+  c->d_links = (int3*)(c->arena + c->off_links);
+  if (!c->links.empty())
+    AETH_CK(c, cudaMemcpyAsync(c->d_links, c->links.data(), c->links.size() * sizeof(int3),
+                               cudaMemcpyHostToDevice, c->stream));
   for (int kind = 0; kind < PK_N; ++kind)
     c->d_tmap[kind] = c->tmap_n[kind] > 0 ? (int2*)(c->arena + c->off_tmap[kind]) : nullptr;
   s = build_tables(c);

@@ -127,6 +127,9 @@ struct aeth_ctx {
   int2* d_tmap[aeth::PK_N] = {};
   long long tmap_n[aeth::PK_N] = {};
   void* d_tab = nullptr;              // BlockPtrs<R>[nb]
+  std::vector<int3> links;            // block links (below, axis, above)
+  size_t off_links = 0;
+  int3* d_links = nullptr;            // the same on the device (face mirror pass)
   int* d_prefix = nullptr;            // [PK_N][nb + 1]
   std::vector<int> h_prefix;          // host copy
   int kchunk = 0;                     // z extent of a flux tile (0: choose;
