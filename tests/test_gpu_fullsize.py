@@ -310,3 +310,67 @@ def test_linear_wave_512_fp64_one_step_sampled_single_and_128_blocks():
             errs += [rel_l1(cen[q], ref[q]) for q in (1, 2, 3)]
             assert max(errs[v] for v in (0, 4, 5, 6, 7)) < 1e-12, (c0, errs)
             assert max(errs[1:4]) < 1e-9, (c0, errs)
+
+
+def test_taylor_green_128_lhllc_fp32_one_step_whole_grid():
+    """The low-Mach bench input (128^3, Mach 0.01, PLM + LHLLC + RK2) in
+    FP32, one step, against the oracle on the whole grid.  FP32 bound at
+    Mach 0.01: the stored energy (~9000) rounds to 5e-4 in p against O(1)
+    pressure forces, so one step's momentum carries ~1e-5 relative error:
+    1e-4 for the momenta, 1e-5 for rho and E."""
+    import torch
+    st = I.taylor_green(128, 0.01)
+    b = st.block
+    g = O.make_grid(b.n, b.lo, b.hi)
+    p = O.make_params(gamma=st.gamma, recon=O.PLM, integrator=O.RK2, mhd=False, riemann=O.LHLLD)
+    ref = O.State(st.cons)
+    dt = O.compute_dt(g, p, ref)
+    O.step(g, p, dt, ref)
+    cfg = A.make_config(gamma=st.gamma, recon=A.PLM, integrator=A.RK2, precision=A.FP32, mhd=False,
+                        riemann=A.LHLLD)
+    sv = A.Solver(cfg, [A.make_block(b.n, b.lo, b.hi)], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, st.cons)
+        sv.step(dt)
+        gc = sv.get_state(0)[0]
+    finally:
+        sv.close()
+    mnorm = sum(np.sum(np.abs(ref.cons[q])) for q in (1, 2, 3)) / 3
+    errs = [rel_l1(gc[0], ref.cons[0]), rel_l1(gc[4], ref.cons[4])]
+    errs += [float(np.sum(np.abs(gc[q] - ref.cons[q])) / mnorm) for q in (1, 2, 3)]
+    assert max(errs[:2]) < 1e-5 and max(errs[2:]) < 1e-4, errs
+
+
+def test_turbulence_256_dual_energy_fp32_one_step_sampled():
+    """The dual-energy bench (256^3 turbulence, FP32): one step, sampled
+    sub-boxes against the oracle with the entropy initialised the same way
+    (FP64, from E) on both sides; conserved variables, face fields and S."""
+    import torch
+    n = 256
+    st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
+    g = O.make_grid((n, n, n))
+    p = O.make_params(gamma=st.gamma, recon=O.PLM, dual=True)
+    full = O.dual_init(g, p, O.State(st.cons, st.b1, st.b2, st.b3))
+    dt = O.compute_dt(g, p, full)
+    cfg = A.make_config(gamma=st.gamma, recon=A.PLM, precision=A.FP32, dual=True)
+    sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        sv.step(dt)
+        gc, g1, g2, g3 = sv.get_state(0)
+        gs = sv.get_entropy(0)
+    finally:
+        sv.close()
+    m = 16
+    for c0 in [(0, 0, 0), (200, 31, 129)]:
+        lo = tuple(c0[d] - HALO for d in range(3))
+        size = (m + 2 * HALO,) * 3
+        sub = _cut_box(full.cons, full.b1, full.b2, full.b3, lo, size, n)
+        s = O.State(*sub)
+        O.step(O.make_grid(size, hi=tuple(x / n for x in size)), p, dt, s)
+        hh = slice(HALO, HALO + m)
+        cen = _cut_box(np.concatenate([gc, gs[None]]), g1, g2, g3, c0, (m,) * 3, n)
+        errs = [rel_l1(cen[0][v], s.cons[v, hh, hh, hh]) for v in range(6)]
+        bnorm = sum(np.mean(np.abs(x)) for x in (s.b1, s.b2, s.b3)) / 3
+        errs += [float(np.mean(np.abs(cen[1] - s.b1[hh, hh, HALO:HALO + m + 1]))) / bnorm]
+        assert max(errs) < 1e-5, (c0, errs)
