@@ -191,6 +191,22 @@ aeth_status aeth_link_blocks(aeth_ctx* c, int lo, int axis, int hi) {
       return fail(c, AETH_ERR_ARG, "linked blocks differ across the shared face (axis %d)", e);
   if (A.n[axis] < c->g || B.n[axis] < c->g)
     return fail(c, AETH_ERR_ARG, "linked blocks need >= %d cells along the link axis", c->g);
+  {
+    // one uniform grid: equal cell widths on every axis and coinciding
+    // extents across the shared face
+    const aeth_block_desc& a = c->blocks[lo].desc;
+    const aeth_block_desc& b = c->blocks[hi].desc;
+    const double alo[3] = {a.x1min, a.x2min, a.x3min}, ahi[3] = {a.x1max, a.x2max, a.x3max};
+    const double blo[3] = {b.x1min, b.x2min, b.x3min}, bhi[3] = {b.x1max, b.x2max, b.x3max};
+    for (int e = 0; e < 3; ++e) {
+      const double da = (ahi[e] - alo[e]) / A.n[e], db = (bhi[e] - blo[e]) / B.n[e];
+      const double tol = 1e-9 * std::max(std::fabs(da), std::fabs(db));
+      if (std::fabs(da - db) > tol)
+        return fail(c, AETH_ERR_ARG, "linked blocks differ in cell width along axis %d", e);
+      if (e != axis && (std::fabs(alo[e] - blo[e]) > tol || std::fabs(ahi[e] - bhi[e]) > tol))
+        return fail(c, AETH_ERR_ARG, "linked blocks are not aligned across the face (axis %d)", e);
+    }
+  }
   if (c->cfg.path != AETH_PATH_FUSED || c->cfg.n_dust > 0)
     return fail(c, AETH_ERR_UNSUPPORTED, "linked blocks run on the fused gas path");
   A.lnk[axis][1] = hi;

@@ -127,7 +127,7 @@ def test_single_block_linked_to_itself_is_periodic():
 def test_link_validation():
     import torch
     cfg = A.make_config()
-    d = [A.make_block((8, 8, 8)), A.make_block((8, 6, 8))]
+    d = [A.make_block((8, 8, 8)), A.make_block((8, 6, 8), hi=(1.0, 0.75, 1.0))]
     ctx = A.aeth_create(cfg)
     try:
         for b in d:
@@ -144,6 +144,18 @@ def test_link_validation():
         assert e.value.code == -1
     finally:
         A.aeth_destroy(ctx)
+    # a different cell width, and a transverse offset, are rejected
+    for other in (A.make_block((8, 8, 8), hi=(2.0, 1.0, 1.0)),
+                  A.make_block((8, 8, 8), lo=(0.0, 0.5, 0.0), hi=(1.0, 1.5, 1.0))):
+        ctx = A.aeth_create(cfg)
+        try:
+            A.aeth_add_block(ctx, d[0])
+            A.aeth_add_block(ctx, other)
+            with pytest.raises(A.AethError) as e:
+                A.aeth_link_blocks(ctx, 0, 0, 1)
+            assert e.value.code == -1
+        finally:
+            A.aeth_destroy(ctx)
     ctx = A.aeth_create(A.make_config(path=A.UNFUSED))
     try:
         A.aeth_add_block(ctx, d[0])
