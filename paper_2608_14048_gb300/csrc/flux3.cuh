@@ -61,12 +61,12 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // 1. flux pass.  Persistent: CTAs stride over the tiles of all blocks.
 //    AETH_FLUX_MINB CTAs per SM in FP32; FP64 takes the full register file.
 // ------------------------------------------------------------------------
-// SOLVER 0: HLLD; 2: HLLE; 1: write the face states (wl, wr, bn) for the learned
-// flux instead of solving; 3: isothermal HLLD; 4: isothermal HLLE; 5: the
-// low-dissipation HLLD (LHLLD).  For the
-// isothermal solvers the `gamma` argument carries the sound speed cs, the
-// primitive pressure is cs^2 rho and is not reconstructed (the isothermal
-// fluxes take the pressure from the reconstructed density).
+// SOLVER 0: HLLD; 2: HLLE; 1: write the face states (wl, wr, bn) for the
+// learned flux instead of solving; 3: isothermal HLLD; 4: isothermal HLLE;
+// 5: the low-dissipation HLLD (LHLLD).  For the isothermal solvers the
+// `gamma` argument carries the sound speed cs, the primitive pressure is
+// cs^2 rho and is not reconstructed (the isothermal fluxes take the
+// pressure from the reconstructed density).
 // DUAL: dual energy (Sec. 2.7): the pressure of an untrusted internal energy
 // (below alpha_switch x kinetic + magnetic) comes from the entropy, and each
 // face also gets the entropy flux, its mass flux times the reconstructed
