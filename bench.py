@@ -197,11 +197,16 @@ def nvtx_pop():
 
 
 def kernel_source_hash():
-    """Hash of the dominant (flux) kernel's sources: a committed traffic
-    figure is only reported while these are unchanged."""
+    """Hash of the dominant (flux) kernel's sources, comments and blank
+    lines left out: a committed traffic figure is only reported while the
+    code is unchanged."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2608_14048_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2608_14048_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        code = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in code if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
