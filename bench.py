@@ -210,17 +210,46 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key):
-    """Per-launch DRAM traffic of the dominant kernel from the committed ncu
-    summary, or None if absent or taken on a different kernel source."""
+def ncu_figure(kernel_key, field):
+    """A per-launch figure of the dominant kernel (DRAM bytes, warp
+    instructions) from the committed ncu summary, or None if absent or
+    taken on a different kernel source."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel_key is None:
         return None
     d = json.load(open(p))
     e = d.get(kernel_key)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("bytes_per_launch")
+    return e.get(field)
+
+
+def ncu_traffic(kernel_key):
+    return ncu_figure(kernel_key, "bytes_per_launch")
+
+
+def issue_roofline(kernel_key, kernel_ms, sm_mhz, sms=152):
+    """The flux pass is bound by instruction issue, not by HBM or an FP
+    pipe: its warp instructions per launch (ncu) over its live launch time,
+    against 4 issue slots per SM per cycle at the sampled SM clock."""
+    inst = ncu_figure(kernel_key, "warp_inst_per_launch")
+    if not inst or not kernel_ms or not sm_mhz:
+        return None
+    achieved = inst / (kernel_ms * 1e-3) / 1e12
+    peak = 4.0 * sms * sm_mhz * 1e6 / 1e12
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "T warp-inst/s",
+            "frac": achieved / peak, "warp_inst_per_launch": inst,
+            "peak_kind": f"4 issue slots x {sms} SMs x sampled SM clock"}
+
+
+def alu_peaks(A):
+    """Measured FP32 and FP64 FMA throughput of this GPU (TFLOP/s)."""
+    try:
+        return {"fp32_tflops": A.aeth_probe_fma(A.FP32) / 1e12,
+                "fp64_tflops": A.aeth_probe_fma(A.FP64) / 1e12,
+                "how": "aeth_probe_fma: 8 independent FMA chains per thread, 8 CTAs x 256 per SM"}
+    except Exception as e:   # reported, not fatal
+        return {"error": str(e)}
 
 
 class ClockSampler:
@@ -593,6 +622,7 @@ def main():
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1) if flush is None else ms_acc
     clocks = clk.stop()
+    peaks_alu = alu_peaks(A) if rank == 0 else None
     kms, klaunch, kbytes, all_launches = A.aeth_profile_read(sv.ctx)
     A.aeth_profile(sv.ctx, False)
     sv.sync()
@@ -687,7 +717,7 @@ def main():
     hbm, peak_kind = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None
     kernel_key = (f"{a.path}_{a.prec}_{a.recon}" + ("_iso" if a.iso else "")
-                  + ("_dual" if a.dual else "")
+                  + ("_dual" if a.dual else "") + (f"_b{a.block_size}" if a.block_size else "")
                   if a.workload == "turb256" else None)
     traffic = ncu_traffic(kernel_key) if kernel_key else None
     launches_per_step = klaunch / max(a.steps, 1)
@@ -706,6 +736,10 @@ def main():
                      "kernel_ms_per_launch": kms / max(klaunch, 1),
                      "kernel_share_of_step": (kms / ms) if ms > 0 else None,
                      "cell_rate_hbm_frac": value / ws * bytes_per_cell_update(a) / (hbm * 1e9)},
+        "roofline_issue": issue_roofline(kernel_key, kms / max(klaunch, 1),
+                                         clocks.get("sm_mhz") if isinstance(clocks, dict) else None,
+                                         torch.cuda.get_device_properties(dev).multi_processor_count),
+        "alu_peaks": peaks_alu,
         "cpu_baseline": base,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": ke},

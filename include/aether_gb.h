@@ -352,6 +352,14 @@ aeth_status aeth_cfl_dt_noalloc(const double* d_cons, const double* d_b1,
                                 double rho_floor, double p_floor, double cfl,
                                 int mhd, double* d_dt, void* cuda_stream);
 
+/* Measured fused-multiply-add throughput of the current device in FLOP/s
+ * (two per FMA) for AETH_FP32 or AETH_FP64: one launch of 8 independent FMA
+ * chains per thread over 8 CTAs of 256 threads per SM, timed with CUDA
+ * events after a warm-up launch.  The arithmetic roofs for kernels that no
+ * HBM or tensor figure bounds.  Synchronises the device; AETH_ERR_ARG for
+ * another precision. */
+aeth_status aeth_probe_fma(int precision, double* flops_per_s);
+
 /* Reason for the last failure on ctx (static storage inside ctx). */
 const char* aeth_last_error(const aeth_ctx* ctx);
 

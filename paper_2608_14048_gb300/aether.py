@@ -39,7 +39,7 @@ EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
            "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
-           "aeth_cfl_dt_noalloc", "aeth_get_entropy", "aeth_link_blocks",
+           "aeth_cfl_dt_noalloc", "aeth_get_entropy", "aeth_link_blocks", "aeth_probe_fma",
            "aeth_last_error", "aeth_destroy"]
 
 
@@ -182,6 +182,13 @@ def aeth_set_state(ctx, block, cons, b1=None, b2=None, b3=None):
 
 def aeth_get_state(ctx, block, cons, b1=None, b2=None, b3=None):
     _check(ctx, load_library().aeth_get_state(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2), _ptr(b3)))
+
+
+def aeth_probe_fma(precision) -> float:
+    """Measured FMA throughput (FLOP/s) of the current device, FP32 or FP64."""
+    f = C.c_double(0)
+    _check(None, load_library().aeth_probe_fma(int(precision), C.byref(f)))
+    return f.value
 
 
 def aeth_link_blocks(ctx, lo, axis, hi):
