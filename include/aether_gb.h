@@ -332,8 +332,9 @@ aeth_status aeth_autotune(aeth_ctx* ctx, int* kchunk);
  * for callers that may not allocate device memory, e.g. code running inside
  * another framework's caching allocator or a host callback, or under a
  * budget that forbids cudaMalloc after start-up).  Computes the dt of
- * Eq. 11 for ONE Cartesian block whose FP64 state the caller already holds
- * on the device in the host-array layout above (cons[5][nz][ny][nx],
+ * Eq. 11 (ideal-gas closure with the given gamma; no isothermal or
+ * dual-energy variant) for ONE Cartesian block whose FP64 state the caller
+ * already holds on the device in the host-array layout above (cons[5][nz][ny][nx],
  * b1/b2/b3 face arrays; b* ignored and may be NULL when mhd = 0), with cell
  * widths dx1, dx2, dx3 and Cmax = 1, and writes it to the device double
  * *d_dt on `cuda_stream` (NULL = legacy default stream).  Asynchronous.
