@@ -7,11 +7,13 @@ Gaussian velocity with P(k) ~ k^-2 on 2 <= k <= 8, rms Mach 2, gamma =
 the device), counted once per cell (zone-cycles).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--prec fp32|fp64|fp32_p64] [--recon plm|ppm] [--n 256]
+                  [--prec fp32|fp64|fp32_p64] [--recon plm|ppm|ppm5] [--n 256]
+                  [--workload turb256|batched512|dust128|wave32|learned512|wave512|tgv128]
+                  [--iso] [--dual] [--block-size N] [--hydro] [--riemann lhlld|hlld]
 
 Prints ONE JSON line (rank 0).  With --gpus N > 1 (torchrun) every rank
-advances its own independent replica (the step has no cross-GPU exchange in
-this build: replicas only); value = all ranks' cell-updates / max time.
+advances its own independent replica (weak scaling, no cross-GPU exchange
+in the step); value = all ranks' cell-updates / max time.
 """
 from __future__ import annotations
 
