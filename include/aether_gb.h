@@ -56,8 +56,7 @@ typedef enum {
 /* equation of state (Sec. 2.1): ideal gas p = (gamma - 1) e, or the
  * isothermal closure p = cs_iso^2 rho (no energy equation: the energy slot
  * of the state is carried with zero flux; the isothermal HLLD of Mignone
- * (2007) or the isothermal HLLE solves the faces; Cartesian blocks, gas
- * only) */
+ * (2007) or the isothermal HLLE solves the faces; gas only) */
 enum {
   AETH_EOS_ADIABATIC_MHD = 0,
   AETH_EOS_ADIABATIC_HYDRO = 1,

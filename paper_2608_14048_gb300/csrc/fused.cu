@@ -151,7 +151,8 @@ __device__ __forceinline__ void ct_store(const BlockPtrs<R>& B, const int* P, lo
 
 template <typename R, bool P64, bool MHD, bool SPH, bool DUAL = false>
 __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P, int src, int out,
-                                            R w0, R w1, R bdt, R gamma, R rho_floor, R p_floor) {
+                                            R w0, R w1, R bdt, R gamma, R rho_floor, R p_floor,
+                                            R cs2) {
   const Layout& L = B.L;
   const Geometry<R>& geo = B.geo;
   const int i = P[0], j = P[1], k = P[2];
@@ -180,7 +181,8 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) s.p[v] = B.reg[src][v];
       R w[8];
-      prim_cell<R, P64, MHD>(L, s, c, gamma - R(1), rho_floor, p_floor, w);
+      if (cs2 > R(0)) prim_cell<R, P64, MHD, true>(L, s, c, cs2, rho_floor, p_floor, w);
+      else prim_cell<R, P64, MHD>(L, s, c, gamma - R(1), rho_floor, p_floor, w);
       const R rho = w[0], vv[3] = {w[1], w[2], w[3]};
       const R bb[3] = {w[5], w[6], w[7]};
       const R ps = w[4] + R(0.5) * (bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2]);
@@ -247,10 +249,11 @@ __device__ __forceinline__ void update_cell(const BlockPtrs<R>& B, const int* P,
 
 // COORD: 0 every block Cartesian, 1 every block spherical, 2 mixed (the
 // coordinate system is then read per tile).
+// cs2 > 0: the isothermal closure (the spherical sources take p = cs2 rho)
 template <typename R, bool P64, bool MHD, int COORD, typename Src, bool DUAL = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
     k_update_f(Src S, int t0, int t1, int src, int out, R w0, R w1, R beta,
-               const double* __restrict__ dt, R gamma, R rho_floor, R p_floor) {
+               const double* __restrict__ dt, R gamma, R rho_floor, R p_floor, R cs2) {
   const int add[3] = {1, 1, 1};
   const R bdt = beta * (R)(*dt);
   for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
@@ -260,10 +263,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
     if (ct.P[0] > B.L.n[0] || ct.P[1] > B.L.n[1] || ct.P[2] > B.L.n[2]) continue;
     if (COORD == 1 || (COORD == 2 && B.L.coord == AETH_COORD_SPH))
       update_cell<R, P64, MHD, true, DUAL>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor,
-                                           p_floor);
+                                           p_floor, cs2);
     else
       update_cell<R, P64, MHD, false, DUAL>(B, ct.P, src, out, w0, w1, bdt, gamma, rho_floor,
-                                            p_floor);
+                                            p_floor, cs2);
   }
 }
 
@@ -490,10 +493,12 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
   with_src<R>(c, PK_CELL, -1, [&](auto S, TileRange r) {
     if (MHD) k_emf_ref<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1);
     const R g = (R)c->cfg.gamma, rf = (R)c->cfg.rho_floor, pf = (R)c->cfg.p_floor;
+    const R cs2 = is_iso(c) ? (R)(c->cfg.cs_iso * c->cfg.cs_iso) : R(0);
     const int n = r.t1 - r.t0;
     using Src = decltype(S);
     auto upd = [&](auto kernel) {
-      kernel<<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta, c->d_dt, g, rf, pf);
+      kernel<<<n, 256, 0, c->stream>>>(S, r.t0, r.t1, src, out, w0, w1, beta, c->d_dt, g, rf, pf,
+                                       cs2);
     };
     if constexpr (!P64) {
       if (dual) {

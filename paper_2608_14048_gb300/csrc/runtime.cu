@@ -145,8 +145,6 @@ aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
       return fail(c, AETH_ERR_ARG, "periodic axis %d needs n >= ghost width %d (or n == 1)", q, g);
   if (d->coord == AETH_COORD_SPH && c->cfg.integrator == AETH_INT_RK3)
     return fail(c, AETH_ERR_UNSUPPORTED, "SSP-RK3 runs on Cartesian blocks only");
-  if (d->coord == AETH_COORD_SPH && is_iso(c))
-    return fail(c, AETH_ERR_UNSUPPORTED, "the isothermal closure runs on Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH && c->cfg.n_dust > 0)
     return fail(c, AETH_ERR_UNSUPPORTED, "dust runs support Cartesian blocks only");
   if (d->coord == AETH_COORD_SPH) {
