@@ -67,3 +67,39 @@ def test_bench_workload_names():
     assert cfg["workload"] == "linear_wave_512x512x256_mhd_blocks128"
     assert cfg["blocks"].startswith("32 linked blocks")
     assert bench.parse(["--workload", "wave512"]).prec == "fp64"
+
+
+def test_issue_roofline_and_alu_peaks_helpers():
+    # issue roofline: instructions per launch over the launch time, against
+    # 4 slots per SM per cycle; absent figures give None
+    r = bench.issue_roofline("fused_fp32_plm", 1.5, 2000.0, 100)
+    if r is not None:   # present while the committed figures match the kernel source
+        assert r["peak"] == pytest.approx(4 * 100 * 2000e6 / 1e12)
+        assert r["achieved"] == pytest.approx(r["warp_inst_per_launch"] / 1.5e-3 / 1e12)
+        assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert bench.issue_roofline("no_such_key", 1.5, 2000.0) is None
+    assert bench.issue_roofline("fused_fp32_plm", 0.0, 2000.0) is None
+
+    class FakeA:
+        FP32, FP64 = 1, 0
+
+        @staticmethod
+        def aeth_probe_fma(prec):
+            return 8e13 if prec == 1 else 1.25e12
+
+    p = bench.alu_peaks(FakeA)
+    assert p["fp32_tflops"] == pytest.approx(80.0) and p["fp64_tflops"] == pytest.approx(1.25)
+
+    class Broken(FakeA):
+        @staticmethod
+        def aeth_probe_fma(prec):
+            raise RuntimeError("no device")
+
+    assert "error" in bench.alu_peaks(Broken)
+
+
+def test_committed_traffic_figures_match_the_kernel_source():
+    """The committed ncu figures are keyed to the flux kernel's code; the
+    default workload's entry must match the current source."""
+    assert bench.ncu_traffic("fused_fp32_plm") is not None
+    assert bench.ncu_figure("fused_fp32_plm", "warp_inst_per_launch") is not None
