@@ -336,9 +336,11 @@ __global__ void __launch_bounds__(256) k_dual_sync(Src S, int t0, int t1, int re
 }
 
 // ------------------------------------------------------------------------
-// ghost fill of one register, one axis per launch (Sec. 2.3)
+// ghost fill of one register, one axis per launch (Sec. 2.3); LINKS and ENT
+// compile the linked-block and entropy copies in only where the context has
+// them (each costs registers in the plain fill)
 // ------------------------------------------------------------------------
-template <typename R, typename Src>
+template <typename R, typename Src, bool LINKS, bool ENT>
 __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, int nv, int d) {
   for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
     int loc;
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
     const long long dst = L.idx(c[0], c[1], c[2]);
     // a linked side copies from the neighbouring block's cells (and faces)
     // beyond it: cells n_nb + p on the low side, p - n on the high side
-    const int lk = L.lnk[d][p < 0 ? 0 : 1];
+    const int lk = LINKS ? L.lnk[d][p < 0 ? 0 : 1] : -1;
     const BlockPtrs<R>& SB = (lk < 0 || lk == L.self) ? B : B.tab[lk];
     // every source is loaded before the first store (the stores go through
     // pointer arrays the compiler cannot prove disjoint from the loads)
@@ -397,7 +399,8 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
     for (int v = 0; v < NVAR; ++v)
       if (on[v]) B.reg[reg][v][dst] = val[v];
     // dual energy: the entropy is a cell variable like the density
-    if (R* e = B.ent[reg]) {
+    if constexpr (ENT) {
+      R* e = B.ent[reg];
       int sc[3] = {c[0], c[1], c[2]};
       if (lk >= 0) sc[d] = p < 0 ? SB.L.n[d] + p : p - n;
       else sc[d] = L.bc[d] == AETH_BC_PERIODIC ? ((p % n) + n) % n : (p < 0 ? 0 : n - 1);
@@ -409,15 +412,25 @@ __global__ void __launch_bounds__(256) k_fill_b(Src S, int t0, int t1, int reg, 
 // ------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------
-template <typename R>
-static void launch_fill_all(aeth_ctx* c, int reg, int nv, int block) {
+template <typename R, bool LINKS, bool ENT>
+static void launch_fill_axes(aeth_ctx* c, int reg, int nv, int block) {
   for (int d = 0; d < 3; ++d) {
     with_src<R>(c, PK_FILL0 + d, block, [&](auto S, TileRange r) {
       if (r.t1 <= r.t0) return;
-      k_fill_b<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1, reg, nv, d);
+      k_fill_b<R, decltype(S), LINKS, ENT><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1,
+                                                                               reg, nv, d);
     });
   }
   c->n_launch += 3;
+}
+
+template <typename R>
+static void launch_fill_all(aeth_ctx* c, int reg, int nv, int block) {
+  const bool links = !c->links.empty(), ent = is_dual(c);
+  if (links && ent) launch_fill_axes<R, true, true>(c, reg, nv, block);
+  else if (links) launch_fill_axes<R, true, false>(c, reg, nv, block);
+  else if (ent) launch_fill_axes<R, false, true>(c, reg, nv, block);
+  else launch_fill_axes<R, false, false>(c, reg, nv, block);
 }
 
 template <typename R>
