@@ -28,6 +28,7 @@ PERIODIC, OUTFLOW = 0, 1
 DONOR, PLM, PPM, PPM5 = 0, 1, 2, 3
 VL2, RK2, RK3 = 0, 1, 2
 HLLD, HLLE, LHLLD = 0, 1, 2
+DRAG_TSTOP, DRAG_COEFF = 0, 1
 
 
 class Grid(C.Structure):
@@ -52,7 +53,8 @@ class Diag(C.Structure):
 
 class DustParams(C.Structure):
     _fields_ = [("nd", C.c_int), ("t_stop", C.POINTER(C.c_double)),
-                ("rho_floor_dust", C.c_double), ("gas_accel", C.c_double * 3)]
+                ("rho_floor_dust", C.c_double), ("gas_accel", C.c_double * 3),
+                ("law", C.c_int)]
 
 
 def build(force: bool = False, openmp: bool = True) -> str:
@@ -283,9 +285,12 @@ def run(grid: Grid, params: Params, s: State, nsteps: int = None, t_end: float =
 
 # ---- multifluid dust (dust.c) ------------------------------------------
 
-def make_dust_params(t_stop, rho_floor_dust=1e-20, gas_accel=(0.0, 0.0, 0.0)):
+def make_dust_params(t_stop, rho_floor_dust=1e-20, gas_accel=(0.0, 0.0, 0.0), law=DRAG_TSTOP):
+    """Dust parameters (Sec. 2.2).  ``t_stop`` holds the stopping times t_k
+    (law DRAG_TSTOP) or the drag coefficients K_k of the constant-coefficient
+    law t_k = rho_k / K_k (law DRAG_COEFF)."""
     ts = np.ascontiguousarray(t_stop, dtype=np.float64)
-    dp = DustParams(len(ts), _dp(ts), rho_floor_dust, (C.c_double * 3)(*gas_accel))
+    dp = DustParams(len(ts), _dp(ts), rho_floor_dust, (C.c_double * 3)(*gas_accel), law)
     dp._keep = ts
     return dp
 

@@ -2,11 +2,14 @@
  * FP64 oracle: multifluid dust (paper Sec. 2.2, Eqs. 6-7) with the IMEX2P
  * integrator of Sec. 2.6.  TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
- * Gas: adiabatic hydro (B = 0), reconstruction + HLLD (= HLLC at B = 0) as in
- * mhd.c.  Dust: N pressureless species, same reconstruction, Rusanov flux
- * with speed max(|v_n,L|, |v_n,R|).  Drag rho_k (v - v_k) / t_k on species k
- * and the opposite reaction on the gas, integrated implicitly; the drift
- * energy the drag removes becomes gas heat (total energy conserved).
+ * Gas: hydro (B = 0), adiabatic or isothermal, reconstruction + HLLD (= HLLC
+ * at B = 0) as in mhd.c.  Dust: N pressureless species, same reconstruction,
+ * Rusanov flux with speed max(|v_n,L|, |v_n,R|).  Drag rho_k (v - v_k) / t_k
+ * on species k and the opposite reaction on the gas, integrated implicitly;
+ * t_k is a constant per species, or rho_k / K_k for the constant-coefficient
+ * law.  With the adiabatic closure the drift energy the drag removes becomes
+ * gas heat (total energy conserved); the isothermal closure has no energy
+ * equation.
  *
  * IMEX2P (reading): the two-stage IMEX pair of Ascher, Ruuth & Spiteri with
  * implicit weight gamma = lambda = 1 + 1/sqrt 2 (stiffly accurate, L-stable)
@@ -47,8 +50,8 @@ void orc_drag_solve(int nd, double h, double rho_g, const double* rho_d,
 }
 
 /* Drag solve on every interior cell of (gas u[5], dust d[4 nd]) in place. */
-static long drag_cells(const Mesh* m, const orc_dust_params* dp, double h, double** u,
-                       double** d) {
+static long drag_cells(const Mesh* m, const orc_dust_params* dp, int iso, double h,
+                       double** u, double** d) {
   int nd = dp->nd;
   long hits = 0;
 #pragma omp parallel for collapse(2) reduction(+ : hits)
@@ -56,9 +59,13 @@ static long drag_cells(const Mesh* m, const orc_dust_params* dp, double h, doubl
     for (int j = 0; j < m->n[1]; ++j)
       for (int i = 0; i < m->n[0]; ++i) {
         long c = IDX(m, i, j, k);
-        double rd[32], vd[32], vd0[32];
+        double rd[32], vd[32], vd0[32], ts[32];
         double rg = u[0][c];
         for (int s = 0; s < nd; ++s) rd[s] = d[4 * s][c];
+        /* the drag leaves the densities alone, so t_k = rho_k / K_k of the
+         * stage's density holds through the implicit solve */
+        for (int s = 0; s < nd; ++s)
+          ts[s] = dp->law == ORC_DRAG_COEFF ? rd[s] / dp->t_stop[s] : dp->t_stop[s];
         double ke_before = 0.0, ke_after = 0.0;
         for (int q = 0; q < 3; ++q) {
           double vg = u[1 + q][c] / rg;
@@ -66,7 +73,7 @@ static long drag_cells(const Mesh* m, const orc_dust_params* dp, double h, doubl
             vd[s] = rd[s] > 0 ? d[4 * s + 1 + q][c] / rd[s] : 0.0;
             vd0[s] = vd[s];
           }
-          orc_drag_solve(nd, h, rg, rd, dp->t_stop, &vg, vd);
+          orc_drag_solve(nd, h, rg, rd, ts, &vg, vd);
           u[1 + q][c] = rg * vg;
           for (int s = 0; s < nd; ++s) {
             d[4 * s + 1 + q][c] = rd[s] * vd[s];
@@ -75,8 +82,9 @@ static long drag_cells(const Mesh* m, const orc_dust_params* dp, double h, doubl
           }
         }
         /* total energy conserved: the dust kinetic energy lost to drag
-         * (and the gas kinetic change) is accounted in the gas total E */
-        u[4][c] -= ke_after - ke_before;
+         * (and the gas kinetic change) is accounted in the gas total E;
+         * the isothermal closure carries its energy slot unchanged */
+        if (!iso) u[4][c] -= ke_after - ke_before;
         /* dust floor: reset to the floor with zero velocity */
         for (int s = 0; s < nd; ++s)
           if (d[4 * s][c] < dp->rho_floor_dust) {
@@ -235,6 +243,7 @@ static void store_dust(const Mesh* m, int nd, double** d, double* dust) {
 int orc_dust_step(const orc_grid* g, const orc_params* p, const orc_dust_params* dp,
                   double dt, double* cons, double* dust, long* floor_hits) {
   if (p->mhd || dp->nd < 0 || dp->nd > 32) return -1;
+  if (dp->law != ORC_DRAG_TSTOP && dp->law != ORC_DRAG_COEFF) return -1;
   Mesh m;
   if (orc_mesh_init(&m, g, orc_ghost_width(p->recon)) != 0) return -1;
   int nd = dp->nd, nv = 4 * nd;
@@ -275,7 +284,7 @@ int orc_dust_step(const orc_grid* g, const orc_params* p, const orc_dust_params*
   /* U2 = drag(X) stored in U/D; dt R(U2) = (U2 - X) / g */
   for (int v = 0; v < 5; ++v) memcpy(U[v], X[v], (size_t)m.size * sizeof(double));
   for (int v = 0; v < nv; ++v) memcpy(D[v], XD[v], (size_t)m.size * sizeof(double));
-  hits += drag_cells(&m, dp, h, U, D);
+  hits += drag_cells(&m, dp, p->iso, h, U, D);
   for (int k = 0; k < m.n[2]; ++k)
     for (int j = 0; j < m.n[1]; ++j)
       for (int i = 0; i < m.n[0]; ++i) {
@@ -293,7 +302,7 @@ int orc_dust_step(const orc_grid* g, const orc_params* p, const orc_dust_params*
         for (int v = 0; v < 5; ++v) U[v][c] = A[v][c] + (1.0 - dE) * dt * Lu[v][c];
         for (int v = 0; v < nv; ++v) D[v][c] = AD[v][c] + (1.0 - dE) * dt * LD[v][c];
       }
-  hits += drag_cells(&m, dp, h, U, D);
+  hits += drag_cells(&m, dp, p->iso, h, U, D);
 
   orc_store(&m, U, 5, NULL, cons, NULL, NULL, NULL);
   store_dust(&m, nd, D, dust);
@@ -318,10 +327,15 @@ double orc_dust_dt(const orc_grid* g, const orc_params* p, const orc_dust_params
         double rho = cons[c];
         if (rho < p->rho_floor) rho = p->rho_floor;
         double v[3] = {cons[nc + c] / rho, cons[2 * nc + c] / rho, cons[3 * nc + c] / rho};
-        double pr = (p->gamma - 1.0) *
-                    (cons[4 * nc + c] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
-        if (pr < p->p_floor) pr = p->p_floor;
-        double cs = sqrt(p->gamma * pr / rho);
+        double cs;
+        if (p->iso) {
+          cs = p->cs_iso;
+        } else {
+          double pr = (p->gamma - 1.0) *
+                      (cons[4 * nc + c] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+          if (pr < p->p_floor) pr = p->p_floor;
+          cs = sqrt(p->gamma * pr / rho);
+        }
         double w[3];
         orc_widths(&m, i, j, k, w);
         for (int d = 0; d < 3; ++d) {

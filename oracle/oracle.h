@@ -137,13 +137,18 @@ double orc_corner_emf(double ea_m, double ea_p, double eb_m, double eb_p,
                       double fb_m, double fb_p);
 
 /* ---- multifluid dust (dust.c) ---------------------------------------- */
+enum { ORC_DRAG_TSTOP = 0, ORC_DRAG_COEFF = 1 };
+
 typedef struct {
   int nd;                 /* number of dust species N */
-  const double* t_stop;   /* [nd] constant stopping times */
+  const double* t_stop;   /* [nd] ORC_DRAG_TSTOP: constant stopping times t_k;
+                             ORC_DRAG_COEFF: drag coefficients K_k */
   double rho_floor_dust;
   double gas_accel[3];    /* uniform external acceleration on the gas only
                              (explicit term; used by the forced-relaxation
                              test, zero otherwise) */
+  int law;                /* drag law (Sec. 2.2): constant stopping time, or
+                             constant coefficient, t_k = rho_k / K_k */
 } orc_dust_params;
 
 /* Closed-form implicit drag solve of one cell and one velocity component
@@ -152,8 +157,9 @@ typedef struct {
 void orc_drag_solve(int nd, double h, double rho_g, const double* rho_d,
                     const double* t_stop, double* v_g, double* v_d);
 
-/* One IMEX2P step of adiabatic hydro gas + nd pressureless dust species.
- * dust[nd][4][nz][ny][nx] holds (rho_k, M1_k, M2_k, M3_k). */
+/* One IMEX2P step of hydro gas (adiabatic, or isothermal with p->iso) + nd
+ * pressureless dust species.  dust[nd][4][nz][ny][nx] holds (rho_k, M1_k,
+ * M2_k, M3_k). */
 int orc_dust_step(const orc_grid* g, const orc_params* p,
                   const orc_dust_params* dp, double dt, double* cons,
                   double* dust, long* floor_hits);
