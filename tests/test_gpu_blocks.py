@@ -122,45 +122,3 @@ def test_single_block_linked_to_itself_is_periodic():
     ref, dts = oracle_run(st, "ppm", "vl2", nsteps=3)
     (cons, b1, b2, b3), _, _ = _run_blocks(st, ([12], [10], [8]), dts, "ppm", "vl2")
     assert max(compare((cons, b1, b2, b3), ref)) < FP64_TOL
-
-
-def test_link_validation():
-    import torch
-    cfg = A.make_config()
-    d = [A.make_block((8, 8, 8)), A.make_block((8, 6, 8), hi=(1.0, 0.75, 1.0))]
-    ctx = A.aeth_create(cfg)
-    try:
-        for b in d:
-            A.aeth_add_block(ctx, b)
-        with pytest.raises(A.AethError) as e:
-            A.aeth_link_blocks(ctx, 0, 0, 1)          # ny differs across the x face
-        assert e.value.code == -1
-        A.aeth_link_blocks(ctx, 0, 1, 1)              # along y: nx, nz agree
-        with pytest.raises(A.AethError) as e:
-            A.aeth_link_blocks(ctx, 0, 1, 1)          # side already linked
-        assert e.value.code == -1
-        with pytest.raises(A.AethError) as e:
-            A.aeth_link_blocks(ctx, 0, 3, 1)
-        assert e.value.code == -1
-    finally:
-        A.aeth_destroy(ctx)
-    # a different cell width, and a transverse offset, are rejected
-    for other in (A.make_block((8, 8, 8), hi=(2.0, 1.0, 1.0)),
-                  A.make_block((8, 8, 8), lo=(0.0, 0.5, 0.0), hi=(1.0, 1.5, 1.0))):
-        ctx = A.aeth_create(cfg)
-        try:
-            A.aeth_add_block(ctx, d[0])
-            A.aeth_add_block(ctx, other)
-            with pytest.raises(A.AethError) as e:
-                A.aeth_link_blocks(ctx, 0, 0, 1)
-            assert e.value.code == -1
-        finally:
-            A.aeth_destroy(ctx)
-    ctx = A.aeth_create(A.make_config(path=A.UNFUSED))
-    try:
-        A.aeth_add_block(ctx, d[0])
-        with pytest.raises(A.AethError) as e:
-            A.aeth_link_blocks(ctx, 0, 0, 0)
-        assert e.value.code == -8
-    finally:
-        A.aeth_destroy(ctx)
