@@ -65,6 +65,8 @@ def parse(argv=None):
                     help="turb256: isothermal closure p = cs^2 rho with cs = 1 (the sound "
                          "speed of the generator) and the isothermal HLLD")
     a = ap.parse_args(argv)
+    if a.steps < 1 or a.warmup < 0:
+        ap.error("--steps must be >= 1 and --warmup >= 0")
     if a.prec is None:
         a.prec = "fp64" if a.workload == "wave512" else "fp32"
     if a.iso and a.workload != "turb256":
@@ -370,52 +372,120 @@ def make_input(a):
     return I.turbulence_box(n=a.n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
 
 
-def cpu_baseline(a, st_full):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    same generator on a 64^3 box (64 x 64 x 32 of the 2 x 2 x 1 box for the
-    linear wave), stepped until ~10 s of CPU work."""
+SAMPLE_PROBE = {"dust128": 32, "wave32": 32}   # other workloads: 64
+
+
+def _oracle_sample(a, n):
+    """The FP64 oracle's bounded sample of the workload at linear size n: the
+    same generator on a smaller box (n x n x n/2 of the 2 x 2 x 1 box for
+    the linear wave; for the 512 uneven boxes, the first 8 (n/64)^3 of them
+    with one global dt).  Returns (step, cells, description): step() runs
+    one step of the sample with its initial CFL dt."""
     import oracle as O
     from paper_2608_14048_gb300 import inputs as I
-    n = 64
+
+    def gas_step(g, p, s):
+        if getattr(a, "dual", False):
+            s = O.dual_init(g, p, s)
+        dt = O.compute_dt(g, p, s)
+        return lambda: O.step(g, p, dt, s)
+
+    if a.workload == "dust128":
+        gas, dust, ts = I.dust_box(I.Block((n, n, n)), 20260817, nd=8)
+        g = O.make_grid((n, n, n))
+        p = O.make_params(gamma=gas.gamma, recon=O.PLM, mhd=False)
+        dp = O.make_dust_params(ts)
+        cons, d = gas.cons.copy(), dust.copy()
+        dt = O.dust_dt(g, p, dp, cons, d)
+        return (lambda: O.dust_step(g, p, dp, dt, cons, d)), n ** 3, \
+            f"{n}^3 gas + 8 dust species of the same generator (IMEX2P, FP64 drag)"
+    if a.workload == "batched512":
+        m = max(1, round(8 * (n / 64) ** 3))
+        boxes = I.batched_boxes(m, 20260818, gl=2)
+        runs = []
+        for st in boxes:
+            b = st.block
+            g = O.make_grid(b.n, b.lo, b.hi, b.coord, b.bc)
+            p = O.make_params(gamma=st.gamma, recon=O.PLM)
+            runs.append((g, p, O.State(st.cons, st.b1, st.b2, st.b3)))
+        dt = min(O.compute_dt(g, p, s) for g, p, s in runs)
+
+        def step():
+            for g, p, s in runs:
+                O.step(g, p, dt, s)
+        cells = sum(math.prod(st.block.n) for st in boxes)
+        return step, cells, f"the first {m} of the 512 uneven boxes ({cells} cells, one dt)"
+    if a.workload == "wave32":
+        st = I.linear_fast_wave(n)
+        g = O.make_grid((n, n, n))
+        p = O.make_params(gamma=st.gamma, recon=O.PLM)
+        return gas_step(g, p, O.State(st.cons, st.b1, st.b2, st.b3)), n ** 3, \
+            f"fast wave {n}^3 (PLM + HLLD + VL2)"
     if a.workload == "wave512":
-        st = I.linear_wave_box((64, 64, 32), (2.0, 2.0, 1.0), mhd=not a.hydro)
-        g = O.make_grid((64, 64, 32), hi=(2.0, 2.0, 1.0))
+        shape = (n, n, max(2, n // 2))
+        st = I.linear_wave_box(shape, (2.0, 2.0, 1.0), mhd=not a.hydro)
+        g = O.make_grid(shape, hi=(2.0, 2.0, 1.0))
         p = O.make_params(gamma=st.gamma, recon=O.PLM, integrator=O.RK2, riemann=O.HLLE,
                           mhd=not a.hydro)
-        cells = 64 * 64 * 32
-        what = f"{'hydro' if a.hydro else 'MHD'} linear wave 64x64x32 (PLM+HLLE+RK2)"
-    elif a.workload == "tgv128":
+        what = (f"{'hydro' if a.hydro else 'MHD'} linear wave {shape[0]}x{shape[1]}x{shape[2]} "
+                f"(PLM+HLLE+RK2)")
+        return gas_step(g, p, O.State(st.cons, st.b1, st.b2, st.b3)), \
+            shape[0] * shape[1] * shape[2], what
+    if a.workload == "tgv128":
         st = I.taylor_green(n, 0.01)
         g = O.make_grid((n, n, n), hi=(2 * math.pi,) * 3)
         p = O.make_params(gamma=st.gamma, recon=O.PLM, integrator=O.RK2, mhd=False,
                           riemann=O.LHLLD if a.riemann == "lhlld" else O.HLLD)
-        cells = n ** 3
-        what = f"Taylor-Green vortex {n}^3 at Mach 0.01 (PLM + {solver_label(a)} + RK2)"
-    else:
-        st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
+        return gas_step(g, p, O.State(st.cons, st.b1, st.b2, st.b3)), n ** 3, \
+            f"Taylor-Green vortex {n}^3 at Mach 0.01 (PLM + {solver_label(a)} + RK2)"
+    if a.workload == "learned512":
+        # the oracle has no learned flux: HLLD on the same Mach-4 input
+        st = I.turbulence_box(n=n, seed=20260820, mach=4.0, beta_modulated=True, gamma=1.0001)
         g = O.make_grid((n, n, n))
-        p = O.make_params(gamma=st.gamma, recon={"plm": O.PLM, "ppm": O.PPM, "ppm5": O.PPM5}[a.recon],
-                          iso=a.iso, cs=1.0, dual=a.dual)
-        cells = n ** 3
-        what = f"{n}^3 box of the same turbulence generator" + (", isothermal" if a.iso else "")
-        if a.dual:
-            what += ", dual energy"
-    s = O.State(st.cons, st.b1, st.b2, st.b3)
-    if getattr(a, "dual", False):
-        s = O.dual_init(g, p, s)
-    dt = O.compute_dt(g, p, s)
+        p = O.make_params(gamma=st.gamma, recon=O.PLM)
+        return gas_step(g, p, O.State(st.cons, st.b1, st.b2, st.b3)), n ** 3, \
+            f"{n}^3 box of the same Mach-4 generator, HLLD (the oracle has no learned flux)"
+    st = I.turbulence_box(n=n, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001)
+    g = O.make_grid((n, n, n))
+    p = O.make_params(gamma=st.gamma, recon={"plm": O.PLM, "ppm": O.PPM, "ppm5": O.PPM5}[a.recon],
+                      iso=a.iso, cs=1.0, dual=a.dual)
+    what = f"{n}^3 box of the same turbulence generator" + (", isothermal" if a.iso else "")
+    if a.dual:
+        what += ", dual energy"
+    return gas_step(g, p, O.State(st.cons, st.b1, st.b2, st.b3)), n ** 3, what
+
+
+def _host_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(a, st_full):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload
+    (64^3 or its equivalent), stepped until ~10 s of CPU work."""
+    step, cells, what = _oracle_sample(a, SAMPLE_PROBE.get(a.workload, 64))
     t0 = time.perf_counter()
-    O.step(g, p, dt, s)
+    step()
     one = time.perf_counter() - t0
     k = max(1, min(20, int(10.0 / max(one, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(k):
-        O.step(g, p, dt, s)
+        step()
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = _host_threads()
     return {"value": cells * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, {what}, {k} steps ({el:.1f} s), OpenMP over {cores} "
                       f"host threads"}
+
+
+def reference_sample_size(t_probe, n_probe, steps, budget_s=150.0):
+    """Linear size of the oracle's sample box so that `steps` steps take
+    about budget_s, from one measured step of t_probe seconds at n_probe
+    (the step's cost grows with the cell count, n^3); at most n_probe,
+    a multiple of 8, at least 16."""
+    if steps * t_probe <= budget_s:
+        return n_probe
+    n = n_probe * (budget_s / (steps * t_probe)) ** (1.0 / 3.0)
+    return max(16, int(n) // 8 * 8)
 
 
 def solver_label(a):
@@ -468,15 +538,33 @@ def whole_job_rate(units_per_rank, ws, seconds):
 
 
 def run_reference(a):
+    """The reference arm: the FP64 oracle as it stands, on the host cores,
+    W untimed and K timed steps of a bounded sample of the workload (64^3,
+    smaller when K + W steps of it would take more than a few minutes)."""
     ws, rank, local = dist_env()
     if ws > 1 and rank != 0:
         return
-    st = None
-    base = cpu_baseline(a, st)
-    steps = a.steps
+    n0 = SAMPLE_PROBE.get(a.workload, 64)
+    step, cells, what = _oracle_sample(a, n0)
+    t0 = time.perf_counter()
+    step()                                    # first warm-up step, also the size probe
+    n = reference_sample_size(time.perf_counter() - t0, n0, a.steps + a.warmup)
+    if n != n0:
+        step, cells, what = _oracle_sample(a, n)
+        step()
+    for _ in range(a.warmup - 1):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    el = time.perf_counter() - t0
+    cores = _host_threads()
+    base = {"value": cells * a.steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {what}, {max(1, a.warmup)} untimed + {a.steps} timed steps "
+                      f"({el:.1f} s), OpenMP over {cores} host threads"}
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
-            "n_gpus": a.gpus, "steps": steps, "warmup": a.warmup,
-            "ms_per_step": (64 * 64 * 32 if a.workload == "wave512" else 64 ** 3) / base["value"] * 1e3,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": el / a.steps * 1e3,
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(a), "cpu_baseline": base,
@@ -504,8 +592,7 @@ def main():
 
     # CPU baseline first (rank 0, N = 1), before the GPU work starts
     base = None
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload in ("turb256", "wave512",
-                                                                         "tgv128"):
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         base = cpu_baseline(a, None)
 
     prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]

@@ -103,3 +103,20 @@ def test_committed_traffic_figures_match_the_kernel_source():
     default workload's entry must match the current source."""
     assert bench.ncu_traffic("fused_fp32_plm") is not None
     assert bench.ncu_figure("fused_fp32_plm", "warp_inst_per_launch") is not None
+
+
+def test_reference_sample_size_keeps_the_reference_arm_within_minutes():
+    # fits: the probe size stays
+    assert bench.reference_sample_size(0.3, 64, 20) == 64
+    # too long: the cell count shrinks with the budget (n^3 scaling), to a
+    # multiple of 8, never below 16
+    n = bench.reference_sample_size(0.3, 64, 1000)
+    assert n % 8 == 0 and 16 <= n < 64
+    assert 1000 * 0.3 * (n / 64) ** 3 <= 150.0
+    assert bench.reference_sample_size(0.3, 64, 10 ** 7) == 16
+
+
+@pytest.mark.parametrize("argv", [["--steps", "0"], ["--warmup", "-1"]])
+def test_bench_rejects_empty_timing(argv):
+    with pytest.raises(SystemExit):
+        bench.parse(argv)
