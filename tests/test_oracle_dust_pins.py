@@ -297,19 +297,23 @@ def test_isothermal_gas_keeps_its_energy_slot_under_drag():
     assert not kept
 
 
-def test_isothermal_dust_dt_closed_form():
-    # Eq. 11 with the isothermal sound speed and C_max = 1/lambda of IMEX2P
-    # (lambda = 1 + 1/sqrt 2); the dust's own speed bounds it where faster
+@pytest.mark.parametrize("iso", [True, False])
+def test_dust_dt_closed_form(iso):
+    # Eq. 11 with C_max = 1/lambda of IMEX2P (lambda = 1 + 1/sqrt 2): the gas
+    # bound |v| + c_s per axis (isothermal c_s, or sqrt(gamma p / rho) of the
+    # adiabatic gas), and each species' own speed where it is faster
     n = (4, 4, 4)
-    cons, dust = _uniform([0.5], [3.0], 0.4, n=n)
-    cons[4] = 123.0                           # ignored by the isothermal closure
+    cs = 0.7
+    cons, dust = _uniform([0.5], [3.0], 0.4, cs=cs, n=n)   # adiabatic gas with c_s = 0.7
+    if iso:
+        cons[4] = 123.0                       # ignored by the isothermal closure
     g = O.make_grid(n, hi=(1.0, 2.0, 0.5))
-    p = O.make_params(mhd=False, iso=True, cs=0.7, cfl=0.4)
+    p = O.make_params(mhd=False, iso=iso, cs=cs, cfl=0.4)
     dp = O.make_dust_params([1.0], law=O.DRAG_COEFF)
     lam = 1 + 1 / math.sqrt(2)
-    # x: gas |0.4| + 0.7 over 0.25 vs dust 3 over 0.25; z: gas 0.7 over 0.125
+    # x: gas 0.4 + 0.7 over 0.25 vs dust 3 over 0.25; y: 0.7 over 0.5; z: 0.7 over 0.125
     want = 0.4 / lam * min(0.25 / 1.1, 0.25 / 3.0, 0.5 / 0.7, 0.125 / 0.7)
-    assert O.dust_dt(g, p, dp, cons, dust) == pytest.approx(want, rel=1e-14)
+    assert O.dust_dt(g, p, dp, cons, dust) == pytest.approx(want, rel=1e-13)
 
 
 def _paper_shock_values():
