@@ -380,13 +380,29 @@ def _run_1d(st, t_end, recon=O.PLM, integ=O.VL2, cfl=0.3, riemann=O.HLLD):
     return s
 
 
-def test_sod_star_state_golden():
-    # Toro's tabulated star state of the Sod problem (paper Sec. 5.1 set-up)
-    vals = dict(l.split() for l in open(os.path.join(GOLDEN, "sod_star.txt"))
-                if l.strip() and not l.startswith("#"))
-    p, u = ER.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
-    assert p == pytest.approx(float(vals["p_star"]), abs=1e-5)
-    assert u == pytest.approx(float(vals["u_star"]), abs=1e-5)
+def test_sod_star_state_satisfies_the_jump_conditions():
+    # the exact solver used by the shock-tube pins, on the paper's Sod set-up
+    # (Sec. 5.1: gamma = 1.4, (rho, u, p) = (1, 0, 1) | (0.125, 0, 0.1)):
+    # its star state must satisfy, with nothing stored,
+    # * across the right shock (Rankine-Hugoniot): the mass flux m and the
+    #   shock speed S from mass and momentum, then the energy condition
+    #   gamma/(gamma-1) p/rho + (u - S)^2 / 2 equal on both sides;
+    # * across the left rarefaction: isentropic rho* = rho_L (p*/p_L)^(1/gamma)
+    #   and the Riemann invariant u + 2c/(gamma - 1) conserved.
+    # The two conditions fix (p*, u*) uniquely.
+    g = 1.4
+    rl, ul, pl, rr, ur, pr = 1.0, 0.0, 1.0, 0.125, 0.0, 0.1
+    p, u = ER.star_state(rl, ul, pl, rr, ur, pr, g)
+    m = (p - pr) / (u - ur)                  # m = rho (w) with w = u - S, shock frame
+    S = ur + m / rr
+    rs = m / (S - u)
+    h = lambda pp, rho, w: g / (g - 1) * pp / rho + 0.5 * w * w
+    assert h(pr, rr, ur - S) == pytest.approx(h(p, rs, u - S), rel=1e-10)
+    rls = rl * (p / pl) ** (1 / g)
+    cl, cls = math.sqrt(g * pl / rl), math.sqrt(g * p / rls)
+    assert ul + 2 * cl / (g - 1) == pytest.approx(u + 2 * cls / (g - 1), rel=1e-10)
+    # a shock to the right, a rarefaction to the left
+    assert pr < p < pl and S > u > 0 and rs > rr
 
 
 def test_sod_shock_tube_against_exact():
