@@ -153,6 +153,29 @@ def _iso_tube(n, riemann):
     return float(np.mean(np.abs(s.cons[0, 0, 0, :] - rho_ex)))
 
 
+def test_exact_isothermal_star_state_satisfies_the_jump_conditions():
+    # the exact isothermal solver used by the tube pin, on its tube
+    # (rho, u) = (1, 0) | (0.25, 0), c = 1: the star state must satisfy,
+    # with nothing stored,
+    # * across the right shock: mass fixes the shock speed S, then momentum
+    #   rho (u - S)^2 + c^2 rho is continuous;
+    # * across the left rarefaction: the invariant u + c ln(rho) holds.
+    c = 1.0
+    rl, ul, rr, ur = 1.0, 0.0, 0.25, 0.0
+    rs, us = ER.iso_star(rl, ul, rr, ur, c)
+    S = (rs * us - rr * ur) / (rs - rr)
+    mom = lambda r, u: r * (u - S) ** 2 + c * c * r
+    assert mom(rr, ur) == pytest.approx(mom(rs, us), rel=1e-12)
+    assert ul + c * math.log(rl) == pytest.approx(us + c * math.log(rs), abs=1e-12)
+    assert rr < rs < rl and S > us > 0
+    # a perturbed star density breaks the pair of conditions
+    rs2 = rs * (1 + 1e-6)
+    us2 = ul + c * math.log(rl / rs2)
+    S2 = (rs2 * us2 - rr * ur) / (rs2 - rr)
+    m2 = lambda r, u: r * (u - S2) ** 2 + c * c * r
+    assert abs(m2(rr, ur) / m2(rs2, us2) - 1) > 1e-7
+
+
 @pytest.mark.parametrize("riemann", [O.HLLD, O.HLLE])
 def test_iso_shock_tube_against_exact(riemann):
     e1, e2 = _iso_tube(128, riemann), _iso_tube(256, riemann)
