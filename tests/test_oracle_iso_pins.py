@@ -168,6 +168,13 @@ def test_exact_isothermal_star_state_satisfies_the_jump_conditions():
     assert mom(rr, ur) == pytest.approx(mom(rs, us), rel=1e-12)
     assert ul + c * math.log(rl) == pytest.approx(us + c * math.log(rs), abs=1e-12)
     assert rr < rs < rl and S > us > 0
+    # the sampled solution at t = 0.2 on [-0.5, 0.5] (every wave inside)
+    # keeps its mass, and its momentum grows by c^2 (rho_L - rho_R) t
+    n, t = 200000, 0.2
+    x = (np.arange(n) + 0.5) / n - 0.5
+    rho, u = ER.iso_sample(x, t, (rl, ul), (rr, ur), c)
+    assert np.sum(rho) / n == pytest.approx(0.5 * (rl + rr), abs=2e-5)
+    assert np.sum(rho * u) / n == pytest.approx(c * c * (rl - rr) * t, abs=2e-5)
     # a perturbed star density breaks the pair of conditions
     rs2 = rs * (1 + 1e-6)
     us2 = ul + c * math.log(rl / rs2)

@@ -405,6 +405,22 @@ def test_sod_star_state_satisfies_the_jump_conditions():
     assert pr < p < pl and S > u > 0 and rs > rr
 
 
+def test_exact_sod_solution_conserves_mass_momentum_energy():
+    # the exact solver's sampled solution at t = 0.25 on [-0.5, 0.5], where
+    # every wave stays inside: mass and energy as at t = 0, momentum grown
+    # by the pressure difference of the two constant ends, (p_L - p_R) t
+    # (midpoint rule on 2e5 cells; each discontinuity costs O(h))
+    g, t = 1.4, 0.25
+    n = 200000
+    x = (np.arange(n) + 0.5) / n - 0.5
+    rho, u, p = ER.sample(x, t, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), g)
+    h = 1.0 / n
+    assert np.sum(rho) * h == pytest.approx(0.5 * 1.0 + 0.5 * 0.125, abs=2e-5)
+    assert np.sum(rho * u) * h == pytest.approx((1.0 - 0.1) * t, abs=2e-5)
+    E = p / (g - 1) + 0.5 * rho * u * u
+    assert np.sum(E) * h == pytest.approx(0.5 / (g - 1) * (1.0 + 0.1), abs=2e-5)
+
+
 def test_sod_shock_tube_against_exact():
     errs = []
     for n in (128, 256):
