@@ -65,6 +65,7 @@ def parse(argv=None):
                     help="turb256: isothermal closure p = cs^2 rho with cs = 1 (the sound "
                          "speed of the generator) and the isothermal HLLD")
     a = ap.parse_args(argv)
+    a.argv = list(sys.argv[1:] if argv is None else argv)
     if a.steps < 1 or a.warmup < 0:
         ap.error("--steps must be >= 1 and --warmup >= 0")
     if a.prec is None:
@@ -459,22 +460,53 @@ def _host_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-def cpu_baseline(a, st_full):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload
-    (64^3 or its equivalent), stepped until ~10 s of CPU work."""
-    step, cells, what = _oracle_sample(a, SAMPLE_PROBE.get(a.workload, 64))
+def _oracle_rate(a, n, seconds):
+    """Cell-updates/s of the oracle on the workload's sample at linear size
+    n, stepped for about `seconds` after one untimed step."""
+    step, cells, what = _oracle_sample(a, n)
     t0 = time.perf_counter()
     step()
     one = time.perf_counter() - t0
-    k = max(1, min(20, int(10.0 / max(one, 1e-3))))
+    k = max(1, min(20, int(seconds / max(one, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(k):
         step()
     el = time.perf_counter() - t0
+    return {"value": cells * k / el, "steps": k, "seconds": el, "what": what}
+
+
+def single_thread_rate(a, n, seconds=5.0):
+    """The same measurement on one host thread, in a child process started
+    with OMP_NUM_THREADS=1 (the OpenMP team size is fixed per process)."""
+    code = ("import json, sys; import bench; a = bench.parse(json.loads(sys.argv[1])); "
+            "print(json.dumps(bench._oracle_rate(a, int(sys.argv[2]), float(sys.argv[3]))))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code, json.dumps(a.argv), str(n), str(seconds)],
+                       cwd=os.path.dirname(os.path.abspath(__file__)), env=env,
+                       capture_output=True, text=True, timeout=300)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(a, st_full):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload
+    (64^3 or its equivalent), stepped until ~10 s of CPU work over all host
+    threads; beside it the rate on one thread, on the half-size sample."""
+    n = SAMPLE_PROBE.get(a.workload, 64)
+    r = _oracle_rate(a, n, 10.0)
     cores = _host_threads()
-    return {"value": cells * k / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, {what}, {k} steps ({el:.1f} s), OpenMP over {cores} "
-                      f"host threads"}
+    one = single_thread_rate(a, max(8, n // 2))
+    base = {"value": r["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {r['what']}, {r['steps']} steps ({r['seconds']:.1f} s), "
+                      f"OpenMP over {cores} host threads"}
+    if "value" in one:
+        base["single_thread"] = {"value": one["value"], "unit": UNIT,
+                                 "sample": f"{one['what']}, {one['steps']} steps "
+                                           f"({one['seconds']:.1f} s), 1 thread"}
+    else:
+        base["single_thread"] = one
+    return base
 
 
 def reference_sample_size(t_probe, n_probe, steps, budget_s=150.0):

@@ -120,3 +120,8 @@ def test_reference_sample_size_keeps_the_reference_arm_within_minutes():
 def test_bench_rejects_empty_timing(argv):
     with pytest.raises(SystemExit):
         bench.parse(argv)
+
+
+def test_single_thread_oracle_rate_runs_in_a_child_process():
+    r = bench.single_thread_rate(bench.parse(["--workload", "wave32"]), 8, seconds=0.2)
+    assert r["value"] > 0 and r["steps"] >= 1 and "fast wave 8^3" in r["what"]
