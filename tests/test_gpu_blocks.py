@@ -107,7 +107,7 @@ def test_blocks_device_cfl_run_and_fp32():
     assert max(compare((c32, f1, f2, f3), ref)) < 1e-5
 
 
-def test_blocks_with_dual_energy_and_lhlld():
+def test_blocks_with_lhlld():
     n = (16, 12, 10)
     st = _box(n, 114)
     ref, dts = oracle_run(st, "plm", "rk2", nsteps=3, riemann="lhlld")
