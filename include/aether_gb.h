@@ -287,7 +287,8 @@ aeth_status aeth_selftest_wait_timeout(aeth_ctx* ctx);
  * features, 16 floats per sample, device array d_X) and the network
  * targets y = (F_HLLD - F_E) / (k J) of their HLLD fluxes (computed in
  * FP64; zero where J < 1e-9; 8 floats per sample, last one zero, d_Y).  At most
- * `capacity` samples are written; *n_out receives the count.  Synchronous. */
+ * `capacity` samples are written; *n_out receives the count.  Synchronous.
+ * AETH_ERR_UNSUPPORTED for dust runs and for contexts with linked blocks. */
 aeth_status aeth_mlp_collect(aeth_ctx* ctx, int stride, float* d_X, float* d_Y,
                              long long capacity, long long* n_out);
 

@@ -342,6 +342,10 @@ extern "C" aeth_status aeth_mlp_collect(aeth_ctx* c, int stride, float* d_X, flo
   if (!c || !d_X || !d_Y || stride < 1 || capacity < 0) return AETH_ERR_ARG;
   if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
   if (c->cfg.n_dust > 0) return fail(c, AETH_ERR_UNSUPPORTED, "no learned flux for dust runs");
+  // the sample stencils take their ghosts from a per-block fill, which
+  // knows no linked neighbour (and would rewrite a linked block's face n)
+  if (!c->links.empty())
+    return fail(c, AETH_ERR_UNSUPPORTED, "training samples come from contexts without linked blocks");
   return c->elem == 8 ? collect_T<double>(c, stride, d_X, d_Y, capacity, n_out)
                       : collect_T<float>(c, stride, d_X, d_Y, capacity, n_out);
 }
