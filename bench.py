@@ -14,6 +14,11 @@ the device), counted once per cell (zone-cycles).
 Prints ONE JSON line (rank 0).  With --gpus N > 1 (torchrun) every rank
 advances its own independent replica (weak scaling, no cross-GPU exchange
 in the step); value = all ranks' cell-updates / max time.
+
+--impl reference times the FP64 CPU oracle instead, on the host cores: W
+untimed and K timed steps of a bounded sample of the same workload (64^3 of
+its generator, smaller when K + W steps would take more than a few
+minutes); rank 0 alone runs it.
 """
 from __future__ import annotations
 
