@@ -9,6 +9,8 @@
 * Damped dusty sound wave (paper Sec. 5.9.1): the 10x10 linearisation gives
   the paper's eigenvalue -0.912 +- 5.494 i, and the oracle follows that
   eigenmode on 128 cells.
+* Pressureless Rusanov transport alone: decoupled dust carried at unit
+  speed returns after one period at second order, identically along x, y, z.
 * Constant-coefficient drag (Sec. 2.2, t_s = rho_k / K_k): a uniform
   two-fluid mixture relaxes at K (1/rho_g + 1/rho_d), at second order; the
   isothermal closure takes no drag heating and its dust CFL uses c_s.
@@ -422,3 +424,45 @@ def test_steady_dusty_shock_structure_holds_in_the_oracle():
     assert np.allclose(rd_end, g["compression"][0], rtol=1e-4)
     eg2, ed2, front2, _, _, _ = _run_dusty_shock(O.DRAG_TSTOP)
     assert eg2 > 1.5e-2 and max(ed2) > 3e-2, (eg2, ed2)
+
+
+def _decoupled_dust_advection(n, axis):
+    """L1 error after one period of a smooth dust density carried at unit
+    speed along `axis` through gas at rest, with no coupling (t_s = 1e30)."""
+    shape = [2, 2, 2]
+    shape[axis] = n
+    nx, ny, nz = shape
+    g = O.make_grid((nx, ny, nz))
+    p = O.make_params(mhd=False)
+    dp = O.make_dust_params([1e30])
+    cons = np.zeros((5, nz, ny, nx))
+    cons[0] = 1.0
+    cons[4] = 1.0 / (5 / 3 - 1)
+    x = (np.arange(n) + 0.5) / n
+    k, h = 2 * math.pi, 1.0 / n
+    prof = 1.0 + 0.2 * np.sin(k * x) * math.sin(k * h / 2) / (k * h / 2)   # cell averages
+    shp = [1, 1, 1]
+    shp[2 - axis] = n
+    dust = np.zeros((1, 4, nz, ny, nx))
+    dust[0, 0] = np.broadcast_to(prof.reshape(shp), (nz, ny, nx))
+    dust[0, 1 + axis] = dust[0, 0]
+    d0 = dust[0, 0].copy()
+    t = 0.0
+    while t < 1.0 - 1e-12:
+        dt = min(O.dust_dt(g, p, dp, cons, dust), 1.0 - t)
+        O.dust_step(g, p, dp, dt, cons, dust)
+        t += dt
+    return float(np.mean(np.abs(dust[0, 0] - d0))), float(np.max(np.abs(cons[1:4])))
+
+
+def test_decoupled_dust_advection_second_order_on_every_axis():
+    # the pressureless Rusanov transport with PLM (Sec. 2.2) on its own: a
+    # translated profile returns after one period with an error falling at
+    # second order (measured 1.87, 1.98), the same along x, y and z; the
+    # gas it does not couple to stays at rest
+    e = [_decoupled_dust_advection(n, 0) for n in (32, 64, 128)]
+    assert max(m for _, m in e) < 1e-20
+    assert math.log2(e[0][0] / e[1][0]) > 1.8 and math.log2(e[1][0] / e[2][0]) > 1.9, e
+    for axis in (1, 2):
+        a, m = _decoupled_dust_advection(32, axis)
+        assert a == pytest.approx(e[0][0], rel=1e-12) and m < 1e-20
