@@ -10,7 +10,8 @@
   the paper's eigenvalue -0.912 +- 5.494 i, and the oracle follows that
   eigenmode on 128 cells.
 * Pressureless Rusanov transport alone: decoupled dust carried at unit
-  speed returns after one period at second order, identically along x, y, z.
+  speed returns after one period at second order, identically along x, y, z;
+  converging dust forms a delta shock holding the free-flight mass.
 * Constant-coefficient drag (Sec. 2.2, t_s = rho_k / K_k): a uniform
   two-fluid mixture relaxes at K (1/rho_g + 1/rho_d), at second order; the
   isothermal closure takes no drag heating and its dust CFL uses c_s.
@@ -466,3 +467,37 @@ def test_decoupled_dust_advection_second_order_on_every_axis():
     for axis in (1, 2):
         a, m = _decoupled_dust_advection(32, axis)
         assert a == pytest.approx(e[0][0], rel=1e-12) and m < 1e-20
+
+
+def test_converging_dust_forms_the_sticky_particle_delta_shock():
+    # decoupled dust converging on x = 1/2 with v = sin(2 pi (1/2 - x)) forms
+    # a delta shock (Sec. 2.2: the diffusive Rusanov default passes through
+    # them); in free flight a particle at distance d reaches the centre at
+    # t = d / sin(2 pi d), so at t = 1/2 the mass within w of the centre is
+    # 2 d_w with d_w - sin(2 pi d_w) / 2 = w (0.767 for w = 0.05, against
+    # 0.1 at the start).  The oracle: 0.766 at 64 cells, with mass conserved
+    # and the density positive and finite.
+    from scipy.optimize import brentq
+    n = 64
+    g = O.make_grid((n, 2, 2))
+    p = O.make_params(mhd=False)
+    dp = O.make_dust_params([1e30])
+    cons = np.zeros((5, 2, 2, n))
+    cons[0] = 1.0
+    cons[4] = 1.5
+    x = (np.arange(n) + 0.5) / n
+    dust = np.zeros((1, 4, 2, 2, n))
+    dust[0, 0] = 1.0
+    dust[0, 1] = np.sin(2 * math.pi * (0.5 - x))
+    m0 = dust[0, 0].sum()
+    t = 0.0
+    while t < 0.5 - 1e-12:
+        dt = min(O.dust_dt(g, p, dp, cons, dust), 0.5 - t)
+        O.dust_step(g, p, dp, dt, cons, dust)
+        t += dt
+    assert np.isfinite(dust).all() and dust[0, 0].min() > 0
+    assert abs(dust[0, 0].sum() / m0 - 1) < 1e-13
+    w = 0.05
+    dw = brentq(lambda d: d - 0.5 * math.sin(2 * math.pi * d) - w, 0.3, 0.499)
+    frac = dust[0, 0, 0, 0][np.abs(x - 0.5) < w].sum() / n
+    assert frac == pytest.approx(2 * dw, abs=0.01), (frac, 2 * dw)
