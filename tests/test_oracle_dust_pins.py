@@ -501,3 +501,32 @@ def test_converging_dust_forms_the_sticky_particle_delta_shock():
     dw = brentq(lambda d: d - 0.5 * math.sin(2 * math.pi * d) - w, 0.3, 0.499)
     frac = dust[0, 0, 0, 0][np.abs(x - 0.5) < w].sum() / n
     assert frac == pytest.approx(2 * dw, abs=0.01), (frac, 2 * dw)
+
+
+def test_dust_floor_resets_evacuated_cells_with_zero_velocity():
+    # Sec. 2.2: cells whose dust density falls below the floor are reset to
+    # it with zero velocity.  Decoupled dust diverging from x = 1/2 empties
+    # the centre: the resets fire, no step ends below the floor, and cells
+    # left at the floor carry no momentum.
+    n, fl = 64, 0.2
+    g = O.make_grid((n, 2, 2))
+    p = O.make_params(mhd=False)
+    dp = O.make_dust_params([1e30], rho_floor_dust=fl)
+    cons = np.zeros((5, 2, 2, n))
+    cons[0] = 1.0
+    cons[4] = 1.5
+    x = (np.arange(n) + 0.5) / n
+    dust = np.zeros((1, 4, 2, 2, n))
+    dust[0, 0] = 1.0
+    dust[0, 1] = np.sin(2 * math.pi * (x - 0.5))
+    t, hits, at_floor = 0.0, 0, 0
+    while t < 0.8 - 1e-12:
+        dt = min(O.dust_dt(g, p, dp, cons, dust), 0.8 - t)
+        hits += O.dust_step(g, p, dp, dt, cons, dust)
+        t += dt
+        assert dust[0, 0].min() >= fl
+        at = dust[0, 0] == fl
+        at_floor += int(at.sum())
+        if at.any():
+            assert np.abs(dust[0, 1:][:, at]).max() < 1e-30
+    assert hits > 0 and at_floor > 0
