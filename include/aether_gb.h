@@ -117,7 +117,7 @@ typedef struct {
                          AETH_MLP_MMA_SYNC */
   double cs_iso;      /* isothermal sound speed (> 0, finite) of the
                          AETH_EOS_ISOTHERMAL_* closures; ignored otherwise */
-  int dual_energy;    /* 1: dual-energy formalism (Sec. 2.7, Bryan 1995 in the
+  int dual_energy;    /* 1: dual-energy formalism (Sec. 2.8, Bryan 1995 in the
                          entropy form): the entropy S = p / rho^(gamma-1) is
                          advected alongside the state (mass flux x S/rho of
                          the upwind side); at every stage start a cell whose
@@ -155,13 +155,20 @@ typedef struct {
  * enums/values, AETH_ERR_UNSUPPORTED for combinations not built. */
 aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out);
 
-/* Enqueue all further device work on `cuda_stream` (a cudaStream_t, e.g.
- * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */
+/* Execution backend (Sec. 3.4: the Mesh constructor names the backend a run
+ * executes on; Sec. 3.2: every kernel is launched on it).  Here the backend
+ * is one CUDA stream: enqueue all further device work on `cuda_stream` (a
+ * cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream); NULL = legacy
+ * default stream.  AETH_ERR_ARG for a NULL ctx. */
 aeth_status aeth_bind_stream(aeth_ctx* ctx, void* cuda_stream);
 
-/* Use [dev_ptr, dev_ptr + bytes) as the device arena instead of allocating.
- * Must be called before aeth_finalize; dev_ptr must be 256-byte aligned and
- * outlive the context.  Query the size with aeth_plan. */
+/* Device memory of the state (Sec. 3.3: on GPU systems the solver's arrays,
+ * ghost zones included, live in device memory).  Use [dev_ptr, dev_ptr +
+ * bytes) as the device arena instead of allocating.  Must be called before
+ * aeth_finalize; dev_ptr must be 256-byte aligned and outlive the context;
+ * the caller keeps ownership.  Query the size with aeth_plan.
+ * AETH_ERR_STATE after aeth_finalize, AETH_ERR_ARG for a misaligned
+ * pointer. */
 aeth_status aeth_bind_arena(aeth_ctx* ctx, void* dev_ptr, size_t bytes);
 
 /* Add one mesh block (Sec. 2.3; blocks may differ in size, coordinates and
@@ -186,23 +193,35 @@ aeth_status aeth_add_block(aeth_ctx* ctx, const aeth_block_desc* desc,
  * path or dust. */
 aeth_status aeth_link_blocks(aeth_ctx* ctx, int lo, int axis, int hi);
 
-/* Compute the device-memory layout; *bytes_needed receives the arena size. */
+/* Close the mesh description (Sec. 3.4: the Mesh constructor fixes the
+ * domain, resolution and block decomposition before any state exists) and
+ * compute the device-memory layout; *bytes_needed receives the arena size.
+ * Host only: no CUDA call.  AETH_ERR_STATE when no block was added. */
 aeth_status aeth_plan(aeth_ctx* ctx, size_t* bytes_needed);
 
-/* Lay out device memory (in the bound arena, else cudaMalloc) and build
- * the launch tables.  *bytes_needed (may be NULL) receives the size.
- * AETH_ERR_ARG if a bound arena is too small. */
+/* Complete the Mesh/Simulation construction of Sec. 3.4: lay out device
+ * memory (in the bound arena, else cudaMalloc) and build the launch tables
+ * of every block (Sec. 2.3).  *bytes_needed (may be NULL) receives the
+ * size.  AETH_ERR_ARG if a bound arena is too small, AETH_ERR_OOM if the
+ * allocation fails. */
 aeth_status aeth_finalize(aeth_ctx* ctx, size_t* bytes_needed);
 
-/* Copy one block's state from host FP64 arrays (layout above) to the
- * device, converting to the working precision.  Synchronous with respect
- * to the host arrays (they may be reused when the call returns). */
+/* Initial condition of one block (Sec. 3.4, the set_initial_condition!
+ * step of the problem setup): copy the conserved variables of Eq. 1 and the
+ * face-averaged field of Eq. 9 from host FP64 arrays (layout above) to the
+ * device, converting to the working precision.  The face field should come
+ * from a vector potential (Sec. 3.4) so that div B starts at round-off.
+ * Synchronous with respect to the host arrays (they may be reused when the
+ * call returns).  AETH_ERR_STATE before aeth_finalize, AETH_ERR_ARG for a
+ * bad block index or NULL cons (b1f..b3f may be NULL in hydro). */
 aeth_status aeth_set_state(aeth_ctx* ctx, int block, const double* cons,
                            const double* b1f, const double* b2f,
                            const double* b3f);
 
-/* Copy one block's state back to host FP64 arrays.  Synchronises the
- * stream; returns any latched device error. */
+/* Read the state back (Sec. 3.4: the state stays inspectable after run!
+ * returns): copy one block's conserved variables and face field to host
+ * FP64 arrays (layout above; caller-owned).  Synchronises the stream;
+ * returns any latched device error. */
 aeth_status aeth_get_state(aeth_ctx* ctx, int block, double* cons,
                            double* b1f, double* b2f, double* b3f);
 
@@ -220,17 +239,24 @@ aeth_status aeth_get_entropy(aeth_ctx* ctx, int block, double* S);
  * aeth_step(ctx, 0). */
 aeth_status aeth_compute_dt(aeth_ctx* ctx, double* dt);
 
-/* Enqueue one full step (all stages) of length dt on every block.
- * dt > 0: use it; dt == 0: use the device-resident dt of the last
- * aeth_compute_dt / aeth_run.  Asynchronous. */
+/* One cycle of the time integrator (Sec. 2.6: every stage forms the
+ * fluxes of Sec. 2.4, the CT update of Sec. 2.5 and the finite-volume
+ * update of Eq. 8, combined in the two registers of Eq. 10; the dust runs
+ * add the implicit drag of Sec. 2.2): enqueue one full step of length dt on
+ * every block.  dt > 0: use it; dt == 0: use the device-resident dt of the
+ * last aeth_compute_dt / aeth_run.  Asynchronous; device errors surface at
+ * the next synchronising call. */
 aeth_status aeth_step(aeth_ctx* ctx, double dt);
 
-/* Enqueue nsteps steps, each using the CFL step of Eq. 11 computed on the
- * device from the current state (no host round trip); the step sequence is
- * captured once into a CUDA graph and replayed.  Asynchronous. */
+/* run! of Sec. 3.4 for a fixed number of cycles: enqueue nsteps steps
+ * (Sec. 2.6), each using the CFL step of Eq. 11 computed on the device
+ * from the current state after every cycle (no host round trip); the step
+ * sequence is captured once into a CUDA graph and replayed.  Asynchronous;
+ * AETH_ERR_ARG for nsteps < 0. */
 aeth_status aeth_run(aeth_ctx* ctx, int nsteps);
 
-/* Wait for the stream; return the latched device status. */
+/* End of a run! (Sec. 3.4): wait for the stream and return the latched
+ * device status (non-finite state, strict floors, timed-out waits). */
 aeth_status aeth_sync(aeth_ctx* ctx);
 
 /* FP64 volume integrals and max relative div B over all blocks (the
@@ -364,7 +390,9 @@ aeth_status aeth_probe_fma(int precision, double* flops_per_s);
 /* Reason for the last failure on ctx (static storage inside ctx). */
 const char* aeth_last_error(const aeth_ctx* ctx);
 
-/* Release device memory the library allocated and the context itself.
+/* End of the Simulation's lifetime (Sec. 3.4: the state stays available
+ * until the caller lets it go): release device memory the library
+ * allocated and the context itself.
  * A bound arena is not freed.  NULL is ignored. */
 void aeth_destroy(aeth_ctx* ctx);
 

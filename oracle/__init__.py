@@ -140,7 +140,7 @@ def make_params(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, mhd=True,
                 rho_floor=1e-12, p_floor=1e-10, riemann=HLLD, iso=False, cs=1.0, dual=False,
                 alpha_switch=1e-3, alpha_sync=1e-1) -> Params:
     """iso=True: the isothermal closure p = cs^2 rho (gamma unused).
-    dual=True: the dual-energy formalism (Sec. 2.7); the state's cons then
+    dual=True: the dual-energy formalism (Sec. 2.8); the state's cons then
     has six variables, the sixth the entropy S (see dual_init)."""
     return Params(gamma, rho_floor, p_floor, recon, integrator, cfl, 1 if mhd else 0, riemann,
                   1 if iso else 0, cs, 1 if dual else 0, alpha_switch, alpha_sync)

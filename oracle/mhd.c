@@ -137,7 +137,7 @@ void orc_fill_ghosts(const Mesh* m, double** u, int nu, double** b) {
 /* Conserved -> primitive (Sec. 2.1, Eq. 5) with floors                 */
 /* ------------------------------------------------------------------ */
 
-/* Dual-energy selection (Sec. 2.7): the internal energy from the total,
+/* Dual-energy selection (Sec. 2.8): the internal energy from the total,
  * eint = E - kinetic - magnetic, is untrusted when it is below alpha_switch
  * times the kinetic plus magnetic energy (written as a product so that a
  * fluid at rest without field compares eint with 0). */
@@ -146,7 +146,7 @@ static int dual_use_entropy(const orc_params* p, double eint, double kin_mag) {
 }
 
 /* Dual-energy synchronisation of the interior cells of a stage state
- * (Sec. 2.7), before its ghost fill: where eint is untrusted, E is
+ * (Sec. 2.8), before its ghost fill: where eint is untrusted, E is
  * rewritten from S (eint = S rho^(gamma-1) / (gamma-1)); where eint exceeds
  * alpha_sync times the kinetic plus magnetic energy, S is resynchronised
  * from E; in between neither changes. */
@@ -203,7 +203,7 @@ static long cons_to_prim(const Mesh* m, const orc_params* p, double** u,
         if (p->iso) {
           pr = p->cs_iso * p->cs_iso * rho;
         } else if (p->dual && dual_use_entropy(p, u[4][c] - ke - me, ke + me)) {
-          /* dual energy (Sec. 2.7): the subtraction is untrusted, the
+          /* dual energy (Sec. 2.8): the subtraction is untrusted, the
            * pressure comes from the advected entropy */
           pr = u[5][c] * pow(rho, p->gamma - 1.0);
           if (pr < p->p_floor) { pr = p->p_floor; ++hits; }
@@ -747,7 +747,7 @@ static long stage(const Mesh* m, const orc_params* p, int recon, Work* wk,
           wk->e[d][0][fc] = fx[6];
           wk->e[d][1][fc] = -fx[5];
           if (p->dual) {
-            /* entropy flux (Sec. 2.7): mass flux times the specific entropy
+            /* entropy flux (Sec. 2.8): mass flux times the specific entropy
              * of the upwind side, reconstructed like the primitives */
             double s6[6], sl, sr;
             for (int t = 0; t < 6; ++t) {

@@ -51,7 +51,7 @@ typedef struct {
   int iso;            /* 1: isothermal closure p = cs_iso^2 rho (Sec. 2.1): no
                          energy equation (the energy slot is carried, unused) */
   double cs_iso;      /* isothermal sound speed */
-  int dual;           /* 1: dual-energy formalism (Sec. 2.7): the state carries a
+  int dual;           /* 1: dual-energy formalism (Sec. 2.8): the state carries a
                          sixth cell variable S = p / rho^(gamma-1) */
   double alpha_switch, alpha_sync;  /* its thresholds (1e-3, 1e-1 by default) */
 } orc_params;
@@ -62,7 +62,7 @@ typedef struct {
   long floor_hits;              /* cells where a floor was applied */
 } orc_diag;
 
-/* Dual-energy formalism (Sec. 2.7): the entropy S = p / rho^(gamma-1) of
+/* Dual-energy formalism (Sec. 2.8): the entropy S = p / rho^(gamma-1) of
  * every interior cell from its conserved state (cons[5] of a 6-variable
  * state; p from E with the floors of the cons->prim conversion). */
 void orc_dual_init(const orc_grid* g, const orc_params* p, double* cons, const double* b1,

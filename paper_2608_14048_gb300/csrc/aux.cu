@@ -447,7 +447,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // takes TPI tiles and loads all of them before using any, so each thread
 // keeps TPI independent load groups in flight.
 // DUAL: dual energy, the pressure of an untrusted internal energy comes
-// from the entropy (Sec. 2.7)
+// from the entropy (Sec. 2.8)
 template <typename R, bool P64, typename Src, bool DUAL = false>
 __global__ void __launch_bounds__(256)
     k_dt(Src S, int total, int mhd, double gamma, double rho_floor, double p_floor, int nd,

@@ -67,7 +67,7 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // `gamma` argument carries the sound speed cs, the primitive pressure is
 // cs^2 rho and is not reconstructed (the isothermal fluxes take the
 // pressure from the reconstructed density).
-// DUAL: dual energy (Sec. 2.7): the pressure of an untrusted internal energy
+// DUAL: dual energy (Sec. 2.8): the pressure of an untrusted internal energy
 // (below alpha_switch x kinetic + magnetic) comes from the entropy, and each
 // face also gets the entropy flux, its mass flux times the reconstructed
 // specific entropy S/rho of the upwind side, in scratch slot 3 + D.

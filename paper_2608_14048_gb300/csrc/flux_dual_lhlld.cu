@@ -1,4 +1,4 @@
-// Flux pass instantiations with the dual-energy formalism (Sec. 2.7):
+// Flux pass instantiations with the dual-energy formalism (Sec. 2.8):
 // LHLLD plus the upwinded entropy flux, FP64 and FP32.
 #include "flux3.cuh"
 

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) k_mirror_faces(const BlockPtrs<R>* __rest
 
 // ------------------------------------------------------------------------
 // dual-energy synchronisation of the interior cells of register `reg` at a
-// stage start, before its ghost fill (Sec. 2.7): where the internal energy
+// stage start, before its ghost fill (Sec. 2.8): where the internal energy
 // from E is below alpha_switch x (kinetic + magnetic), E is rewritten from
 // the entropy, e = S rho^(gamma-1) / (gamma-1); above alpha_sync x
 // (kinetic + magnetic), S is resynchronised from E; in between neither

@@ -1,8 +1,10 @@
 // Learned-flux network on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// A CTA holds one copy of the BF16 weights in shared memory and two
-// independent warpgroups; each warpgroup pushes pairs of 128-row tiles
-// (faces) through the 14(16) -> 128 -> 128 -> 128 -> 7(16) network:
+// A CTA holds one copy of the BF16 weights in shared memory and, by default
+// (AETH_TC_TPW = 1), four independent warpgroups of 128 threads; each
+// warpgroup pushes one 128-row tile (128 faces) at a time through the
+// 14(16) -> 128 -> 128 -> 128 -> 7(16) network, so four tiles are in flight
+// per CTA (512 TMEM columns):
 //   * operands in shared memory, no swizzle, K-major "core matrices" of
 //     8 rows x 8 BF16 (128 contiguous bytes); core matrices adjacent in K are
 //     128 B apart (leading byte offset), 8-row groups K/8 * 128 B apart
@@ -21,10 +23,12 @@
 //     (the next 32 columns in flight while the current ones are used),
 //     applies SiLU and stores the next layer's A tile (BF16) to shared
 //     memory with 16-byte, bank-conflict-free stores.
-// The two tiles of a warpgroup alternate (ping-pong): the tensor core runs
-// one tile's next layer while the warpgroup runs the other tile's SiLU, so
-// the tensor pipe and the MUFU/FP32 pipes overlap inside every warpgroup
-// rather than only across warpgroups (which drift into lockstep).
+// The tensor pipe and the MUFU/FP32 pipes overlap across the four
+// warpgroups: while one warpgroup runs its SiLU epilogue, the tensor core
+// runs another's next layer.  The alternative build AETH_TC_TPW = 2 gives
+// two warpgroups of two ping-pong tiles each (one tile's MMAs overlap the
+// same warpgroup's SiLU on the other); it measured slower than four
+// single-tile warpgroups and is kept selectable only.
 // Every mbarrier wait is bounded (probes and wall time): on time-out the
 // warpgroup stops, raises the time-out status bit, drains its MMAs (again
 // bounded) and the CTA still releases its TMEM.

@@ -269,7 +269,7 @@ inline size_t array_pitch_bytes(long long cells, int elem) {
   return ((size_t)cells * elem + 255) / 256 * 256;
 }
 
-// dual-energy formalism (Sec. 2.7) on
+// dual-energy formalism (Sec. 2.8) on
 inline bool is_dual(const aeth_ctx* c) { return c->cfg.dual_energy != 0; }
 
 // internal solver codes of the unfused face kernel, distinct from every

@@ -51,7 +51,7 @@ __device__ __forceinline__ int prim_cell_s(const Layout& L, const R* __restrict_
   return prim_cell<R, P64, MHD, ISO>(L, u, c, gm1, rho_floor, p_floor, w);
 }
 
-// Dual energy (Sec. 2.7): the primitives of cell c with the pressure from
+// Dual energy (Sec. 2.8): the primitives of cell c with the pressure from
 // the entropy S = ent[c] where the internal energy from E is below
 // alpha_switch times the kinetic plus magnetic energy, else from E; the
 // floors of Eq. 5; sp = S / rho, the specific entropy the faces

@@ -1,4 +1,4 @@
-"""GPU parity of the dual-energy formalism (Sec. 2.7): the CUDA library
+"""GPU parity of the dual-energy formalism (Sec. 2.8): the CUDA library
 through its C ABI against the pinned FP64 oracle, element by element, on
 seeded inputs with the oracle's dt sequence: the five conserved variables,
 the face fields and the advected entropy S.  Tolerances: 1e-12 relative L1

@@ -1,4 +1,4 @@
-"""Pins of the oracle's dual-energy formalism (Sec. 2.7): the entropy
+"""Pins of the oracle's dual-energy formalism (Sec. 2.8): the entropy
 S = p / rho^(gamma-1) advected as a sixth cell variable with the flux
 (mass flux) x (S/rho of the upwind side); the pressure taken from S where
 the internal energy from E is below alpha_switch times the kinetic plus

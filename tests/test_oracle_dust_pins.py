@@ -4,9 +4,9 @@
   elimination and conserves total momentum.
 * Two-fluid relaxation converges to the exact exponential at second order
   and the amplification vanishes as dt / t_s -> infinity (L-stability).
-* Forced relaxation (paper Sec. 5.9.3 set-up): the stiff run recovers the
+* Forced relaxation (paper Sec. 5.8.3 set-up): the stiff run recovers the
   terminal drift a t_s,k with a = g rho_g / rho_tot to 1e-8.
-* Damped dusty sound wave (paper Sec. 5.9.1): the 10x10 linearisation gives
+* Damped dusty sound wave (paper Sec. 5.8.1): the 10x10 linearisation gives
   the paper's eigenvalue -0.912 +- 5.494 i, and the oracle follows that
   eigenmode on 128 cells.
 * Pressureless Rusanov transport alone: decoupled dust carried at unit
@@ -15,7 +15,7 @@
 * Constant-coefficient drag (Sec. 2.2, t_s = rho_k / K_k): a uniform
   two-fluid mixture relaxes at K (1/rho_g + 1/rho_d), at second order; the
   isothermal closure takes no drag heating and its dust CFL uses c_s.
-* Steady isothermal dusty shock (paper Sec. 5.9.2): an ODE integration of
+* Steady isothermal dusty shock (paper Sec. 5.8.2): an ODE integration of
   the stationary equations (scipy, independent of the oracle) reaches the
   paper's far-downstream compression 16, and the oracle holds that
   structure; a planted drag-law mistake in the oracle fails.
@@ -330,7 +330,7 @@ def _paper_shock_values():
 
 class _SteadyDustyShock:
     """Stationary 1-D structure behind an isothermal shock carrying N dust
-    species with constant drag coefficients K_k (paper Sec. 5.9.2), reduced
+    species with constant drag coefficients K_k (paper Sec. 5.8.2), reduced
     to ODEs in x: every species keeps its mass flux j = rho v; the mixture
     keeps its momentum flux sum rho v^2 + c_s^2 rho_g; each species obeys
     j dv_k/dx = K_k (v_g - v_k); the gas speed follows from the momentum
