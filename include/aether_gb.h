@@ -369,9 +369,17 @@ aeth_status aeth_autotune(aeth_ctx* ctx, int* kchunk);
  * that loads the library keeps it until exit); larger grids are rejected
  * with AETH_ERR_ARG.  A non-finite state makes *d_dt NaN.  The first call
  * on each device looks up that device's scratch address and should happen
- * before any stream capture.  All calls share the scratch: calls that
- * overlap on the GPU race; serialise them.  Returns AETH_ERR_ARG for bad
- * sizes or pointers, AETH_ERR_CUDA if a launch fails. */
+ * before any stream capture; with CUDA's lazy module loading (the default)
+ * that first call is also when the library's device code, and with it the
+ * static array, is loaded onto the device, so it may fail with
+ * AETH_ERR_CUDA where no device memory is left: make one call at start-up,
+ * after which calls allocate nothing.  The cached address belongs to the
+ * device's primary context (the one the CUDA runtime and PyTorch use);
+ * callers that switch to another CUcontext on the same device are not
+ * supported.  All calls share the scratch: calls that overlap on the GPU
+ * (other streams or other host threads) race; serialise them.  Returns
+ * AETH_ERR_ARG for bad sizes or pointers, AETH_ERR_CUDA if a launch
+ * fails. */
 aeth_status aeth_cfl_dt_noalloc(const double* d_cons, const double* d_b1,
                                 const double* d_b2, const double* d_b3,
                                 int nx, int ny, int nz, double dx1,

@@ -10,9 +10,14 @@
 // scratch, which lives in the file-scope device array below.
 //
 // The scratch is a static __device__ array: every GPU that loads this
-// library holds it (about 2 MiB) until the process exits.  All calls share
-// it, so calls whose work overlaps on the GPU (different streams, or
-// different host threads) race on it; serialise them.
+// library's device code holds it (about 2 MiB) until the process exits.
+// With the runtime's default lazy module loading, the device code (and the
+// array) is loaded at the first kernel launch or symbol lookup on that
+// device, so the first call may need device memory; later calls need none.
+// The address cache is per device ordinal and assumes the device's primary
+// context.  All calls share the array, so calls whose work overlaps on the
+// GPU (different streams, or different host threads) race on it; serialise
+// them.
 #include <mutex>
 
 #include "runtime.hpp"

@@ -36,11 +36,19 @@ def test_noalloc_cfl_matches_context_dt_twice():
         dev = _device_state(st, torch)
         out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
         dx = [1.0 / n[0], 1.0 / n[1], 1.0 / n[2]]
+        mem = []
         for call in range(2):
+            torch.cuda.synchronize()
+            mem.append((torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]))
             A.aeth_cfl_dt_noalloc(dev[0].data_ptr(), dev[1].data_ptr(), dev[2].data_ptr(),
                                   dev[3].data_ptr(), n, dx, 5.0 / 3.0, 1e-12, 1e-10, 0.3, True,
                                   out[call].data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
+        mem.append((torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]))
+        # the second call allocates nothing: neither torch's allocator nor
+        # the device's free memory moves across it (the first call may load
+        # the library's device code, and with it the static scratch)
+        assert mem[2] == mem[1], mem
         got = out.cpu().numpy()
         assert np.all(np.abs(got - dt_ref) <= 1e-14 * dt_ref), (got, dt_ref)
 
