@@ -300,6 +300,23 @@ aeth_status aeth_load_mlp(aeth_ctx* ctx, const float* params, size_t n);
 aeth_status aeth_mlp_infer(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 aeth_status aeth_mlp_infer_tc(aeth_ctx* ctx, const float* d_X, float* d_Y, int n);
 
+/* The learned face flux on caller-given faces (no counterpart in the paper):
+ * the per-face function the flux pass applies under AETH_RIEMANN_MLP --
+ * features, the tcgen05 network, F = F_E + k J y, the acceptance checks and
+ * the HLLD fallback described at aeth_load_mlp -- on n faces given in the
+ * face frame of Sec. 2.4: d_states[n][15] = (rho, vn, vt1, vt2, p, Bt1,
+ * Bt2) left, the same right, then Bn (device FP32, caller-owned).  Writes
+ * the fluxes d_flux[n][7] = (rho, Mn, Mt1, Mt2, E, Bt1, Bt2) and
+ * d_accept[n] (1: the network's flux, 0: HLLD), both device, caller-owned;
+ * the fallbacks also count in aeth_diag.mlp_fallbacks.  Asynchronous on the
+ * bound stream.  The context must be finalized with the learned flux's
+ * configuration (FP32 or FP32_P64 adiabatic gas, its gamma, mlp_tau and
+ * MHD or hydro mode) and a loaded network; AETH_ERR_STATE otherwise,
+ * AETH_ERR_UNSUPPORTED for FP64, isothermal or dust contexts, AETH_ERR_ARG
+ * for n < 0 or NULL arrays. */
+aeth_status aeth_mlp_face_flux(aeth_ctx* ctx, const float* d_states, float* d_flux,
+                               int* d_accept, int n);
+
 /* Self-test of the bounded device waits (no counterpart in the paper): one
  * warp waits, through the wait the tcgen05 network kernels use, on an
  * mbarrier that never receives an arrival.  The wait gives up after its

@@ -18,7 +18,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["mhd.c", "dust.c", "mlp.c"]
+_SRCS = ["mhd.c", "dust.c", "mlp.c", "learned.c"]
 _LIB_PATH = os.path.join(_HERE, "liborc.so")
 _lock = threading.Lock()
 _lib = None
@@ -121,6 +121,15 @@ def lib():
                 L.orc_mlp_forward.restype = None
                 L.orc_mlp_grad.argtypes = [C.c_int, ip, dp, C.c_int, dp, dp, dp]
                 L.orc_mlp_grad.restype = C.c_double
+            if hasattr(L, "orc_learned_flux_batch"):
+                ip = C.POINTER(C.c_int)
+                L.orc_learned_flux_batch.argtypes = [C.c_double, C.c_int, dp, dp, dp, dp,
+                                                     C.c_double, C.c_int, dp, ip, dp]
+                L.orc_learned_flux_batch.restype = None
+                L.orc_learned_target.argtypes = [C.c_double, dp, dp, C.c_double, dp]
+                L.orc_learned_target.restype = None
+                L.orc_learned_features.argtypes = [C.c_double, dp, dp, C.c_double, dp, dp]
+                L.orc_learned_features.restype = None
             _lib = L
     return _lib
 
@@ -348,3 +357,40 @@ def mlp_grad(dims, params, x, target):
 
 def mlp_param_count(dims):
     return sum(dims[l + 1] * dims[l] + dims[l + 1] for l in range(len(dims) - 1))
+
+
+def learned_flux(gamma, wl, wr, bn, params, tau=0.25, mhd=True, info=False):
+    """The learned face flux (learned.c) of n face-frame states: wl, wr
+    [n][7], bn [n], the 14-128-128-128-7 network params (packed W then b per
+    layer).  Returns (flux [n][7], accepted [n] bool) and, with info=True,
+    the per-face record [n][24] (candidate F, J, k, the two margins, y)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64).reshape(-1, 7)
+    wr = np.ascontiguousarray(wr, dtype=np.float64).reshape(-1, 7)
+    bn = np.ascontiguousarray(bn, dtype=np.float64).reshape(-1)
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    n = wl.shape[0]
+    flux = np.zeros((n, 7))
+    acc = np.zeros(n, dtype=np.int32)
+    rec = np.zeros((n, 24)) if info else None
+    lib().orc_learned_flux_batch(float(gamma), n, _dp(wl), _dp(wr), _dp(bn), _dp(prm),
+                                 float(tau), 1 if mhd else 0, _dp(flux),
+                                 acc.ctypes.data_as(C.POINTER(C.c_int)),
+                                 _dp(rec) if info else None)
+    return (flux, acc.astype(bool), rec) if info else (flux, acc.astype(bool))
+
+
+def learned_target(gamma, wl, wr, bn):
+    """The network's training target y = (F_HLLD - F_E) / (k J) of one face."""
+    y = np.zeros(7)
+    lib().orc_learned_target(float(gamma), _dp(np.ascontiguousarray(wl, dtype=np.float64)),
+                             _dp(np.ascontiguousarray(wr, dtype=np.float64)), float(bn), _dp(y))
+    return y
+
+
+def learned_features(gamma, wl, wr, bn):
+    """The 14 features and the 7 flux scales k of one face."""
+    x, k = np.zeros(14), np.zeros(7)
+    lib().orc_learned_features(float(gamma), _dp(np.ascontiguousarray(wl, dtype=np.float64)),
+                               _dp(np.ascontiguousarray(wr, dtype=np.float64)), float(bn),
+                               _dp(x), _dp(k))
+    return x, k

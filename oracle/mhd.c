@@ -354,6 +354,14 @@ static void side_flux(double gamma, const double* w, double bn, double* u,
   *pt_out = pt;
 }
 
+/* The two helpers above for the other files of the oracle (learned.c). */
+double orc_fast_speed(double gamma, double rho, double p, double bn, double bt1, double bt2) {
+  return fast_speed(gamma, rho, p, bn, bt1, bt2);
+}
+void orc_side_flux(double gamma, const double* w, double bn, double* u, double* f, double* pt) {
+  side_flux(gamma, w, bn, u, f, pt);
+}
+
 /* Physical flux and conserved vector of one isothermal side (p = a2 rho),
  * face frame; the energy entries are zero. */
 static void side_flux_iso(double a2, const double* w, double bn, double* u, double* f) {

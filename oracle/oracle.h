@@ -178,6 +178,31 @@ void orc_mlp_forward(int nl, const int* dims, const double* params, int n,
 double orc_mlp_grad(int nl, const int* dims, const double* params, int n,
                     const double* x, const double* target, double* grad);
 
+/* ---- learned face flux (learned.c; no counterpart in the paper) ------ */
+/* The learned flux of one face in the face frame of orc_hlld, with the
+ * 14-128-128-128-7 network params (FP64, packed as for orc_mlp_forward):
+ * features, network, F = F_E + k J y, acceptance (tau: the fraction of the
+ * HLL dissipation bracket; positivity of the implied HLL-fan states), HLLD
+ * fallback; mhd = 0: hydro face (no induction fluxes).  Returns 1 where the
+ * network's flux is accepted, 0 where HLLD replaced it.  info (24 doubles,
+ * may be NULL): [0..6] the candidate F, [7] J, [8..14] k, [15] the
+ * bracket margin and [16] the positivity margin, both in units of the
+ * network output and positive where the check passes (the decision can
+ * only flip under a change of y larger than min(info[15], info[16]) in
+ * magnitude), [17..23] the network output y.  The batch form takes n
+ * faces (wl, wr [n][7], bn [n]) and 24 info doubles per face. */
+int orc_learned_flux(double gamma, const double* wl, const double* wr, double bn,
+                     const double* params, double tau, int mhd, double* flux, double* info);
+void orc_learned_flux_batch(double gamma, int n, const double* wl, const double* wr,
+                            const double* bn, const double* params, double tau, int mhd,
+                            double* flux, int* accepted, double* info);
+/* The network's training target of one face: y = (F_HLLD - F_E) / (k J),
+ * zero where J <= 1e-9. */
+void orc_learned_target(double gamma, const double* wl, const double* wr, double bn, double* y);
+/* The features x[14] and flux scales k[7] of one face. */
+void orc_learned_features(double gamma, const double* wl, const double* wr, double bn,
+                          double* x, double* k);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,11 @@ void orc_store(const Mesh* m, double** u, int nu, double** b, double* cons,
 
 
 
+/* Fast magnetosonic speed along the normal of a face-frame state, and the
+ * conserved vector, physical flux and total pressure of one side (mhd.c). */
+double orc_fast_speed(double gamma, double rho, double p, double bn, double bt1, double bt2);
+void orc_side_flux(double gamma, const double* w, double bn, double* u, double* f, double* pt);
+
 /* L(U) of Eq. 8 (gas, hydro or MHD) on the interior; see mhd.c. */
 long orc_rhs(const Mesh* m, const orc_params* p, int recon, double** u, double** b,
              double** out_u, double** out_b);

@@ -37,7 +37,7 @@ FUSED, UNFUSED = 0, 1
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
            "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
-           "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
+           "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_mlp_face_flux", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
            "aeth_cfl_dt_noalloc", "aeth_get_entropy", "aeth_link_blocks", "aeth_probe_fma",
            "aeth_last_error", "aeth_destroy"]
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "aeth_load_mlp": ([P, P, C.c_size_t], C.c_int),
         "aeth_mlp_infer": ([P, P, P, C.c_int], C.c_int),
         "aeth_mlp_infer_tc": ([P, P, P, C.c_int], C.c_int),
+        "aeth_mlp_face_flux": ([P, P, P, P, C.c_int], C.c_int),
         "aeth_selftest_wait_timeout": ([P], C.c_int),
         "aeth_mlp_collect": ([P, C.c_int, P, P, C.c_longlong, C.POINTER(C.c_longlong)], C.c_int),
         "aeth_mlp_work_floats": ([C.c_int, C.POINTER(C.c_size_t)], C.c_int),
@@ -285,6 +286,14 @@ def aeth_mlp_infer(ctx, d_X: int, d_Y: int, n: int):
 
 def aeth_mlp_infer_tc(ctx, d_X: int, d_Y: int, n: int):
     _check(ctx, load_library().aeth_mlp_infer_tc(ctx, C.c_void_p(d_X), C.c_void_p(d_Y), int(n)))
+
+
+def aeth_mlp_face_flux(ctx, d_states: int, d_flux: int, d_accept: int, n: int):
+    """Learned face flux (network + checks + HLLD fallback) of n face-frame
+    states d_states[n][15] into d_flux[n][7] and d_accept[n] (device
+    pointers); asynchronous on the bound stream."""
+    _check(ctx, load_library().aeth_mlp_face_flux(ctx, C.c_void_p(d_states), C.c_void_p(d_flux),
+                                                  C.c_void_p(d_accept), int(n)))
 
 
 def aeth_selftest_wait_timeout(ctx) -> int:

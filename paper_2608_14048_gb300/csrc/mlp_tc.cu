@@ -478,29 +478,21 @@ struct FaceIn {
   bool valid;
 };
 
-// Learned flux of the faces of direction D of one block (the tcgen05 twin
-// of the mma.sync flux kernel): face states from the dump arrays, network,
-// acceptance test, HLLD on rejected faces, fluxes and face EMFs into the
-// arrays of the HLLD flux pass.  A tile is 4 work units of 32 faces along
-// x; a warpgroup iteration covers two tiles.
-template <typename R, int D, int TPW>
-__global__ void __launch_bounds__(512 / TPW, 1)
-    k_mlp_flux_tc(BlockPtrs<R> P, const R* __restrict__ fs, const unsigned char* __restrict__ wimg,
-                  R gamma, R tau, int mhd, unsigned long long* fallbacks, int* status) {
-  using namespace tc;
-  constexpr int NWG = 4 / TPW;
-  extern __shared__ __align__(1024) unsigned char sm[];
-  WG<TPW> g = setup<NWG, TPW>(sm, wimg);
-  const int wg = threadIdx.x >> 7, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Layout L = P.L;
-  const long long pitch = P.pitch;
-  const int nseg = (L.n[0] + 2 + 31) / 32;
-  const long long nwork = (long long)nseg * (L.n[1] + 2) * (L.n[2] + 2);
-  const long long niter = (nwork + 4 * TPW - 1) / (4 * TPW);
-  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  unsigned long long fb = 0;
-  bool ok = true;
-  auto load = [&](long long wk, FaceIn<R>& f, float* x) -> FaceScale {
+// Face source and sink of the learned-flux kernel.  A work unit is 32
+// faces, one per lane of a warp; a 128-row tile is 4 work units.
+//
+// BlockFaces: the faces of direction D of one block in the flux pass: face
+// states from the dump arrays (32 faces along x per work unit), fluxes and
+// face EMFs into the arrays of the HLLD flux pass.
+template <typename R, int D>
+struct BlockFaces {
+  BlockPtrs<R> P;
+  long long nwork;
+  int nseg;
+  __device__ __forceinline__ void load(long long wk, int lane, FaceIn<R>& f) const {
+    const Layout& L = P.L;
+    const long long pitch = P.pitch;
+    const R* __restrict__ fs = P.fstate;
     f.valid = wk < nwork;
     const long long wkc = f.valid ? wk : 0;
     const int seg = (int)(wkc % nseg);
@@ -517,7 +509,69 @@ __global__ void __launch_bounds__(512 / TPW, 1)
         f.wr[q] = fs[(D * 15 + 7 + q) * pitch + f.fc];
       }
       f.bn = fs[(D * 15 + 14) * pitch + f.fc];
-    } else {
+    }
+  }
+  __device__ __forceinline__ void store(const FaceIn<R>& f, const R* F, bool) const {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const long long pitch = P.pitch;
+    R* sbp = P.w[0];
+    R* fl = sbp + (8 + 5 * D) * pitch + f.fc;
+    fl[0] = F[0];
+    fl[(1 + D) * pitch] = F[1];
+    fl[(1 + T1) * pitch] = F[2];
+    fl[(1 + T2) * pitch] = F[3];
+    fl[4 * pitch] = F[4];
+    R* e = sbp + (23 + 2 * D) * pitch + f.fc;
+    e[0] = F[6];
+    e[pitch] = -F[5];
+  }
+};
+
+// FlatFaces: n caller-given faces, st[n][15] = (wl 7, wr 7, bn) in the face
+// frame, fluxes into flux[n][7] and the decision into acc[n] (1: network
+// accepted, 0: HLLD fallback).
+template <typename R>
+struct FlatFaces {
+  const R* st;
+  R* flux;
+  int* acc;
+  long long n, nwork;
+  __device__ __forceinline__ void load(long long wk, int lane, FaceIn<R>& f) const {
+    const long long r = wk * 32 + lane;
+    f.valid = wk < nwork && r < n;
+    f.fc = f.valid ? r : 0;
+    if (f.valid) {
+      const R* s = st + f.fc * 15;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) { f.wl[q] = s[q]; f.wr[q] = s[7 + q]; }
+      f.bn = s[14];
+    }
+  }
+  __device__ __forceinline__ void store(const FaceIn<R>& f, const R* F, bool accepted) const {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) flux[f.fc * 7 + q] = F[q];
+    acc[f.fc] = accepted ? 1 : 0;
+  }
+};
+
+// Learned flux of the faces of one face source (the tcgen05 twin of the
+// mma.sync flux kernel): face states, network, acceptance test, HLLD on
+// rejected faces, fluxes out.  A warpgroup iteration covers TPW tiles.
+template <typename R, int TPW, typename IO>
+__global__ void __launch_bounds__(512 / TPW, 1)
+    k_mlp_flux_tc(IO io, const unsigned char* __restrict__ wimg, R gamma, R tau, int mhd,
+                  unsigned long long* fallbacks, int* status) {
+  using namespace tc;
+  constexpr int NWG = 4 / TPW;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  WG<TPW> g = setup<NWG, TPW>(sm, wimg);
+  const int wg = threadIdx.x >> 7, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long niter = (io.nwork + 4 * TPW - 1) / (4 * TPW);
+  unsigned long long fb = 0;
+  bool ok = true;
+  auto load = [&](long long wk, FaceIn<R>& f, float* x) -> FaceScale {
+    io.load(wk, lane, f);
+    if (!f.valid) {
 #pragma unroll
       for (int q = 0; q < 7; ++q) f.wl[q] = f.wr[q] = R(0);
       f.wl[0] = f.wr[0] = R(1); f.wl[4] = f.wr[4] = R(1);
@@ -530,20 +584,12 @@ __global__ void __launch_bounds__(512 / TPW, 1)
     float k7[7];
     mlp_scale_out(sc, (float)gamma, k7);
     R F[7];
-    if (!mlp_compose(gamma, f.wl, f.wr, f.bn, y, k7, tau, mhd != 0, F)) {
+    const bool accepted = mlp_compose(gamma, f.wl, f.wr, f.bn, y, k7, tau, mhd != 0, F);
+    if (!accepted) {
       hlld(gamma, f.wl, f.wr, f.bn, F);
       ++fb;
     }
-    R* sbp = P.w[0];
-    R* fl = sbp + (8 + 5 * D) * pitch + f.fc;
-    fl[0] = F[0];
-    fl[(1 + D) * pitch] = F[1];
-    fl[(1 + T1) * pitch] = F[2];
-    fl[(1 + T2) * pitch] = F[3];
-    fl[4 * pitch] = F[4];
-    R* e = sbp + (23 + 2 * D) * pitch + f.fc;
-    e[0] = F[6];
-    e[pitch] = -F[5];
+    io.store(f, F, accepted);
   };
   for (long long it = (long long)blockIdx.x * NWG + wg; it < niter; it += (long long)gridDim.x * NWG) {
     FaceIn<R> f[TPW];
@@ -583,9 +629,13 @@ void mlp_flux_pass_tc(aeth_ctx* c, int block) {
   const int mhd = is_mhd(c);
   const unsigned char* w = (const unsigned char*)c->d_mlp_tc;
   constexpr int SM = tc::smem_bytes(NWG * TPW);
-  k_mlp_flux_tc<R, 0, TPW><<<grid, NWG * 128, SM, c->stream>>>(P, P.fstate, w, g, tau, mhd, c->d_fallback, c->d_status);
-  k_mlp_flux_tc<R, 1, TPW><<<grid, NWG * 128, SM, c->stream>>>(P, P.fstate, w, g, tau, mhd, c->d_fallback, c->d_status);
-  k_mlp_flux_tc<R, 2, TPW><<<grid, NWG * 128, SM, c->stream>>>(P, P.fstate, w, g, tau, mhd, c->d_fallback, c->d_status);
+  const long long nwork = nseg * (L.n[1] + 2) * (L.n[2] + 2);
+  k_mlp_flux_tc<R, TPW><<<grid, NWG * 128, SM, c->stream>>>(
+      BlockFaces<R, 0>{P, nwork, (int)nseg}, w, g, tau, mhd, c->d_fallback, c->d_status);
+  k_mlp_flux_tc<R, TPW><<<grid, NWG * 128, SM, c->stream>>>(
+      BlockFaces<R, 1>{P, nwork, (int)nseg}, w, g, tau, mhd, c->d_fallback, c->d_status);
+  k_mlp_flux_tc<R, TPW><<<grid, NWG * 128, SM, c->stream>>>(
+      BlockFaces<R, 2>{P, nwork, (int)nseg}, w, g, tau, mhd, c->d_fallback, c->d_status);
   c->n_launch += 3;
 }
 template void mlp_flux_pass_tc<float>(aeth_ctx*, int);
@@ -639,12 +689,13 @@ aeth_status mlp_tc_prepare(aeth_ctx* c) {
   const int sb = smem_bytes(NWG * TPW);
   cudaError_t e = big_smem(k_mlp_tc, sb);
   constexpr int T32 = tpw_of<float>(), T64 = tpw_of<double>();
-  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, 0, T32>, sb);
-  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, 1, T32>, sb);
-  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, 2, T32>, sb);
-  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<double, 0, T64>, sb);
-  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<double, 1, T64>, sb);
-  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<double, 2, T64>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, T32, BlockFaces<float, 0>>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, T32, BlockFaces<float, 1>>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, T32, BlockFaces<float, 2>>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<double, T64, BlockFaces<double, 0>>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<double, T64, BlockFaces<double, 1>>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<double, T64, BlockFaces<double, 2>>, sb);
+  if (e == cudaSuccess) e = big_smem(k_mlp_flux_tc<float, T32, FlatFaces<float>>, sb);
   if (e != cudaSuccess) return fail(c, AETH_ERR_CUDA, "tcgen05 network smem attribute: %s", cudaGetErrorString(e));
   return AETH_OK;
 }
@@ -697,6 +748,30 @@ extern "C" aeth_status aeth_mlp_infer_tc(aeth_ctx* c, const float* d_X, float* d
   const int grid = (int)std::max(1LL, std::min((iters + tc::NWG - 1) / tc::NWG, (long long)c->num_sms));
   k_mlp_tc<<<grid, tc::NWG * 128, tc::smem_bytes(tc::NWG * tc::TPW), c->stream>>>(
       d_X, d_Y, n, (const unsigned char*)c->d_mlp_tc, c->d_status);
+  AETH_CK(c, cudaGetLastError());
+  c->n_launch += 1;
+  return AETH_OK;
+}
+
+extern "C" aeth_status aeth_mlp_face_flux(aeth_ctx* c, const float* d_states, float* d_flux,
+                                          int* d_accept, int n) {
+  using namespace aeth;
+  if (!c || n < 0 || (n > 0 && (!d_states || !d_flux || !d_accept))) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  if (!c->d_mlp_tc) return fail(c, AETH_ERR_STATE, "call aeth_load_mlp first");
+  if (c->cfg.precision == AETH_FP64 || is_iso(c) || c->cfg.n_dust > 0)
+    return fail(c, AETH_ERR_UNSUPPORTED, "the learned flux runs FP32 adiabatic gas only");
+  if (n == 0) return AETH_OK;
+  constexpr int TPW = tpw_of<float>();
+  constexpr int NWG = 4 / TPW;
+  const long long nwork = ((long long)n + 31) / 32;
+  const long long niter = (nwork + 4 * TPW - 1) / (4 * TPW);
+  const int grid = (int)std::max(1LL, std::min((niter + NWG - 1) / NWG, (long long)c->num_sms));
+  const float tau = (float)(c->cfg.mlp_tau > 0 ? c->cfg.mlp_tau : 0.25);
+  k_mlp_flux_tc<float, TPW><<<grid, NWG * 128, tc::smem_bytes(NWG * TPW), c->stream>>>(
+      FlatFaces<float>{d_states, d_flux, d_accept, (long long)n, nwork},
+      (const unsigned char*)c->d_mlp_tc, (float)c->cfg.gamma, tau, is_mhd(c) ? 1 : 0,
+      c->d_fallback, c->d_status);
   AETH_CK(c, cudaGetLastError());
   c->n_launch += 1;
   return AETH_OK;
