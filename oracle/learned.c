@@ -28,8 +28,10 @@
  *  7. acceptance: for every component |F_q - F_E,q| <= tau (S_R - S_L)
  *     |U_R,q - U_L,q| + 0.02 k_q (within a fraction tau of the HLL
  *     dissipation bracket around F_E), and the HLL-fan states the candidate
- *     implies, U_L - (F - F_L) / S_L where S_L < 0 and U_R - (F - F_R) / S_R
- *     where S_R > 0, keep rho > 0 and p > 0;
+ *     implies keep rho > 0 and p > 0: by the jump condition across the outer
+ *     wave at S, F - F_side = S (U* - U_side), those are U_L + (F - F_L) /
+ *     S_L where S_L < 0 and U_R + (F - F_R) / S_R where S_R > 0 (for
+ *     F = F_E both are the HLL state);
  *  8. a rejected face takes the HLLD flux of mhd.c.
  *
  * The network's training target (orc_learned_target) is the HLLD flux in the
@@ -135,7 +137,7 @@ int orc_learned_flux(double gamma, const double* wl, const double* wr, double bn
     const double* u = side == 0 ? h.ul : h.ur;
     const double* f = side == 0 ? h.fl : h.fr;
     double us[7], rho, p;
-    for (int q = 0; q < 7; ++q) us[q] = u[q] - (F[q] - f[q]) / s;
+    for (int q = 0; q < 7; ++q) us[q] = u[q] + (F[q] - f[q]) / s;
     lf_rho_p(gamma, us, bn, &rho, &p);
     if (!(rho > 0.0 && p > 0.0)) ok = 0;
     if (info && h.J > 0.0) {

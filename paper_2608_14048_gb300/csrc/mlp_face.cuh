@@ -151,16 +151,19 @@ __device__ __forceinline__ bool mlp_compose(R gamma, const R* wl, const R* wr, R
     const R tol = tau * (h.sr - h.sl) * fabs(h.ur[q] - h.ul[q]) + R(2e-2) * (R)k[q];
     if (!(fabs(F[q] - h.fe[q]) <= tol)) return false;
   }
+  // the state between the outer wave at S and the face obeys the jump
+  // condition across that wave, F - F_side = S (U* - U_side), so
+  // U* = U_side + (F - F_side) / S (for F = F_E both give the HLL state)
   if (h.sl < R(0)) {
     R us[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) us[q] = h.ul[q] - (F[q] - h.fl[q]) / h.sl;
+    for (int q = 0; q < 7; ++q) us[q] = h.ul[q] + (F[q] - h.fl[q]) / h.sl;
     if (!state_ok(gamma, us, bn)) return false;
   }
   if (h.sr > R(0)) {
     R us[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) us[q] = h.ur[q] - (F[q] - h.fr[q]) / h.sr;
+    for (int q = 0; q < 7; ++q) us[q] = h.ur[q] + (F[q] - h.fr[q]) / h.sr;
     if (!state_ok(gamma, us, bn)) return false;
   }
   return true;

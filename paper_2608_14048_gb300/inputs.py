@@ -576,3 +576,48 @@ def mlp_init_params(seed: int, dims=MLP_DIMS, bias_scale=0.0):
         parts.append(rng.normal(size=(nout, nin)) / math.sqrt(nin))
         parts.append(rng.normal(size=nout) * bias_scale)
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def face_states(n: int, seed: int, mhd=True, gamma=5.0 / 3.0, mach=2.0,
+                log_beta=(-1.0, 1.0), jumps=((0.70, 1e-3, 2e-2), (0.25, 2e-2, 0.3),
+                                              (0.05, 0.3, 1.5))):
+    """Random face-frame interface states (wl, wr [n][7], bn [n]; w = rho,
+    vn, vt1, vt2, p, Bt1, Bt2) like those of the turbulence workloads: the
+    left state has rho log-uniform in [0.3, 3], p = rho^gamma / gamma x
+    U(0.5, 2), velocity components N(0, mach / sqrt 3) in units of c_s = 1,
+    and (MHD) a field of random direction whose magnitude gives plasma beta
+    10^U(log_beta); the right state is the left one with every entry
+    perturbed by a relative jump whose size is log-uniform in one of the
+    `jumps` classes (fraction, smallest, largest): mostly smooth flow, some
+    strong gradients, a few shock-like jumps.  Density and pressure stay
+    positive; bn is shared by both sides."""
+    rng = np.random.default_rng(seed)
+    rho = np.exp(rng.uniform(np.log(0.3), np.log(3.0), n))
+    p = rho ** gamma / gamma * rng.uniform(0.5, 2.0, n)
+    v = rng.normal(size=(n, 3)) * mach / math.sqrt(3.0)
+    wl = np.zeros((n, 7))
+    wl[:, 0], wl[:, 1:4], wl[:, 4] = rho, v, p
+    bn = np.zeros(n)
+    if mhd:
+        beta = 10.0 ** rng.uniform(log_beta[0], log_beta[1], n)
+        bmag = np.sqrt(2.0 * p / beta)
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        bn = bmag * d[:, 0]
+        wl[:, 5:7] = bmag[:, None] * d[:, 1:3]
+    frac = np.array([j[0] for j in jumps])
+    cls = rng.choice(len(jumps), size=n, p=frac / frac.sum())
+    lo = np.array([j[1] for j in jumps])[cls]
+    hi = np.array([j[2] for j in jumps])[cls]
+    size = np.exp(rng.uniform(np.log(lo), np.log(hi)))
+    # scale of each entry: the density and pressure themselves, the sound
+    # speed for velocities, the field magnitude for fields
+    cs = np.sqrt(gamma * p / rho)
+    bscale = np.sqrt(bn ** 2 + wl[:, 5] ** 2 + wl[:, 6] ** 2) + 1e-300
+    scale = np.stack([rho, cs, cs, cs, p, bscale, bscale], axis=1)
+    wr = wl + size[:, None] * scale * rng.normal(size=(n, 7))
+    wr[:, 0] = np.maximum(wr[:, 0], 0.2 * wl[:, 0])
+    wr[:, 4] = np.maximum(wr[:, 4], 0.2 * wl[:, 4])
+    if not mhd:
+        wr[:, 5:7] = 0.0
+    return wl, wr, bn
