@@ -1,0 +1,222 @@
+"""The learned face flux on the GPU against its FP64 oracle, face by face,
+and what the trained network gains over the method without it.
+
+* Per-face parity: aeth_mlp_face_flux (the tcgen05 network kernel the flux
+  pass runs, fed caller-given face states) against oracle/learned.c on the
+  same FP32 face states, with the network's weights rounded to BF16 as the
+  GPU stores them.  The GPU network rounds its inputs and three hidden
+  activations to BF16 (8 significant bits, 2^-9 each) and sums in FP32:
+  a few 1e-3 of the output scale, bounded here by delta = 2e-2 of the
+  largest |y| (the bound of the network tests).  A face whose decision
+  differs must have its oracle margin (how far y may move before the
+  decision flips) within delta; every other face carries the same decision,
+  and its flux agrees within k_q (J delta + 1e-5) (the network's error
+  scaled into flux units, plus FP32 rounding of F_E or of HLLD).
+* Gain: the learned flux corrects HLLE towards HLLD, so the method without
+  the network is plain HLLE.  On a held-out Mach-4 turbulence box the
+  trained learned step's relative L1 against the FP64 HLLD oracle is below
+  plain FP32 HLLE's for every variable.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_14048_gb300 import aether as A
+from paper_2608_14048_gb300 import inputs as I
+from tests.gpu_helpers import oracle_run, rel_l1
+
+pytestmark = pytest.mark.gpu
+GAMMA = 1.0001          # the turbulence workloads' near-isothermal gas
+DIMS = list(I.MLP_DIMS)
+
+
+def _bf16(x):
+    """Round FP32 values to BF16 (nearest, ties to even), returned as FP32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def _as_stored(p):
+    """The network as the GPU holds it: every weight rounded to BF16 (the
+    hidden layers' halving is exact), biases kept (the GPU carries hidden
+    biases as a BF16 hi + lo pair and the output bias in FP32)."""
+    q = p.astype(np.float32).copy()
+    off = 0
+    for l in range(4):
+        nin, nout = DIMS[l], DIMS[l + 1]
+        q[off:off + nin * nout] = _bf16(q[off:off + nin * nout])
+        off += nin * nout + nout
+    return q.astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """A network trained by the library's own kernels on interface states
+    of an HLLD run of the Mach-4, beta-modulated turbulence generator
+    (48^3, four snapshots, HLLD targets)."""
+    import torch
+    n = 48
+    st = I.turbulence_box(n=n, seed=20260821, mach=4.0, beta_modulated=True, gamma=GAMMA)
+    cfg = A.make_config(gamma=GAMMA, precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+    cap = 3 * n ** 3 * 4
+    X = torch.zeros((cap, 16), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")
+    got = 0
+    try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        for _ in range(4):
+            got += A.aeth_mlp_collect(sv.ctx, 1, X[got:].data_ptr(), Y[got:].data_ptr(), cap - got)
+            sv.run(4)
+    finally:
+        sv.close()
+    X, Y = X[:got], Y[:got]
+    p = torch.from_numpy(I.mlp_init_params(13)).cuda()
+    m, v, g = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    batch, steps, lr = 8192, 3000, 2e-3
+    wf = A.aeth_mlp_work_floats(batch)
+    work = torch.zeros(wf, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(13)
+    s = torch.cuda.current_stream().cuda_stream
+    losses = []
+    for it in range(1, steps + 1):
+        idx = torch.randint(0, got, (batch,), device="cuda", generator=gen)
+        xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+        A.aeth_mlp_grad(p.data_ptr(), xb.data_ptr(), yb.data_ptr(), batch, g.data_ptr(),
+                        work.data_ptr(), wf, loss.data_ptr(), s)
+        lr_t = 5e-5 + 0.5 * (lr - 5e-5) * (1 + math.cos(math.pi * it / steps))
+        A.aeth_mlp_adam(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), it,
+                        lr_t, stream=s)
+        if it == 1 or it == steps:
+            torch.cuda.synchronize()
+            losses.append(loss.item())
+    print("training samples", got, "loss first/last", losses)
+    assert losses[-1] < 0.2 * losses[0]
+    return p.cpu().numpy()
+
+
+def _gpu_face_flux(params, wl, wr, bn, mhd, tau=0.25):
+    import torch
+    n = len(bn)
+    st = np.zeros((n, 15), np.float32)
+    st[:, :7], st[:, 7:14], st[:, 14] = wl, wr, bn
+    cfg = A.make_config(gamma=GAMMA, precision=A.FP32, riemann=A.MLP, mlp_tau=tau, mhd=mhd)
+    sv = A.Solver(cfg, [A.make_block((8, 8, 8))], stream=torch.cuda.current_stream())
+    try:
+        A.aeth_load_mlp(sv.ctx, params)
+        d_st = torch.from_numpy(st).cuda()
+        d_f = torch.full((max(n, 1), 7), float("nan"), dtype=torch.float32, device="cuda")
+        d_a = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+        A.aeth_mlp_face_flux(sv.ctx, d_st.data_ptr(), d_f.data_ptr(), d_a.data_ptr(), n)
+        torch.cuda.synchronize()
+        fb = sv.diagnostics()["mlp_fallbacks"]
+        return d_f.cpu().numpy()[:n].astype(np.float64), d_a.cpu().numpy()[:n], fb
+    finally:
+        sv.close()
+
+
+def _faces(n, seed, mhd):
+    wl, wr, bn = I.face_states(n, seed, mhd=mhd, gamma=GAMMA, mach=3.0)
+    # special faces: equal states (J = 0) and identical copies across a
+    # ragged tail
+    wr[:64] = wl[:64]
+    # the GPU works on FP32 states: both sides see the same FP32 numbers
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    return f32(wl), f32(wr), f32(bn)
+
+
+@pytest.mark.parametrize("mhd", [True, False])
+def test_face_flux_matches_oracle(trained, mhd):
+    n = 30000 + 77                     # not a multiple of the 128-face tile
+    wl, wr, bn = _faces(n, 31 if mhd else 32, mhd)
+    F, acc, fb = _gpu_face_flux(trained, wl, wr, bn, mhd)
+    Fo, acco, rec = O.learned_flux(GAMMA, wl, wr, bn, _as_stored(trained), tau=0.25, mhd=mhd,
+                                   info=True)
+    assert set(np.unique(acc)) <= {0, 1}
+    acc = acc.astype(bool)
+    assert fb == int((~acc).sum())     # fallbacks counted by the context
+    y = rec[:, 17:24]
+    delta = 2e-2 * np.max(np.abs(y))
+    margin = np.minimum(rec[:, 15], rec[:, 16])
+    differ = acc != acco
+    border = np.abs(margin) <= delta
+    print(f"mhd={mhd}: accepted GPU {acc.mean():.3f} oracle {acco.mean():.3f}; decisions differ "
+          f"on {differ.sum()} faces, all within the margin: {bool(np.all(border[differ]))}; "
+          f"{border.sum()} faces have a margin within delta = {delta:.3g}")
+    assert np.all(border[differ]), np.flatnonzero(differ & ~border)[:10]
+    assert 0.5 < acco.mean() < 1.0     # both branches are exercised
+    same = ~differ
+    k, J = rec[:, 8:15], rec[:, 7:8]
+    tol = np.where(acco[:, None], k * J * delta, 0.0) + 1e-5 * np.maximum(k, np.abs(Fo))
+    err = np.abs(F - Fo)
+    bad = same[:, None] & ~(err <= tol)
+    worst = np.max(np.where(same[:, None], err / tol, 0.0))
+    print(f"worst flux error / tolerance over agreeing faces: {worst:.3g}")
+    assert not bad.any(), np.argwhere(bad)[:10]
+    # equal states: J = 0, so the flux is the physical flux on both sides
+    assert np.all(acc[:64]) and np.all(acco[:64])
+
+
+def test_face_flux_rejects_bad_calls(trained):
+    import torch
+    cfg = A.make_config(gamma=GAMMA, precision=A.FP32, riemann=A.MLP)
+    sv = A.Solver(cfg, [A.make_block((8, 8, 8))], stream=torch.cuda.current_stream())
+    st = torch.ones((4, 15), dtype=torch.float32, device="cuda")
+    fl = torch.zeros((4, 7), dtype=torch.float32, device="cuda")
+    ac = torch.zeros(4, dtype=torch.int32, device="cuda")
+    try:
+        with pytest.raises(A.AethError) as e:                # no network loaded yet
+            A.aeth_mlp_face_flux(sv.ctx, st.data_ptr(), fl.data_ptr(), ac.data_ptr(), 4)
+        assert e.value.code == -7
+        A.aeth_load_mlp(sv.ctx, trained)
+        with pytest.raises(A.AethError) as e:
+            A.aeth_mlp_face_flux(sv.ctx, 0, 0, 0, 4)       # NULL arrays
+        assert e.value.code == -1
+        A.aeth_mlp_face_flux(sv.ctx, 0, 0, 0, 0)           # nothing to do
+    finally:
+        sv.close()
+
+
+def _errors(out, ref):
+    """Relative L1 per variable; face-field components against the whole
+    field's mean component norm (B_y, B_z start at zero for uniform B_x)."""
+    cons, b1, b2, b3 = out
+    errs = {nm: rel_l1(cons[v], ref.cons[v]) for v, nm in enumerate(("rho", "M1", "M2", "M3", "E"))}
+    bnorm = sum(np.mean(np.abs(x)) for x in (ref.b1, ref.b2, ref.b3)) / 3
+    for nm, a, b in (("B1f", b1, ref.b1), ("B2f", b2, ref.b2), ("B3f", b3, ref.b3)):
+        errs[nm] = float(np.mean(np.abs(a - b))) / bnorm
+    return errs
+
+
+def test_trained_network_beats_plain_hlle(trained):
+    import torch
+    n = 32
+    # held out: another seed of the generator the network was trained on
+    st = I.turbulence_box(n=n, seed=20260822, mach=4.0, beta_modulated=True, gamma=GAMMA)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)      # FP64 HLLD oracle
+
+    def run(riemann, params=None):
+        cfg = A.make_config(gamma=GAMMA, precision=A.FP32, riemann=riemann)
+        sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+        try:
+            if params is not None:
+                A.aeth_load_mlp(sv.ctx, params)
+            sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+            for dt in dts:
+                sv.step(dt)
+            return sv.get_state(0), sv.diagnostics()
+        finally:
+            sv.close()
+
+    (learned, dl), (hlle, _), (hlld, _) = run(A.MLP, trained), run(A.HLLE), run(A.HLLD)
+    el, ee, ed = _errors(learned, ref), _errors(hlle, ref), _errors(hlld, ref)
+    faces = 3 * (n + 1) * (n + 2) ** 2 * 2 * len(dts)
+    print("fallback fraction", dl["mlp_fallbacks"] / faces)
+    for nm in el:
+        print(f"{nm}: learned {el[nm]:.3e}  HLLE {ee[nm]:.3e}  FP32 HLLD {ed[nm]:.3e}")
+    assert all(el[nm] < ee[nm] for nm in el), (el, ee)
