@@ -85,8 +85,15 @@ enum { AETH_MLP_TCGEN05 = 0, AETH_MLP_MMA_SYNC = 1 };
  * middle stage updates the stage register in place) */
 enum { AETH_INT_VL2 = 0, AETH_INT_RK2 = 1, AETH_INT_IMEX2P = 2, AETH_INT_RK3 = 3 };
 /* working precision: all-FP64; FP32; FP32 with the pressure recovery of
- * Eq. 5 (E minus kinetic minus magnetic energy) evaluated in FP64 */
-enum { AETH_FP64 = 0, AETH_FP32 = 1, AETH_FP32_P64 = 2 };
+ * Eq. 5 (E minus kinetic minus magnetic energy) evaluated in FP64 in every
+ * cell; FP32 with that FP64 recovery only in the cells that need it
+ * (AETH_FP32_SEL64: where kinetic + magnetic energy exceeds p64_ratio
+ * times the internal energy, so that the FP32 subtraction would lose more
+ * than a few bits -- low plasma beta or high Mach number; every other cell
+ * takes the FP32 recovery) */
+enum { AETH_FP64 = 0, AETH_FP32 = 1, AETH_FP32_P64 = 2, AETH_FP32_SEL64 = 3 };
+/* precision of the implicit drag solve of dust runs (drag_precision) */
+enum { AETH_DRAG_FP64 = 0, AETH_DRAG_FP32 = 1, AETH_DRAG_SEL64 = 2 };
 /* coordinates (Sec. 2.3) */
 enum { AETH_COORD_CART = 0, AETH_COORD_SPH = 1 };
 /* boundary kind per axis, both sides (Sec. 2.3) */
@@ -104,13 +111,17 @@ typedef struct {
   int riemann;        /* AETH_RIEMANN_* */
   int integrator;     /* AETH_INT_* */
   double cfl;         /* Courant factor C of Eq. 11 */
-  int precision;      /* AETH_FP64 / AETH_FP32 / AETH_FP32_P64 */
+  int precision;      /* AETH_FP64 / AETH_FP32 / AETH_FP32_P64 / AETH_FP32_SEL64 */
   int path;           /* AETH_PATH_FUSED (default) or AETH_PATH_UNFUSED */
   int strict_floors;  /* 1: a floor hit latches AETH_ERR_FLOOR */
   int n_dust;         /* number of pressureless dust species (0: none) */
   const double* t_stop; /* [n_dust] constant stopping times (copied) */
-  int drag_precision; /* AETH_FP64 (default, 0): implicit drag solve in FP64;
-                         AETH_FP32: in FP32 (dust runs only) */
+  int drag_precision; /* AETH_DRAG_FP64 (default, 0): implicit drag solve in
+                         FP64; AETH_DRAG_FP32: in FP32; AETH_DRAG_SEL64: in
+                         FP64 only for the species whose implicit weight
+                         h / t_k (h = the stage's implicit step) exceeds
+                         drag_ratio, in FP32 for the others (dust runs
+                         only; AETH_FP64 and AETH_FP32 keep their values) */
   double mlp_tau;     /* learned flux: residual-check tolerance (fraction of the
                          HLL dissipation bracket); <= 0 selects 0.25 */
   int mlp_engine;     /* learned flux: AETH_MLP_TCGEN05 (default, 0) or
@@ -132,6 +143,13 @@ typedef struct {
                          and read back with aeth_get_entropy. */
   double alpha_switch; /* <= 0 selects 1e-3 */
   double alpha_sync;   /* <= 0 selects 1e-1 */
+  double p64_ratio;    /* AETH_FP32_SEL64: a cell takes the FP64 pressure
+                          recovery where (kinetic + magnetic) > p64_ratio x
+                          internal energy (its FP32 estimate); <= 0 selects
+                          4, where the FP32 subtraction's relative error,
+                          about 4 ulp x the ratio, stays below 1e-6 */
+  double drag_ratio;   /* AETH_DRAG_SEL64: species with h / t_k > drag_ratio
+                          are solved in FP64; <= 0 selects 1 */
 } aeth_config;
 
 typedef struct {
@@ -272,8 +290,11 @@ aeth_status aeth_get_dust(aeth_ctx* ctx, int block, int k, double* rho_mom);
 /* Learned Riemann flux (no counterpart in the paper, which solves every face
  * with HLLD): a 14 -> 128 -> 128 -> 128 -> 7 MLP with SiLU hidden layers.
  * Inputs: the face-frame left/right primitive states and the normal field,
- * divided by rho_L and c = max(c_f,L, c_f,R) (rho_L = 1 dropped, zero-padded
- * to 16); outputs y: the face flux as a correction of the HLLE flux F_E
+ * made dimensionless with rho_L and c = max(c_f,L, c_f,R): the left state
+ * (rho_L = 1 dropped) and Bn, then the jump dW = W_R - W_L on the same
+ * scales as d (1 + |dW|) with d = dW / |dW| (its direction at full BF16
+ * resolution whatever its size; zero for equal states); zero-padded to 16.
+ * Outputs y: the face flux as a correction of the HLLE flux F_E
  * scaled by the jump, F = F_E + k J y, with k the flux scales rho_L c,
  * rho_L c^2 (x3), rho_L c^3 gamma/(gamma-1), sqrt(rho_L) c^2 (x2) and
  * J = (S_R - S_L) (sum_q ((U_R,q - U_L,q) / k_q)^2)^(1/2) the dimensionless

@@ -13,9 +13,12 @@
  *
  *  1. scales: rho_L and c = max(c_f,L, c_f,R), the fast magnetosonic speeds
  *     along the face normal (the outer-speed estimate of the HLLD solver);
- *  2. the 14 dimensionless features: the left state without its density,
- *     the right state, and bn, each divided by its natural scale (rho_L,
- *     c, rho_L c^2 for pressures, sqrt(rho_L) c for fields);
+ *  2. the 14 dimensionless features: the left state without its density
+ *     and bn, each divided by its natural scale (c for speeds, rho_L c^2 for
+ *     pressures, sqrt(rho_L) c for fields), then the jump dW = W_R - W_L on
+ *     the same scales (density on rho_L) as d (1 + |dW|), d = dW / |dW|
+ *     (zero where the states coincide): an invertible encoding of the two
+ *     states that keeps the jump's direction whatever its size;
  *  3. the network output y (7 numbers), the MLP of mlp.c;
  *  4. the flux scales k = (rho_L c, rho_L c^2 (x3), rho_L c^3 gamma /
  *     (gamma - 1), sqrt(rho_L) c^2 (x2));
@@ -56,10 +59,15 @@ static void lf_scales(double gamma, const double* wl, const double* wr, double b
   if (x) {
     x[0] = wl[1] / sv; x[1] = wl[2] / sv; x[2] = wl[3] / sv;
     x[3] = wl[4] / sp; x[4] = wl[5] / sb; x[5] = wl[6] / sb;
-    x[6] = wr[0] / rho;
-    x[7] = wr[1] / sv; x[8] = wr[2] / sv; x[9] = wr[3] / sv;
-    x[10] = wr[4] / sp; x[11] = wr[5] / sb; x[12] = wr[6] / sb;
-    x[13] = bn / sb;
+    x[6] = bn / sb;
+    const double scale[7] = {rho, sv, sv, sv, sp, sb, sb};
+    double dw[7], m = 0.0;
+    for (int q = 0; q < 7; ++q) {
+      dw[q] = (wr[q] - wl[q]) / scale[q];
+      m += dw[q] * dw[q];
+    }
+    m = sqrt(m);
+    for (int q = 0; q < 7; ++q) x[7 + q] = m > 0.0 ? dw[q] / m * (1.0 + m) : 0.0;
   }
   k[0] = rho * c;
   k[1] = k[2] = k[3] = rho * c * c;

@@ -451,7 +451,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename R, bool P64, typename Src, bool DUAL = false>
 __global__ void __launch_bounds__(256)
     k_dt(Src S, int total, int mhd, double gamma, double rho_floor, double p_floor, int nd,
-         double cs2, double alpha_switch, double* __restrict__ partial, int* status) {
+         double cs2, double alpha_switch, float p64_ratio, double* __restrict__ partial,
+         int* status) {
   constexpr bool dual = DUAL;
   // cs2 > 0: isothermal closure p = cs2 rho, fast speed with gamma = 1
   const bool iso = cs2 > 0.0;
@@ -514,10 +515,21 @@ __global__ void __launch_bounds__(256)
         pr = eint < (R)alpha_switch * (ke + me) ? sv[q] * pow(rho, (R)(gamma - 1.0))
                                                 : (R)(gamma - 1.0) * eint;
       } else if (P64) {
-        double ke = 0.5 * ((double)a[q][1] * a[q][1] + (double)a[q][2] * a[q][2] +
-                           (double)a[q][3] * a[q][3]) / (double)rho;
-        double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
-        pr = (R)((gamma - 1.0) * ((double)a[q][4] - ke - me));
+        // FP64 subtraction in every cell, or only where the FP32 one cancels
+        bool wide = true;
+        if (p64_ratio > 0.0f) {
+          const R ke = R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          const R me = R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+          const R ei = a[q][4] - ke - me;
+          wide = ke + me > (R)p64_ratio * ei;
+          pr = (R)(gamma - 1.0) * ei;
+        }
+        if (wide) {
+          double ke = 0.5 * ((double)a[q][1] * a[q][1] + (double)a[q][2] * a[q][2] +
+                             (double)a[q][3] * a[q][3]) / (double)rho;
+          double me = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] + (double)bc[2] * bc[2]);
+          pr = (R)((gamma - 1.0) * ((double)a[q][4] - ke - me));
+        }
       } else {
         pr = (R)(gamma - 1.0) * (a[q][4] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
                                  R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
@@ -589,6 +601,8 @@ static aeth_status dt_T(aeth_ctx* c) {
     auto kernel = dual_a > 0.0 ? k_dt<R, P64, Src, true> : k_dt<R, P64, Src, false>;
     kernel<<<grid, 256, 0, c->stream>>>(src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor,
                                          c->cfg.p_floor, c->cfg.n_dust, cs2, dual_a,
+                                         c->cfg.precision == AETH_FP32_SEL64
+                                             ? (float)c->cfg.p64_ratio : 0.0f,
                                          c->d_partials, c->d_status);
   };
   if (nb == 1) {

@@ -26,6 +26,9 @@ struct Layout {
   int lnk[3][2];   // per axis, low / high side: the block whose cells lie
                    // beyond that side (its ghost cells are copied from
                    // there and the side's bc is not used), or -1
+  float p64_ratio; // FP32 states with the FP64 pressure recovery: 0 = in
+                   // every cell; > 0 = only where kinetic + magnetic energy
+                   // exceeds p64_ratio x the internal energy (FP32 estimate)
   long long sx, sy, sz;   // padded extents (sx multiple of 4)
   __host__ __device__ long long idx(int i, int j, int k) const {
     return ((long long)(k + g) * sy + (j + g)) * sx + (i + OX);

@@ -95,15 +95,23 @@ struct DustUpd {
 };
 
 // Stage combination in the working precision R, implicit drag in DT.
-template <typename R, typename DT, int NDMAX>
+// SEL (DT = double, R = float): per-species precision -- the species whose
+// implicit weight a_k = h / t_k exceeds sel_ratio are solved in FP64, the
+// others in FP32; the gas sums over species (the denominator, the momentum
+// numerators and the drag heating) accumulate in FP64.
+template <typename R, typename DT, int NDMAX, bool SEL = false>
 __global__ void __launch_bounds__(256)
     k_dust_update(Layout L, R idx1, R idx2, R idx3, DustUpd<R> A, int nd, int stage,
-                  unsigned long long* floor_hits) {
+                  unsigned long long* floor_hits, float sel_ratio = 0.0f) {
   // per-species drag constants of this stage, the same for every cell:
   // a_k = h / t_k, 1 / (1 + a_k), w_k = a_k / (1 + a_k) with h = g dt
   __shared__ DT s_ak[NDMAX], s_ia[NDMAX], s_wk[NDMAX];
+  __shared__ float f_ak[SEL ? NDMAX : 1], f_ia[SEL ? NDMAX : 1], f_wk[SEL ? NDMAX : 1];
+  __shared__ unsigned s_wide;   // SEL: bit s set = species s in FP64
   {
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (SEL && tid == 0) s_wide = 0u;
+    __syncthreads();
     if (tid < nd && tid < NDMAX) {
       const DT h = (DT)kImexG * (DT)(*A.dt);
       const DT a = h * (DT)A.inv_t_stop[tid];
@@ -111,6 +119,14 @@ __global__ void __launch_bounds__(256)
       s_ak[tid] = a;
       s_ia[tid] = ia;
       s_wk[tid] = a * ia;
+      if constexpr (SEL) {
+        const float af = (float)h * (float)A.inv_t_stop[tid];
+        const float iaf = 1.0f / (1.0f + af);
+        f_ak[tid] = af;
+        f_ia[tid] = iaf;
+        f_wk[tid] = af * iaf;
+        if (a > (DT)sel_ratio) atomicOr(&s_wide, 1u << tid);
+      }
     }
     __syncthreads();
   }
@@ -160,6 +176,52 @@ __global__ void __launch_bounds__(256)
   R gy[5], dy[NDMAX][4];
   const DT rg = gx[0];
   gy[0] = gx[0];
+  if constexpr (SEL) {
+    // per-species precision: FP64 for the stiff species (s_wide), FP32 for
+    // the rest; one FP64 division for the denominator, reciprocals of the
+    // densities in each species' own precision
+    const unsigned wide = s_wide;
+    DT den = rg;
+#pragma unroll
+    for (int s = 0; s < NDMAX; ++s) {
+      if (s >= nd) break;
+      dy[s][0] = dx[s][0];
+      if ((wide >> s) & 1u) den += (DT)dx[s][0] * s_wk[s];
+      else den += (DT)((float)dx[s][0] * f_wk[s]);
+    }
+    const DT inv_den = DT(1) / den;
+    DT dke2 = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      DT num = gx[1 + q];
+#pragma unroll
+      for (int s = 0; s < NDMAX; ++s) {
+        if (s >= nd) break;
+        if ((wide >> s) & 1u) num += s_wk[s] * (DT)dx[s][1 + q];
+        else num += (DT)(f_wk[s] * (float)dx[s][1 + q]);
+      }
+      const DT vg = num * inv_den;
+      gy[1 + q] = (R)(rg * vg);
+      const float vgf = (float)vg;
+#pragma unroll
+      for (int s = 0; s < NDMAX; ++s) {
+        if (s >= nd) break;
+        const R r = dx[s][0];
+        if ((wide >> s) & 1u) {
+          const DT rk = r, m0 = dx[s][1 + q];
+          const DT m1 = (m0 + rk * s_ak[s] * vg) * s_ia[s];
+          dy[s][1 + q] = (R)m1;
+          if (rk > DT(0)) dke2 += (m1 - m0) * (m1 + m0) / rk;
+        } else {
+          const float rk = (float)r, m0 = (float)dx[s][1 + q];
+          const float m1 = (m0 + rk * f_ak[s] * vgf) * f_ia[s];
+          dy[s][1 + q] = (R)m1;
+          if (rk > 0.0f) dke2 += (DT)((m1 - m0) * (m1 + m0) / rk);
+        }
+      }
+    }
+    gy[4] = (R)((DT)gx[4] - DT(0.5) * dke2);
+  } else {
   DT rk[NDMAX], rak[NDMAX], ir[NDMAX];
   DT den = rg;
 #pragma unroll
@@ -224,6 +286,7 @@ __global__ void __launch_bounds__(256)
   const DT dke = DT(0.5) * dke2;
   // total energy conserved: drift energy becomes gas heat
   gy[4] = (R)((DT)gx[4] - dke);
+  }
   int hits = 0;
 #pragma unroll
   for (int s = 0; s < NDMAX; ++s) {
@@ -358,8 +421,23 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
   const R i2 = (R)(B.desc.ny / (B.desc.x2max - B.desc.x2min));
   const R i3 = (R)(B.desc.nz / (B.desc.x3max - B.desc.x3min));
   dim3 grd2((L.n[0] + 31) / 32, (L.n[1] + 3) / 4, (L.n[2] + 1) / 2);
-  const bool d64 = c->cfg.drag_precision == AETH_FP64;
-  if (nd <= 8) {
+  const bool d64 = c->cfg.drag_precision == AETH_DRAG_FP64;
+  bool done = false;
+  if constexpr (sizeof(R) == 4) {
+    if (c->cfg.drag_precision == AETH_DRAG_SEL64) {
+      // per-species precision: FP64 for the species with h / t_k > drag_ratio
+      const float ratio = (float)c->cfg.drag_ratio;
+      if (nd <= 8)
+        k_dust_update<R, double, 8, true><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage,
+                                                                c->d_floor, ratio);
+      else
+        k_dust_update<R, double, 32, true><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage,
+                                                                 c->d_floor, ratio);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (nd <= 8) {
     if (d64) k_dust_update<R, double, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
     else k_dust_update<R, R, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
   } else {

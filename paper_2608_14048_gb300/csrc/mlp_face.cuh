@@ -34,12 +34,25 @@ __device__ __forceinline__ FaceScale mlp_features(const R* wl, const R* wr, R bn
   s.c = (float)fmax(cl, cr);
   s.sq = sqrtf(s.rho);
   const float ic = 1.0f / s.c, ip = 1.0f / (s.rho * s.c * s.c), ib = 1.0f / (s.sq * s.c);
+  // the left state (rho_L = 1 dropped) and the normal field
   x[0] = (float)wl[1] * ic;  x[1] = (float)wl[2] * ic;  x[2] = (float)wl[3] * ic;
   x[3] = (float)wl[4] * ip;  x[4] = (float)wl[5] * ib;  x[5] = (float)wl[6] * ib;
-  x[6] = (float)wr[0] / s.rho;
-  x[7] = (float)wr[1] * ic;  x[8] = (float)wr[2] * ic;  x[9] = (float)wr[3] * ic;
-  x[10] = (float)wr[4] * ip; x[11] = (float)wr[5] * ib; x[12] = (float)wr[6] * ib;
-  x[13] = (float)bn * ib;
+  x[6] = (float)bn * ib;
+  // the jump W_R - W_L on the same scales: its direction d = dW / |dW| at
+  // full resolution whatever the jump size (BF16 inputs would lose a jump
+  // below 2^-9 of the state if the two states came separately), with the
+  // size in the length, x = d (1 + |dW|)
+  const float sc7[7] = {1.0f / s.rho, ic, ic, ic, ip, ib, ib};
+  float dw[7], m2 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    dw[q] = (float)(wr[q] - wl[q]) * sc7[q];
+    m2 += dw[q] * dw[q];
+  }
+  const float m = sqrtf(m2);
+  const float f = m > 0.0f ? (1.0f + m) / m : 0.0f;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) x[7 + q] = dw[q] * f;
   x[14] = 0.0f; x[15] = 0.0f;
   return s;
 }

@@ -58,12 +58,12 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   if (cfg->recon < AETH_RECON_DONOR || cfg->recon > AETH_RECON_PPM5) bad = AETH_ERR_ARG;
   if (cfg->riemann < AETH_RIEMANN_HLLD || cfg->riemann > AETH_RIEMANN_LHLLD) bad = AETH_ERR_ARG;
   if (cfg->integrator < AETH_INT_VL2 || cfg->integrator > AETH_INT_RK3) bad = AETH_ERR_ARG;
-  if (cfg->precision < AETH_FP64 || cfg->precision > AETH_FP32_P64) bad = AETH_ERR_ARG;
+  if (cfg->precision < AETH_FP64 || cfg->precision > AETH_FP32_SEL64) bad = AETH_ERR_ARG;
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) bad = AETH_ERR_ARG;
   if (cfg->path != AETH_PATH_FUSED && cfg->path != AETH_PATH_UNFUSED) bad = AETH_ERR_ARG;
   if (cfg->n_dust < 0 || cfg->n_dust > 32) bad = AETH_ERR_ARG;
   if (cfg->n_dust > 0 && !cfg->t_stop) bad = AETH_ERR_ARG;
-  if (cfg->drag_precision != AETH_FP64 && cfg->drag_precision != AETH_FP32) bad = AETH_ERR_ARG;
+  if (cfg->drag_precision < AETH_DRAG_FP64 || cfg->drag_precision > AETH_DRAG_SEL64) bad = AETH_ERR_ARG;
   if (cfg->mlp_engine != AETH_MLP_TCGEN05 && cfg->mlp_engine != AETH_MLP_MMA_SYNC) bad = AETH_ERR_ARG;
   if (bad != AETH_OK) {
     delete c;
@@ -84,7 +84,8 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
   }
   if (cfg->dual_energy != 0) {
     // dual energy: adiabatic gas, fused path, FP64 or FP32, a classical solver
-    const bool ok = !iso && cfg->path == AETH_PATH_FUSED && cfg->precision != AETH_FP32_P64 &&
+    const bool ok = !iso && cfg->path == AETH_PATH_FUSED &&
+                    (cfg->precision == AETH_FP64 || cfg->precision == AETH_FP32) &&
                     cfg->riemann != AETH_RIEMANN_MLP && cfg->n_dust == 0;
     if (!ok) {
       delete c;
@@ -101,6 +102,8 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
     delete c;
     return AETH_ERR_UNSUPPORTED;   // the learned flux runs with FP32 adiabatic states, gas only
   }
+  if (cfg->precision == AETH_FP32_SEL64 && !(c->cfg.p64_ratio > 0.0)) c->cfg.p64_ratio = 4.0;
+  if (cfg->drag_precision == AETH_DRAG_SEL64 && !(c->cfg.drag_ratio > 0.0)) c->cfg.drag_ratio = 1.0;
   c->elem = cfg->precision == AETH_FP64 ? 8 : 4;
   c->g = ghost_width(cfg->recon);
   *out = c;
@@ -163,6 +166,7 @@ aeth_status aeth_add_block(aeth_ctx* c, const aeth_block_desc* d, int* id) {
   L.coord = d->coord;
   L.self = (int)c->blocks.size();
   for (int q = 0; q < 3; ++q) L.lnk[q][0] = L.lnk[q][1] = -1;
+  L.p64_ratio = c->cfg.precision == AETH_FP32_SEL64 ? (float)c->cfg.p64_ratio : 0.0f;
   L.sx = ((long long)OX + d->nx + g + 1 + 3) / 4 * 4;
   L.sy = d->ny + 2 * g + 1;
   L.sz = d->nz + 2 * g + 1;

@@ -27,10 +27,22 @@ __device__ __forceinline__ int prim_cell(const Layout& L, const ConstArr8<R>& u,
   if (ISO) {
     pr = gm1 * rho;
   } else if (P64) {
-    const double m1 = u.p[1][c], m2 = u.p[2][c], m3 = u.p[3][c];
-    const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / (double)rho;
-    const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
-    pr = (R)((double)gm1 * ((double)u.p[4][c] - ke - me));
+    // FP64 subtraction of Eq. 5 in every cell, or (p64_ratio > 0) only where
+    // the FP32 one would cancel: kinetic + magnetic > ratio x internal
+    bool wide = true;
+    if (L.p64_ratio > 0.0f) {
+      const R ke = R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3);
+      const R me = R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3);
+      const R ei = u.p[4][c] - ke - me;
+      wide = ke + me > (R)L.p64_ratio * ei;
+      pr = gm1 * ei;
+    }
+    if (wide) {
+      const double m1 = u.p[1][c], m2 = u.p[2][c], m3 = u.p[3][c];
+      const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / (double)rho;
+      const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
+      pr = (R)((double)gm1 * ((double)u.p[4][c] - ke - me));
+    }
   } else {
     pr = gm1 * (u.p[4][c] - R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3) -
                 R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3));

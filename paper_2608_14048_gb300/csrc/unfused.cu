@@ -35,10 +35,21 @@ __global__ void k_prim(Layout L, ConstArr8<R> u, Arr8<R> w, int mhd, double gamm
   if (cs2 > 0.0) {
     pr = (R)cs2 * rho;   // isothermal closure: no energy, no pressure floor
   } else if (P64) {
-    const double r = rho;
-    const double ke = 0.5 * r * ((double)v1 * v1 + (double)v2 * v2 + (double)v3 * v3);
-    const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
-    pr = (R)((gamma - 1.0) * ((double)u.p[4][c] - ke - me));
+    // FP64 subtraction in every cell, or only where the FP32 one cancels
+    bool wide = true;
+    if (L.p64_ratio > 0.0f) {
+      const R ke = R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3);
+      const R me = R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3);
+      const R ei = u.p[4][c] - ke - me;
+      wide = ke + me > (R)L.p64_ratio * ei;
+      pr = (R)(gamma - 1.0) * ei;
+    }
+    if (wide) {
+      const double r = rho;
+      const double ke = 0.5 * r * ((double)v1 * v1 + (double)v2 * v2 + (double)v3 * v3);
+      const double me = 0.5 * ((double)b1 * b1 + (double)b2 * b2 + (double)b3 * b3);
+      pr = (R)((gamma - 1.0) * ((double)u.p[4][c] - ke - me));
+    }
   } else {
     const R ke = R(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3);
     const R me = R(0.5) * (b1 * b1 + b2 * b2 + b3 * b3);

@@ -370,10 +370,11 @@ def solenoidal_gaussian_velocity(n: int, seed: int, kmin=2.0, kmax=8.0, slope=-2
 
 
 def turbulence_box(n=256, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001,
-                   beta_modulated=False) -> InitialState:
+                   beta_modulated=False, log_beta=(-1.0, 1.0)) -> InitialState:
     """Decaying MHD turbulence: rho = 1, P = 1/gamma (c_s = 1), uniform B_x
-    with plasma beta (or beta varying with y as log10 beta = sin(2 pi y) when
-    beta_modulated), solenoidal Gaussian velocity, rms Mach `mach`."""
+    with plasma beta (or, when beta_modulated, beta varying with y as
+    log10 beta = m + a sin(2 pi y) spanning log_beta = (m - a, m + a), by
+    default 0.1 .. 10), solenoidal Gaussian velocity, rms Mach `mach`."""
     b = Block((n, n, n))
     v = solenoidal_gaussian_velocity(n, seed)
     v = [q * mach for q in v]
@@ -383,7 +384,8 @@ def turbulence_box(n=256, seed=20260816, mach=2.0, beta=1.0, gamma=1.0001,
     nx = ny = nz = n
     if beta_modulated:
         yc = b.centers(1)
-        bx_row = np.sqrt(2 * p0 / 10.0 ** np.sin(2 * math.pi * yc))   # depends on y only
+        m, a = 0.5 * (log_beta[0] + log_beta[1]), 0.5 * (log_beta[1] - log_beta[0])
+        bx_row = np.sqrt(2 * p0 / 10.0 ** (m + a * np.sin(2 * math.pi * yc)))   # y only
         b1 = np.broadcast_to(bx_row[None, :, None], (nz, ny, nx + 1)).copy()
     else:
         b1 = np.full((nz, ny, nx + 1), math.sqrt(2 * p0 / beta))

@@ -29,6 +29,10 @@ from tests.gpu_helpers import oracle_run, rel_l1
 
 pytestmark = pytest.mark.gpu
 GAMMA = 1.0001          # the turbulence workloads' near-isothermal gas
+# the FP32 path computes with gamma rounded to FP32 (1.0001 -> 1 + 1.00017e-4:
+# the internal energy p / (gamma - 1) then differs by 1.7e-4 relative), so
+# the oracle takes that same number for the per-face comparison
+GAMMA32 = float(np.float32(GAMMA))
 DIMS = list(I.MLP_DIMS)
 
 
@@ -135,7 +139,7 @@ def test_face_flux_matches_oracle(trained, mhd):
     n = 30000 + 77                     # not a multiple of the 128-face tile
     wl, wr, bn = _faces(n, 31 if mhd else 32, mhd)
     F, acc, fb = _gpu_face_flux(trained, wl, wr, bn, mhd)
-    Fo, acco, rec = O.learned_flux(GAMMA, wl, wr, bn, _as_stored(trained), tau=0.25, mhd=mhd,
+    Fo, acco, rec = O.learned_flux(GAMMA32, wl, wr, bn, _as_stored(trained), tau=0.25, mhd=mhd,
                                    info=True)
     assert set(np.unique(acc)) <= {0, 1}
     acc = acc.astype(bool)

@@ -1,0 +1,157 @@
+"""FP64 only where the arithmetic needs it: the selective precision modes.
+
+* AETH_FP32_SEL64 takes the FP64 pressure recovery of Eq. 5 only in cells
+  whose kinetic + magnetic energy exceeds p64_ratio (4) times the internal
+  energy.  Parity with the FP64 oracle at the FP32 bound (1e-5) on a box
+  whose plasma beta spans 0.03 .. 10 (cells on both sides of the ratio);
+  where every cell exceeds the ratio it is the all-cell FP64 recovery bit
+  for bit; and a per-cell selection it is: the selective run differs from
+  both global modes on the mixed box.
+* AETH_DRAG_SEL64 solves the implicit drag (Sec. 2.2) in FP64 only for the
+  species whose implicit weight h / t_k exceeds drag_ratio (1).  Parity at
+  1e-5 on eight species with stopping times down to 1e-6; the drift
+  velocity v_k - v_g of the stiffest species -- the quantity the FP32 solve
+  degrades, (1 + h / t_k) times the rounding of v_k -- matches the
+  all-FP64 solve's accuracy, where FP32 drag is worse.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_14048_gb300 import aether as A
+from paper_2608_14048_gb300 import inputs as I
+from tests.gpu_helpers import compare, oracle_run, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(st, dts, prec, n):
+    import torch
+    cfg = A.make_config(gamma=st.gamma, recon=A.PLM, precision=prec)
+    sv = A.Solver(cfg, [A.make_block((n, n, n))], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        for dt in dts:
+            sv.step(dt)
+        return sv.get_state(0), sv.diagnostics()
+    finally:
+        sv.close()
+
+
+def _pressure(c, b1, b2, b3, g):
+    e = c[4] - 0.5 * (c[1] ** 2 + c[2] ** 2 + c[3] ** 2) / c[0]
+    e = e - 0.5 * ((0.5 * (b1[..., :-1] + b1[..., 1:])) ** 2
+                   + (0.5 * (b2[..., :-1, :] + b2[..., 1:, :])) ** 2
+                   + (0.5 * (b3[:-1] + b3[1:])) ** 2)
+    return (g - 1.0) * e
+
+
+def _errors(out, ref, g):
+    e = compare(out, ref)
+    # face fields against the whole field's norm (B_y, B_z start at zero)
+    bnorm = sum(np.mean(np.abs(x)) for x in (ref.b1, ref.b2, ref.b3)) / 3
+    e[5:] = [float(np.mean(np.abs(a - b))) / bnorm
+             for a, b in ((out[1], ref.b1), (out[2], ref.b2), (out[3], ref.b3))]
+    p = rel_l1(_pressure(*out, g), _pressure(ref.cons, ref.b1, ref.b2, ref.b3, g))
+    return e, p
+
+
+def test_selective_pressure_recovery_parity_mixed_beta():
+    n = 32
+    st = I.turbulence_box(n=n, seed=20260816, mach=1.0, gamma=5.0 / 3.0, beta_modulated=True,
+                          log_beta=(-1.5, 1.0))
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=8)
+    out = {}
+    for nm, prec in (("fp32", A.FP32), ("sel", A.FP32_SEL64), ("all", A.FP32_P64)):
+        out[nm], diag = _run(st, dts, prec, n)
+        e, p = _errors(out[nm], ref, st.gamma)
+        print(nm, "max L1", max(e), "p L1", p, "floors", diag["floor_hits"])
+        assert diag["floor_hits"] == 0
+        assert max(e) < 1e-5 and p < 1e-5, (nm, e, p)
+    # a per-cell choice: neither all-FP32 nor all-FP64 recovery
+    assert not np.array_equal(out["sel"][0], out["fp32"][0])
+    assert not np.array_equal(out["sel"][0], out["all"][0])
+
+
+def test_selective_pressure_recovery_is_the_fp64_one_where_every_cell_needs_it():
+    # beta = 0.02 everywhere: magnetic / internal = (1 / beta) (gamma - 1) = 33 > 4
+    n = 24
+    st = I.turbulence_box(n=n, seed=11, mach=0.5, gamma=5.0 / 3.0, beta=0.02)
+    ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)
+    sel, _ = _run(st, dts, A.FP32_SEL64, n)
+    glob, _ = _run(st, dts, A.FP32_P64, n)
+    for a, b in zip(sel, glob):
+        assert np.array_equal(a, b)
+    e, p = _errors(sel, ref, st.gamma)
+    assert max(e) < 1e-5, e
+
+
+def test_selective_pressure_rejected_with_dual_energy():
+    import torch
+    cfg = A.make_config(precision=A.FP32_SEL64, dual=True)
+    with pytest.raises(A.AethError) as e:
+        A.Solver(cfg, [A.make_block((8, 8, 8))], stream=torch.cuda.current_stream())
+    assert e.value.code == -8
+
+
+def _dust_case(ts_min, nsteps=5, n=24):
+    ts = list(np.logspace(np.log10(ts_min), 0.0, 8))
+    gas, dust, ts = I.dust_box(I.Block((n, n, n)), 81, nd=8, t_stop=ts)
+    b = gas.block
+    g = O.make_grid(b.n, b.lo, b.hi, b.coord, b.bc)
+    p = O.make_params(gamma=gas.gamma, recon=O.PLM, mhd=False)
+    dp = O.make_dust_params(ts)
+    rc, rd = gas.cons.copy(), dust.copy()
+    dts = []
+    for _ in range(nsteps):
+        dt = O.dust_dt(g, p, dp, rc, rd)
+        O.dust_step(g, p, dp, dt, rc, rd)
+        dts.append(dt)
+    return gas, dust, ts, dts, rc, rd
+
+
+def _dust_gpu(gas, dust, ts, dts, drag):
+    import torch
+    b = gas.block
+    cfg = A.make_config(gamma=gas.gamma, recon=A.PLM, integrator=A.IMEX2P, precision=A.FP32,
+                        mhd=False, t_stop=ts, drag_precision=drag)
+    sv = A.Solver(cfg, [A.make_block(b.n, b.lo, b.hi, b.coord, b.bc)],
+                  stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, gas.cons)
+        for k in range(len(ts)):
+            A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]))
+        for dt in dts:
+            sv.step(dt)
+        cons = sv.get_state(0)[0]
+        d = np.empty_like(dust)
+        for k in range(len(ts)):
+            buf = np.empty(dust.shape[1:])
+            A.aeth_get_dust(sv.ctx, 0, k, buf)
+            d[k] = buf
+    finally:
+        sv.close()
+    return cons, d
+
+
+def _drift_error(cons, d, rc, rd, k):
+    ref = rd[k, 1:4] / rd[k, 0] - rc[1:4] / rc[0]
+    got = d[k, 1:4] / d[k, 0] - cons[1:4] / cons[0]
+    return float(np.sum(np.abs(got - ref)) / np.sum(np.abs(ref)))
+
+
+@pytest.mark.parametrize("ts_min", [1e-4, 1e-6])
+def test_selective_drag_parity_and_stiff_drift(ts_min):
+    gas, dust, ts, dts, rc, rd = _dust_case(ts_min)
+    res = {}
+    for nm, drag in (("fp32", A.DRAG_FP32), ("sel", A.DRAG_SEL64), ("fp64", A.DRAG_FP64)):
+        cons, d = _dust_gpu(gas, dust, ts, dts, drag)
+        errs = [rel_l1(cons[v], rc[v]) for v in range(5)]
+        errs += [rel_l1(d[k, q], rd[k, q]) for k in range(8) for q in range(4)]
+        res[nm] = (max(errs), _drift_error(cons, d, rc, rd, 0))
+        print(nm, "max L1", res[nm][0], "stiffest drift L1", res[nm][1])
+        assert max(errs) < 1e-5, (nm, errs)
+    # the stiffest species (h / t_k ~ 70 and ~ 7000) has the all-FP64
+    # solve's drift accuracy under the selective solve; FP32 is worse
+    assert res["sel"][1] <= 1.1 * res["fp64"][1], res
+    assert res["fp32"][1] >= 1.3 * res["fp64"][1], res

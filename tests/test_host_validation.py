@@ -48,12 +48,12 @@ def _cfg(**kw):
     dict(raw=dict(recon=4)),
     dict(raw=dict(riemann=4)),
     dict(raw=dict(integrator=4)),
-    dict(raw=dict(precision=3)),
+    dict(raw=dict(precision=4)),
     dict(cfl=0.0),
     dict(cfl=1.5),
     dict(cfl=float("nan")),
     dict(raw=dict(path=2)),
-    dict(raw=dict(drag_precision=2)),
+    dict(raw=dict(drag_precision=3)),
     dict(raw=dict(mlp_engine=2)),
     dict(raw=dict(n_dust=33)),
     dict(raw=dict(n_dust=2)),                              # no stopping times given
