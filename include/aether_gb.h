@@ -94,6 +94,10 @@ enum { AETH_INT_VL2 = 0, AETH_INT_RK2 = 1, AETH_INT_IMEX2P = 2, AETH_INT_RK3 = 3
 enum { AETH_FP64 = 0, AETH_FP32 = 1, AETH_FP32_P64 = 2, AETH_FP32_SEL64 = 3 };
 /* precision of the implicit drag solve of dust runs (drag_precision) */
 enum { AETH_DRAG_FP64 = 0, AETH_DRAG_FP32 = 1, AETH_DRAG_SEL64 = 2 };
+/* drag law of dust runs (Sec. 2.2): constant stopping times t_k, or constant
+ * drag coefficients K_k with t_k = rho_k / K_k (the law of the paper's
+ * steady dusty shock, Sec. 5.8.2) */
+enum { AETH_DRAG_LAW_TSTOP = 0, AETH_DRAG_LAW_COEFF = 1 };
 /* coordinates (Sec. 2.3) */
 enum { AETH_COORD_CART = 0, AETH_COORD_SPH = 1 };
 /* boundary kind per axis, both sides (Sec. 2.3) */
@@ -114,8 +118,11 @@ typedef struct {
   int precision;      /* AETH_FP64 / AETH_FP32 / AETH_FP32_P64 / AETH_FP32_SEL64 */
   int path;           /* AETH_PATH_FUSED (default) or AETH_PATH_UNFUSED */
   int strict_floors;  /* 1: a floor hit latches AETH_ERR_FLOOR */
-  int n_dust;         /* number of pressureless dust species (0: none) */
-  const double* t_stop; /* [n_dust] constant stopping times (copied) */
+  int n_dust;         /* number of pressureless dust species (0: none); the
+                         gas is adiabatic or isothermal hydro, IMEX2P */
+  const double* t_stop; /* [n_dust] constant stopping times t_k, or with
+                           drag_law = AETH_DRAG_LAW_COEFF the drag
+                           coefficients K_k (copied; each > 0) */
   int drag_precision; /* AETH_DRAG_FP64 (default, 0): implicit drag solve in
                          FP64; AETH_DRAG_FP32: in FP32; AETH_DRAG_SEL64: in
                          FP64 only for the species whose implicit weight
@@ -150,6 +157,10 @@ typedef struct {
                           about 4 ulp x the ratio, stays below 1e-6 */
   double drag_ratio;   /* AETH_DRAG_SEL64: species with h / t_k > drag_ratio
                           are solved in FP64; <= 0 selects 1 */
+  int drag_law;        /* AETH_DRAG_LAW_TSTOP (default, 0) or
+                          AETH_DRAG_LAW_COEFF; the latter takes a_k =
+                          h K_k / rho_k per cell (a species with rho_k <= 0
+                          feels no drag) and not AETH_DRAG_SEL64 */
 } aeth_config;
 
 typedef struct {

@@ -30,6 +30,7 @@ TCGEN05, MMA_SYNC = 0, 1          # tensor-core engine of the learned flux
 VL2, RK2, IMEX2P, RK3 = 0, 1, 2, 3
 FP64, FP32, FP32_P64, FP32_SEL64 = 0, 1, 2, 3
 DRAG_FP64, DRAG_FP32, DRAG_SEL64 = 0, 1, 2      # drag_precision
+DRAG_TSTOP, DRAG_COEFF = 0, 1                    # drag_law
 CART, SPH = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 FUSED, UNFUSED = 0, 1
@@ -59,7 +60,7 @@ class aeth_config(C.Structure):
                 ("mlp_tau", C.c_double), ("mlp_engine", C.c_int), ("cs_iso", C.c_double),
                 ("dual_energy", C.c_int), ("alpha_switch", C.c_double),
                 ("alpha_sync", C.c_double), ("p64_ratio", C.c_double),
-                ("drag_ratio", C.c_double)]
+                ("drag_ratio", C.c_double), ("drag_law", C.c_int)]
 
 
 class aeth_block_desc(C.Structure):
@@ -390,7 +391,7 @@ def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=F
                 path=FUSED, rho_floor=1e-12, p_floor=1e-10, strict_floors=0, t_stop=None,
                 riemann=HLLD, drag_precision=FP64, mlp_tau=0.0, mlp_engine=TCGEN05, iso=False,
                 cs=1.0, dual=False, alpha_switch=0.0, alpha_sync=0.0, p64_ratio=0.0,
-                drag_ratio=0.0):
+                drag_ratio=0.0, drag_law=0):
     """iso=True selects the isothermal closure p = cs^2 rho (gamma unused);
     dual=True the dual-energy formalism (alpha_* <= 0: the defaults);
     p64_ratio / drag_ratio: thresholds of FP32_SEL64 / DRAG_SEL64 (<= 0: the
@@ -403,7 +404,7 @@ def make_config(gamma=5.0 / 3.0, recon=PLM, integrator=VL2, cfl=0.3, precision=F
     cfg.cs_iso = cs
     cfg.dual_energy = 1 if dual else 0
     cfg.alpha_switch, cfg.alpha_sync = alpha_switch, alpha_sync
-    cfg.p64_ratio, cfg.drag_ratio = p64_ratio, drag_ratio
+    cfg.p64_ratio, cfg.drag_ratio, cfg.drag_law = p64_ratio, drag_ratio, drag_law
     cfg.gamma, cfg.rho_floor, cfg.p_floor = gamma, rho_floor, p_floor
     cfg.recon, cfg.riemann, cfg.integrator, cfg.cfl = recon, riemann, integrator, cfl
     cfg.precision, cfg.path, cfg.strict_floors = precision, path, strict_floors

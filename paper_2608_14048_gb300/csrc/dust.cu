@@ -89,7 +89,8 @@ struct DustUpd {
   R* da;               // dust register A (base)
   R* db;               // dust register B (base)
   const R* df;         // dust fluxes (base)
-  double inv_t_stop[32];   // 1 / t_stop
+  double drag_c[32];   // per species: 1 / t_k (constant stopping time) or
+                       // K_k (constant coefficient, t_k = rho_k / K_k)
   const double* dt;
   R dfloor;
 };
@@ -99,10 +100,13 @@ struct DustUpd {
 // implicit weight a_k = h / t_k exceeds sel_ratio are solved in FP64, the
 // others in FP32; the gas sums over species (the denominator, the momentum
 // numerators and the drag heating) accumulate in FP64.
-template <typename R, typename DT, int NDMAX, bool SEL = false>
+// COEFF: the constant-coefficient drag law (drag_c = K_k, a_k = h K_k /
+// rho_k per cell).  iso: isothermal gas, whose energy slot takes no drag
+// heating.
+template <typename R, typename DT, int NDMAX, bool SEL = false, bool COEFF = false>
 __global__ void __launch_bounds__(256)
     k_dust_update(Layout L, R idx1, R idx2, R idx3, DustUpd<R> A, int nd, int stage,
-                  unsigned long long* floor_hits, float sel_ratio = 0.0f) {
+                  unsigned long long* floor_hits, float sel_ratio, int iso) {
   // per-species drag constants of this stage, the same for every cell:
   // a_k = h / t_k, 1 / (1 + a_k), w_k = a_k / (1 + a_k) with h = g dt
   __shared__ DT s_ak[NDMAX], s_ia[NDMAX], s_wk[NDMAX];
@@ -114,13 +118,13 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (tid < nd && tid < NDMAX) {
       const DT h = (DT)kImexG * (DT)(*A.dt);
-      const DT a = h * (DT)A.inv_t_stop[tid];
+      const DT a = h * (DT)A.drag_c[tid];
       const DT ia = DT(1) / (DT(1) + a);
       s_ak[tid] = a;
       s_ia[tid] = ia;
       s_wk[tid] = a * ia;
       if constexpr (SEL) {
-        const float af = (float)h * (float)A.inv_t_stop[tid];
+        const float af = (float)h * (float)A.drag_c[tid];
         const float iaf = 1.0f / (1.0f + af);
         f_ak[tid] = af;
         f_ia[tid] = iaf;
@@ -176,7 +180,46 @@ __global__ void __launch_bounds__(256)
   R gy[5], dy[NDMAX][4];
   const DT rg = gx[0];
   gy[0] = gx[0];
-  if constexpr (SEL) {
+  if constexpr (COEFF) {
+    // constant-coefficient law (Sec. 2.2): t_k = rho_k / K_k with the
+    // stage's dust density, which the drag leaves unchanged, so the weight
+    // a_k = h K_k / rho_k is fixed per cell through the solve; a species
+    // with no density (rho_k <= 0) feels no drag
+    const DT h = (DT)kImexG * (DT)(*A.dt);
+    DT rk[NDMAX], ak[NDMAX], ia[NDMAX];
+    DT den = rg;
+#pragma unroll
+    for (int s = 0; s < NDMAX; ++s) {
+      if (s >= nd) break;
+      rk[s] = dx[s][0];
+      ak[s] = rk[s] > DT(0) ? h * (DT)A.drag_c[s] / rk[s] : DT(0);
+      ia[s] = DT(1) / (DT(1) + ak[s]);
+      den += rk[s] * ak[s] * ia[s];
+      dy[s][0] = dx[s][0];
+    }
+    const DT inv_den = DT(1) / den;
+    DT dke2 = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      DT num = gx[1 + q];
+#pragma unroll
+      for (int s = 0; s < NDMAX; ++s) {
+        if (s >= nd) break;
+        num += ak[s] * ia[s] * (DT)dx[s][1 + q];
+      }
+      const DT vg = num * inv_den;
+      gy[1 + q] = (R)(rg * vg);
+#pragma unroll
+      for (int s = 0; s < NDMAX; ++s) {
+        if (s >= nd) break;
+        const DT m0 = dx[s][1 + q];
+        const DT m1 = (m0 + rk[s] * ak[s] * vg) * ia[s];
+        dy[s][1 + q] = (R)m1;
+        if (rk[s] > DT(0)) dke2 += (m1 - m0) * (m1 + m0) / rk[s];
+      }
+    }
+    gy[4] = iso ? gx[4] : (R)((DT)gx[4] - DT(0.5) * dke2);
+  } else if constexpr (SEL) {
     // per-species precision: FP64 for the stiff species (s_wide), FP32 for
     // the rest; one FP64 division for the denominator, reciprocals of the
     // densities in each species' own precision
@@ -220,7 +263,7 @@ __global__ void __launch_bounds__(256)
         }
       }
     }
-    gy[4] = (R)((DT)gx[4] - DT(0.5) * dke2);
+    gy[4] = iso ? gx[4] : (R)((DT)gx[4] - DT(0.5) * dke2);
   } else {
   DT rk[NDMAX], rak[NDMAX], ir[NDMAX];
   DT den = rg;
@@ -284,8 +327,9 @@ __global__ void __launch_bounds__(256)
     }
   }
   const DT dke = DT(0.5) * dke2;
-  // total energy conserved: drift energy becomes gas heat
-  gy[4] = (R)((DT)gx[4] - dke);
+  // total energy conserved: drift energy becomes gas heat (the isothermal
+  // closure carries its energy slot unchanged)
+  gy[4] = iso ? gx[4] : (R)((DT)gx[4] - dke);
   }
   int hits = 0;
 #pragma unroll
@@ -413,7 +457,8 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
   u.da = P.dust[0];
   u.db = P.dust[1];
   u.df = P.dflux;
-  for (int q = 0; q < nd; ++q) u.inv_t_stop[q] = 1.0 / c->t_stop[q];
+  const bool coeff = c->cfg.drag_law == AETH_DRAG_LAW_COEFF;
+  for (int q = 0; q < nd; ++q) u.drag_c[q] = coeff ? c->t_stop[q] : 1.0 / c->t_stop[q];
   u.dt = c->d_dt;
   u.dfloor = dfl;
   // inverse cell widths (Cartesian: area / volume = 1 / dx_d)
@@ -422,27 +467,30 @@ static void stage_dust(aeth_ctx* c, int b, int src, int stage) {
   const R i3 = (R)(B.desc.nz / (B.desc.x3max - B.desc.x3min));
   dim3 grd2((L.n[0] + 31) / 32, (L.n[1] + 3) / 4, (L.n[2] + 1) / 2);
   const bool d64 = c->cfg.drag_precision == AETH_DRAG_FP64;
+  const int iso = is_iso(c) ? 1 : 0;
+  const float ratio = (float)c->cfg.drag_ratio;
+  auto launch = [&](auto kernel) {
+    kernel<<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor, ratio, iso);
+  };
   bool done = false;
   if constexpr (sizeof(R) == 4) {
     if (c->cfg.drag_precision == AETH_DRAG_SEL64) {
       // per-species precision: FP64 for the species with h / t_k > drag_ratio
-      const float ratio = (float)c->cfg.drag_ratio;
-      if (nd <= 8)
-        k_dust_update<R, double, 8, true><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage,
-                                                                c->d_floor, ratio);
-      else
-        k_dust_update<R, double, 32, true><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage,
-                                                                 c->d_floor, ratio);
+      if (nd <= 8) launch(k_dust_update<R, double, 8, true>);
+      else launch(k_dust_update<R, double, 32, true>);
       done = true;
     }
   }
   if (done) {
+  } else if (coeff) {
+    if (nd <= 8) d64 ? launch(k_dust_update<R, double, 8, false, true>)
+                     : launch(k_dust_update<R, R, 8, false, true>);
+    else d64 ? launch(k_dust_update<R, double, 32, false, true>)
+             : launch(k_dust_update<R, R, 32, false, true>);
   } else if (nd <= 8) {
-    if (d64) k_dust_update<R, double, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
-    else k_dust_update<R, R, 8><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+    d64 ? launch(k_dust_update<R, double, 8>) : launch(k_dust_update<R, R, 8>);
   } else {
-    if (d64) k_dust_update<R, double, 32><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
-    else k_dust_update<R, R, 32><<<grd2, blk, 0, s>>>(L, i1, i2, i3, u, nd, stage, c->d_floor);
+    d64 ? launch(k_dust_update<R, double, 32>) : launch(k_dust_update<R, R, 32>);
   }
   c->n_launch += 3 + 1;
 }

@@ -69,8 +69,16 @@ aeth_status aeth_create(const aeth_config* cfg, aeth_ctx** out) {
     delete c;
     return bad;
   }
+  if (cfg->drag_law != AETH_DRAG_LAW_TSTOP && cfg->drag_law != AETH_DRAG_LAW_COEFF) {
+    delete c;
+    return AETH_ERR_ARG;
+  }
   if (cfg->n_dust > 0) {
-    if (cfg->eos != AETH_EOS_ADIABATIC_HYDRO || cfg->integrator != AETH_INT_IMEX2P) {
+    // hydro gas (adiabatic or isothermal) under IMEX2P; the per-species
+    // FP64 selection needs per-species weights (constant stopping times)
+    if ((cfg->eos != AETH_EOS_ADIABATIC_HYDRO && cfg->eos != AETH_EOS_ISOTHERMAL_HYDRO) ||
+        cfg->integrator != AETH_INT_IMEX2P ||
+        (cfg->drag_law == AETH_DRAG_LAW_COEFF && cfg->drag_precision == AETH_DRAG_SEL64)) {
       delete c;
       return AETH_ERR_UNSUPPORTED;
     }

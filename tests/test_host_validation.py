@@ -59,6 +59,7 @@ def _cfg(**kw):
     dict(raw=dict(n_dust=2)),                              # no stopping times given
     dict(mhd=False, integrator=A.IMEX2P, t_stop=[0.1, 0.0]),
     dict(mhd=False, integrator=A.IMEX2P, t_stop=[0.1, -1.0]),
+    dict(raw=dict(drag_law=2)),
 ])
 def test_create_rejects_invalid_values(kw):
     assert _create_code(_cfg(**kw)) == ARG
@@ -68,8 +69,10 @@ def test_create_rejects_invalid_values(kw):
     dict(t_stop=[0.1], integrator=A.IMEX2P),               # dust under MHD gas
     dict(t_stop=[0.1], mhd=False),                         # dust without IMEX2P
     dict(mhd=False, integrator=A.IMEX2P),                  # IMEX2P without dust
-    dict(t_stop=[0.1], mhd=False, integrator=A.IMEX2P, iso=True),
+    dict(t_stop=[0.1], mhd=False, integrator=A.IMEX2P, drag_law=A.DRAG_COEFF,
+         precision=A.FP32, drag_precision=A.DRAG_SEL64),   # per-species choice needs t_k
     dict(dual=True, iso=True),
+    dict(dual=True, precision=A.FP32_SEL64),
     dict(dual=True, path=A.UNFUSED),
     dict(dual=True, precision=A.FP32_P64),
     dict(dual=True, riemann=A.MLP, precision=A.FP32),
@@ -92,6 +95,10 @@ def test_create_rejects_combinations_not_built(kw):
     dict(mhd=False, integrator=A.IMEX2P, t_stop=[1e-4, 1e-2, 1.0], precision=A.FP32,
          drag_precision=A.FP32),
     dict(riemann=A.MLP, precision=A.FP32, mlp_engine=A.MMA_SYNC),
+    dict(precision=A.FP32_SEL64, p64_ratio=8.0),
+    dict(mhd=False, integrator=A.IMEX2P, t_stop=[1e-4, 1.0], precision=A.FP32,
+         drag_precision=A.DRAG_SEL64, drag_ratio=2.0),
+    dict(t_stop=[1.0, 3.0], mhd=False, integrator=A.IMEX2P, iso=True, drag_law=A.DRAG_COEFF),
 ])
 def test_create_accepts_every_built_family(kw):
     assert _create_code(_cfg(**kw)) == 0
