@@ -78,9 +78,9 @@ def test_selective_pressure_recovery_parity_mixed_beta():
 
 
 def test_selective_pressure_recovery_is_the_fp64_one_where_every_cell_needs_it():
-    # beta = 0.02 everywhere: magnetic / internal = (1 / beta) (gamma - 1) = 33 > 4
+    # beta = 0.05 everywhere: magnetic / internal = (1 / beta) (gamma - 1) = 13 > 4
     n = 24
-    st = I.turbulence_box(n=n, seed=11, mach=0.5, gamma=5.0 / 3.0, beta=0.02)
+    st = I.turbulence_box(n=n, seed=11, mach=0.5, gamma=5.0 / 3.0, beta=0.05)
     ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)
     sel, _ = _run(st, dts, A.FP32_SEL64, n)
     glob, _ = _run(st, dts, A.FP32_P64, n)
