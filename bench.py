@@ -104,6 +104,11 @@ WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512", "wave51
 PAPER_WAVE512 = {"mhd": 300e6, "hydro": 709e6}
 
 
+def learned_n(a):
+    """Grid of the learned-flux workload: 512^3 unless --n is given."""
+    return a.n if any(x == "--n" or x.startswith("--n=") for x in a.argv) else 512
+
+
 def workload_config(a):
     cfg = _workload_config(a)
     if a.block_size:
@@ -131,7 +136,7 @@ def _workload_config(a):
                 "seed": 20260817,
                 "l2": "inputs larger than L2 (128^3 x 37 vars x 2 registers)"}
     if a.workload == "learned512":
-        n = a.n if a.n != 256 else 512
+        n = learned_n(a)
         return {"workload": f"learned_flux_mhd_turbulence_{n}^3", "grid": [n, n, n],
                 "riemann": f"BF16 MLP 14-128-128-128-7 ({a.mlp_engine}) + HLLD fallback",
                 "recon": "PLM", "integrator": "VL2", "mach_rms": 4.0,
@@ -810,7 +815,7 @@ def main():
         states = [gas]
     elif a.workload == "learned512":
         from paper_2608_14048_gb300 import inputs as I
-        n = a.n if a.n != 256 else 512
+        n = learned_n(a)
         learned = train_learned_flux(A, I, torch, dev)
         states = [I.turbulence_box(n=n, seed=20260820, mach=4.0, beta_modulated=True,
                                    gamma=1.0001)]

@@ -271,6 +271,217 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
 }
 
 // ------------------------------------------------------------------------
+// 3'. the same update for FP32 Cartesian blocks, four consecutive x cells
+// per thread: 16-byte loads and stores (the flux and corner-EMF arrays
+// through the read-only path), the x-neighbour of the fourth cell as one
+// scalar.  A thread's four cells sit at i = 4m .. 4m + 3, so the group is
+// 16-byte aligned (interior cell 0 at x offset 4, row pitch a multiple of
+// 4, every array 256-byte aligned).  Groups that reach the block's upper
+// face layers (i + 3 >= n_x, j = n_y or k = n_z) take the per-cell path.
+// One 32 x 4 x 2 cell tile per CTA of 64 threads.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float4 ldg4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float at4(const float4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+// Corner EMFs of four consecutive x cells per thread (FP32 Cartesian
+// blocks): every operand is a 16-byte load at the group's own column or a
+// y / z neighbour, or, for the x-shifted operands (the b = x side of E_y,
+// the a = x side of E_z), the same load shifted by one scalar from column
+// i - 1.  Groups at the upper x end take the per-cell path.
+__device__ __forceinline__ float4 shl(const float4& v, float s) {
+  return make_float4(s, v.x, v.y, v.z);
+}
+
+template <typename Src>
+__global__ void __launch_bounds__(64) k_emf_v4(Src S, int t0) {
+  int loc;
+  const BlockPtrs<float>& A = S.get(t0 + (int)blockIdx.x, loc);
+  const Layout& L = A.L;
+  const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
+  const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
+  const int i4 = bx * CELL_BX + 4 * ((int)threadIdx.x % (CELL_BX / 4));
+  const int j = by * CELL_BY + ((int)threadIdx.x / (CELL_BX / 4)) % CELL_BY;
+  const int k = bz * CELL_BZ + (int)threadIdx.x / ((CELL_BX / 4) * CELL_BY);
+  if (i4 > L.n[0] || j > L.n[1] || k > L.n[2]) return;
+  if (i4 + 3 >= L.n[0]) {
+    for (int q = 0; q < 4 && i4 + q <= L.n[0]; ++q) {
+      const int P[3] = {i4 + q, j, k};
+      const long long iP = L.idx(P[0], P[1], P[2]);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        if (P[cc] >= L.n[cc]) continue;
+        const int a = (cc + 1) % 3, b = (cc + 2) % 3;
+        const long long sa = L.stride(a), sb = L.stride(b);
+        const long long iA = iP - sa, iB = iP - sb, iAB = iP - sa - sb;
+        const float* er = A.w[cc];
+        A.edge[cc][iP] = corner_emf(A.e[a][1][iB], A.e[a][1][iP], A.e[b][0][iA], A.e[b][0][iP],
+                                    er[iAB], er[iB], er[iA], er[iP], A.f[a][0][iB],
+                                    A.f[a][0][iP], A.f[b][0][iA], A.f[b][0][iP]);
+      }
+    }
+    return;
+  }
+  const long long c = L.idx(i4, j, k);
+  const long long sy = L.sx, sz = L.sx * L.sy;
+  auto emf4 = [&](const float4& ea_m, const float4& ea_p, const float4& eb_m, const float4& eb_p,
+                  const float4& r00, const float4& r01, const float4& r10, const float4& r11,
+                  const float4& fa_m, const float4& fa_p, const float4& fb_m,
+                  const float4& fb_p) {
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      o[q] = corner_emf(at4(ea_m, q), at4(ea_p, q), at4(eb_m, q), at4(eb_p, q), at4(r00, q),
+                        at4(r01, q), at4(r10, q), at4(r11, q), at4(fa_m, q), at4(fa_p, q),
+                        at4(fb_m, q), at4(fb_p, q));
+    return make_float4(o[0], o[1], o[2], o[3]);
+  };
+  // E_x (a = y, b = z): every operand aligned
+  {
+    const float* er = A.w[0];
+    st4(A.edge[0] + c,
+        emf4(ldg4(A.e[1][1] + c - sz), ldg4(A.e[1][1] + c), ldg4(A.e[2][0] + c - sy),
+             ldg4(A.e[2][0] + c), ldg4(er + c - sy - sz), ldg4(er + c - sz), ldg4(er + c - sy),
+             ldg4(er + c), ldg4(A.f[1][0] + c - sz), ldg4(A.f[1][0] + c),
+             ldg4(A.f[2][0] + c - sy), ldg4(A.f[2][0] + c)));
+  }
+  // E_y (a = z, b = x): the b side shifted by one column
+  if (j < L.n[1]) {
+    const float* er = A.w[1];
+    const float4 ea_p = ldg4(A.e[2][1] + c), fa_p = ldg4(A.f[2][0] + c);
+    const float4 ea_m = shl(ea_p, __ldg(A.e[2][1] + c - 1));
+    const float4 fa_m = shl(fa_p, __ldg(A.f[2][0] + c - 1));
+    const float4 rA = ldg4(er + c - sz), rP = ldg4(er + c);
+    st4(A.edge[1] + c,
+        emf4(ea_m, ea_p, ldg4(A.e[0][0] + c - sz), ldg4(A.e[0][0] + c),
+             shl(rA, __ldg(er + c - sz - 1)), shl(rP, __ldg(er + c - 1)), rA, rP, fa_m, fa_p,
+             ldg4(A.f[0][0] + c - sz), ldg4(A.f[0][0] + c)));
+  }
+  // E_z (a = x, b = y): the a side shifted by one column
+  if (k < L.n[2]) {
+    const float* er = A.w[2];
+    const float4 eb_p = ldg4(A.e[1][0] + c), fb_p = ldg4(A.f[1][0] + c);
+    const float4 eb_m = shl(eb_p, __ldg(A.e[1][0] + c - 1));
+    const float4 fb_m = shl(fb_p, __ldg(A.f[1][0] + c - 1));
+    const float4 rB = ldg4(er + c - sy), rP = ldg4(er + c);
+    st4(A.edge[2] + c,
+        emf4(ldg4(A.e[0][1] + c - sy), ldg4(A.e[0][1] + c), eb_m, eb_p,
+             shl(rB, __ldg(er + c - sy - 1)), rB, shl(rP, __ldg(er + c - 1)), rP,
+             ldg4(A.f[0][0] + c - sy), ldg4(A.f[0][0] + c), fb_m, fb_p));
+  }
+}
+
+// resident CTAs per SM requested for it (its per-cell path for the face
+// layers holds the most registers)
+#ifndef AETH_UPD4_MINB
+#define AETH_UPD4_MINB 12
+#endif
+// 0: the one-cell-per-thread corner-EMF pass everywhere
+#ifndef AETH_EMF_V4
+#define AETH_EMF_V4 1
+#endif
+// 0: the one-cell-per-thread update pass everywhere
+#ifndef AETH_UPD_V4
+#define AETH_UPD_V4 1
+#endif
+
+template <bool MHD, typename Src>
+__global__ void __launch_bounds__(64, AETH_UPD4_MINB)
+    k_update_v4(Src S, int t0, int src, int out, float w0, float w1, float beta,
+                const double* __restrict__ dt) {
+  const float bdt = beta * (float)(*dt);
+  int loc;
+  const BlockPtrs<float>& B = S.get(t0 + (int)blockIdx.x, loc);
+  const Layout& L = B.L;
+  const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
+  const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
+  const int i4 = bx * CELL_BX + 4 * ((int)threadIdx.x % (CELL_BX / 4));
+  const int j = by * CELL_BY + ((int)threadIdx.x / (CELL_BX / 4)) % CELL_BY;
+  const int k = bz * CELL_BZ + (int)threadIdx.x / ((CELL_BX / 4) * CELL_BY);
+  if (i4 > L.n[0] || j > L.n[1] || k > L.n[2]) return;
+  if (i4 + 3 >= L.n[0] || j >= L.n[1] || k >= L.n[2]) {
+    for (int q = 0; q < 4 && i4 + q <= L.n[0]; ++q) {
+      const int P[3] = {i4 + q, j, k};
+      update_cell<float, false, MHD, false>(B, P, src, out, w0, w1, bdt, 0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    return;
+  }
+  const long long c = L.idx(i4, j, k);
+  const long long sy = L.sx, sz = L.sx * L.sy;
+  const Geometry<float>& geo = B.geo;
+  const float V = geo.vol(0, 0, 0);
+  const float Ar[3] = {geo.area[0](0, 0, 0), geo.area[1](0, 0, 0), geo.area[2](0, 0, 0)};
+  const bool has_b = w1 != 0.0f;
+  float* const* outp = B.reg[out];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const float4 fx = ldg4(B.f[0][v] + c);
+    const float fx4 = __ldg(B.f[0][v] + c + 4);
+    const float4 fy0 = ldg4(B.f[1][v] + c), fy1 = ldg4(B.f[1][v] + c + sy);
+    const float4 fz0 = ldg4(B.f[2][v] + c), fz1 = ldg4(B.f[2][v] + c + sz);
+    const float4 u0 = ld4(B.reg[0][v] + c);
+    const float4 u1 = has_b ? ld4(B.reg[1][v] + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float fxp = q < 3 ? at4(fx, q + 1) : fx4;
+      float div = 0.0f;
+      div += Ar[0] * fxp - Ar[0] * at4(fx, q);
+      div += Ar[1] * at4(fy1, q) - Ar[1] * at4(fy0, q);
+      div += Ar[2] * at4(fz1, q) - Ar[2] * at4(fz0, q);
+      float base = w0 * at4(u0, q);
+      if (has_b) base += w1 * at4(u1, q);
+      r[q] = base + bdt * (-div / V);
+    }
+    st4(outp[v] + c, make_float4(r[0], r[1], r[2], r[3]));
+  }
+  if constexpr (MHD) {
+    // corner EMFs around the three lower faces of each cell (Eq. 9)
+    const float l0 = geo.edge[0](0, 0, 0), l1 = geo.edge[1](0, 0, 0), l2 = geo.edge[2](0, 0, 0);
+    const float4 e0c = ldg4(B.edge[0] + c), e0y = ldg4(B.edge[0] + c + sy),
+                 e0z = ldg4(B.edge[0] + c + sz);
+    const float4 e1c = ldg4(B.edge[1] + c), e1z = ldg4(B.edge[1] + c + sz);
+    const float4 e2c = ldg4(B.edge[2] + c), e2y = ldg4(B.edge[2] + c + sy);
+    const float e1x4 = __ldg(B.edge[1] + c + 4), e2x4 = __ldg(B.edge[2] + c + 4);
+    float nb[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float4 b0 = ld4(B.reg[0][5 + d] + c);
+      const float4 b1 = has_b ? ld4(B.reg[1][5 + d] + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float e1xp = q < 3 ? at4(e1c, q + 1) : e1x4;
+        const float e2xp = q < 3 ? at4(e2c, q + 1) : e2x4;
+        float circ;
+        if (d == 0)
+          circ = at4(e2y, q) * l2 - at4(e2c, q) * l2 - (at4(e1z, q) * l1 - at4(e1c, q) * l1);
+        else if (d == 1)
+          circ = at4(e0z, q) * l0 - at4(e0c, q) * l0 - (e2xp * l2 - at4(e2c, q) * l2);
+        else
+          circ = e1xp * l1 - at4(e1c, q) * l1 - (at4(e0y, q) * l0 - at4(e0c, q) * l0);
+        float base = w0 * at4(b0, q);
+        if (has_b) base += w1 * at4(b1, q);
+        nb[d][q] = base - bdt * circ / Ar[d];
+      }
+      st4(outp[5 + d] + c, make_float4(nb[d][0], nb[d][1], nb[d][2], nb[d][3]));
+    }
+    // periodic axis: face n is the image of face 0
+    if (L.bc[0] == AETH_BC_PERIODIC && i4 == 0) outp[5][c + L.n[0]] = nb[0][0];
+    if (L.bc[1] == AETH_BC_PERIODIC && j == 0)
+      st4(outp[6] + c + (long long)L.n[1] * sy, make_float4(nb[1][0], nb[1][1], nb[1][2], nb[1][3]));
+    if (L.bc[2] == AETH_BC_PERIODIC && k == 0)
+      st4(outp[7] + c + (long long)L.n[2] * sz, make_float4(nb[2][0], nb[2][1], nb[2][2], nb[2][3]));
+  }
+}
+
+// ------------------------------------------------------------------------
 // Block links (Sec. 2.3): after an update, face n along the link axis of the
 // block below takes the value of face 0 of the block above (both are the
 // shared face; the block above's CT owns it).  blockIdx.y = link, threads
@@ -504,7 +715,14 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
   for (const auto& B : c->blocks) nsph += B.L.coord == AETH_COORD_SPH;
   const int mode = nsph == 0 ? 0 : (nsph == (int)c->blocks.size() ? 1 : 2);
   with_src<R>(c, PK_CELL, -1, [&](auto S, TileRange r) {
-    if (MHD) k_emf_ref<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1);
+    bool emf_done = false;
+    if constexpr (sizeof(R) == 4) {
+      if (MHD && mode == 0 && AETH_EMF_V4) {
+        k_emf_v4<<<r.t1 - r.t0, (CELL_BX / 4) * CELL_BY * CELL_BZ, 0, c->stream>>>(S, r.t0);
+        emf_done = true;
+      }
+    }
+    if (MHD && !emf_done) k_emf_ref<R><<<r.t1 - r.t0, 256, 0, c->stream>>>(S, r.t0, r.t1);
     const R g = (R)c->cfg.gamma, rf = (R)c->cfg.rho_floor, pf = (R)c->cfg.p_floor;
     const R cs2 = is_iso(c) ? (R)(c->cfg.cs_iso * c->cfg.cs_iso) : R(0);
     const int n = r.t1 - r.t0;
@@ -518,6 +736,14 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
         if (mode == 0) upd(k_update_f<R, P64, MHD, 0, Src, true>);
         else if (mode == 1) upd(k_update_f<R, P64, MHD, 1, Src, true>);
         else upd(k_update_f<R, P64, MHD, 2, Src, true>);
+        return;
+      }
+    }
+    if constexpr (sizeof(R) == 4) {
+      if (mode == 0 && AETH_UPD_V4) {
+        // FP32 Cartesian blocks: four x cells per thread, one tile per CTA
+        k_update_v4<MHD, Src><<<n, (CELL_BX / 4) * CELL_BY * CELL_BZ, 0, c->stream>>>(
+            S, r.t0, src, out, (float)w0, (float)w1, (float)beta, c->d_dt);
         return;
       }
     }
