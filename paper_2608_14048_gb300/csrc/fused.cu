@@ -278,7 +278,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
 // 16-byte aligned (interior cell 0 at x offset 4, row pitch a multiple of
 // 4, every array 256-byte aligned).  Groups that reach the block's upper
 // face layers (i + 3 >= n_x, j = n_y or k = n_z) take the per-cell path.
-// One 32 x 4 x 2 cell tile per CTA of 64 threads.
+// One 32 x 4 x 2 cell tile per CTA of 64 threads.  COORD 2: a context with
+// spherical blocks too; a spherical block's tile takes the per-cell path
+// with the curvilinear sources.
 // ------------------------------------------------------------------------
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(64) k_emf_v4(Src S, int t0) {
 // resident CTAs per SM requested for it (its per-cell path for the face
 // layers holds the most registers)
 #ifndef AETH_UPD4_MINB
-#define AETH_UPD4_MINB 12
+#define AETH_UPD4_MINB 16
 #endif
 // 0: the one-cell-per-thread corner-EMF pass everywhere
 #ifndef AETH_EMF_V4
@@ -392,14 +394,30 @@ __global__ void __launch_bounds__(64) k_emf_v4(Src S, int t0) {
 #define AETH_UPD_V4 1
 #endif
 
-template <bool MHD, typename Src>
-__global__ void __launch_bounds__(64, AETH_UPD4_MINB)
+template <bool P64, bool MHD, int COORD, typename Src>
+__global__ void __launch_bounds__(64, COORD == 0 ? AETH_UPD4_MINB : 12)
     k_update_v4(Src S, int t0, int src, int out, float w0, float w1, float beta,
-                const double* __restrict__ dt) {
+                const double* __restrict__ dt, float gamma, float rho_floor, float p_floor,
+                float cs2) {
   const float bdt = beta * (float)(*dt);
   int loc;
   const BlockPtrs<float>& B = S.get(t0 + (int)blockIdx.x, loc);
   const Layout& L = B.L;
+  if (COORD == 2 && L.coord == AETH_COORD_SPH) {
+    // a spherical block: the per-cell path with the sources of Eq. 12
+    const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
+    const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
+    const int i4 = bx * CELL_BX + 4 * ((int)threadIdx.x % (CELL_BX / 4));
+    const int j = by * CELL_BY + ((int)threadIdx.x / (CELL_BX / 4)) % CELL_BY;
+    const int k = bz * CELL_BZ + (int)threadIdx.x / ((CELL_BX / 4) * CELL_BY);
+    if (j > L.n[1] || k > L.n[2]) return;
+    for (int q = 0; q < 4 && i4 + q <= L.n[0]; ++q) {
+      const int P[3] = {i4 + q, j, k};
+      update_cell<float, P64, MHD, true>(B, P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor,
+                                         cs2);
+    }
+    return;
+  }
   const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
   const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
   const int i4 = bx * CELL_BX + 4 * ((int)threadIdx.x % (CELL_BX / 4));
@@ -409,7 +427,8 @@ __global__ void __launch_bounds__(64, AETH_UPD4_MINB)
   if (i4 + 3 >= L.n[0] || j >= L.n[1] || k >= L.n[2]) {
     for (int q = 0; q < 4 && i4 + q <= L.n[0]; ++q) {
       const int P[3] = {i4 + q, j, k};
-      update_cell<float, false, MHD, false>(B, P, src, out, w0, w1, bdt, 0.0f, 0.0f, 0.0f, 0.0f);
+      update_cell<float, P64, MHD, false>(B, P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor,
+                                          cs2);
     }
     return;
   }
@@ -740,10 +759,16 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
       }
     }
     if constexpr (sizeof(R) == 4) {
-      if (mode == 0 && AETH_UPD_V4) {
+      if (mode != 1 && AETH_UPD_V4) {
         // FP32 Cartesian blocks: four x cells per thread, one tile per CTA
-        k_update_v4<MHD, Src><<<n, (CELL_BX / 4) * CELL_BY * CELL_BZ, 0, c->stream>>>(
-            S, r.t0, src, out, (float)w0, (float)w1, (float)beta, c->d_dt);
+        // (spherical blocks of a mixed context per cell)
+        auto v4 = [&](auto kernel) {
+          kernel<<<n, (CELL_BX / 4) * CELL_BY * CELL_BZ, 0, c->stream>>>(
+              S, r.t0, src, out, (float)w0, (float)w1, (float)beta, c->d_dt, (float)g,
+              (float)rf, (float)pf, (float)cs2);
+        };
+        if (mode == 0) v4(k_update_v4<P64, MHD, 0, Src>);
+        else v4(k_update_v4<P64, MHD, 2, Src>);
         return;
       }
     }
