@@ -104,6 +104,14 @@ WORKLOADS = ("turb256", "batched512", "dust128", "wave32", "learned512", "wave51
 PAPER_WAVE512 = {"mhd": 300e6, "hydro": 709e6}
 
 
+def flux_tile_record(A, current, tuned):
+    """The flux pass's tile shape in the bench line: width x height x
+    z-chunk, and whether the autotuner timed it now or its cache gave it."""
+    tx, kc = current
+    return {"tx": tx, "ty": 256 // tx, "kchunk": kc,
+            "source": tuned[2] if tuned else "default (no autotune)"}
+
+
 def learned_n(a):
     """Grid of the learned-flux workload: 512^3 unless --n is given."""
     return a.n if any(x == "--n" or x.startswith("--n=") for x in a.argv) else 512
@@ -856,11 +864,12 @@ def main():
                                 else host_dust[k])
 
     upload()
-    kchunk = None
+    tile = None
     if not a.no_autotune and a.workload not in ("dust128", "learned512"):
-        # tile shape chosen by the autotuner on this workload's own state,
-        # then the state is reloaded (the autotuner advances it)
-        kchunk = A.aeth_autotune(sv.ctx)
+        # tile shape chosen by the autotuner on this workload's own state
+        # (or its cached choice for this configuration, block sizes and
+        # GPU), then the state is reloaded (the autotuner advances it)
+        tile = sv.tune_tiles(device=torch.cuda.get_device_name(dev))
         upload()
     cells = sum(int(np.prod(s_.block.n)) for s_ in states)
     flush = None
@@ -1003,6 +1012,7 @@ def main():
                 A.aeth_get_dust(sv.ctx, 0, k, dbuf[k])
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, device=dev)
     e2e_val = whole_job_rate(cells * ke, ws, e2e_s)
+    sv_tile = A.aeth_get_flux_tile(sv.ctx)
     sv.close()
     l1 = None
     if rank == 0 and a.l1_steps > 0:
@@ -1061,7 +1071,7 @@ def main():
         "gpu_launches_how": "the library's launch counter over an eager pass of the same K "
                             "steps; the timed CUDA graph replays the same launches",
         "diag_after": {"max_divb_rel": diag["max_divb_rel"], "floor_hits": diag["floor_hits"]},
-        "flux_tile": {"tx": 32, "ty": 8, "kchunk": kchunk, "autotuned": kchunk is not None},
+        "flux_tile": flux_tile_record(A, sv_tile, tile),
         **extra,
     }
     if rank == 0:

@@ -41,6 +41,7 @@ EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
            "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_mlp_face_flux", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
+           "aeth_set_flux_tile", "aeth_get_flux_tile",
            "aeth_cfl_dt_noalloc", "aeth_get_entropy", "aeth_link_blocks", "aeth_probe_fma",
            "aeth_last_error", "aeth_destroy"]
 
@@ -118,7 +119,9 @@ def load_library(path: str = LIB_PATH):
         "aeth_profile": ([P, C.c_int], C.c_int),
         "aeth_profile_read": ([P, dp, C.POINTER(C.c_longlong), dp, C.POINTER(C.c_longlong)],
                               C.c_int),
-        "aeth_autotune": ([P, C.POINTER(C.c_int)], C.c_int),
+        "aeth_autotune": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+        "aeth_set_flux_tile": ([P, C.c_int, C.c_int], C.c_int),
+        "aeth_get_flux_tile": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "aeth_cfl_dt_noalloc": ([P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_int, P, P], C.c_int),
@@ -348,12 +351,70 @@ def aeth_profile_read(ctx):
     return ms.value, n.value, b.value, al.value
 
 
-def aeth_autotune(ctx) -> int:
-    """Time the flux pass's z-chunk candidates on the current state (which
-    it advances) and keep the fastest; returns the chosen chunk."""
-    kc = C.c_int(0)
-    _check(ctx, load_library().aeth_autotune(ctx, C.byref(kc)))
-    return kc.value
+def aeth_autotune(ctx):
+    """Time the flux pass's tile candidates (widths 32 / 16, z-chunks 8..64)
+    on the current state (which it advances) and keep the fastest; returns
+    (flux_tx, kchunk)."""
+    tx, kc = C.c_int(0), C.c_int(0)
+    _check(ctx, load_library().aeth_autotune(ctx, C.byref(tx), C.byref(kc)))
+    return tx.value, kc.value
+
+
+def aeth_set_flux_tile(ctx, flux_tx: int, kchunk: int):
+    _check(ctx, load_library().aeth_set_flux_tile(ctx, int(flux_tx), int(kchunk)))
+
+
+def aeth_get_flux_tile(ctx):
+    tx, kc = C.c_int(0), C.c_int(0)
+    _check(ctx, load_library().aeth_get_flux_tile(ctx, C.byref(tx), C.byref(kc)))
+    return tx.value, kc.value
+
+
+def tile_cache_key(cfg, descs, device=""):
+    """Key of a tuned flux-tile shape: the configuration fields that change
+    the flux pass, the block sizes (as a multiset) and the device name."""
+    import hashlib
+    import json
+    blocks = {}
+    for d in descs:
+        k = f"{d.nx}x{d.ny}x{d.nz}:{d.coord}"
+        blocks[k] = blocks.get(k, 0) + 1
+    body = {"eos": cfg.eos, "precision": cfg.precision, "recon": cfg.recon,
+            "riemann": cfg.riemann, "integrator": cfg.integrator, "path": cfg.path,
+            "dual": cfg.dual_energy, "n_dust": cfg.n_dust,
+            "blocks": sorted(blocks.items()), "device": device}
+    return hashlib.sha256(json.dumps(body, sort_keys=True).encode()).hexdigest()[:24], body
+
+
+def default_tile_cache():
+    """JSON file of tuned flux-tile shapes ($AETHER_TILE_CACHE, else
+    ~/.cache/aether_gb/flux_tiles.json)."""
+    return os.environ.get("AETHER_TILE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "aether_gb", "flux_tiles.json")
+
+
+def load_tile_cache(path):
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store_tile_cache(path, key, entry):
+    """Add one entry to the cache file (written to a temporary file, then
+    moved into place, so a concurrent reader never sees half a file)."""
+    import json
+    import tempfile
+    d = load_tile_cache(path)
+    d[key] = entry
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=os.path.dirname(os.path.abspath(path)), suffix=".tmp")
+    with os.fdopen(fd, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def aeth_cfl_dt_noalloc(d_cons, d_b1, d_b2, d_b3, n, dx, gamma, rho_floor, p_floor, cfl, mhd,
@@ -496,6 +557,25 @@ class Solver:
 
     def compute_dt(self):
         return aeth_compute_dt(self.ctx)
+
+    def tune_tiles(self, cache=None, device=""):
+        """Flux-tile shape for this context: taken from the JSON cache when
+        the same configuration, block sizes and device were tuned before,
+        else timed with aeth_autotune (which ADVANCES the state: load the
+        real state afterwards) and stored.  Returns (flux_tx, kchunk,
+        "cache" | "tuned")."""
+        path = cache or default_tile_cache()
+        key, body = tile_cache_key(self.cfg, self.descs, device)
+        e = load_tile_cache(path).get(key)
+        if e is not None:
+            try:
+                aeth_set_flux_tile(self.ctx, e["flux_tx"], e["kchunk"])
+                return e["flux_tx"], e["kchunk"], "cache"
+            except (AethError, KeyError, TypeError):
+                pass   # a stale or foreign entry: tune again
+        tx, kc = aeth_autotune(self.ctx)
+        store_tile_cache(path, key, {"flux_tx": tx, "kchunk": kc, "what": body})
+        return tx, kc, "tuned"
 
     def step(self, dt):
         aeth_step(self.ctx, dt)

@@ -165,7 +165,7 @@ static int default_kchunk(const aeth_ctx* c) {
   const int want = 4 * c->num_sms;
   for (int kc : {64, 32, 16, 8, 4}) {
     long long tiles = 0;
-    for (const auto& B : c->blocks) tiles += tiles_of(B.L, PK_FLUX, kc);
+    for (const auto& B : c->blocks) tiles += tiles_of(B.L, PK_FLUX, kc, c->flux_tx);
     if (tiles >= want) return kc;
   }
   return 4;
@@ -183,7 +183,7 @@ static aeth_status build_tables_T(aeth_ctx* c) {
     long long acc = 0;
     for (int b = 0; b < nb; ++b) {
       p[b] = (int)acc;
-      acc += tiles_of(c->blocks[b].L, kind, c->kchunk);
+      acc += tiles_of(c->blocks[b].L, kind, c->kchunk, c->flux_tx);
     }
     if (acc > (1ll << 30)) return fail(c, AETH_ERR_ARG, "too many tiles (%lld)", acc);
     p[nb] = (int)acc;

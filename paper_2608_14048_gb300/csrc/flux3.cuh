@@ -16,9 +16,8 @@
 
 namespace aeth {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int NT = TX * TY;
+constexpr int NT = FLUX_NT;   // threads of a flux tile; its x width TXT is a
+                              // template parameter (32 or 16), the y width NT / TXT
 // resident CTAs per SM requested for the FP32 flux pass (register budget
 // 65536 / (256 * FLUX_MINB) per thread)
 #ifndef AETH_FLUX_MINB
@@ -72,10 +71,11 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // face also gets the entropy flux, its mass flux times the reconstructed
 // specific entropy S/rho of the upwind side, in scratch slot 3 + D.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0,
-          bool DUAL = false>
+          bool DUAL = false, int TXT = FLUX_TX>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits, R alpha_switch) {
+  constexpr int TX = TXT, TY = NT / TXT;
   constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
   constexpr int QN = RL + RH + 1;
@@ -286,9 +286,21 @@ static void launch_flux3(aeth_ctx* c, int src, int block) {
   const int per_sm = sizeof(R) == 4 ? AETH_FLUX_MINB : 1;
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
-    k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL><<<grid, NT, 0, c->stream>>>(
-        S, r.t0, r.t1, src, (R)(iso_solver(SOLVER) ? c->cfg.cs_iso : c->cfg.gamma),
-        (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk, c->d_floor, (R)c->cfg.alpha_switch);
+    auto go = [&](auto kernel) {
+      kernel<<<grid, NT, 0, c->stream>>>(
+          S, r.t0, r.t1, src, (R)(iso_solver(SOLVER) ? c->cfg.cs_iso : c->cfg.gamma),
+          (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk, c->d_floor,
+          (R)c->cfg.alpha_switch);
+    };
+    // the 16-wide tile is built for the FP32 solver passes (the contexts
+    // whose tiles the autotuner may switch: tile_shape_tunable)
+    if constexpr (sizeof(R) == 4 && !DUAL && SOLVER != 1) {
+      if (c->flux_tx == 16) {
+        go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 16>);
+        return;
+      }
+    }
+    go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 32>);
   });
   c->n_launch += 1;
 }

@@ -642,35 +642,68 @@ aeth_status aeth_profile_read(aeth_ctx* c, double* ms, long long* n, double* byt
   return AETH_OK;
 }
 
-aeth_status aeth_autotune(aeth_ctx* c, int* kchunk_out) {
+aeth_status aeth_set_flux_tile(aeth_ctx* c, int flux_tx, int kchunk) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  if (flux_tx != 32 && flux_tx != 16) return fail(c, AETH_ERR_ARG, "flux tile width 32 or 16");
+  if (!(kchunk >= 1 && kchunk <= 1024)) return fail(c, AETH_ERR_ARG, "z-chunk 1..1024");
+  if (flux_tx != 32 && !tile_shape_tunable(c))
+    return fail(c, AETH_ERR_UNSUPPORTED, "this configuration keeps the 32-wide flux tile");
+  c->flux_tx = flux_tx;
+  c->kchunk = kchunk;
+  aeth_status s = build_tables(c);
+  if (s != AETH_OK) return s;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return AETH_OK;
+}
+
+aeth_status aeth_get_flux_tile(aeth_ctx* c, int* flux_tx, int* kchunk) {
+  if (!c) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  if (flux_tx) *flux_tx = c->flux_tx;
+  if (kchunk) *kchunk = c->kchunk;
+  return AETH_OK;
+}
+
+aeth_status aeth_autotune(aeth_ctx* c, int* tx_out, int* kchunk_out) {
   if (!c) return AETH_ERR_ARG;
   if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
   // three timed steps per candidate (the state advances, as documented)
   const bool prof = c->profile;
   c->profile = true;
-  int best = c->kchunk;
+  int best_tx = c->flux_tx, best_kc = c->kchunk;
   double best_ms = 1e300;
-  for (int kc : {8, 16, 32, 64}) {
-    c->kchunk = kc;
-    aeth_status s = build_tables(c);
-    if (s != AETH_OK) return s;
-    c->prof_used = 0;
-    c->prof_bytes = 0;
-    for (int rep = 0; rep < 3; ++rep) {
-      s = enqueue_dt(c);
-      if (s == AETH_OK) s = enqueue_step(c, false);
+  std::vector<int> widths = {32};
+  if (tile_shape_tunable(c)) widths.push_back(16);
+  for (int tx : widths) {
+    for (int kc : {8, 16, 32, 64}) {
+      c->flux_tx = tx;
+      c->kchunk = kc;
+      aeth_status s = build_tables(c);
       if (s != AETH_OK) return s;
-    }
-    double ms = 0;
-    long long n = 0;
-    s = aeth_profile_read(c, &ms, &n, nullptr, nullptr);
-    if (s != AETH_OK) return s;
-    if (n > 0 && ms / n < best_ms) {
-      best_ms = ms / n;
-      best = kc;
+      c->prof_used = 0;
+      c->prof_bytes = 0;
+      for (int rep = 0; rep < 3; ++rep) {
+        s = enqueue_dt(c);
+        if (s == AETH_OK) s = enqueue_step(c, false);
+        if (s != AETH_OK) return s;
+      }
+      double ms = 0;
+      long long n = 0;
+      s = aeth_profile_read(c, &ms, &n, nullptr, nullptr);
+      if (s != AETH_OK) return s;
+      if (n > 0 && ms / n < best_ms) {
+        best_ms = ms / n;
+        best_tx = tx;
+        best_kc = kc;
+      }
     }
   }
-  c->kchunk = best;
+  c->flux_tx = best_tx;
+  c->kchunk = best_kc;
   aeth_status s = build_tables(c);
   if (s != AETH_OK) return s;
   c->profile = prof;
@@ -680,7 +713,8 @@ aeth_status aeth_autotune(aeth_ctx* c, int* kchunk_out) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  if (kchunk_out) *kchunk_out = best;
+  if (tx_out) *tx_out = best_tx;
+  if (kchunk_out) *kchunk_out = best_kc;
   return AETH_OK;
 }
 

@@ -55,17 +55,19 @@ enum PassKind : int { PK_FLUX = 0, PK_CELL = 1, PK_FILL0 = 2, PK_FILL1 = 3, PK_F
                       PK_ROWS = 5, PK_N = 6 };
 
 // Tile geometry of each pass kind (threads per tile fixed per kind).
-constexpr int FLUX_TX = 32, FLUX_TY = 8;
+constexpr int FLUX_TX = 32, FLUX_TY = 8;   // default flux tile (256 threads)
+constexpr int FLUX_NT = FLUX_TX * FLUX_TY;
 constexpr int CELL_BX = 32, CELL_BY = 4, CELL_BZ = 2;
 constexpr int FILL_TILE = 256;   // ghost cells per tile of the fill pass
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// Tiles of one block for a pass kind (kchunk: z extent of a flux tile).
-inline int tiles_of(const Layout& L, int kind, int kchunk) {
+// Tiles of one block for a pass kind (kchunk: z extent of a flux tile,
+// tx: its x width, FLUX_NT / tx its y width).
+inline int tiles_of(const Layout& L, int kind, int kchunk, int tx = FLUX_TX) {
   const int g = L.g;
   if (kind == PK_FLUX)
-    return ceil_div(L.n[0] + 2, FLUX_TX) * ceil_div(L.n[1] + 2, FLUX_TY) *
+    return ceil_div(L.n[0] + 2, tx) * ceil_div(L.n[1] + 2, FLUX_NT / tx) *
            ceil_div(L.n[2] + 2, kchunk);
   if (kind == PK_CELL)
     return ceil_div(L.n[0] + 1, CELL_BX) * ceil_div(L.n[1] + 1, CELL_BY) *
@@ -134,6 +136,8 @@ struct aeth_ctx {
   std::vector<int> h_prefix;          // host copy
   int kchunk = 0;                     // z extent of a flux tile (0: choose;
                                       // aeth_autotune times candidates)
+  int flux_tx = 32;                   // x width of a flux tile (32 or 16; the y
+                                      // width is 256 / flux_tx)
   int num_sms = 152;
   int dt_grid = 1;                    // CTAs of the batched reductions
   // error text
@@ -271,6 +275,14 @@ inline size_t array_pitch_bytes(long long cells, int elem) {
 
 // dual-energy formalism (Sec. 2.8) on
 inline bool is_dual(const aeth_ctx* c) { return c->cfg.dual_energy != 0; }
+
+// The flux tile's width may be switched to 16 (FP32 states, the classical
+// solvers without dual energy, fused path; the learned flux's state dump
+// and the other passes keep the 32-wide tile).
+inline bool tile_shape_tunable(const aeth_ctx* c) {
+  return c->cfg.precision != AETH_FP64 && !is_dual(c) && c->cfg.riemann != AETH_RIEMANN_MLP &&
+         c->cfg.path == AETH_PATH_FUSED;
+}
 
 // internal solver codes of the unfused face kernel, distinct from every
 // AETH_RIEMANN_* value
