@@ -573,6 +573,130 @@ __global__ void __launch_bounds__(256)
   if (bad) atomicOr(status, ST_NONFINITE);
 }
 
+// 0: the one-cell-per-thread CFL pass everywhere
+#ifndef AETH_DT_V4
+#define AETH_DT_V4 1
+#endif
+
+// The same CFL step for FP32 gas without dual energy or dust, four
+// consecutive x cells per thread: 16-byte loads of the state (the x-face
+// field's fifth face as one scalar), the per-cell arithmetic of k_dt.  A
+// CTA of 256 threads takes four 32 x 4 x 2 cell tiles per iteration.  A
+// group of four cells that is not whole inside the block (the x end of the
+// row) is done cell by cell.
+__device__ __forceinline__ float4 ld4c(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float el4(const float4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+template <bool P64, typename Src>
+__global__ void __launch_bounds__(256)
+    k_dt_v4(Src S, int total, int mhd, float gamma, float rho_floor, float p_floor, float cs2,
+            float p64_ratio, double* __restrict__ partial, int* status) {
+  __shared__ double sm[8];
+  const bool iso = cs2 > 0.0f;
+  float m = INFINITY;
+  bool bad = false;
+  const int lt = (int)threadIdx.x & 63, sub = (int)threadIdx.x >> 6;
+  const int tx4 = 4 * (lt % (CELL_BX / 4)), ty = (lt / (CELL_BX / 4)) % CELL_BY;
+  const int tz = lt / ((CELL_BX / 4) * CELL_BY);
+  // one cell's Eq. 11 term: min over directions of width / (|v| + c_f)
+  auto cell = [&](float rho, float m1, float m2, float m3, float e, const float* bc,
+                  const float* wd) {
+    if (!(rho >= rho_floor)) { if (!(rho == rho)) bad = true; rho = rho_floor; }
+    const float v[3] = {m1 / rho, m2 / rho, m3 / rho};
+    float pr;
+    if (iso) {
+      pr = cs2 * rho;
+    } else {
+      const float ke = 0.5f * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const float me = 0.5f * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+      bool wide = P64;
+      if (P64 && p64_ratio > 0.0f) {
+        const float ei = e - ke - me;
+        wide = ke + me > p64_ratio * ei;
+        pr = (gamma - 1.0f) * ei;
+      }
+      if (wide) {
+        const double ked = 0.5 * ((double)m1 * m1 + (double)m2 * m2 + (double)m3 * m3) / (double)rho;
+        const double med = 0.5 * ((double)bc[0] * bc[0] + (double)bc[1] * bc[1] +
+                                  (double)bc[2] * bc[2]);
+        pr = (float)(((double)gamma - 1.0) * ((double)e - ked - med));
+      } else if (!P64) {
+        pr = (gamma - 1.0f) * (e - ke - me);
+      }
+    }
+    if (!(pr >= p_floor)) { if (!(pr == pr)) bad = true; pr = p_floor; }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float cf = fast_speed(iso ? 1.0f : gamma, rho, pr, bc[d], bc[(d + 1) % 3],
+                                  bc[(d + 2) % 3]);
+      const float dtd = wd[d] / (fabsf(v[d]) + cf);
+      if (!(dtd > 0.0f)) bad = true;
+      m = fminf(m, dtd);
+    }
+  };
+  for (int t = blockIdx.x * 4 + sub; t < total; t += gridDim.x * 4) {
+    int loc;
+    const BlockPtrs<float>& P = S.get(t, loc);
+    const Layout& L = P.L;
+    const int ntx = (L.n[0] + CELL_BX) / CELL_BX, nty = (L.n[1] + CELL_BY) / CELL_BY;
+    const int i4 = (loc % ntx) * CELL_BX + tx4, j = ((loc / ntx) % nty) * CELL_BY + ty;
+    const int k = (loc / (ntx * nty)) * CELL_BZ + tz;
+    if (i4 >= L.n[0] || j >= L.n[1] || k >= L.n[2]) continue;
+    const long long c = L.idx(i4, j, k);
+    const float* const* u = P.reg[0];
+    if (i4 + 3 >= L.n[0]) {
+      for (int q = 0; i4 + q < L.n[0]; ++q) {
+        const long long cq = c + q;
+        float bc[3] = {0.0f, 0.0f, 0.0f};
+        if (mhd) {
+          bc[0] = 0.5f * (u[5][cq] + u[5][cq + 1]);
+          bc[1] = 0.5f * (u[6][cq] + u[6][cq + L.sx]);
+          bc[2] = 0.5f * (u[7][cq] + u[7][cq + L.sx * L.sy]);
+        }
+        const float wd[3] = {P.geo.width[0](i4 + q, j, k), P.geo.width[1](i4 + q, j, k),
+                             P.geo.width[2](i4 + q, j, k)};
+        cell(u[0][cq], u[1][cq], u[2][cq], u[3][cq], iso ? 0.0f : u[4][cq], bc, wd);
+      }
+      continue;
+    }
+    const float4 r4 = ld4c(u[0] + c), a4 = ld4c(u[1] + c), b4 = ld4c(u[2] + c),
+                 c4 = ld4c(u[3] + c);
+    const float4 e4 = iso ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4c(u[4] + c);
+    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), y0 = x0, y1 = x0, z0 = x0, z1 = x0;
+    float x4 = 0.0f;
+    if (mhd) {
+      x0 = ld4c(u[5] + c);
+      x4 = u[5][c + 4];
+      y0 = ld4c(u[6] + c);
+      y1 = ld4c(u[6] + c + L.sx);
+      z0 = ld4c(u[7] + c);
+      z1 = ld4c(u[7] + c + L.sx * L.sy);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float xp = q < 3 ? el4(x0, q + 1) : x4;
+      const float bc[3] = {0.5f * (el4(x0, q) + xp), 0.5f * (el4(y0, q) + el4(y1, q)),
+                           0.5f * (el4(z0, q) + el4(z1, q))};
+      const float wd[3] = {P.geo.width[0](i4 + q, j, k), P.geo.width[1](i4 + q, j, k),
+                           P.geo.width[2](i4 + q, j, k)};
+      cell(el4(r4, q), el4(a4, q), el4(b4, q), el4(c4, q), el4(e4, q), bc, wd);
+    }
+  }
+  const double md = warp_min((double)m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = md;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;
+    v = warp_min(v);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
 __global__ void k_dt_final(const double* __restrict__ partial, int n, double scale,
                            double* __restrict__ dt) {
   __shared__ double sm[32];
@@ -596,24 +720,39 @@ static aeth_status dt_T(aeth_ctx* c) {
   const int grid = std::max(1, std::min(c->dt_grid, (total + 1) / 2));
   const double cs2 = is_iso(c) ? c->cfg.cs_iso * c->cfg.cs_iso : 0.0;
   const double dual_a = is_dual(c) ? c->cfg.alpha_switch : 0.0;
-  auto launch = [&](auto src) {
+  // returns the number of partial minima written
+  auto launch = [&](auto src) -> int {
     using Src = decltype(src);
+    if constexpr (sizeof(R) == 4) {
+      if (dual_a <= 0.0 && c->cfg.n_dust == 0 && AETH_DT_V4) {
+        // FP32 gas: four x cells per thread
+        const int g4 = std::max(1, std::min(c->dt_grid, (total + 3) / 4));
+        k_dt_v4<P64, Src><<<g4, 256, 0, c->stream>>>(
+            src, total, is_mhd(c), (float)c->cfg.gamma, (float)c->cfg.rho_floor,
+            (float)c->cfg.p_floor, (float)cs2,
+            c->cfg.precision == AETH_FP32_SEL64 ? (float)c->cfg.p64_ratio : 0.0f, c->d_partials,
+            c->d_status);
+        return g4;
+      }
+    }
     auto kernel = dual_a > 0.0 ? k_dt<R, P64, Src, true> : k_dt<R, P64, Src, false>;
     kernel<<<grid, 256, 0, c->stream>>>(src, total, is_mhd(c), c->cfg.gamma, c->cfg.rho_floor,
                                          c->cfg.p_floor, c->cfg.n_dust, cs2, dual_a,
                                          c->cfg.precision == AETH_FP32_SEL64
                                              ? (float)c->cfg.p64_ratio : 0.0f,
                                          c->d_partials, c->d_status);
+    return grid;
   };
+  int nparts;
   if (nb == 1) {
-    launch(ParamSrc<R>{block_ptrs<R>(c, 0), 0});
+    nparts = launch(ParamSrc<R>{block_ptrs<R>(c, 0), 0});
   } else {
-    launch(TableSrc<R>{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1), nb,
-                       c->d_tmap[PK_CELL]});
+    nparts = launch(TableSrc<R>{(const BlockPtrs<R>*)c->d_tab, c->d_prefix + PK_CELL * (nb + 1),
+                                nb, c->d_tmap[PK_CELL]});
   }
   c->n_launch += 2;
   const double scale = c->cfg.cfl * cmax_of(c->cfg.integrator);
-  k_dt_final<<<1, 1024, 0, c->stream>>>(c->d_partials, grid, scale, c->d_dt);
+  k_dt_final<<<1, 1024, 0, c->stream>>>(c->d_partials, nparts, scale, c->d_dt);
   AETH_CK(c, cudaGetLastError());
   return AETH_OK;
 }
