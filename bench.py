@@ -7,7 +7,7 @@ Gaussian velocity with P(k) ~ k^-2 on 2 <= k <= 8, rms Mach 2, gamma =
 the device), counted once per cell (zone-cycles).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--prec fp32|fp64|fp32_p64] [--recon plm|ppm|ppm5] [--n 256]
+                  [--prec fp32|fp64|fp32_p64|fp32_sel64] [--recon plm|ppm|ppm5] [--n 256]
                   [--workload turb256|batched512|dust128|wave32|learned512|wave512|tgv128]
                   [--iso] [--dual] [--block-size N] [--hydro] [--riemann lhlld|hlld]
 
@@ -46,7 +46,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fp32_p64"],
+    ap.add_argument("--prec", default=None, choices=["fp32", "fp64", "fp32_p64", "fp32_sel64"],
                     help="working precision (default: fp64 for wave512, the paper's, else fp32)")
     ap.add_argument("--recon", default="plm", choices=["plm", "ppm", "ppm5"])
     ap.add_argument("--path", default="fused", choices=["fused", "unfused"])
@@ -54,7 +54,8 @@ def parse(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="turb256", choices=WORKLOADS)
-    ap.add_argument("--drag", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--drag", default="fp64", choices=["fp64", "fp32", "sel"],
+                    help="dust128: drag solve in FP64, FP32, or FP64 only for the stiff species")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--l1-steps", type=int, default=None,
                     help="steps of the L1 statement against the FP64 GPU path (default: the "
@@ -85,7 +86,7 @@ def parse(argv=None):
         ap.error("--iso applies to the turb256 workload")
     if a.block_size and a.workload not in ("turb256", "wave512", "tgv128"):
         ap.error("--block-size applies to turb256, wave512 and tgv128")
-    if a.dual and (a.workload != "turb256" or a.iso or a.prec == "fp32_p64"):
+    if a.dual and (a.workload != "turb256" or a.iso or a.prec in ("fp32_p64", "fp32_sel64")):
         ap.error("--dual applies to the adiabatic turb256 workload in fp32 or fp64")
     return a
 
@@ -585,7 +586,8 @@ def workload_cfg(a, A, gamma, prec, riemann=None, drag=None, t_stop=None):
         return A.make_config(gamma=5.0 / 3.0, recon=rec, integrator=A.VL2, cfl=0.3,
                              precision=prec, path=path)
     if a.workload == "dust128":
-        d = drag if drag is not None else (A.FP64 if a.drag == "fp64" else A.FP32)
+        d = drag if drag is not None else {"fp64": A.DRAG_FP64, "fp32": A.DRAG_FP32,
+                                           "sel": A.DRAG_SEL64}[a.drag]
         return A.make_config(gamma=gamma, recon=rec, integrator=A.IMEX2P, cfl=0.3,
                              precision=prec, mhd=False, t_stop=t_stop, drag_precision=d)
     if a.workload == "learned512":
@@ -659,7 +661,7 @@ def l1_statement(a, A, torch, stream, states, dust, t_stop, blocks, links, mlp_p
                         "oracle by the parity tests"}
     t0 = time.perf_counter()
     gamma = states[0].gamma
-    prec = {"fp32": A.FP32, "fp32_p64": A.FP32_P64}[a.prec]
+    prec = {"fp32": A.FP32, "fp32_p64": A.FP32_P64, "fp32_sel64": A.FP32_SEL64}[a.prec]
     learned = a.workload == "learned512"
     mhd = not (a.workload in ("dust128", "tgv128") or (a.workload == "wave512" and a.hydro))
     cfgs = {"fp64": workload_cfg(a, A, gamma, A.FP64, t_stop=t_stop, drag=A.FP64,
@@ -811,7 +813,8 @@ def main():
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         base = cpu_baseline(a, None)
 
-    prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64}[a.prec]
+    prec = {"fp32": A.FP32, "fp64": A.FP64, "fp32_p64": A.FP32_P64,
+            "fp32_sel64": A.FP32_SEL64}[a.prec]
     dust = None
     learned = None
     if a.workload == "batched512":
@@ -1038,7 +1041,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": vs_paper(a, value),
-        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32+f64"}[a.prec],
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32+f64",
+                  "fp32_sel64": "f32+f64"}[a.prec],
         "data": "synthetic", "config": workload_config(a),
         "l1": l1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
