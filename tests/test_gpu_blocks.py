@@ -122,3 +122,23 @@ def test_single_block_linked_to_itself_is_periodic():
     ref, dts = oracle_run(st, "ppm", "vl2", nsteps=3)
     (cons, b1, b2, b3), _, _ = _run_blocks(st, ([12], [10], [8]), dts, "ppm", "vl2")
     assert max(compare((cons, b1, b2, b3), ref)) < FP64_TOL
+
+
+def test_linked_blocks_with_dual_energy():
+    """Dual energy (Sec. 2.8) across block links: the entropy is a cell
+    variable that the fill copies across linked faces like the density.  The
+    random MHD box in 12 ragged blocks (most cells trust E) and the cold
+    Mach-800 shear in two blocks along x (every cell takes p from S, so the
+    entropy crossing the link decides the result) against the dual-energy
+    oracle on the whole domain."""
+    from tests.test_gpu_dual import _cold_shear, _oracle as _dual_oracle
+    st = _box((24, 20, 14), 116)
+    ref, dts, _ = _dual_oracle(st, "plm", "vl2", nsteps=4)
+    got, diag, _ = _run_blocks(st, ([9, 15], [8, 5, 7], [6, 8]), dts, dual=True)
+    assert max(compare(got, ref)) < FP64_TOL
+    assert diag["max_divb_rel"] < 1e-12
+    sh = _cold_shear()
+    ref2, dts2, _ = _dual_oracle(sh, "plm", "rk2", nsteps=12, mhd=False)
+    got2, _, _ = _run_blocks(sh, ([24, 40], [4], [4]), dts2, "plm", "rk2", mhd=False, dual=True)
+    errs = [rel_l1(got2[0][v], ref2.cons[v]) for v in (0, 1, 2, 4)]
+    assert max(errs) < FP64_TOL, errs
