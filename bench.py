@@ -1033,9 +1033,10 @@ def main():
     kms_launch = kms / max(klaunch, 1)
     achieved = algo_launch / (kms_launch * 1e-3) / 1e9 if kms > 0 else None
     impl_launch = kbytes / max(klaunch, 1)
+    # the committed ncu figures hold for the 256^3 default grid only
     kernel_key = (f"{a.path}_{a.prec}_{a.recon}" + ("_iso" if a.iso else "")
                   + ("_dual" if a.dual else "") + (f"_b{a.block_size}" if a.block_size else "")
-                  if a.workload == "turb256" else None)
+                  if a.workload == "turb256" and a.n == 256 else None)
     traffic = ncu_traffic(kernel_key) if kernel_key else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,

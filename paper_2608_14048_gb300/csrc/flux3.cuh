@@ -18,10 +18,13 @@ namespace aeth {
 
 constexpr int NT = FLUX_NT;   // threads of a flux tile; its x width TXT is a
                               // template parameter (32 or 16), the y width NT / TXT
-// resident CTAs per SM requested for the FP32 flux pass (register budget
-// 65536 / (256 * FLUX_MINB) per thread)
+// resident CTAs per SM requested for the FP32 flux pass with donor or PLM
+// reconstruction (register budget 65536 / (256 * FLUX_MINB) per thread:
+// 3 CTAs, 85 registers, measured 1.3% faster at 256^3 than 2 CTAs with 106
+// registers); the PPM and PPM5 stencils keep 2 CTAs (at 85 registers they
+// spill about 250 bytes per thread)
 #ifndef AETH_FLUX_MINB
-#define AETH_FLUX_MINB 2
+#define AETH_FLUX_MINB 3
 #endif
 
 __host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
@@ -72,7 +75,7 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // specific entropy S/rho of the upwind side, in scratch slot 3 + D.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0,
           bool DUAL = false, int TXT = FLUX_TX>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? AETH_FLUX_MINB : 1)
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits, R alpha_switch) {
   constexpr int TX = TXT, TY = NT / TXT;
@@ -283,7 +286,7 @@ static void with_src(aeth_ctx* c, int kind, int block, F launch) {
 
 template <typename R, bool P64, int RECON, bool MHD, int SOLVER, bool DUAL>
 static void launch_flux3(aeth_ctx* c, int src, int block) {
-  const int per_sm = sizeof(R) == 4 ? AETH_FLUX_MINB : 1;
+  const int per_sm = sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1;
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
     auto go = [&](auto kernel) {
