@@ -186,13 +186,14 @@ __global__ void __launch_bounds__(256)
     // a_k = h K_k / rho_k is fixed per cell through the solve; a species
     // with no density (rho_k <= 0) feels no drag
     const DT h = (DT)kImexG * (DT)(*A.dt);
-    DT rk[NDMAX], ak[NDMAX], ia[NDMAX];
+    DT rk[NDMAX], ak[NDMAX], ia[NDMAX], irk[NDMAX];
     DT den = rg;
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
       rk[s] = dx[s][0];
-      ak[s] = rk[s] > DT(0) ? h * (DT)A.drag_c[s] / rk[s] : DT(0);
+      irk[s] = rk[s] > DT(0) ? DT(1) / rk[s] : DT(0);
+      ak[s] = h * (DT)A.drag_c[s] * irk[s];
       ia[s] = DT(1) / (DT(1) + ak[s]);
       den += rk[s] * ak[s] * ia[s];
       dy[s][0] = dx[s][0];
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(256)
         const DT m0 = dx[s][1 + q];
         const DT m1 = (m0 + rk[s] * ak[s] * vg) * ia[s];
         dy[s][1 + q] = (R)m1;
-        if (rk[s] > DT(0)) dke2 += (m1 - m0) * (m1 + m0) / rk[s];
+        dke2 += (m1 - m0) * (m1 + m0) * irk[s];
       }
     }
     gy[4] = iso ? gx[4] : (R)((DT)gx[4] - DT(0.5) * dke2);
@@ -225,12 +226,21 @@ __global__ void __launch_bounds__(256)
     // densities in each species' own precision
     const unsigned wide = s_wide;
     DT den = rg;
+    DT ir64[NDMAX];    // 1 / rho_k of the FP64 species (0 for rho_k <= 0)
+    float ir32[NDMAX]; // the same for the FP32 species
 #pragma unroll
     for (int s = 0; s < NDMAX; ++s) {
       if (s >= nd) break;
       dy[s][0] = dx[s][0];
-      if ((wide >> s) & 1u) den += (DT)dx[s][0] * s_wk[s];
-      else den += (DT)((float)dx[s][0] * f_wk[s]);
+      ir64[s] = DT(0);
+      ir32[s] = 0.0f;
+      if ((wide >> s) & 1u) {
+        den += (DT)dx[s][0] * s_wk[s];
+        if ((DT)dx[s][0] > DT(0)) ir64[s] = DT(1) / (DT)dx[s][0];
+      } else {
+        den += (DT)((float)dx[s][0] * f_wk[s]);
+        if ((float)dx[s][0] > 0.0f) ir32[s] = 1.0f / (float)dx[s][0];
+      }
     }
     const DT inv_den = DT(1) / den;
     DT dke2 = 0;
@@ -254,12 +264,12 @@ __global__ void __launch_bounds__(256)
           const DT rk = r, m0 = dx[s][1 + q];
           const DT m1 = (m0 + rk * s_ak[s] * vg) * s_ia[s];
           dy[s][1 + q] = (R)m1;
-          if (rk > DT(0)) dke2 += (m1 - m0) * (m1 + m0) / rk;
+          dke2 += (m1 - m0) * (m1 + m0) * ir64[s];
         } else {
           const float rk = (float)r, m0 = (float)dx[s][1 + q];
           const float m1 = (m0 + rk * f_ak[s] * vgf) * f_ia[s];
           dy[s][1 + q] = (R)m1;
-          if (rk > 0.0f) dke2 += (DT)((m1 - m0) * (m1 + m0) / rk);
+          dke2 += (DT)((m1 - m0) * (m1 + m0) * ir32[s]);
         }
       }
     }
