@@ -112,8 +112,8 @@ def flux_tile_record(A, current, tuned):
     """The flux pass's tile shape in the bench line: width x height x
     z-chunk, and whether the autotuner timed it now or its cache gave it."""
     tx, kc = current
-    return {"tx": tx, "ty": 256 // tx, "kchunk": kc,
-            "source": tuned[2] if tuned else "default (no autotune)"}
+    shape = {"tx": tx, "ty": 256 // tx} if tx else {"tx": "band", "ty": "256 / (n_x + 2) rows"}
+    return {**shape, "kchunk": kc, "source": tuned[2] if tuned else "default (no autotune)"}
 
 
 def learned_n(a):

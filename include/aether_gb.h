@@ -397,9 +397,12 @@ aeth_status aeth_profile_read(aeth_ctx* ctx, double* total_ms,
 
 /* Tile shape of the fused flux pass (no counterpart in the paper): a CTA of
  * 256 threads owns a flux_tx x (256 / flux_tx) column tile of cells and
- * marches kchunk planes along z.  flux_tx = 32 (default) or 16 (FP32 and
- * FP32_P64 / FP32_SEL64 contexts with a classical solver, no dual energy,
- * fused path; AETH_ERR_UNSUPPORTED otherwise); kchunk in 1 .. 1024 (the
+ * marches kchunk planes along z.  flux_tx = 32 (default), 16, or 0 for band
+ * tiles: whole rows of a block (its n_x + 2 flux columns), 256 / (n_x + 2)
+ * rows at a time, which keep the lanes of blocks narrower than a 2-D tile
+ * busy (every block at most 128 cells wide).  16 and 0 are built for FP32
+ * and FP32_P64 / FP32_SEL64 contexts with a classical solver, no dual
+ * energy, fused path (AETH_ERR_UNSUPPORTED otherwise); kchunk in 1 .. 1024 (the
  * default is the largest of 64, 32, 16, 8, 4 that gives every SM four
  * tiles).  The results do not depend on the shape: each face is solved
  * once by the same code.  aeth_set_flux_tile rebuilds the launch tables
@@ -410,10 +413,10 @@ aeth_status aeth_get_flux_tile(aeth_ctx* ctx, int* flux_tx, int* kchunk);
 
 /* Autotuner of the flux pass's tile shape (no counterpart in the paper):
  * times the fused flux pass for z-chunks of 8, 16, 32 and 64 planes per
- * tile, with the 32-wide and (where built) the 16-wide tile, on the current
- * state, and keeps the fastest (written to *flux_tx and *kchunk, either may
- * be NULL).  NOTE: it ADVANCES the state by 3 steps per candidate (24 with
- * both widths) with the current device dt; call it on a scratch copy or
+ * tile, with the 32-wide and (where built) the 16-wide and band tiles, on
+ * the current state, and keeps the fastest (written to *flux_tx and
+ * *kchunk, either may be NULL).  NOTE: it ADVANCES the state by 3 steps per
+ * candidate (up to 36) with the current device dt; call it on a scratch copy or
  * before loading the real state.  The Python helper Solver.tune_tiles
  * keeps each choice in a JSON cache keyed by the block sizes and the
  * configuration. */

@@ -352,9 +352,9 @@ def aeth_profile_read(ctx):
 
 
 def aeth_autotune(ctx):
-    """Time the flux pass's tile candidates (widths 32 / 16, z-chunks 8..64)
-    on the current state (which it advances) and keep the fastest; returns
-    (flux_tx, kchunk)."""
+    """Time the flux pass's tile candidates (widths 32 / 16 / band tiles,
+    z-chunks 8..64) on the current state (which it advances) and keep the
+    fastest; returns (flux_tx, kchunk), flux_tx 0 for band tiles."""
     tx, kc = C.c_int(0), C.c_int(0)
     _check(ctx, load_library().aeth_autotune(ctx, C.byref(tx), C.byref(kc)))
     return tx.value, kc.value

@@ -29,6 +29,18 @@ constexpr int NT = FLUX_NT;   // threads of a flux tile; its x width TXT is a
 
 __host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
 
+// Shared-memory plane of a band tile (TXT = 0, see band_rows): the largest
+// (rows + halo) x (width + halo) over the widths the band tile takes.
+__host__ __device__ constexpr int band_smem(int halo) {
+  int m = 0;
+  for (int w = 3; w <= FLUX_BAND_WMAX; ++w) {
+    const int br = band_rows(w - 2);
+    const int a = (br + halo) * (w + halo);
+    m = a > m ? a : m;
+  }
+  return m;
+}
+
 // Solver families 3 and 4 are the isothermal ones.
 constexpr bool iso_solver(int solver) { return solver == 3 || solver == 4; }
 
@@ -73,19 +85,23 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // (below alpha_switch x kinetic + magnetic) comes from the entropy, and each
 // face also gets the entropy flux, its mass flux times the reconstructed
 // specific entropy S/rho of the upwind side, in scratch slot 3 + D.
+// TXT: the tile's x width (32 or 16; y width NT / TXT), or 0 for a band
+// tile: whole rows of the block (x from -1 to n_x), band_rows(n_x) of them,
+// so that a block narrower than the 2-D tile keeps its lanes busy.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0,
           bool DUAL = false, int TXT = FLUX_TX>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1)
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits, R alpha_switch) {
-  constexpr int TX = TXT, TY = NT / TXT;
+  constexpr bool BAND = TXT == 0;
+  constexpr int TX = BAND ? 1 : TXT, TY = NT / TX;
   constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
   constexpr int QN = RL + RH + 1;
   constexpr int NW = NPRIM + (DUAL ? 1 : 0);   // staged planes (+ S/rho)
   constexpr int NQ = 7 + (DUAL ? 1 : 0);       // z-queue variables (+ S/rho)
-  __shared__ R sw[NW][WY][WX];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  constexpr int SN = BAND ? band_smem(RL + RH) : WX * WY;
+  __shared__ R sw[NW][SN];   // plane (tile + halo), row pitch wxr
   constexpr bool ISO = iso_solver(SOLVER);
   const R gm1 = ISO ? gamma * gamma : gamma - R(1);   // cs^2 for ISO
   int hits = 0;
@@ -94,18 +110,38 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
     int loc;
     const BlockPtrs<R>& P = S.get(t, loc);
     const Layout L = P.L;
-    const int ntx = ceil_div_d(L.n[0] + 2, TX), nty = ceil_div_d(L.n[1] + 2, TY);
-    const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
     const R* __restrict__ ub = P.reg[src][0];   // state arrays at ub + v * pitch
     const R* __restrict__ eb = P.ent[src];       // entropy (DUAL)
     R* __restrict__ sb = P.w[0];                 // scratch arrays at sb + slot * pitch
     const long long pitch = P.pitch;
-    const int i0 = -1 + bx * TX, j0 = -1 + by * TY;
-    const int i = i0 + tx, j = j0 + ty;
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    int i0, j0, bz, tx, ty, wxr, wyr;
+    if constexpr (BAND) {
+      const int W = nx + 2, br = band_rows(nx);
+      const int nb = ceil_div_d(ny + 2, br);
+      bz = loc / nb;
+      i0 = -1;
+      j0 = -1 + (loc % nb) * br;
+      tx = (int)threadIdx.x % W;
+      ty = (int)threadIdx.x / W;   // >= br: an idle thread of the band
+      wxr = W + RL + RH;
+      wyr = br + RL + RH;
+    } else {
+      const int ntx = ceil_div_d(nx + 2, TX), nty = ceil_div_d(ny + 2, TY);
+      const int bx = loc % ntx, by = (loc / ntx) % nty;
+      bz = loc / (ntx * nty);
+      i0 = -1 + bx * TX;
+      j0 = -1 + by * TY;
+      tx = (int)threadIdx.x % TX;
+      ty = (int)threadIdx.x / TX;
+      wxr = WX;
+      wyr = WY;
+    }
+    const int i = i0 + tx, j = j0 + ty;
     const int k0 = -1 + bz * kchunk;
     const int k1 = min(nz, k0 + kchunk - 1);
-    const bool active = i <= nx && j <= ny;
+    const bool active =
+        i <= nx && j <= ny && (!BAND || ty < band_rows(nx));
 
     // primitives of cell cc (+ specific entropy sp with DUAL); returns floor hits
     auto prim_at = [&](long long cc, R* w, R& sp) -> int {
@@ -138,8 +174,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
     for (int k = k0; k <= k1; ++k) {
       __syncthreads();
       // stage plane k (tile + halo) in shared memory
-      for (int s = threadIdx.x; s < WX * WY; s += NT) {
-        const int rx = s % WX, ry = s / WX;
+      for (int s = threadIdx.x; s < wxr * wyr; s += NT) {
+        const int rx = s % wxr, ry = s / wxr;
         const int ci = i0 - RL + rx, cj = j0 - RL + ry;
         R w[8], sp = R(1);
         if (in_prim_range(L, ci, cj, k)) {
@@ -148,8 +184,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
           w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
         }
 #pragma unroll
-        for (int v = 0; v < NPRIM; ++v) sw[v][ry][rx] = w[v];
-        if constexpr (DUAL) sw[NW - 1][ry][rx] = sp;
+        for (int v = 0; v < NPRIM; ++v) sw[v][s] = w[v];
+        if constexpr (DUAL) sw[NW - 1][s] = sp;
       }
       // advance the z queue: drop plane k-RL-1, add plane k+RH
 #pragma unroll
@@ -169,7 +205,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
           if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
-          recon_var<RECON>([&](int off) { return sw[slot[v]][sy][sx + off]; }, wl[v], wr[v]);
+          recon_var<RECON>([&](int off) { return sw[slot[v]][sy * wxr + sx + off]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[5 * pitch + fc] : R(0);
         if (SOLVER != 1) {
@@ -177,7 +213,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
           store_face<0>(sb, pitch, fc, fx);
           if constexpr (DUAL) {
             R sl, sr;
-            recon_var<RECON>([&](int off) { return sw[NW - 1][sy][sx + off]; }, sl, sr);
+            recon_var<RECON>([&](int off) { return sw[NW - 1][sy * wxr + sx + off]; }, sl, sr);
             sb[3 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
           }
         } else {
@@ -193,7 +229,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
           if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
-          recon_var<RECON>([&](int off) { return sw[slot[v]][sy + off][sx]; }, wl[v], wr[v]);
+          recon_var<RECON>([&](int off) { return sw[slot[v]][(sy + off) * wxr + sx]; }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[6 * pitch + fc] : R(0);
         if (SOLVER != 1) {
@@ -201,7 +237,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
           store_face<1>(sb, pitch, fc, fx);
           if constexpr (DUAL) {
             R sl, sr;
-            recon_var<RECON>([&](int off) { return sw[NW - 1][sy + off][sx]; }, sl, sr);
+            recon_var<RECON>([&](int off) { return sw[NW - 1][(sy + off) * wxr + sx]; }, sl, sr);
             sb[4 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
           }
         } else {
@@ -236,8 +272,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
       }
       // ---- cell-centred reference EMF, E = -v x B
       if (MHD) {
-        const R vx = sw[1][sy][sx], vy = sw[2][sy][sx], vz = sw[3][sy][sx];
-        const R bx_ = sw[5][sy][sx], by_ = sw[6][sy][sx], bz_ = sw[7][sy][sx];
+        const int sc = sy * wxr + sx;
+        const R vx = sw[1][sc], vy = sw[2][sc], vz = sw[3][sc];
+        const R bx_ = sw[5][sc], by_ = sw[6][sc], bz_ = sw[7][sc];
         sb[fc] = -(vy * bz_ - vz * by_);
         sb[pitch + fc] = -(vz * bx_ - vx * bz_);
         sb[2 * pitch + fc] = -(vx * by_ - vy * bx_);
@@ -300,6 +337,10 @@ static void launch_flux3(aeth_ctx* c, int src, int block) {
     if constexpr (sizeof(R) == 4 && !DUAL && SOLVER != 1) {
       if (c->flux_tx == 16) {
         go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 16>);
+        return;
+      }
+      if (c->flux_tx == 0) {
+        go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 0>);
         return;
       }
     }

@@ -45,21 +45,25 @@ __device__ __forceinline__ double warp_min_na(double v) {
   return v;
 }
 
-// Eq. 11 on the plain FP64 layout of the C ABI: one CUDA block per x-row
-// writes that row's minimum of dx_d / (|v_d| + c_f,d).
-__global__ void __launch_bounds__(256)
+// Eq. 11 on the plain FP64 layout of the C ABI: one warp per x-row writes
+// that row's minimum of dx_d / (|v_d| + c_f,d) (eight rows per CUDA block,
+// so short rows do not leave most of a block idle).
+constexpr int kRowsPerBlock = 8;
+
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
     k_dt_rows_plain(const double* __restrict__ cons, const double* __restrict__ b1,
                     const double* __restrict__ b2, const double* __restrict__ b3, int nx, int ny,
                     int nz, double dx1, double dx2, double dx3, double gamma, double rho_floor,
                     double p_floor, int mhd, NoAllocScratch* s) {
-  __shared__ double sm[8];
-  const int r = blockIdx.x;
+  const int r = blockIdx.x * kRowsPerBlock + (int)(threadIdx.x >> 5);
+  const int lane = (int)threadIdx.x & 31;
+  if (r >= ny * nz) return;   // whole warps leave together
   const int j = r % ny, k = r / ny;
   const long long nc = (long long)nx * ny * nz;
   const double w[3] = {dx1, dx2, dx3};
   double m = INFINITY;
   bool bad = false;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+  for (int i = lane; i < nx; i += 32) {
     const long long c = ((long long)k * ny + j) * nx + i;
     double rho = cons[c];
     if (!(rho >= rho_floor)) { if (!(rho == rho)) bad = true; rho = rho_floor; }
@@ -85,13 +89,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   m = warp_min_na(m);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : INFINITY;
-    v = warp_min_na(v);
-    if (threadIdx.x == 0) s->partial[r] = v;
-  }
+  if (lane == 0) s->partial[r] = m;
   if (bad) atomicOr(&s->status, 1);
 }
 
@@ -143,8 +141,9 @@ extern "C" aeth_status aeth_cfl_dt_noalloc(const double* d_cons, const double* d
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // the status word must start at zero; the partials are all rewritten
   if (cudaMemsetAsync(&s->status, 0, sizeof(int), st) != cudaSuccess) return AETH_ERR_CUDA;
-  k_dt_rows_plain<<<(unsigned)rows, 256, 0, st>>>(d_cons, d_b1, d_b2, d_b3, nx, ny, nz, dx1, dx2,
-                                                  dx3, gamma, rho_floor, p_floor, mhd, s);
+  k_dt_rows_plain<<<(unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock), 32 * kRowsPerBlock, 0,
+                    st>>>(d_cons, d_b1, d_b2, d_b3, nx, ny, nz, dx1, dx2, dx3, gamma, rho_floor,
+                          p_floor, mhd, s);
   k_dt_rows_final<<<1, 1024, 0, st>>>(s, (int)rows, cfl, d_dt);
   if (cudaGetLastError() != cudaSuccess) return AETH_ERR_CUDA;
   return AETH_OK;

@@ -645,10 +645,14 @@ aeth_status aeth_profile_read(aeth_ctx* c, double* ms, long long* n, double* byt
 aeth_status aeth_set_flux_tile(aeth_ctx* c, int flux_tx, int kchunk) {
   if (!c) return AETH_ERR_ARG;
   if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
-  if (flux_tx != 32 && flux_tx != 16) return fail(c, AETH_ERR_ARG, "flux tile width 32 or 16");
+  if (flux_tx != 32 && flux_tx != 16 && flux_tx != 0)
+    return fail(c, AETH_ERR_ARG, "flux tile width 32, 16 or 0 (band tiles)");
   if (!(kchunk >= 1 && kchunk <= 1024)) return fail(c, AETH_ERR_ARG, "z-chunk 1..1024");
   if (flux_tx != 32 && !tile_shape_tunable(c))
     return fail(c, AETH_ERR_UNSUPPORTED, "this configuration keeps the 32-wide flux tile");
+  if (flux_tx == 0 && !band_tiles_fit(c))
+    return fail(c, AETH_ERR_UNSUPPORTED, "band tiles need blocks at most %d cells wide",
+                FLUX_BAND_WMAX - 2);
   c->flux_tx = flux_tx;
   c->kchunk = kchunk;
   aeth_status s = build_tables(c);
@@ -678,6 +682,7 @@ aeth_status aeth_autotune(aeth_ctx* c, int* tx_out, int* kchunk_out) {
   double best_ms = 1e300;
   std::vector<int> widths = {32};
   if (tile_shape_tunable(c)) widths.push_back(16);
+  if (band_tiles_fit(c)) widths.push_back(0);
   for (int tx : widths) {
     for (int kc : {8, 16, 32, 64}) {
       c->flux_tx = tx;

@@ -57,15 +57,23 @@ enum PassKind : int { PK_FLUX = 0, PK_CELL = 1, PK_FILL0 = 2, PK_FILL1 = 3, PK_F
 // Tile geometry of each pass kind (threads per tile fixed per kind).
 constexpr int FLUX_TX = 32, FLUX_TY = 8;   // default flux tile (256 threads)
 constexpr int FLUX_NT = FLUX_TX * FLUX_TY;
+// Band tiles (flux tile width 0): whole rows of a block, x from -1 to n_x,
+// as many rows as fit the 256 threads; for blocks with n_x + 2 <= 130.
+constexpr int FLUX_BAND_WMAX = 130;
+__host__ __device__ constexpr int band_rows(int nx) {
+  return FLUX_NT / (nx + 2) > 1 ? FLUX_NT / (nx + 2) : 1;
+}
 constexpr int CELL_BX = 32, CELL_BY = 4, CELL_BZ = 2;
 constexpr int FILL_TILE = 256;   // ghost cells per tile of the fill pass
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Tiles of one block for a pass kind (kchunk: z extent of a flux tile,
-// tx: its x width, FLUX_NT / tx its y width).
+// tx: its x width, FLUX_NT / tx its y width; tx = 0: band tiles).
 inline int tiles_of(const Layout& L, int kind, int kchunk, int tx = FLUX_TX) {
   const int g = L.g;
+  if (kind == PK_FLUX && tx == 0)
+    return ceil_div(L.n[1] + 2, band_rows(L.n[0])) * ceil_div(L.n[2] + 2, kchunk);
   if (kind == PK_FLUX)
     return ceil_div(L.n[0] + 2, tx) * ceil_div(L.n[1] + 2, FLUX_NT / tx) *
            ceil_div(L.n[2] + 2, kchunk);
@@ -137,7 +145,7 @@ struct aeth_ctx {
   int kchunk = 0;                     // z extent of a flux tile (0: choose;
                                       // aeth_autotune times candidates)
   int flux_tx = 32;                   // x width of a flux tile (32 or 16; the y
-                                      // width is 256 / flux_tx)
+                                      // width is 256 / flux_tx), or 0: band tiles
   int num_sms = 152;
   int dt_grid = 1;                    // CTAs of the batched reductions
   // error text
@@ -282,6 +290,15 @@ inline bool is_dual(const aeth_ctx* c) { return c->cfg.dual_energy != 0; }
 inline bool tile_shape_tunable(const aeth_ctx* c) {
   return c->cfg.precision != AETH_FP64 && !is_dual(c) && c->cfg.riemann != AETH_RIEMANN_MLP &&
          c->cfg.path == AETH_PATH_FUSED;
+}
+
+// Band tiles need every block at most FLUX_BAND_WMAX cells wide (with the
+// two extra flux columns).
+inline bool band_tiles_fit(const aeth_ctx* c) {
+  if (!tile_shape_tunable(c)) return false;
+  for (const auto& B : c->blocks)
+    if (B.L.n[0] + 2 > FLUX_BAND_WMAX) return false;
+  return true;
 }
 
 // internal solver codes of the unfused face kernel, distinct from every
