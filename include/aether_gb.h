@@ -400,7 +400,7 @@ aeth_status aeth_profile_read(aeth_ctx* ctx, double* total_ms,
  * marches kchunk planes along z.  flux_tx = 32 (default), 16, or 0 for band
  * tiles: whole rows of a block (its n_x + 2 flux columns), 256 / (n_x + 2)
  * rows at a time, which keep the lanes of blocks narrower than a 2-D tile
- * busy (every block at most 128 cells wide).  16 and 0 are built for FP32
+ * busy (every block at most 64 cells wide).  16 and 0 are built for FP32
  * and FP32_P64 / FP32_SEL64 contexts with a classical solver, no dual
  * energy, fused path (AETH_ERR_UNSUPPORTED otherwise); kchunk in 1 .. 1024 (the
  * default is the largest of 64, 32, 16, 8, 4 that gives every SM four

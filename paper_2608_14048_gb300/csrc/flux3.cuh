@@ -2,8 +2,9 @@
 // reconstruction and the Riemann solver for all three face directions of
 // every cell in one sweep.  A CTA owns a TX x TY column tile and marches
 // along z: each x-y plane of primitives (with the reconstruction halo) is
-// staged in shared memory for the x- and y-faces, while every thread keeps
-// the z-stencil of its own column in a register queue for the z-faces.
+// staged in a ring of shared-memory planes for the x- and y-faces, while
+// every thread keeps the z-stencil of its own column in a register queue
+// for the z-faces, filled from the ring.
 // Each face is solved exactly once.  Outputs: hydro fluxes, face EMFs (the
 // transverse induction fluxes) and the cell-centred reference EMF of the
 // upwind CT scheme.
@@ -29,17 +30,33 @@ constexpr int NT = FLUX_NT;   // threads of a flux tile; its x width TXT is a
 
 __host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
 
-// Shared-memory plane of a band tile (TXT = 0, see band_rows): the largest
-// (rows + halo) x (width + halo) over the widths the band tile takes.
+// Shared-memory plane (one variable, tile + halo) of a band tile (TXT = 0,
+// see band_rows): the largest (rows + halo) x (width + halo) over the
+// widths a band tile takes, so that its stride is a compile-time constant.
 __host__ __device__ constexpr int band_smem(int halo) {
   int m = 0;
   for (int w = 3; w <= FLUX_BAND_WMAX; ++w) {
-    const int br = band_rows(w - 2);
-    const int a = (br + halo) * (w + halo);
+    const int a = (band_rows(w - 2) + halo) * (w + halo);
     m = a > m ? a : m;
   }
   return m;
 }
+
+// Values of one staged variable plane of a flux tile TXT wide (0: band).
+template <int RECON>
+__host__ __device__ constexpr int flux_plane(int txt) {
+  return txt ? (txt + 2 * recon_reach<RECON>() + 1) * (FLUX_NT / txt + 2 * recon_reach<RECON>() + 1)
+             : band_smem(2 * recon_reach<RECON>() + 1);
+}
+
+// Planes in the shared-memory ring of a 2-D flux tile: the z-queue takes
+// plane k + RH while the x- and y-faces read plane k, and the next plane is
+// staged while slower warps still read plane k - 1.  Band tiles stage one
+// plane at a time (two barriers per plane, the z queue from memory): on the
+// small blocks they serve, the ring's larger shared-memory footprint cost
+// more in L1 hits than its one barrier per plane saved.
+template <int RECON>
+__host__ __device__ constexpr int flux_ring(int txt) { return txt ? recon_reach<RECON>() + 2 : 1; }
 
 // Solver families 3 and 4 are the isothermal ones.
 constexpr bool iso_solver(int solver) { return solver == 3 || solver == 4; }
@@ -88,6 +105,8 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // TXT: the tile's x width (32 or 16; y width NT / TXT), or 0 for a band
 // tile: whole rows of the block (x from -1 to n_x), band_rows(n_x) of them,
 // so that a block narrower than the 2-D tile keeps its lanes busy.
+// Dynamic shared memory: flux_ring<RECON>(TXT) x NW planes of
+// flux_plane<RECON>(TXT) values.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0,
           bool DUAL = false, int TXT = FLUX_TX>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1)
@@ -98,10 +117,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
   constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
   constexpr int QN = RL + RH + 1;
-  constexpr int NW = NPRIM + (DUAL ? 1 : 0);   // staged planes (+ S/rho)
+  constexpr int NB = flux_ring<RECON>(TXT);
+  constexpr bool RING = NB > 1;
+  constexpr int NW = NPRIM + (DUAL ? 1 : 0);   // staged variables (+ S/rho)
   constexpr int NQ = 7 + (DUAL ? 1 : 0);       // z-queue variables (+ S/rho)
-  constexpr int SN = BAND ? band_smem(RL + RH) : WX * WY;
-  __shared__ R sw[NW][SN];   // plane (tile + halo), row pitch wxr
+  extern __shared__ __align__(16) unsigned char flux_smem[];
+  R* __restrict__ sw = reinterpret_cast<R*>(flux_smem);
+  constexpr int SN = flux_plane<RECON>(TXT);   // values of one staged plane
+  // variable v of ring plane b at plane offset s (row pitch wxr)
+  auto at = [&](int b, int v, int s) -> R& { return sw[(b * NW + v) * SN + s]; };
   constexpr bool ISO = iso_solver(SOLVER);
   const R gm1 = ISO ? gamma * gamma : gamma - R(1);   // cs^2 for ISO
   int hits = 0;
@@ -154,50 +178,94 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
       }
     };
     // z register queue of the own column: planes k-RL .. k+RH, 7 variables
-    // (+ S/rho; the z-face normal field comes from the face array)
+    // (+ S/rho; the z-face normal field comes from the face array), in the
+    // z-face frame order rho, vz, vx, vy, p, Bx, By
     R q[NQ][QN];
-    auto load_q = [&](int slot, int kk) {
+    auto load_q = [&](int slot, int kk) {   // from memory (planes below the chunk)
       R w[8], sp = R(1);
       if (active && in_prim_range(L, i, j, kk)) {
         prim_at(L.idx(i, j, kk), w, sp);
       } else {
         w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
       }
-      // z-face frame order: rho, vz, vx, vy, p, Bx, By
       q[0][slot] = w[0]; q[1][slot] = w[3]; q[2][slot] = w[1]; q[3][slot] = w[2];
       q[4][slot] = w[4]; q[5][slot] = w[5]; q[6][slot] = w[6];
       if constexpr (DUAL) q[NQ - 1][slot] = sp;
     };
-#pragma unroll
-    for (int s = 0; s < QN - 1; ++s) load_q(s + 1, k0 - RL + s);
-
-    for (int k = k0; k <= k1; ++k) {
-      __syncthreads();
-      // stage plane k (tile + halo) in shared memory
+    const int sx = tx + RL, sy = ty + RL, so = sy * wxr + sx;   // own cell in a plane
+    auto ring_q = [&](int slot, int b) {    // from the staged plane in ring slot b
+      if (!active) return;
+      q[0][slot] = at(b, 0, so); q[1][slot] = at(b, 3, so); q[2][slot] = at(b, 1, so);
+      q[3][slot] = at(b, 2, so); q[4][slot] = at(b, 4, so); q[5][slot] = at(b, 5, so);
+      q[6][slot] = at(b, 6, so);
+      if constexpr (DUAL) q[NQ - 1][slot] = at(b, NW - 1, so);
+    };
+    // stage plane kk (tile + halo) into ring slot b
+    auto stage = [&](int kk, int b) {
       for (int s = threadIdx.x; s < wxr * wyr; s += NT) {
         const int rx = s % wxr, ry = s / wxr;
         const int ci = i0 - RL + rx, cj = j0 - RL + ry;
         R w[8], sp = R(1);
-        if (in_prim_range(L, ci, cj, k)) {
-          hits += prim_at(L.idx(ci, cj, k), w, sp);
+        if (in_prim_range(L, ci, cj, kk)) {
+          const int h = prim_at(L.idx(ci, cj, kk), w, sp);
+          if (kk <= k1) hits += h;   // the planes above the chunk are the next one's
         } else {
           w[0] = R(1); w[1] = w[2] = w[3] = R(0); w[4] = R(1); w[5] = w[6] = w[7] = R(0);
         }
 #pragma unroll
-        for (int v = 0; v < NPRIM; ++v) sw[v][s] = w[v];
-        if constexpr (DUAL) sw[NW - 1][s] = sp;
+        for (int v = 0; v < NPRIM; ++v) at(b, v, s) = w[v];
+        if constexpr (DUAL) at(b, NW - 1, s) = sp;
       }
-      // advance the z queue: drop plane k-RL-1, add plane k+RH
+    };
+    // the previous tile's last plane is read until every warp is past here
+    __syncthreads();
+    if constexpr (RING) {
 #pragma unroll
-      for (int v = 0; v < NQ; ++v)
+      for (int s = 0; s < RL; ++s) load_q(s, k0 - RL + s);
 #pragma unroll
-        for (int s = 0; s < QN - 1; ++s) q[v][s] = q[v][s + 1];
-      load_q(QN - 1, k + RH);
-      __syncthreads();
+      for (int m = 0; m < RH; ++m) stage(k0 + m, m);
+    } else {
+#pragma unroll
+      for (int s = 0; s < QN - 1; ++s) load_q(s + 1, k0 - RL + s);
+    }
+    for (int k = k0; k <= k1; ++k) {
+      int bk = 0;
+      if constexpr (RING) {
+        // plane k + RH goes to ring slot (k - k0 + RH) % NB, which last held
+        // plane k - 2, read by no warp past the previous barrier: one
+        // barrier per plane, and each warp stages the next plane as soon as
+        // its faces are done
+        const int m = k - k0;
+        const int bq = (m + RH) % NB;
+        bk = m % NB;
+        stage(k + RH, bq);
+        __syncthreads();
+        if (m == 0) {
+#pragma unroll
+          for (int s = 0; s <= RH; ++s) ring_q(RL + s, s);
+        } else {
+          // advance the z queue: drop plane k-RL-1, add plane k+RH
+#pragma unroll
+          for (int v = 0; v < NQ; ++v)
+#pragma unroll
+            for (int s = 0; s < QN - 1; ++s) q[v][s] = q[v][s + 1];
+          ring_q(QN - 1, bq);
+        }
+      } else {
+        // one staged plane, the z queue from memory
+        if (k > k0) __syncthreads();
+        stage(k, 0);
+#pragma unroll
+        for (int v = 0; v < NQ; ++v)
+#pragma unroll
+          for (int s = 0; s < QN - 1; ++s) q[v][s] = q[v][s + 1];
+        load_q(QN - 1, k + RH);
+        __syncthreads();
+      }
       if (!active) continue;
 
+      // the faces of plane k from ring slot bk (x, y, E_ref) and the z queue
       const long long fc = L.idx(i, j, k);
-      const int sx = tx + RL, sy = ty + RL;
       R wl[7], wr[7], fx[7];
       // ---- x-face (i-1/2, j, k): frame (rho, vx, vy, vz, p, By, Bz)
       if (i >= 0) {
@@ -205,7 +273,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
           if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
-          recon_var<RECON>([&](int off) { return sw[slot[v]][sy * wxr + sx + off]; }, wl[v], wr[v]);
+          recon_var<RECON>([&](int off) { return at(bk, slot[v], so + off); }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[5 * pitch + fc] : R(0);
         if (SOLVER != 1) {
@@ -213,7 +281,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
           store_face<0>(sb, pitch, fc, fx);
           if constexpr (DUAL) {
             R sl, sr;
-            recon_var<RECON>([&](int off) { return sw[NW - 1][sy * wxr + sx + off]; }, sl, sr);
+            recon_var<RECON>([&](int off) { return at(bk, NW - 1, so + off); }, sl, sr);
             sb[3 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
           }
         } else {
@@ -229,7 +297,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
           if ((!MHD && v >= 5) || (ISO && v == 4)) { wl[v] = wr[v] = R(0); continue; }
-          recon_var<RECON>([&](int off) { return sw[slot[v]][(sy + off) * wxr + sx]; }, wl[v], wr[v]);
+          recon_var<RECON>([&](int off) { return at(bk, slot[v], so + off * wxr); }, wl[v], wr[v]);
         }
         const R bn = MHD ? ub[6 * pitch + fc] : R(0);
         if (SOLVER != 1) {
@@ -237,7 +305,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
           store_face<1>(sb, pitch, fc, fx);
           if constexpr (DUAL) {
             R sl, sr;
-            recon_var<RECON>([&](int off) { return sw[NW - 1][(sy + off) * wxr + sx]; }, sl, sr);
+            recon_var<RECON>([&](int off) { return at(bk, NW - 1, so + off * wxr); }, sl, sr);
             sb[4 * pitch + fc] = fx[0] >= R(0) ? fx[0] * sl : fx[0] * sr;
           }
         } else {
@@ -272,9 +340,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FL
       }
       // ---- cell-centred reference EMF, E = -v x B
       if (MHD) {
-        const int sc = sy * wxr + sx;
-        const R vx = sw[1][sc], vy = sw[2][sc], vz = sw[3][sc];
-        const R bx_ = sw[5][sc], by_ = sw[6][sc], bz_ = sw[7][sc];
+        const R vx = at(bk, 1, so), vy = at(bk, 2, so), vz = at(bk, 3, so);
+        const R bx_ = at(bk, 5, so), by_ = at(bk, 6, so), bz_ = at(bk, 7, so);
         sb[fc] = -(vy * bz_ - vz * by_);
         sb[pitch + fc] = -(vz * bx_ - vx * bz_);
         sb[2 * pitch + fc] = -(vx * by_ - vy * bx_);
@@ -324,10 +391,17 @@ static void with_src(aeth_ctx* c, int kind, int block, F launch) {
 template <typename R, bool P64, int RECON, bool MHD, int SOLVER, bool DUAL>
 static void launch_flux3(aeth_ctx* c, int src, int block) {
   const int per_sm = sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1;
+  constexpr int NW = NPRIM + (DUAL ? 1 : 0);
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
     const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
-    auto go = [&](auto kernel) {
-      kernel<<<grid, NT, 0, c->stream>>>(
+    // tx: the tile width the kernel was built for (0: band tiles)
+    auto go = [&](auto kernel, int tx) {
+      const int bytes = flux_ring<RECON>(tx) * NW * flux_plane<RECON>(tx) * (int)sizeof(R);
+      // above the 48 KB default (FP64, PPM rings, bands); a plain attribute
+      // call, also legal while a graph is being captured
+      if (bytes > 48 * 1024)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      kernel<<<grid, NT, bytes, c->stream>>>(
           S, r.t0, r.t1, src, (R)(iso_solver(SOLVER) ? c->cfg.cs_iso : c->cfg.gamma),
           (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk, c->d_floor,
           (R)c->cfg.alpha_switch);
@@ -336,15 +410,15 @@ static void launch_flux3(aeth_ctx* c, int src, int block) {
     // whose tiles the autotuner may switch: tile_shape_tunable)
     if constexpr (sizeof(R) == 4 && !DUAL && SOLVER != 1) {
       if (c->flux_tx == 16) {
-        go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 16>);
+        go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 16>, 16);
         return;
       }
       if (c->flux_tx == 0) {
-        go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 0>);
+        go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 0>, 0);
         return;
       }
     }
-    go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 32>);
+    go(k_flux3<R, P64, RECON, MHD, decltype(S), SOLVER, DUAL, 32>, 32);
   });
   c->n_launch += 1;
 }

@@ -58,8 +58,10 @@ enum PassKind : int { PK_FLUX = 0, PK_CELL = 1, PK_FILL0 = 2, PK_FILL1 = 3, PK_F
 constexpr int FLUX_TX = 32, FLUX_TY = 8;   // default flux tile (256 threads)
 constexpr int FLUX_NT = FLUX_TX * FLUX_TY;
 // Band tiles (flux tile width 0): whole rows of a block, x from -1 to n_x,
-// as many rows as fit the 256 threads; for blocks with n_x + 2 <= 130.
-constexpr int FLUX_BAND_WMAX = 130;
+// as many rows as fit the 256 threads; for blocks with n_x + 2 <= 66 (wider
+// blocks keep most lanes of a 2-D tile busy, and the bound keeps the band's
+// shared-memory ring within two PPM CTAs per SM).
+constexpr int FLUX_BAND_WMAX = 66;
 __host__ __device__ constexpr int band_rows(int nx) {
   return FLUX_NT / (nx + 2) > 1 ? FLUX_NT / (nx + 2) : 1;
 }

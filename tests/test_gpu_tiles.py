@@ -7,7 +7,7 @@ blocks.  The band tiles (whole rows of a block) run the same arithmetic in
 a kernel the compiler arranges differently, and its multiply-add
 contractions differ in a few per cent of the faces: their states agree
 with the 2-D tiles' to a few FP32 ulps, and with the oracle at the FP32
-bound on narrow, ragged and 128-wide blocks.  The autotuner picks a built shape, and Solver.tune_tiles
+bound on narrow, ragged and 64-wide blocks.  The autotuner picks a built shape, and Solver.tune_tiles
 stores it in its JSON cache and takes it from there the second time."""
 import numpy as np
 import pytest
@@ -73,12 +73,12 @@ def test_tile_shapes_identical_on_uneven_blocks():
 @pytest.mark.parametrize("recon", ["plm", "ppm"])
 def test_band_tiles_parity_on_narrow_ragged_and_widest_blocks(recon):
     # widths 1 (three flux columns), 14 (16 columns: the band rows fill the
-    # 256 threads exactly), 17 (ragged: 13 rows and 22 idle threads) and 128
-    # (the widest band, two rows); each block is its own periodic box, so
+    # 256 threads exactly), 17 (ragged: 13 rows and 22 idle threads) and 64
+    # (the widest band, three rows); each block is its own periodic box, so
     # the oracle advances each alone with the same dt sequence
     from tests.gpu_helpers import RECON, compare, oracle_run
     sts = [I.smooth_random_mhd(I.Block(n), 70 + q, v_rms=0.4, b_rms=0.5)
-           for q, n in enumerate(((1, 12, 6), (14, 9, 7), (17, 11, 5), (128, 5, 4)))]
+           for q, n in enumerate(((1, 12, 6), (14, 9, 7), (17, 11, 5), (64, 7, 4)))]
     dts = [4e-4] * 3
     cfg = A.make_config(gamma=sts[0].gamma, precision=A.FP32, recon=RECON[recon][1])
     import torch
@@ -111,8 +111,8 @@ def test_tile_shape_rejections():
             assert e.value.code == -1
     finally:
         sv.close()
-    # band tiles take blocks at most 128 cells wide
-    sv = A.Solver(A.make_config(precision=A.FP32), [A.make_block((129, 4, 4))],
+    # band tiles take blocks at most 64 cells wide
+    sv = A.Solver(A.make_config(precision=A.FP32), [A.make_block((65, 4, 4))],
                   stream=torch.cuda.current_stream())
     try:
         with pytest.raises(A.AethError) as e:
