@@ -293,8 +293,9 @@ __device__ __forceinline__ float at4(const float4& v, int q) {
   return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
 
-// Corner EMFs of four consecutive x cells per thread (FP32 Cartesian
-// blocks): every operand is a 16-byte load at the group's own column or a
+// Corner EMFs of four consecutive x cells per thread (FP32 blocks; the
+// upwind corner EMF uses no geometry, so Cartesian and spherical blocks
+// alike): every operand is a 16-byte load at the group's own column or a
 // y / z neighbour, or, for the x-shifted operands (the b = x side of E_y,
 // the a = x side of E_z), the same load shifted by one scalar from column
 // i - 1.  Groups at the upper x end take the per-cell path.
@@ -404,15 +405,17 @@ __global__ void __launch_bounds__(64, COORD == 0 ? AETH_UPD4_MINB : 12)
   const BlockPtrs<float>& B = S.get(t0 + (int)blockIdx.x, loc);
   const Layout& L = B.L;
   if (COORD == 2 && L.coord == AETH_COORD_SPH) {
-    // a spherical block: the per-cell path with the sources of Eq. 12
+    // a spherical block: the per-cell path with the sources of Eq. 12, one
+    // cell per thread in four rounds over the tile (a warp takes 32
+    // consecutive x cells, so its accesses coalesce)
     const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
     const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
-    const int i4 = bx * CELL_BX + 4 * ((int)threadIdx.x % (CELL_BX / 4));
-    const int j = by * CELL_BY + ((int)threadIdx.x / (CELL_BX / 4)) % CELL_BY;
-    const int k = bz * CELL_BZ + (int)threadIdx.x / ((CELL_BX / 4) * CELL_BY);
-    if (j > L.n[1] || k > L.n[2]) return;
-    for (int q = 0; q < 4 && i4 + q <= L.n[0]; ++q) {
-      const int P[3] = {i4 + q, j, k};
+    constexpr int NTH = (CELL_BX / 4) * CELL_BY * CELL_BZ;
+#pragma unroll 1
+    for (int e = (int)threadIdx.x; e < CELL_BX * CELL_BY * CELL_BZ; e += NTH) {
+      const int P[3] = {bx * CELL_BX + e % CELL_BX, by * CELL_BY + (e / CELL_BX) % CELL_BY,
+                        bz * CELL_BZ + e / (CELL_BX * CELL_BY)};
+      if (P[0] > L.n[0] || P[1] > L.n[1] || P[2] > L.n[2]) continue;
       update_cell<float, P64, MHD, true>(B, P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor,
                                          cs2);
     }
@@ -736,7 +739,7 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
   with_src<R>(c, PK_CELL, -1, [&](auto S, TileRange r) {
     bool emf_done = false;
     if constexpr (sizeof(R) == 4) {
-      if (MHD && mode == 0 && AETH_EMF_V4) {
+      if (MHD && AETH_EMF_V4) {   // geometry-free: every block
         k_emf_v4<<<r.t1 - r.t0, (CELL_BX / 4) * CELL_BY * CELL_BZ, 0, c->stream>>>(S, r.t0);
         emf_done = true;
       }
