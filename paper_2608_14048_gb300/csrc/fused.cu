@@ -278,9 +278,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? AETH_UPD_MINB : 2)
 // 16-byte aligned (interior cell 0 at x offset 4, row pitch a multiple of
 // 4, every array 256-byte aligned).  Groups that reach the block's upper
 // face layers (i + 3 >= n_x, j = n_y or k = n_z) take the per-cell path.
-// One 32 x 4 x 2 cell tile per CTA of 64 threads.  COORD 2: a context with
-// spherical blocks too; a spherical block's tile takes the per-cell path
-// with the curvilinear sources.
+// One 32 x 4 x 2 cell tile per CTA of 64 threads.  COORD 1 (every block
+// spherical) and 2 (mixed): a spherical block's groups take update4_sph,
+// with the curvilinear geometry and sources.
 // ------------------------------------------------------------------------
 __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -395,8 +395,121 @@ __global__ void __launch_bounds__(64) k_emf_v4(Src S, int t0) {
 #define AETH_UPD_V4 1
 #endif
 
+// The update of four consecutive x cells of a spherical block (a group
+// with i + 3 < n_x, j < n_y, k < n_z): update_cell<float, P64, MHD, true>
+// cell by cell, in the same expressions, with 16-byte loads and stores of
+// the state, fluxes and corner EMFs, and the geometry factors of Sec. 2.3
+// from their 1-D tables.  The curvilinear sources (Eq. 12) of the four
+// cells are formed first, from the stage state, before any store.
+template <bool P64, bool MHD>
+__device__ __forceinline__ void update4_sph(const BlockPtrs<float>& B, int i4, int j, int k,
+                                            int src, int out, float w0, float w1, float bdt,
+                                            float gamma, float rho_floor, float p_floor,
+                                            float cs2) {
+  const Layout& L = B.L;
+  const Geometry<float>& geo = B.geo;
+  const long long c = L.idx(i4, j, k);
+  const long long sy = L.sx, sz = L.sx * L.sy;
+  const bool has_b = w1 != 0.0f;
+  float* const* outp = B.reg[out];
+  float srcv[4][3];
+  {
+    ConstArr8<float> s;
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) s.p[v] = B.reg[src][v];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float w[8];
+      if (cs2 > 0.0f) prim_cell<float, P64, MHD, true>(L, s, c + q, cs2, rho_floor, p_floor, w);
+      else prim_cell<float, P64, MHD>(L, s, c + q, gamma - 1.0f, rho_floor, p_floor, w);
+      const float rho = w[0], vv[3] = {w[1], w[2], w[3]};
+      const float bb[3] = {w[5], w[6], w[7]};
+      const float ps = w[4] + 0.5f * (bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2]);
+      auto T = [&](int x, int y) {
+        return rho * vv[x] * vv[y] + (x == y ? ps : 0.0f) - bb[x] * bb[y];
+      };
+      const float ir = geo.invr(i4 + q, j, k), ct = geo.cotr(i4 + q, j, k);
+      srcv[q][0] = (T(1, 1) + T(2, 2)) * ir;
+      srcv[q][1] = T(2, 2) * ct - T(0, 1) * ir;
+      srcv[q][2] = -T(2, 0) * ir - T(2, 1) * ct;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const float4 fx = ldg4(B.f[0][v] + c);
+    const float fx4 = __ldg(B.f[0][v] + c + 4);
+    const float4 fy0 = ldg4(B.f[1][v] + c), fy1 = ldg4(B.f[1][v] + c + sy);
+    const float4 fz0 = ldg4(B.f[2][v] + c), fz1 = ldg4(B.f[2][v] + c + sz);
+    const float4 u0 = ld4(B.reg[0][v] + c);
+    const float4 u1 = has_b ? ld4(B.reg[1][v] + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i4 + q;
+      const float fxp = q < 3 ? at4(fx, q + 1) : fx4;
+      float div = 0.0f;
+      div += geo.area[0](i + 1, j, k) * fxp - geo.area[0](i, j, k) * at4(fx, q);
+      div += geo.area[1](i, j + 1, k) * at4(fy1, q) - geo.area[1](i, j, k) * at4(fy0, q);
+      div += geo.area[2](i, j, k + 1) * at4(fz1, q) - geo.area[2](i, j, k) * at4(fz0, q);
+      const float rhs = -div / geo.vol(i, j, k) + (v >= 1 && v <= 3 ? srcv[q][v - 1] : 0.0f);
+      float base = w0 * at4(u0, q);
+      if (has_b) base += w1 * at4(u1, q);
+      r[q] = base + bdt * rhs;
+    }
+    st4(outp[v] + c, make_float4(r[0], r[1], r[2], r[3]));
+  }
+  if constexpr (MHD) {
+    // corner EMFs times edge lengths around the three lower faces (Eq. 9)
+    const float4 e0c = ldg4(B.edge[0] + c), e0y = ldg4(B.edge[0] + c + sy),
+                 e0z = ldg4(B.edge[0] + c + sz);
+    const float4 e1c = ldg4(B.edge[1] + c), e1z = ldg4(B.edge[1] + c + sz);
+    const float4 e2c = ldg4(B.edge[2] + c), e2y = ldg4(B.edge[2] + c + sy);
+    const float e1x4 = __ldg(B.edge[1] + c + 4), e2x4 = __ldg(B.edge[2] + c + 4);
+    float nb[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float4 b0 = ld4(B.reg[0][5 + d] + c);
+      const float4 b1 = has_b ? ld4(B.reg[1][5 + d] + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i4 + q;
+        const float e1xp = q < 3 ? at4(e1c, q + 1) : e1x4;
+        const float e2xp = q < 3 ? at4(e2c, q + 1) : e2x4;
+        const Sep<float>& l0 = geo.edge[0];
+        const Sep<float>& l1 = geo.edge[1];
+        const Sep<float>& l2 = geo.edge[2];
+        float circ;
+        if (d == 0)
+          circ = at4(e2y, q) * l2(i, j + 1, k) - at4(e2c, q) * l2(i, j, k) -
+                 (at4(e1z, q) * l1(i, j, k + 1) - at4(e1c, q) * l1(i, j, k));
+        else if (d == 1)
+          circ = at4(e0z, q) * l0(i, j, k + 1) - at4(e0c, q) * l0(i, j, k) -
+                 (e2xp * l2(i + 1, j, k) - at4(e2c, q) * l2(i, j, k));
+        else
+          circ = e1xp * l1(i + 1, j, k) - at4(e1c, q) * l1(i, j, k) -
+                 (at4(e0y, q) * l0(i, j + 1, k) - at4(e0c, q) * l0(i, j, k));
+        float base = w0 * at4(b0, q);
+        if (has_b) base += w1 * at4(b1, q);
+        nb[d][q] = base - bdt * circ / geo.area[d](i, j, k);
+      }
+      st4(outp[5 + d] + c, make_float4(nb[d][0], nb[d][1], nb[d][2], nb[d][3]));
+    }
+    // periodic axis: face n is the image of face 0
+    if (L.bc[0] == AETH_BC_PERIODIC && i4 == 0) outp[5][c + L.n[0]] = nb[0][0];
+    if (L.bc[1] == AETH_BC_PERIODIC && j == 0)
+      st4(outp[6] + c + (long long)L.n[1] * sy, make_float4(nb[1][0], nb[1][1], nb[1][2], nb[1][3]));
+    if (L.bc[2] == AETH_BC_PERIODIC && k == 0)
+      st4(outp[7] + c + (long long)L.n[2] * sz, make_float4(nb[2][0], nb[2][1], nb[2][2], nb[2][3]));
+  }
+}
+
+// resident CTAs per SM requested in contexts with spherical blocks
+#ifndef AETH_UPD4_SPH_MINB
+#define AETH_UPD4_SPH_MINB 12
+#endif
+
 template <bool P64, bool MHD, int COORD, typename Src>
-__global__ void __launch_bounds__(64, COORD == 0 ? AETH_UPD4_MINB : 12)
+__global__ void __launch_bounds__(64, COORD == 0 ? AETH_UPD4_MINB : AETH_UPD4_SPH_MINB)
     k_update_v4(Src S, int t0, int src, int out, float w0, float w1, float beta,
                 const double* __restrict__ dt, float gamma, float rho_floor, float p_floor,
                 float cs2) {
@@ -404,35 +517,27 @@ __global__ void __launch_bounds__(64, COORD == 0 ? AETH_UPD4_MINB : 12)
   int loc;
   const BlockPtrs<float>& B = S.get(t0 + (int)blockIdx.x, loc);
   const Layout& L = B.L;
-  if (COORD == 2 && L.coord == AETH_COORD_SPH) {
-    // a spherical block: the per-cell path with the sources of Eq. 12, one
-    // cell per thread in four rounds over the tile (a warp takes 32
-    // consecutive x cells, so its accesses coalesce)
-    const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
-    const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
-    constexpr int NTH = (CELL_BX / 4) * CELL_BY * CELL_BZ;
-#pragma unroll 1
-    for (int e = (int)threadIdx.x; e < CELL_BX * CELL_BY * CELL_BZ; e += NTH) {
-      const int P[3] = {bx * CELL_BX + e % CELL_BX, by * CELL_BY + (e / CELL_BX) % CELL_BY,
-                        bz * CELL_BZ + e / (CELL_BX * CELL_BY)};
-      if (P[0] > L.n[0] || P[1] > L.n[1] || P[2] > L.n[2]) continue;
-      update_cell<float, P64, MHD, true>(B, P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor,
-                                         cs2);
-    }
-    return;
-  }
   const int ntx = ceil_div_d(L.n[0] + 1, CELL_BX), nty = ceil_div_d(L.n[1] + 1, CELL_BY);
   const int bx = loc % ntx, by = (loc / ntx) % nty, bz = loc / (ntx * nty);
   const int i4 = bx * CELL_BX + 4 * ((int)threadIdx.x % (CELL_BX / 4));
   const int j = by * CELL_BY + ((int)threadIdx.x / (CELL_BX / 4)) % CELL_BY;
   const int k = bz * CELL_BZ + (int)threadIdx.x / ((CELL_BX / 4) * CELL_BY);
   if (i4 > L.n[0] || j > L.n[1] || k > L.n[2]) return;
+  const bool sph = COORD == 1 || (COORD == 2 && L.coord == AETH_COORD_SPH);
   if (i4 + 3 >= L.n[0] || j >= L.n[1] || k >= L.n[2]) {
     for (int q = 0; q < 4 && i4 + q <= L.n[0]; ++q) {
       const int P[3] = {i4 + q, j, k};
-      update_cell<float, P64, MHD, false>(B, P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor,
-                                          cs2);
+      if (sph)
+        update_cell<float, P64, MHD, true>(B, P, src, out, w0, w1, bdt, gamma, rho_floor, p_floor,
+                                           cs2);
+      else
+        update_cell<float, P64, MHD, false>(B, P, src, out, w0, w1, bdt, gamma, rho_floor,
+                                            p_floor, cs2);
     }
+    return;
+  }
+  if (sph) {
+    update4_sph<P64, MHD>(B, i4, j, k, src, out, w0, w1, bdt, gamma, rho_floor, p_floor, cs2);
     return;
   }
   const long long c = L.idx(i4, j, k);
@@ -762,15 +867,16 @@ static void stage_fused(aeth_ctx* c, int recon, int src, R w0, R w1, R beta, int
       }
     }
     if constexpr (sizeof(R) == 4) {
-      if (mode != 1 && AETH_UPD_V4) {
-        // FP32 Cartesian blocks: four x cells per thread, one tile per CTA
-        // (spherical blocks of a mixed context per cell)
+      if (AETH_UPD_V4) {
+        // FP32: four x cells per thread, one tile per CTA (Cartesian and
+        // spherical groups; the groups at the upper face layers per cell)
         auto v4 = [&](auto kernel) {
           kernel<<<n, (CELL_BX / 4) * CELL_BY * CELL_BZ, 0, c->stream>>>(
               S, r.t0, src, out, (float)w0, (float)w1, (float)beta, c->d_dt, (float)g,
               (float)rf, (float)pf, (float)cs2);
         };
         if (mode == 0) v4(k_update_v4<P64, MHD, 0, Src>);
+        else if (mode == 1) v4(k_update_v4<P64, MHD, 1, Src>);
         else v4(k_update_v4<P64, MHD, 2, Src>);
         return;
       }

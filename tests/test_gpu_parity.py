@@ -205,8 +205,12 @@ def test_spherical_block_parity(mhd, path):
         assert diag["max_divb_rel"] < 1e-12
 
 
-def test_spherical_fp32_parity():
-    st = I.smooth_random_mhd(_sph_block(), 62, v_rms=0.3, b_rms=0.4)
+@pytest.mark.parametrize("n", [(16, 12, 10), (37, 9, 6)])
+def test_spherical_fp32_parity(n):
+    # the FP32 update takes four x cells per thread (the groups below the
+    # upper face layers) and one cell per thread elsewhere: 37 cells span
+    # two tiles and a ragged group
+    st = I.smooth_random_mhd(_sph_block(n), 62, v_rms=0.3, b_rms=0.4)
     ref, dts = oracle_run(st, "plm", "vl2", nsteps=4)
     (out,), _ = gpu_run([st], dts, "plm", "vl2", "fp32")
     assert max(compare(out, ref)) < FP32_TOL
