@@ -112,7 +112,7 @@ def flux_tile_record(A, current, tuned):
     """The flux pass's tile shape in the bench line: width x height x
     z-chunk, and whether the autotuner timed it now or its cache gave it."""
     tx, kc = current
-    shape = {"tx": tx, "ty": 256 // tx} if tx else {"tx": "band", "ty": "256 / (n_x + 2) rows"}
+    shape = {"tx": tx, "ty": 128 // tx} if tx else {"tx": "band", "ty": "256 / (n_x + 2) rows"}
     return {**shape, "kchunk": kc, "source": tuned[2] if tuned else "default (no autotune)"}
 
 

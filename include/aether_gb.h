@@ -396,16 +396,18 @@ aeth_status aeth_profile_read(aeth_ctx* ctx, double* total_ms,
                               long long* all_launches);
 
 /* Tile shape of the fused flux pass (no counterpart in the paper): a CTA of
- * 256 threads owns a flux_tx x (256 / flux_tx) column tile of cells and
+ * 128 threads owns a flux_tx x (128 / flux_tx) column tile of cells and
  * marches kchunk planes along z.  flux_tx = 32 (default), 16, or 0 for band
- * tiles: whole rows of a block (its n_x + 2 flux columns), 256 / (n_x + 2)
- * rows at a time, which keep the lanes of blocks narrower than a 2-D tile
- * busy (every block at most 64 cells wide).  16 and 0 are built for FP32
+ * tiles: CTAs of 256 threads over whole rows of a block (its n_x + 2 flux
+ * columns), 256 / (n_x + 2) rows at a time, which keep the lanes of blocks
+ * narrower than a 2-D tile busy (every block at most 64 cells wide).  16 and 0 are built for FP32
  * and FP32_P64 / FP32_SEL64 contexts with a classical solver, no dual
  * energy, fused path (AETH_ERR_UNSUPPORTED otherwise); kchunk in 1 .. 1024 (the
  * default is the largest of 64, 32, 16, 8, 4 that gives every SM four
- * tiles).  The results do not depend on the shape: each face is solved
- * once by the same code.  aeth_set_flux_tile rebuilds the launch tables
+ * tiles).  Each face is solved once, by the same code, whatever the shape:
+ * the 2-D shapes give identical states, band tiles states within a few
+ * FP32 ulps of them (the compiler contracts some multiply-adds of that
+ * kernel differently).  aeth_set_flux_tile rebuilds the launch tables
  * (host and device) and drops the captured step graph; call it between
  * steps.  aeth_get_flux_tile reads the current shape. */
 aeth_status aeth_set_flux_tile(aeth_ctx* ctx, int flux_tx, int kchunk);

@@ -17,16 +17,19 @@
 
 namespace aeth {
 
-constexpr int NT = FLUX_NT;   // threads of a flux tile; its x width TXT is a
-                              // template parameter (32 or 16), the y width NT / TXT
 // resident CTAs per SM requested for the FP32 flux pass with donor or PLM
-// reconstruction (register budget 65536 / (256 * FLUX_MINB) per thread:
-// 3 CTAs, 85 registers, measured 1.3% faster at 256^3 than 2 CTAs with 106
-// registers); the PPM and PPM5 stencils keep 2 CTAs (at 85 registers they
-// spill about 250 bytes per thread)
+// reconstruction, in 256-thread units (register budget 65536 / (256 *
+// FLUX_MINB) per thread: 3, 85 registers, measured 1.3% faster at 256^3
+// than 2 with 106 registers); the PPM and PPM5 stencils keep 2 (at 85
+// registers they spill about 250 bytes per thread); FP64 takes the whole
+// register file.  A 128-thread tile counts half.
 #ifndef AETH_FLUX_MINB
 #define AETH_FLUX_MINB 3
 #endif
+template <typename R, int RECON>
+__host__ __device__ constexpr int flux_minb(int txt) {
+  return (sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1) * (256 / flux_threads(txt));
+}
 
 __host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
 
@@ -109,10 +112,11 @@ __device__ __forceinline__ void store_face(R* __restrict__ sb, long long pitch, 
 // flux_plane<RECON>(TXT) values.
 template <typename R, bool P64, int RECON, bool MHD, typename Src, int SOLVER = 0,
           bool DUAL = false, int TXT = FLUX_TX>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1)
+__global__ void __launch_bounds__(flux_threads(TXT), (flux_minb<R, RECON>(TXT)))
     k_flux3(Src S, int t0, int t1, int src, R gamma, R rho_floor, R p_floor, int kchunk,
             unsigned long long* floor_hits, R alpha_switch) {
   constexpr bool BAND = TXT == 0;
+  constexpr int NT = flux_threads(TXT);
   constexpr int TX = BAND ? 1 : TXT, TY = NT / TX;
   constexpr int RH = recon_reach<RECON>(), RL = RH + 1;
   constexpr int WX = TX + RL + RH, WY = TY + RL + RH;
@@ -390,18 +394,19 @@ static void with_src(aeth_ctx* c, int kind, int block, F launch) {
 
 template <typename R, bool P64, int RECON, bool MHD, int SOLVER, bool DUAL>
 static void launch_flux3(aeth_ctx* c, int src, int block) {
-  const int per_sm = sizeof(R) == 4 ? (RECON >= 2 ? 2 : AETH_FLUX_MINB) : 1;
+
   constexpr int NW = NPRIM + (DUAL ? 1 : 0);
   with_src<R>(c, PK_FLUX, block, [&](auto S, TileRange r) {
-    const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
     // tx: the tile width the kernel was built for (0: band tiles)
     auto go = [&](auto kernel, int tx) {
+      const int per_sm = flux_minb<R, RECON>(tx);
+      const int grid = std::max(1, std::min(r.t1 - r.t0, c->num_sms * per_sm));
       const int bytes = flux_ring<RECON>(tx) * NW * flux_plane<RECON>(tx) * (int)sizeof(R);
       // above the 48 KB default (FP64, PPM rings, bands); a plain attribute
       // call, also legal while a graph is being captured
       if (bytes > 48 * 1024)
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-      kernel<<<grid, NT, bytes, c->stream>>>(
+      kernel<<<grid, flux_threads(tx), bytes, c->stream>>>(
           S, r.t0, r.t1, src, (R)(iso_solver(SOLVER) ? c->cfg.cs_iso : c->cfg.gamma),
           (R)c->cfg.rho_floor, (R)c->cfg.p_floor, c->kchunk, c->d_floor,
           (R)c->cfg.alpha_switch);

@@ -55,16 +55,24 @@ enum PassKind : int { PK_FLUX = 0, PK_CELL = 1, PK_FILL0 = 2, PK_FILL1 = 3, PK_F
                       PK_ROWS = 5, PK_N = 6 };
 
 // Tile geometry of each pass kind (threads per tile fixed per kind).
-constexpr int FLUX_TX = 32, FLUX_TY = 8;   // default flux tile (256 threads)
-constexpr int FLUX_NT = FLUX_TX * FLUX_TY;
+// 2-D flux tiles: 128 threads, FLUX_TX x (FLUX_NT / FLUX_TX) by default
+// (32 x 4; the autotuner also takes 16 x 8).  Four warps per barrier wait
+// less on the slowest warp of a plane than eight: at 256^3, 16 x 8 tiles of
+// 128 threads ran 3% faster than 16 x 16 tiles of 256 at the same
+// occupancy, for 16% more staged halo.
+constexpr int FLUX_TX = 32;
+constexpr int FLUX_NT = 128;
 // Band tiles (flux tile width 0): whole rows of a block, x from -1 to n_x,
-// as many rows as fit the 256 threads; for blocks with n_x + 2 <= 66 (wider
+// as many rows as fit FLUX_NT_BAND threads; for blocks with n_x + 2 <= 66 (wider
 // blocks keep most lanes of a 2-D tile busy, and the bound keeps the band's
 // shared-memory ring within two PPM CTAs per SM).
 constexpr int FLUX_BAND_WMAX = 66;
+constexpr int FLUX_NT_BAND = 256;
 __host__ __device__ constexpr int band_rows(int nx) {
-  return FLUX_NT / (nx + 2) > 1 ? FLUX_NT / (nx + 2) : 1;
+  return FLUX_NT_BAND / (nx + 2) > 1 ? FLUX_NT_BAND / (nx + 2) : 1;
 }
+// Threads of a flux tile of width tx (0: band tiles).
+__host__ __device__ constexpr int flux_threads(int tx) { return tx ? FLUX_NT : FLUX_NT_BAND; }
 constexpr int CELL_BX = 32, CELL_BY = 4, CELL_BZ = 2;
 constexpr int FILL_TILE = 256;   // ghost cells per tile of the fill pass
 
@@ -147,7 +155,7 @@ struct aeth_ctx {
   int kchunk = 0;                     // z extent of a flux tile (0: choose;
                                       // aeth_autotune times candidates)
   int flux_tx = 32;                   // x width of a flux tile (32 or 16; the y
-                                      // width is 256 / flux_tx), or 0: band tiles
+                                      // width is 128 / flux_tx), or 0: band tiles
   int num_sms = 152;
   int dt_grid = 1;                    // CTAs of the batched reductions
   // error text

@@ -1,7 +1,7 @@
 """Flux-tile shapes and their autotuner on the GPU.
 
 The flux pass gives each face to exactly one thread whatever the tile
-shape, so the 32 x 8 and 16 x 16 tiles, with any z-chunk, give the same
+shape, so the 32 x 4 and 16 x 8 tiles, with any z-chunk, give the same
 state bit for bit: on one ragged block and on uneven linked and unlinked
 blocks.  The band tiles (whole rows of a block) run the same arithmetic in
 a kernel the compiler arranges differently, and its multiply-add
