@@ -254,6 +254,24 @@ aeth_status aeth_set_state(aeth_ctx* ctx, int block, const double* cons,
 aeth_status aeth_get_state(aeth_ctx* ctx, int block, double* cons,
                            double* b1f, double* b2f, double* b3f);
 
+/* The same two copies (Sec. 3.4's set_initial_condition! and the state
+ * read after run!), enqueued on the context's stream without waiting, so
+ * that a caller with several contexts on several streams overlaps one
+ * context's transfers with another's steps.  The host arrays must be
+ * page-locked (cudaHostAlloc, cudaHostRegister; AETH_ERR_ARG otherwise):
+ * the copy engines move them through the library's device staging buffer
+ * (no SM is used for the host link), and a kernel converts between FP64
+ * and the working precision.  The caller must not modify the arrays of a
+ * set, or read those of a get, before the stream has passed the call
+ * (aeth_sync, or a CUDA event recorded after it).  Calls on one context
+ * run in stream order; device errors are latched as for aeth_step.
+ * b1f..b3f may be NULL in hydro (and, for a get, to skip the field). */
+aeth_status aeth_set_state_async(aeth_ctx* ctx, int block, const double* cons,
+                                 const double* b1f, const double* b2f,
+                                 const double* b3f);
+aeth_status aeth_get_state_async(aeth_ctx* ctx, int block, double* cons,
+                                 double* b1f, double* b2f, double* b3f);
+
 /* Dual-energy entropy S = p / rho^(gamma-1) of block `block` (register A,
  * interior cells) into S[nz][ny][nx] (host FP64, caller-owned).  Pinned,
  * mapped host memory is written directly, anything else through the

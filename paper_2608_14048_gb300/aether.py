@@ -37,7 +37,8 @@ FUSED, UNFUSED = 0, 1
 
 # every symbol include/aether_gb.h declares
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
-           "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_compute_dt", "aeth_step",
+           "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_set_state_async",
+           "aeth_get_state_async", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
            "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_mlp_face_flux", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
@@ -99,6 +100,8 @@ def load_library(path: str = LIB_PATH):
         "aeth_finalize": ([P, C.POINTER(C.c_size_t)], C.c_int),
         "aeth_set_state": ([P, C.c_int, P, P, P, P], C.c_int),
         "aeth_get_state": ([P, C.c_int, P, P, P, P], C.c_int),
+        "aeth_set_state_async": ([P, C.c_int, P, P, P, P], C.c_int),
+        "aeth_get_state_async": ([P, C.c_int, P, P, P, P], C.c_int),
         "aeth_compute_dt": ([P, dp], C.c_int),
         "aeth_step": ([P, C.c_double], C.c_int),
         "aeth_run": ([P, C.c_int], C.c_int),
@@ -189,6 +192,21 @@ def aeth_set_state(ctx, block, cons, b1=None, b2=None, b3=None):
 
 def aeth_get_state(ctx, block, cons, b1=None, b2=None, b3=None):
     _check(ctx, load_library().aeth_get_state(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2), _ptr(b3)))
+
+
+def aeth_set_state_async(ctx, block, cons, b1=None, b2=None, b3=None):
+    """Enqueue the state upload on the context's stream (page-locked host
+    arrays, e.g. torch pin_memory(); keep them unchanged until the stream
+    has passed the call)."""
+    _check(ctx, load_library().aeth_set_state_async(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2),
+                                                     _ptr(b3)))
+
+
+def aeth_get_state_async(ctx, block, cons, b1=None, b2=None, b3=None):
+    """Enqueue the state read-back on the context's stream (page-locked host
+    arrays; valid once the stream has passed the call)."""
+    _check(ctx, load_library().aeth_get_state_async(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2),
+                                                     _ptr(b3)))
 
 
 def aeth_probe_fma(precision) -> float:

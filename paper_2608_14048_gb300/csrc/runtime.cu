@@ -434,6 +434,68 @@ aeth_status aeth_set_state(aeth_ctx* c, int b, const double* cons, const double*
   return AETH_OK;
 }
 
+// true when the caller's host array of `bytes` is page-locked memory the
+// copy engines can read or write asynchronously
+static bool page_locked(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+aeth_status aeth_set_state_async(aeth_ctx* c, int b, const double* cons, const double* b1,
+                                 const double* b2, const double* b3) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (!cons) return fail(c, AETH_ERR_ARG, "cons is NULL");
+  const auto& B = c->blocks[b];
+  const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz, nc = nx * ny * nz;
+  const bool mhd = is_mhd(c);
+  if (mhd && (!b1 || !b2 || !b3)) return fail(c, AETH_ERR_ARG, "face fields are NULL");
+  const size_t bytes[4] = {5 * nc * sizeof(double), nz * ny * (nx + 1) * sizeof(double),
+                           nz * (ny + 1) * nx * sizeof(double), (nz + 1) * ny * nx * sizeof(double)};
+  const double* host[4] = {cons, b1, b2, b3};
+  double* io[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d = c->d_stage;
+  for (int q = 0; q < (mhd ? 4 : 1); ++q) {
+    if (!page_locked(host[q], bytes[q]))
+      return fail(c, AETH_ERR_ARG, "array %d is not page-locked host memory", q);
+    io[q] = d;
+    AETH_CK(c, cudaMemcpyAsync(d, host[q], bytes[q], cudaMemcpyHostToDevice, c->stream));
+    d += bytes[q] / sizeof(double);
+  }
+  return enqueue_load(c, b, io);
+}
+
+aeth_status aeth_get_state_async(aeth_ctx* c, int b, double* cons, double* b1, double* b2,
+                                 double* b3) {
+  aeth_status s = check_block(c, b);
+  if (s != AETH_OK) return s;
+  if (!cons) return fail(c, AETH_ERR_ARG, "cons is NULL");
+  const auto& B = c->blocks[b];
+  const long long nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz, nc = nx * ny * nz;
+  const bool faces = is_mhd(c) && b1 && b2 && b3;
+  const size_t bytes[4] = {5 * nc * sizeof(double), nz * ny * (nx + 1) * sizeof(double),
+                           nz * (ny + 1) * nx * sizeof(double), (nz + 1) * ny * nx * sizeof(double)};
+  double* host[4] = {cons, b1, b2, b3};
+  double* io[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d = c->d_stage;
+  for (int q = 0; q < 4; ++q) {
+    if (q < (faces ? 4 : 1) && !page_locked(host[q], bytes[q]))
+      return fail(c, AETH_ERR_ARG, "array %d is not page-locked host memory", q);
+    io[q] = d;
+    d += bytes[q] / sizeof(double);
+  }
+  s = enqueue_store(c, b, io);
+  if (s != AETH_OK) return s;
+  for (int q = 0; q < (faces ? 4 : 1); ++q)
+    AETH_CK(c, cudaMemcpyAsync(host[q], io[q], bytes[q], cudaMemcpyDeviceToHost, c->stream));
+  return AETH_OK;
+}
+
 aeth_status aeth_get_state(aeth_ctx* c, int b, double* cons, double* b1, double* b2, double* b3) {
   aeth_status s = check_block(c, b);
   if (s != AETH_OK) return s;

@@ -271,6 +271,49 @@ def test_pinned_host_arrays_take_the_direct_path_bit_for_bit():
         assert np.array_equal(a, b)
 
 
+def test_async_state_transfers_on_two_streams_match_the_synchronous_ones():
+    """aeth_set_state_async / aeth_get_state_async through the copy engines:
+    two contexts on two streams, each uploading, stepping and reading back
+    without a host wait in between, give the state of the synchronous calls
+    bit for bit; pageable arrays are refused."""
+    import torch
+    n = (20, 12, 10)
+    st = I.smooth_random_mhd(I.Block(n), 93, v_rms=0.6, b_rms=0.5)
+    cfg = A.make_config(gamma=st.gamma, precision=A.FP32)
+    sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, st.cons, st.b1, st.b2, st.b3)
+        sv.step(1e-3)
+        ref = sv.get_state(0)
+    finally:
+        sv.close()
+    pin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+           for x in (st.cons, st.b1, st.b2, st.b3)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    svs = [A.Solver(cfg, [A.make_block(n)], stream=s_) for s_ in streams]
+    try:
+        outs = [[torch.empty(s_, dtype=torch.float64).pin_memory() for s_ in svs[0].shapes(0)]
+                for _ in svs]
+        for q, s_ in enumerate(svs):
+            A.aeth_set_state_async(s_.ctx, 0, *pin)
+            s_.step(1e-3)
+            A.aeth_get_state_async(s_.ctx, 0, *outs[q])
+        for s_ in svs:
+            s_.sync()
+        for q in range(2):
+            for a, b in zip(ref, outs[q]):
+                assert np.array_equal(a, b.numpy())
+        with pytest.raises(A.AethError) as e:
+            A.aeth_set_state_async(svs[0].ctx, 0, st.cons, st.b1, st.b2, st.b3)
+        assert e.value.code == -1
+        with pytest.raises(A.AethError) as e:
+            A.aeth_get_state_async(svs[0].ctx, 0, np.empty_like(st.cons))
+        assert e.value.code == -1
+    finally:
+        for s_ in svs:
+            s_.close()
+
+
 def test_pinned_dust_arrays_take_the_direct_path_bit_for_bit():
     import torch
     n = (16, 12, 8)
