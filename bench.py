@@ -1065,9 +1065,12 @@ def main():
                 A.aeth_set_flux_tile(sv_q.ctx, *sv_tile)
         except (A.AethError, torch.cuda.OutOfMemoryError):
             pass   # device memory: as many contexts as fit
-        ctxs = [(sv, stream, hout)] + [
-            (sv_q, s_q, [[torch.empty_like(x).pin_memory() if x is not None else None for x in h]
-                         for h in hout]) for sv_q, s_q in more]
+        # the whole mesh's state in one packed, pinned array (one transfer
+        # per direction and step, whatever the number of blocks)
+        packed_in = torch.from_numpy(A.pack_states(
+            [[x.numpy() for x in h if x is not None] for h in hin], mhd=mhd_run)).pin_memory()
+        ctxs = [(sv, stream, torch.empty_like(packed_in).pin_memory())] + [
+            (sv_q, s_q, torch.empty_like(packed_in).pin_memory()) for sv_q, s_q in more]
         try:
             if len(ctxs) > 1:
                 def round_(first=False):
@@ -1075,14 +1078,12 @@ def main():
                     for svq, sq, hq in ctxs:
                         if first and prev is not None:
                             sq.wait_event(prev)
-                        for q in range(len(states)):
-                            A.aeth_set_state_async(svq.ctx, q, *hin[q])
+                        A.aeth_set_state_all_async(svq.ctx, packed_in)
                         if first:
                             prev = torch.cuda.Event()
                             prev.record(sq)
                         svq.run(1)
-                        for q in range(len(states)):
-                            A.aeth_get_state_async(svq.ctx, q, *hq[q])
+                        A.aeth_get_state_all_async(svq.ctx, hq)
 
                 round_()   # captures the other contexts' step graphs
                 torch.cuda.synchronize(dev)
@@ -1095,9 +1096,10 @@ def main():
                 e2e_steps = len(ctxs) * ke
                 e2e_val = whole_job_rate(cells * e2e_steps, ws, e2e_p)
                 e2e_how = (f"{len(ctxs)} contexts on {len(ctxs)} streams, {ke} steps each: per step, "
-                           "aeth_set_state_async from pinned host memory, aeth_run(1), "
-                           "aeth_get_state_async into pinned host memory; one context's copies "
-                           "overlap another's step (the contexts start one upload apart)")
+                           "aeth_set_state_all_async from a pinned host array of every block's "
+                           "state, aeth_run(1), aeth_get_state_all_async into a pinned host "
+                           "array; one context's copies overlap another's step (the contexts "
+                           "start one upload apart)")
         finally:
             for sv_q, _ in more:
                 sv_q.close()

@@ -272,6 +272,18 @@ aeth_status aeth_set_state_async(aeth_ctx* ctx, int block, const double* cons,
 aeth_status aeth_get_state_async(aeth_ctx* ctx, int block, double* cons,
                                  double* b1f, double* b2f, double* b3f);
 
+/* The state of every block in one page-locked host array, block after
+ * block in the order of aeth_add_block, each block as cons [5][nz][ny][nx]
+ * followed in MHD by b1f, b2f, b3f (the layouts above): one copy-engine
+ * transfer for the whole mesh instead of four per block, for meshes of
+ * many small blocks.  *n receives the array's length in doubles.  The
+ * transfers behave as aeth_set_state_async / aeth_get_state_async; the
+ * first call allocates a device buffer of that size (AETH_ERR_OOM if it
+ * cannot), freed by aeth_destroy. */
+aeth_status aeth_state_doubles(aeth_ctx* ctx, size_t* n);
+aeth_status aeth_set_state_all_async(aeth_ctx* ctx, const double* packed);
+aeth_status aeth_get_state_all_async(aeth_ctx* ctx, double* packed);
+
 /* Dual-energy entropy S = p / rho^(gamma-1) of block `block` (register A,
  * interior cells) into S[nz][ny][nx] (host FP64, caller-owned).  Pinned,
  * mapped host memory is written directly, anything else through the

@@ -38,7 +38,8 @@ FUSED, UNFUSED = 0, 1
 # every symbol include/aether_gb.h declares
 EXPORTS = ["aeth_create", "aeth_bind_stream", "aeth_bind_arena", "aeth_add_block", "aeth_plan",
            "aeth_finalize", "aeth_set_state", "aeth_get_state", "aeth_set_state_async",
-           "aeth_get_state_async", "aeth_compute_dt", "aeth_step",
+           "aeth_get_state_async", "aeth_state_doubles", "aeth_set_state_all_async",
+           "aeth_get_state_all_async", "aeth_compute_dt", "aeth_step",
            "aeth_run", "aeth_sync", "aeth_diagnostics", "aeth_set_dust", "aeth_get_dust",
            "aeth_load_mlp", "aeth_mlp_infer", "aeth_mlp_infer_tc", "aeth_mlp_face_flux", "aeth_selftest_wait_timeout", "aeth_mlp_collect", "aeth_mlp_work_floats", "aeth_mlp_grad",
            "aeth_mlp_adam", "aeth_profile", "aeth_profile_read", "aeth_autotune",
@@ -102,6 +103,9 @@ def load_library(path: str = LIB_PATH):
         "aeth_get_state": ([P, C.c_int, P, P, P, P], C.c_int),
         "aeth_set_state_async": ([P, C.c_int, P, P, P, P], C.c_int),
         "aeth_get_state_async": ([P, C.c_int, P, P, P, P], C.c_int),
+        "aeth_state_doubles": ([P, P], C.c_int),
+        "aeth_set_state_all_async": ([P, P], C.c_int),
+        "aeth_get_state_all_async": ([P, P], C.c_int),
         "aeth_compute_dt": ([P, dp], C.c_int),
         "aeth_step": ([P, C.c_double], C.c_int),
         "aeth_run": ([P, C.c_int], C.c_int),
@@ -200,6 +204,36 @@ def aeth_set_state_async(ctx, block, cons, b1=None, b2=None, b3=None):
     has passed the call)."""
     _check(ctx, load_library().aeth_set_state_async(ctx, block, _ptr(cons), _ptr(b1), _ptr(b2),
                                                      _ptr(b3)))
+
+
+def aeth_state_doubles(ctx) -> int:
+    """Length (doubles) of the packed state of every block."""
+    n = C.c_size_t(0)
+    _check(ctx, load_library().aeth_state_doubles(ctx, C.byref(n)))
+    return n.value
+
+
+def aeth_set_state_all_async(ctx, packed):
+    """Enqueue the upload of every block's state from one packed,
+    page-locked host array (block after block: cons, then b1, b2, b3)."""
+    _check(ctx, load_library().aeth_set_state_all_async(ctx, _ptr(packed)))
+
+
+def aeth_get_state_all_async(ctx, packed):
+    """Enqueue the read-back of every block's state into one packed,
+    page-locked host array."""
+    _check(ctx, load_library().aeth_get_state_all_async(ctx, _ptr(packed)))
+
+
+def pack_states(states, mhd=True):
+    """The packed host layout of aeth_set_state_all_async from per-block
+    (cons, b1, b2, b3) arrays (numpy, FP64)."""
+    parts = []
+    for st in states:
+        parts.append(np.ascontiguousarray(st[0], dtype=np.float64).ravel())
+        if mhd:
+            parts += [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in st[1:4]]
+    return np.concatenate(parts)
 
 
 def aeth_get_state_async(ctx, block, cons, b1=None, b2=None, b3=None):

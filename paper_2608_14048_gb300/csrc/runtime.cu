@@ -496,6 +496,81 @@ aeth_status aeth_get_state_async(aeth_ctx* c, int b, double* cons, double* b1, d
   return AETH_OK;
 }
 
+// Doubles of one block's packed state: cons [5][nz][ny][nx], then in MHD
+// b1 [nz][ny][nx+1], b2 [nz][ny+1][nx], b3 [nz+1][ny][nx].
+static size_t packed_doubles(const aeth_ctx* c, int b, size_t part[4]) {
+  const auto& B = c->blocks[b];
+  const size_t nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz;
+  part[0] = 5 * nx * ny * nz;
+  part[1] = is_mhd(c) ? nz * ny * (nx + 1) : 0;
+  part[2] = is_mhd(c) ? nz * (ny + 1) * nx : 0;
+  part[3] = is_mhd(c) ? (nz + 1) * ny * nx : 0;
+  return part[0] + part[1] + part[2] + part[3];
+}
+
+aeth_status aeth_state_doubles(aeth_ctx* c, size_t* n) {
+  if (!c || !n) return AETH_ERR_ARG;
+  if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
+  size_t t = 0, part[4];
+  for (int b = 0; b < (int)c->blocks.size(); ++b) t += packed_doubles(c, b, part);
+  *n = t;
+  return AETH_OK;
+}
+
+static aeth_status pack_buffer(aeth_ctx* c, const void* host, size_t* total) {
+  aeth_status s = aeth_state_doubles(c, total);
+  if (s != AETH_OK) return s;
+  if (!page_locked(host, *total * sizeof(double)))
+    return fail(c, AETH_ERR_ARG, "the packed array is not page-locked host memory");
+  if (!c->d_pack) {
+    if (cudaMalloc(&c->d_pack, *total * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_pack = nullptr;
+      return fail(c, AETH_ERR_OOM, "packed staging buffer (%zu bytes)", *total * sizeof(double));
+    }
+    c->pack_doubles = *total;
+  }
+  return AETH_OK;
+}
+
+aeth_status aeth_set_state_all_async(aeth_ctx* c, const double* packed) {
+  if (!c || !packed) return AETH_ERR_ARG;
+  size_t total = 0;
+  aeth_status s = pack_buffer(c, packed, &total);
+  if (s != AETH_OK) return s;
+  AETH_CK(c, cudaMemcpyAsync(c->d_pack, packed, total * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+  double* d = c->d_pack;
+  for (int b = 0; b < (int)c->blocks.size(); ++b) {
+    size_t part[4];
+    const size_t n = packed_doubles(c, b, part);
+    double* io[4] = {d, d + part[0], d + part[0] + part[1], d + part[0] + part[1] + part[2]};
+    s = enqueue_load(c, b, io);
+    if (s != AETH_OK) return s;
+    d += n;
+  }
+  return AETH_OK;
+}
+
+aeth_status aeth_get_state_all_async(aeth_ctx* c, double* packed) {
+  if (!c || !packed) return AETH_ERR_ARG;
+  size_t total = 0;
+  aeth_status s = pack_buffer(c, packed, &total);
+  if (s != AETH_OK) return s;
+  double* d = c->d_pack;
+  for (int b = 0; b < (int)c->blocks.size(); ++b) {
+    size_t part[4];
+    const size_t n = packed_doubles(c, b, part);
+    double* io[4] = {d, d + part[0], d + part[0] + part[1], d + part[0] + part[1] + part[2]};
+    s = enqueue_store(c, b, io);
+    if (s != AETH_OK) return s;
+    d += n;
+  }
+  AETH_CK(c, cudaMemcpyAsync(packed, c->d_pack, total * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  return AETH_OK;
+}
+
 aeth_status aeth_get_state(aeth_ctx* c, int b, double* cons, double* b1, double* b2, double* b3) {
   aeth_status s = check_block(c, b);
   if (s != AETH_OK) return s;
@@ -791,6 +866,7 @@ void aeth_destroy(aeth_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->own_arena && c->arena) cudaFree(c->arena);
+  if (c->d_pack) cudaFree(c->d_pack);
   if (c->d_mlp) cudaFree(c->d_mlp);
   if (c->d_mlp_tc) cudaFree(c->d_mlp_tc);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);

@@ -127,6 +127,8 @@ struct aeth_ctx {
   unsigned long long* d_fallback = nullptr;
   double* d_diag = nullptr;      // 8 doubles
   double* d_stage = nullptr;
+  double* d_pack = nullptr;           // device copy of the packed state of every
+  size_t pack_doubles = 0;            // block (allocated on first use)
   // CUDA graph of one CFL-driven step (aeth_run)
   cudaGraphExec_t graph = nullptr;
   // MLP parameters (device, bf16/fp32) for the learned flux

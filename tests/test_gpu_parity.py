@@ -314,6 +314,47 @@ def test_async_state_transfers_on_two_streams_match_the_synchronous_ones():
             s_.close()
 
 
+@pytest.mark.parametrize("mhd", [True, False])
+def test_packed_all_block_transfers_match_the_per_block_ones(mhd):
+    """aeth_set_state_all_async / aeth_get_state_all_async: one packed array
+    for uneven blocks (Cartesian and spherical) gives, after a step, the
+    per-block synchronous state bit for bit, and reads back what the
+    per-block calls read."""
+    import torch
+    sts = I.batched_boxes(5, 20260822, sizes=(6, 8, 10, 13), nmodes=3)
+    if not mhd:
+        sts = [I.smooth_random_mhd(s_.block, 40 + q, v_rms=0.3, b_rms=0.0, mhd=False)
+               for q, s_ in enumerate(sts)]
+    cfg = A.make_config(gamma=sts[0].gamma, precision=A.FP32, mhd=mhd)
+    blocks = [A.make_block(s_.block.n, s_.block.lo, s_.block.hi, s_.block.coord, s_.block.bc)
+              for s_ in sts]
+    arrs = [(s_.cons, s_.b1, s_.b2, s_.b3) if mhd else (s_.cons,) for s_ in sts]
+    sv = A.Solver(cfg, blocks, stream=torch.cuda.current_stream())
+    try:
+        for q, a_ in enumerate(arrs):
+            A.aeth_set_state(sv.ctx, q, *a_)
+        sv.step(1e-3)
+        ref = [sv.get_state(q) for q in range(len(sts))]
+    finally:
+        sv.close()
+    packed = torch.from_numpy(A.pack_states(arrs, mhd=mhd)).pin_memory()
+    sv = A.Solver(cfg, blocks, stream=torch.cuda.current_stream())
+    try:
+        assert A.aeth_state_doubles(sv.ctx) == packed.numel()
+        A.aeth_set_state_all_async(sv.ctx, packed)
+        sv.step(1e-3)
+        out = torch.empty_like(packed).pin_memory()
+        A.aeth_get_state_all_async(sv.ctx, out)
+        sv.sync()
+        want = A.pack_states([r if mhd else (r[0],) for r in ref], mhd=mhd)
+        assert np.array_equal(out.numpy(), want)
+        with pytest.raises(A.AethError) as e:
+            A.aeth_set_state_all_async(sv.ctx, np.empty(packed.numel()))
+        assert e.value.code == -1
+    finally:
+        sv.close()
+
+
 def test_pinned_dust_arrays_take_the_direct_path_bit_for_bit():
     import torch
     n = (16, 12, 8)
