@@ -1049,7 +1049,7 @@ def main():
                                     "step, each call synchronous")
     e2e_steps = ke
     sv_tile = A.aeth_get_flux_tile(sv.ctx)
-    if dust is None and a.e2e_contexts > 1:
+    if a.e2e_contexts > 1:
         # the same copies through the asynchronous calls on several contexts
         # and streams: the copy engines move one context's state while
         # another steps, and the host link carries both directions at once
@@ -1068,7 +1068,8 @@ def main():
         # the whole mesh's state in one packed, pinned array (one transfer
         # per direction and step, whatever the number of blocks)
         packed_in = torch.from_numpy(A.pack_states(
-            [[x.numpy() for x in h if x is not None] for h in hin], mhd=mhd_run)).pin_memory()
+            [[x.numpy() for x in h if x is not None] for h in hin], mhd=mhd_run,
+            dust=None if dust is None else [dust])).pin_memory()
         ctxs = [(sv, stream, torch.empty_like(packed_in).pin_memory())] + [
             (sv_q, s_q, torch.empty_like(packed_in).pin_memory()) for sv_q, s_q in more]
         try:
@@ -1097,9 +1098,9 @@ def main():
                 e2e_val = whole_job_rate(cells * e2e_steps, ws, e2e_p)
                 e2e_how = (f"{len(ctxs)} contexts on {len(ctxs)} streams, {ke} steps each: per step, "
                            "aeth_set_state_all_async from a pinned host array of every block's "
-                           "state, aeth_run(1), aeth_get_state_all_async into a pinned host "
-                           "array; one context's copies overlap another's step (the contexts "
-                           "start one upload apart)")
+                           "state (gas and dust), aeth_run(1), aeth_get_state_all_async into a "
+                           "pinned host array; one context's copies overlap another's step (the "
+                           "contexts start one upload apart)")
         finally:
             for sv_q, _ in more:
                 sv_q.close()

@@ -274,7 +274,8 @@ aeth_status aeth_get_state_async(aeth_ctx* ctx, int block, double* cons,
 
 /* The state of every block in one page-locked host array, block after
  * block in the order of aeth_add_block, each block as cons [5][nz][ny][nx]
- * followed in MHD by b1f, b2f, b3f (the layouts above): one copy-engine
+ * followed in MHD by b1f, b2f, b3f (the layouts above) and, with dust, by
+ * every species' rho_mom [4][nz][ny][nx] (as aeth_set_dust): one copy-engine
  * transfer for the whole mesh instead of four per block, for meshes of
  * many small blocks.  *n receives the array's length in doubles.  The
  * transfers behave as aeth_set_state_async / aeth_get_state_async; the

@@ -225,14 +225,17 @@ def aeth_get_state_all_async(ctx, packed):
     _check(ctx, load_library().aeth_get_state_all_async(ctx, _ptr(packed)))
 
 
-def pack_states(states, mhd=True):
+def pack_states(states, mhd=True, dust=None):
     """The packed host layout of aeth_set_state_all_async from per-block
-    (cons, b1, b2, b3) arrays (numpy, FP64)."""
+    (cons, b1, b2, b3) arrays (numpy, FP64), with each block's dust species
+    [nd][4][nz][ny][nx] after it when `dust` (one array per block) is given."""
     parts = []
-    for st in states:
+    for q, st in enumerate(states):
         parts.append(np.ascontiguousarray(st[0], dtype=np.float64).ravel())
         if mhd:
             parts += [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in st[1:4]]
+        if dust is not None:
+            parts.append(np.ascontiguousarray(dust[q], dtype=np.float64).ravel())
     return np.concatenate(parts)
 
 

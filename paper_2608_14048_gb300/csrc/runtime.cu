@@ -497,21 +497,23 @@ aeth_status aeth_get_state_async(aeth_ctx* c, int b, double* cons, double* b1, d
 }
 
 // Doubles of one block's packed state: cons [5][nz][ny][nx], then in MHD
-// b1 [nz][ny][nx+1], b2 [nz][ny+1][nx], b3 [nz+1][ny][nx].
-static size_t packed_doubles(const aeth_ctx* c, int b, size_t part[4]) {
+// b1 [nz][ny][nx+1], b2 [nz][ny+1][nx], b3 [nz+1][ny][nx], then with dust
+// every species' [4][nz][ny][nx] (part[4]: all species).
+static size_t packed_doubles(const aeth_ctx* c, int b, size_t part[5]) {
   const auto& B = c->blocks[b];
   const size_t nx = B.desc.nx, ny = B.desc.ny, nz = B.desc.nz;
   part[0] = 5 * nx * ny * nz;
   part[1] = is_mhd(c) ? nz * ny * (nx + 1) : 0;
   part[2] = is_mhd(c) ? nz * (ny + 1) * nx : 0;
   part[3] = is_mhd(c) ? (nz + 1) * ny * nx : 0;
-  return part[0] + part[1] + part[2] + part[3];
+  part[4] = (size_t)c->cfg.n_dust * 4 * nx * ny * nz;
+  return part[0] + part[1] + part[2] + part[3] + part[4];
 }
 
 aeth_status aeth_state_doubles(aeth_ctx* c, size_t* n) {
   if (!c || !n) return AETH_ERR_ARG;
   if (!c->finalized) return fail(c, AETH_ERR_STATE, "call aeth_finalize first");
-  size_t t = 0, part[4];
+  size_t t = 0, part[5];
   for (int b = 0; b < (int)c->blocks.size(); ++b) t += packed_doubles(c, b, part);
   *n = t;
   return AETH_OK;
@@ -542,11 +544,16 @@ aeth_status aeth_set_state_all_async(aeth_ctx* c, const double* packed) {
                              c->stream));
   double* d = c->d_pack;
   for (int b = 0; b < (int)c->blocks.size(); ++b) {
-    size_t part[4];
+    size_t part[5];
     const size_t n = packed_doubles(c, b, part);
     double* io[4] = {d, d + part[0], d + part[0] + part[1], d + part[0] + part[1] + part[2]};
     s = enqueue_load(c, b, io);
     if (s != AETH_OK) return s;
+    double* dd = d + part[0] + part[1] + part[2] + part[3];
+    for (int k = 0; k < c->cfg.n_dust; ++k) {
+      s = enqueue_dust_load(c, b, k, dd + (size_t)k * (part[4] / c->cfg.n_dust));
+      if (s != AETH_OK) return s;
+    }
     d += n;
   }
   return AETH_OK;
@@ -559,11 +566,16 @@ aeth_status aeth_get_state_all_async(aeth_ctx* c, double* packed) {
   if (s != AETH_OK) return s;
   double* d = c->d_pack;
   for (int b = 0; b < (int)c->blocks.size(); ++b) {
-    size_t part[4];
+    size_t part[5];
     const size_t n = packed_doubles(c, b, part);
     double* io[4] = {d, d + part[0], d + part[0] + part[1], d + part[0] + part[1] + part[2]};
     s = enqueue_store(c, b, io);
     if (s != AETH_OK) return s;
+    double* dd = d + part[0] + part[1] + part[2] + part[3];
+    for (int k = 0; k < c->cfg.n_dust; ++k) {
+      s = enqueue_dust_store(c, b, k, dd + (size_t)k * (part[4] / c->cfg.n_dust));
+      if (s != AETH_OK) return s;
+    }
     d += n;
   }
   AETH_CK(c, cudaMemcpyAsync(packed, c->d_pack, total * sizeof(double), cudaMemcpyDeviceToHost,

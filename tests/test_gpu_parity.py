@@ -355,6 +355,41 @@ def test_packed_all_block_transfers_match_the_per_block_ones(mhd):
         sv.close()
 
 
+def test_packed_transfers_carry_the_dust_species():
+    import torch
+    n = (16, 12, 8)
+    gas, dust, ts = I.dust_box(I.Block(n), 94, nd=3)
+    cfg = A.make_config(gamma=gas.gamma, precision=A.FP32, mhd=False, integrator=A.IMEX2P,
+                        t_stop=ts)
+    sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+    try:
+        sv.set_state(0, gas.cons)
+        for k in range(dust.shape[0]):
+            A.aeth_set_dust(sv.ctx, 0, k, np.ascontiguousarray(dust[k]))
+        sv.step(1e-3)
+        ref_gas = sv.get_state(0)[0]
+        ref_dust = np.empty_like(dust)
+        for k in range(dust.shape[0]):
+            buf = np.empty(dust.shape[1:])
+            A.aeth_get_dust(sv.ctx, 0, k, buf)
+            ref_dust[k] = buf
+    finally:
+        sv.close()
+    packed = torch.from_numpy(A.pack_states([(gas.cons,)], mhd=False, dust=[dust])).pin_memory()
+    sv = A.Solver(cfg, [A.make_block(n)], stream=torch.cuda.current_stream())
+    try:
+        assert A.aeth_state_doubles(sv.ctx) == packed.numel()
+        A.aeth_set_state_all_async(sv.ctx, packed)
+        sv.step(1e-3)
+        out = torch.empty_like(packed).pin_memory()
+        A.aeth_get_state_all_async(sv.ctx, out)
+        sv.sync()
+        want = A.pack_states([(ref_gas,)], mhd=False, dust=[ref_dust])
+        assert np.array_equal(out.numpy(), want)
+    finally:
+        sv.close()
+
+
 def test_pinned_dust_arrays_take_the_direct_path_bit_for_bit():
     import torch
     n = (16, 12, 8)
