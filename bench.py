@@ -13,7 +13,11 @@ the device), counted once per cell (zone-cycles).
 
 Prints ONE JSON line (rank 0).  With --gpus N > 1 (torchrun) every rank
 advances its own independent replica (weak scaling, no cross-GPU exchange
-in the step); value = all ranks' cell-updates / max time.
+in the step); value = all ranks' cell-updates / max time.  `e2e` is the same
+metric with every step's state copied in from, and read back into, pinned
+host memory through the public API: --e2e-contexts (default 3) contexts on
+as many streams, so that one context's copies overlap another's step (1:
+the synchronous calls on one context, also reported as e2e.serial_value).
 
 --impl reference times the FP64 CPU oracle instead, on the host cores: W
 untimed and K timed steps of a bounded sample of the same workload (64^3 of
