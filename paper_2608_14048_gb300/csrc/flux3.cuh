@@ -26,8 +26,9 @@ namespace aeth {
 #ifndef AETH_FLUX_MINB
 #define AETH_FLUX_MINB 3
 #endif
-// the same for the 128-thread 2-D tiles, in CTAs: 5 (102 registers, no
-// spills) measured 1% faster at 256^3 than 6 (80 registers); PPM keeps 4
+// the same for the 128-thread 2-D tiles, in CTAs: 5 (the PLM corrector at
+// 96 registers with a 20-byte spill) measured 1% faster at 256^3 than 6
+// (80 registers, 160 bytes spilled); PPM keeps 4
 #ifndef AETH_FLUX_MINB_2D
 #define AETH_FLUX_MINB_2D 5
 #endif
