@@ -125,3 +125,26 @@ def test_bench_rejects_empty_timing(argv):
 def test_single_thread_oracle_rate_runs_in_a_child_process():
     r = bench.single_thread_rate(bench.parse(["--workload", "wave32"]), 8, seconds=0.2)
     assert r["value"] > 0 and r["steps"] >= 1 and "fast wave 8^3" in r["what"]
+
+
+def test_packed_state_layout_is_block_after_block():
+    """pack_states: each block's cons, then its three face fields (MHD), then
+    its dust species, block after block (the layout of the packed transfers)."""
+    import numpy as np
+    from paper_2608_14048_gb300 import aether as A
+    rng = np.random.default_rng(3)
+    blocks = []
+    for n in ((3, 2, 2), (2, 4, 1)):
+        nx, ny, nz = n
+        blocks.append((rng.random((5, nz, ny, nx)), rng.random((nz, ny, nx + 1)),
+                       rng.random((nz, ny + 1, nx)), rng.random((nz + 1, ny, nx))))
+    dust = [rng.random((2, 4) + b[0].shape[1:]) for b in blocks]
+    p = A.pack_states(blocks, mhd=True, dust=dust)
+    o = 0
+    for b, d in zip(blocks, dust):
+        for arr in list(b) + [d]:
+            assert np.array_equal(p[o:o + arr.size], arr.ravel())
+            o += arr.size
+    assert o == p.size
+    h = A.pack_states([(b[0],) for b in blocks], mhd=False)
+    assert h.size == sum(b[0].size for b in blocks)
