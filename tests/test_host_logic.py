@@ -130,8 +130,6 @@ def test_single_thread_oracle_rate_runs_in_a_child_process():
 def test_packed_state_layout_is_block_after_block():
     """pack_states: each block's cons, then its three face fields (MHD), then
     its dust species, block after block (the layout of the packed transfers)."""
-    import numpy as np
-    from paper_2608_14048_gb300 import aether as A
     rng = np.random.default_rng(3)
     blocks = []
     for n in ((3, 2, 2), (2, 4, 1)):
