@@ -234,7 +234,14 @@ __global__ void k_fill_axis(Layout L, Arr8<R> a, int nv, int d) {
   c[d] = t < g ? t - g : n + (t - g);      // -g..-1, n..n+g
   const int p = c[d];
   const long long dst = L.idx(c[0], c[1], c[2]);
-  for (int v = 0; v < nv; ++v) {
+  // every source loaded before the first store: the stores go through the
+  // same arrays, so interleaving them would serialise the round trips
+  R val[NVAR];
+  bool on[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    on[v] = false;
+    if (v >= nv) continue;
     const bool face_d = (v == 5 + d);
     int s;
     if (L.bc[d] == AETH_BC_PERIODIC) {
@@ -247,8 +254,12 @@ __global__ void k_fill_axis(Layout L, Arr8<R> a, int nv, int d) {
     }
     int sc[3] = {c[0], c[1], c[2]};
     sc[d] = s;
-    a.p[v][dst] = a.p[v][L.idx(sc[0], sc[1], sc[2])];
+    val[v] = a.p[v][L.idx(sc[0], sc[1], sc[2])];
+    on[v] = true;
   }
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v)
+    if (on[v]) a.p[v][dst] = val[v];
 }
 
 template <typename R>

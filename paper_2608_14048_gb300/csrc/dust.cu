@@ -410,7 +410,18 @@ __global__ void __launch_bounds__(256) k_fill_cells(Layout L, R* base, int narr,
   sc[d] = s;
   const long long dst = L.idx(c[0], c[1], c[2]), srcx = L.idx(sc[0], sc[1], sc[2]);
   const long long sz = L.size();
-  for (int a = 0; a < narr; ++a) base[a * sz + dst] = base[a * sz + srcx];
+  // eight arrays at a time, every source loaded before the stores (the
+  // stores go through the same base, so interleaving them would serialise
+  // the round trips)
+  for (int a0 = 0; a0 < narr; a0 += 8) {
+    R v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (a0 + q < narr) v[q] = base[(a0 + q) * sz + srcx];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (a0 + q < narr) base[(a0 + q) * sz + dst] = v[q];
+  }
 }
 
 template <typename R, bool P64>
