@@ -1057,7 +1057,6 @@ def main():
         # the same copies through the asynchronous calls on several contexts
         # and streams: the copy engines move one context's state while
         # another steps, and the host link carries both directions at once
-        # (the second and later contexts start one upload apart)
         more = []
         try:
             for _ in range(a.e2e_contexts - 1):
@@ -1078,23 +1077,30 @@ def main():
             (sv_q, s_q, torch.empty_like(packed_in).pin_memory()) for sv_q, s_q in more]
         try:
             if len(ctxs) > 1:
-                def round_(first=False):
-                    prev = None
+                # the uploads of the contexts follow one another, and so do
+                # the read-backs (events across the streams): each direction
+                # of the link carries one copy at a time, at its full rate,
+                # while the other direction and the steps run beside it
+                chain = {"up": None, "down": None}
+
+                def round_():
                     for svq, sq, hq in ctxs:
-                        if first and prev is not None:
-                            sq.wait_event(prev)
+                        if chain["up"] is not None:
+                            sq.wait_event(chain["up"])
                         A.aeth_set_state_all_async(svq.ctx, packed_in)
-                        if first:
-                            prev = torch.cuda.Event()
-                            prev.record(sq)
+                        chain["up"] = torch.cuda.Event()
+                        chain["up"].record(sq)
                         svq.run(1)
+                        if chain["down"] is not None:
+                            sq.wait_event(chain["down"])
                         A.aeth_get_state_all_async(svq.ctx, hq)
+                        chain["down"] = torch.cuda.Event()
+                        chain["down"].record(sq)
 
                 round_()   # captures the other contexts' step graphs
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
-                round_(first=True)
-                for _ in range(ke - 1):
+                for _ in range(ke):
                     round_()
                 torch.cuda.synchronize(dev)
                 e2e_p = max_over_ranks(time.perf_counter() - t0, ws, device=dev)
@@ -1104,7 +1110,7 @@ def main():
                            "aeth_set_state_all_async from a pinned host array of every block's "
                            "state (gas and dust), aeth_run(1), aeth_get_state_all_async into a "
                            "pinned host array; one context's copies overlap another's step (the "
-                           "contexts start one upload apart)")
+                           "contexts' uploads follow one another, and so do their read-backs)")
         finally:
             for sv_q, _ in more:
                 sv_q.close()
